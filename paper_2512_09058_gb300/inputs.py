@@ -1,0 +1,266 @@
+"""Seeded synthetic linear-quadratic OCP instances (inputs only).
+
+This module defines the in-memory layout of an OCP instance and draws seeded
+random instances shaped like the five benchmark workloads.  It holds none of
+the solver's arithmetic: both the CPU oracle and the CUDA library consume what
+it produces, and nothing here depends on either of them.
+
+Problem (paper Sec. 2, eq. ``ocp-eq`` with E_j = I):
+
+    minimise  sum_k 1/2 [u;x]^T [R_k S_k; S_k^T Q_k] [u;x] + [r_k; q_k]^T [u;x]
+              + 1/2 x_N^T Q_N x_N + q_N^T x_N
+    s.t.      x_0 = x_init,  x_{k+1} = A_k x_k + B_k u_k + c_k   (0 <= k < N)
+
+with S_k in R^{nu x nx} (the paper's orientation, cost term u^T S x), and an
+optional diagonal regularisation Sigma_k added to diag(R_k, Q_k) (and Sigma_N to
+Q_N), read as the augmented-Lagrangian term of Sec. 5.1 with box constraints
+on every input and state.
+
+Flat layout of one instance (all float64, every matrix block column-major):
+
+    Q      (N+1) blocks nx*nx     k = 0..N   (Q_0 is never read: x_0 is fixed)
+    R      N blocks     nu*nu     k = 0..N-1
+    S      N blocks     nu*nx     k = 0..N-1 (S_0 is never read)
+    A      N blocks     nx*nx     k = 0..N-1 (A_0 is never read by the KKT matrix)
+    B      N blocks     nx*nu     k = 0..N-1
+    Sigma  (N+1) records of nu+nx  [Sigma_u_k | Sigma_x_k]; record 0's x part and
+           record N's u part are never read
+    q      (N+1)*nx,  r  N*nu,  c  N*nx,  x0  nx
+
+A batch concatenates the per-instance arrays of each kind in instance order.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+__all__ = [
+    "OCPInstance", "Batch", "CONFIGS", "make_instance", "make_batch",
+    "config_dims", "blocks_to_flat", "flat_to_blocks",
+]
+
+
+def blocks_to_flat(blocks: np.ndarray) -> np.ndarray:
+    """Stack of matrices (K, rows, cols) -> flat column-major blocks."""
+    return np.ascontiguousarray(np.asarray(blocks, dtype=np.float64).transpose(0, 2, 1)).ravel()
+
+
+def flat_to_blocks(flat: np.ndarray, count: int, rows: int, cols: int) -> np.ndarray:
+    """Inverse of :func:`blocks_to_flat` (returns a (count, rows, cols) copy)."""
+    a = np.asarray(flat, dtype=np.float64)[: count * rows * cols]
+    return np.ascontiguousarray(a.reshape(count, cols, rows).transpose(0, 2, 1))
+
+
+@dataclasses.dataclass
+class OCPInstance:
+    N: int
+    nx: int
+    nu: int
+    Q: np.ndarray
+    R: np.ndarray
+    S: np.ndarray
+    A: np.ndarray
+    B: np.ndarray
+    Sigma: Optional[np.ndarray]
+    # one (q, r, c, x0) tuple per right-hand side
+    rhs: List[tuple]
+
+    # ---- block accessors (layout only) ----
+    def Qk(self, k: int) -> np.ndarray:
+        n = self.nx
+        return self.Q[k * n * n:(k + 1) * n * n].reshape(n, n).T.copy()
+
+    def Rk(self, k: int) -> np.ndarray:
+        m = self.nu
+        return self.R[k * m * m:(k + 1) * m * m].reshape(m, m).T.copy()
+
+    def Sk(self, k: int) -> np.ndarray:
+        m, n = self.nu, self.nx
+        return self.S[k * m * n:(k + 1) * m * n].reshape(n, m).T.copy()
+
+    def Ak(self, k: int) -> np.ndarray:
+        n = self.nx
+        return self.A[k * n * n:(k + 1) * n * n].reshape(n, n).T.copy()
+
+    def Bk(self, k: int) -> np.ndarray:
+        m, n = self.nu, self.nx
+        return self.B[k * n * m:(k + 1) * n * m].reshape(m, n).T.copy()
+
+    def Sigma_u(self, k: int) -> np.ndarray:
+        if self.Sigma is None:
+            return np.zeros(self.nu)
+        w = self.nu + self.nx
+        return self.Sigma[k * w:k * w + self.nu].copy()
+
+    def Sigma_x(self, k: int) -> np.ndarray:
+        if self.Sigma is None:
+            return np.zeros(self.nx)
+        w = self.nu + self.nx
+        return self.Sigma[k * w + self.nu:(k + 1) * w].copy()
+
+    @property
+    def kkt_size(self) -> int:
+        """Unknowns u_0..u_{N-1}, x_1..x_N, lambda_0..lambda_{N-1}."""
+        return self.N * (self.nu + 2 * self.nx)
+
+
+@dataclasses.dataclass
+class Batch:
+    """Concatenation of instances; arrays are flat float64 (host)."""
+    N: np.ndarray
+    nx: np.ndarray
+    nu: np.ndarray
+    Q: np.ndarray
+    R: np.ndarray
+    S: np.ndarray
+    A: np.ndarray
+    B: np.ndarray
+    Sigma: Optional[np.ndarray]
+    rhs: List[tuple]   # per right-hand side: (q, r, c, x0) concatenated over instances
+    instances: List[OCPInstance]
+
+    @property
+    def size(self) -> int:
+        return int(len(self.N))
+
+    @property
+    def stages(self) -> int:
+        return int(self.N.sum())
+
+    @property
+    def kkt_size(self) -> int:
+        return int((self.N * (self.nu + 2 * self.nx)).sum())
+
+
+# ---------------------------------------------------------------------------
+# Workload recipes.  Each config names the five benchmark workloads by their
+# shape; the drawing rules are stated in the design notes.
+# ---------------------------------------------------------------------------
+CONFIGS = {
+    # single OCP, N=32, nx=8, nu=4, S=0, Q_N=Q_0, one factor + one solve
+    "single_n32_nx8_nu4": dict(batch=1, N=32, nx=8, nu=4, S=False, sigma=None,
+                               nrhs=1, QN_equals_Q0=True, seed=0),
+    # 1024 OCPs, N=64, nx=12, nu=4, S~0.1N(0,1) (stage block kept SPD), Sigma in LU[1e-6,1e6], 4 RHS
+    "batch1024_n64_nx12_nu4": dict(batch=1024, N=64, nx=12, nu=4, S=True, sigma=(1e-6, 1e6),
+                                   nrhs=4, QN_equals_Q0=False, seed=1),
+    # 8 OCPs, N=4096, nx=32, nu=16, dense random S, Sigma in LU[1e-4,1e4]
+    "long_n4096_nx32_nu16": dict(batch=8, N=4096, nx=32, nu=16, S=True, sigma=(1e-4, 1e4),
+                                 nrhs=1, QN_equals_Q0=False, seed=2),
+    # 4096 OCPs, N~U[16,256], nx~U{4..64}, nu~U{2..32}, Sigma in LU[1e-6,1e6]
+    "uneven4096": dict(batch=4096, N=(16, 256), nx=(4, 64), nu=(2, 32), S=True, sigma=(1e-6, 1e6),
+                       nrhs=1, QN_equals_Q0=False, seed=3),
+    # 512 OCPs, N=128, nx=24, nu=8, S=0, no Sigma (differentiation workload)
+    "adjoint512_n128_nx24_nu8": dict(batch=512, N=128, nx=24, nu=8, S=False, sigma=None,
+                                     nrhs=1, QN_equals_Q0=False, seed=4),
+}
+
+_DIMS_STREAM = 0x5EED_D135
+
+
+def config_dims(cfg: dict, batch: Optional[int] = None):
+    """Per-instance (N, nx, nu) arrays of a config (uniform or drawn)."""
+    b = cfg["batch"] if batch is None else batch
+    if isinstance(cfg["N"], tuple):
+        g = np.random.Generator(np.random.PCG64([cfg["seed"], _DIMS_STREAM]))
+        N = g.integers(cfg["N"][0], cfg["N"][1], size=cfg["batch"], endpoint=True)
+        nx = g.integers(cfg["nx"][0], cfg["nx"][1], size=cfg["batch"], endpoint=True)
+        nu = g.integers(cfg["nu"][0], cfg["nu"][1], size=cfg["batch"], endpoint=True)
+        return (N[:b].astype(np.int32), nx[:b].astype(np.int32), nu[:b].astype(np.int32))
+    return (np.full(b, cfg["N"], np.int32), np.full(b, cfg["nx"], np.int32),
+            np.full(b, cfg["nu"], np.int32))
+
+
+def _spd(g, count, n):
+    M = g.standard_normal((count, n, n))
+    return M @ M.transpose(0, 2, 1) / n + 0.1 * np.eye(n)
+
+
+def make_instance(cfg, index: int, *, N: Optional[int] = None, nx: Optional[int] = None,
+                  nu: Optional[int] = None, nrhs: Optional[int] = None) -> OCPInstance:
+    """Draw instance ``index`` of ``cfg`` (a CONFIGS key or dict).
+
+    Every instance has its own PCG64 stream seeded by (config seed, 1, index),
+    so any subset of a batch can be regenerated alone.  Draw order: A, B, M
+    (for Q), P (for R), S, Sigma, then (q, r, c, x0) for each right-hand side.
+    ``N``/``nx``/``nu`` override the config's dimensions (small test cases).
+    """
+    if isinstance(cfg, str):
+        cfg = CONFIGS[cfg]
+    if isinstance(cfg["N"], tuple):
+        Ns, nxs, nus = config_dims(cfg)
+        dN, dnx, dnu = int(Ns[index]), int(nxs[index]), int(nus[index])
+    else:
+        dN, dnx, dnu = cfg["N"], cfg["nx"], cfg["nu"]
+    N = dN if N is None else int(N)
+    nx = dnx if nx is None else int(nx)
+    nu = dnu if nu is None else int(nu)
+    nrhs = cfg["nrhs"] if nrhs is None else nrhs
+    g = np.random.Generator(np.random.PCG64([cfg["seed"], 1, index]))
+
+    # A_k: Gaussian scaled to spectral radius 0.95
+    G = g.standard_normal((N, nx, nx))
+    rho = np.abs(np.linalg.eigvals(G)).max(axis=1)
+    A = 0.95 * G / rho[:, None, None]
+    # B_k ~ N(0, 1/nx)  (variance 1/nx)
+    B = g.standard_normal((N, nx, nu)) / np.sqrt(nx)
+    # Q_k = M M^T / nx + 0.1 I (k = 0..N), R_k = P P^T / nu + 0.1 I
+    Q = _spd(g, N + 1, nx)
+    if cfg.get("QN_equals_Q0"):
+        Q[N] = Q[0]
+    R = _spd(g, N, nu)
+    if cfg["S"]:
+        S = 0.1 * g.standard_normal((N, nu, nx))
+        # keep the stage block [R S; S^T Q] SPD: shift both diagonal blocks so
+        # that its smallest eigenvalue is at least 0.05
+        H = np.zeros((N, nu + nx, nu + nx))
+        H[:, :nu, :nu] = R
+        H[:, :nu, nu:] = S
+        H[:, nu:, :nu] = S.transpose(0, 2, 1)
+        H[:, nu:, nu:] = Q[:N]
+        lmin = np.linalg.eigvalsh(H)[:, 0]
+        delta = np.maximum(0.0, 0.05 - lmin)
+        R = R + delta[:, None, None] * np.eye(nu)
+        Q[:N] = Q[:N] + delta[:, None, None] * np.eye(nx)
+    else:
+        S = np.zeros((N, nu, nx))
+    Sigma = None
+    if cfg["sigma"] is not None:
+        lo, hi = cfg["sigma"]
+        Sigma = 10.0 ** g.uniform(np.log10(lo), np.log10(hi), size=(N + 1) * (nu + nx))
+    rhs = []
+    for _ in range(nrhs):
+        q = g.standard_normal((N + 1) * nx)
+        r = g.standard_normal(N * nu)
+        c = g.standard_normal(N * nx)
+        x0 = g.standard_normal(nx)
+        rhs.append((q, r, c, x0))
+    return OCPInstance(N=N, nx=nx, nu=nu, Q=blocks_to_flat(Q), R=blocks_to_flat(R),
+                       S=blocks_to_flat(S), A=blocks_to_flat(A), B=blocks_to_flat(B),
+                       Sigma=Sigma, rhs=rhs)
+
+
+def make_batch(cfg, indices: Optional[Sequence[int]] = None, *, instances=None, **overrides) -> Batch:
+    """Concatenate instances (``indices`` of ``cfg``, default all) into a Batch."""
+    if instances is None:
+        if isinstance(cfg, str):
+            cfg = CONFIGS[cfg]
+        if indices is None:
+            indices = range(cfg["batch"])
+        instances = [make_instance(cfg, int(i), **overrides) for i in indices]
+    insts = list(instances)
+    cat = lambda name: np.concatenate([getattr(x, name) for x in insts]) if insts else np.zeros(0)
+    has_sigma = any(x.Sigma is not None for x in insts)
+    if has_sigma:
+        sig = np.concatenate([x.Sigma if x.Sigma is not None else np.zeros((x.N + 1) * (x.nu + x.nx))
+                              for x in insts])
+    else:
+        sig = None
+    nrhs = min(len(x.rhs) for x in insts) if insts else 0
+    rhs = []
+    for j in range(nrhs):
+        rhs.append(tuple(np.concatenate([x.rhs[j][t] for x in insts]) for t in range(4)))
+    return Batch(N=np.array([x.N for x in insts], np.int32), nx=np.array([x.nx for x in insts], np.int32),
+                 nu=np.array([x.nu for x in insts], np.int32), Q=cat("Q"), R=cat("R"), S=cat("S"),
+                 A=cat("A"), B=cat("B"), Sigma=sig, rhs=rhs, instances=insts)
