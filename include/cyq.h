@@ -1,0 +1,201 @@
+/*
+ * cyq — factor and solve the KKT system of linear-quadratic optimal control
+ * problems on one GB300 GPU (sm_103a).  C ABI; every compute call takes device
+ * pointers and a CUDA stream and is stream-ordered (asynchronous).
+ *
+ * Method (arXiv 2512.09058, "Cyqlone"): the horizon of each problem is cut
+ * into P segments; each segment is eliminated by a modified Riccati recursion
+ * (Sec. 4.2, Alg. fact-mod-riccati), the segment couplings form a symmetric
+ * positive definite block-tridiagonal Schur complement in the multipliers
+ * lambda^{b_c} at the segment ends (Sec. 4.3, eq. schur-compl-example-4), and
+ * that system is factored by cyclic reduction (Sec. 3.2.1, Sec. 4.4,
+ * Alg. fact-parallel-riccati-cr, Alg. cr).  The solve is the forward/backward
+ * substitution with the factor of eq. chol-fac-K-cyqlone.  P = 1 is the
+ * factorized Riccati recursion with early elimination of u^0 (Sec. 4.2 footnote).
+ *
+ * ---------------------------------------------------------------------------
+ * Problem and KKT system (Sec. 2, eq. ocp-eq and eq. opt-cond-ocp-eq, E_j = I).
+ * Per instance: horizon N >= 1, nx >= 1 states, nu >= 1 inputs.  Unknowns
+ *   z = (u^0, x^1, lambda^0, u^1, x^2, lambda^1, ..., u^{N-1}, x^N, lambda^{N-1})
+ * i.e. N records of [ u^k (nu) | x^{k+1} (nx) | lambda^k (nx) ].  K z = b with
+ *   R_k u^k + S_k x^k + B_k^T lambda^k                   = b_u^k  (no S_0 x^0 term)
+ *   S_k^T u^k + Q_k x^k + A_k^T lambda^k - lambda^{k-1}  = b_x^k  (0 < k < N)
+ *   Q_N x^N - lambda^{N-1}                               = b_x^N
+ *   B_k u^k + A_k x^k - x^{k+1}                          = b_l^k  (no A_0 x^0 term)
+ * where R_k and Q_k include the optional diagonal regularisation Sigma_k.
+ * The vector b uses the same record layout as z (row of u^k, row of x^{k+1},
+ * row of lambda^k).  cyq_build_rhs forms b = -(r~, q, f~) of the original
+ * problem from (q, r, c, x_init).
+ *
+ * Data layout (float64, device, caller-owned).  Instances are concatenated
+ * kind by kind in instance order; inside an instance the blocks follow stage
+ * order and every block is column-major (element (i,j) at i + j*rows):
+ *   Q      (N+1) blocks nx*nx  (Q_0 is not read)
+ *   R      N blocks     nu*nu
+ *   S      N blocks     nu*nx  (S_k in R^{nu x nx}; S_0 is not read)   may be NULL (S = 0)
+ *   A      N blocks     nx*nx  (A_0 is not read)
+ *   B      N blocks     nx*nu
+ *   Sigma  (N+1) records of nu+nx: [Sigma_u^k | Sigma_x^k]; record 0's x part and
+ *          record N's u part are not read                             may be NULL
+ *   q (N+1)*nx, r N*nu, c N*nx, x_init nx   (cyq_build_rhs / cyq_solve_adjoint)
+ *   b, z   sum_i N_i*(nu_i + 2 nx_i) per right-hand side; several right-hand
+ *          sides are stored one after another (stride = that total).
+ *
+ * Ownership.  The caller owns data, b, z and gradient buffers; the handle
+ * owns its factor and workspace (allocated once by cyq_create).  Data
+ * pointers are BORROWED: the solve and the residual read A, B (and, in
+ * refinement mode, every block) again, so the data must stay valid and
+ * unchanged from cyq_factor until the last cyq_solve / cyq_solve_adjoint.
+ *
+ * Errors.  Host-detectable errors are returned immediately.  Numerical
+ * errors found on the device (a non-positive or non-finite Cholesky pivot,
+ * refinement that did not reach the tolerance) are written to a per-instance
+ * device status word; cyq_get_instance_status synchronises the stream and
+ * copies it.  No kernel traps, asserts or waits without a bound.
+ */
+#ifndef CYQ_H
+#define CYQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cyq_status {
+    CYQ_OK = 0,
+    CYQ_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, unsupported shape */
+    CYQ_ERR_NOT_PD = 2,        /* a stage or coupling Cholesky pivot <= 0 or not finite */
+    CYQ_ERR_NOT_CONVERGED = 3, /* refinement stopped above tol after it_max steps */
+    CYQ_ERR_CUDA = 4,          /* a CUDA runtime call failed (message: cyq_last_error) */
+    CYQ_ERR_TIMEOUT = 5,       /* a bounded device wait expired */
+    CYQ_ERR_NO_FACTOR = 6,     /* solve called before a successful factor */
+    CYQ_ERR_UNIMPLEMENTED = 7,
+    CYQ_ERR_NO_DEVICE = 8      /* no CUDA device visible */
+} cyq_status;
+
+typedef enum cyq_precision {
+    CYQ_FP64 = 0,          /* factor and solve in float64 */
+    CYQ_FP32_REFINE = 1    /* float32 factor/solve, float64 residual + iterative refinement */
+} cyq_precision;
+
+/* Opaque handle (host object owning device workspace). */
+typedef struct cyq_handle_s *cyq_handle;
+/* ABI-compatible with cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *cyq_stream;
+
+/* Host-side description, read (and copied) by cyq_create. */
+typedef struct cyq_desc {
+    int32_t batch;          /* number of independent instances, >= 1 */
+    const int32_t *N;       /* host array [batch]: horizon of each instance, >= 1 */
+    const int32_t *nx;      /* host array [batch]: states, >= 1 */
+    const int32_t *nu;      /* host array [batch]: inputs, >= 1 */
+    int32_t precision;      /* cyq_precision */
+    int32_t P;              /* horizon segments per instance; 0 = automatic.  Clamped to N. */
+    const int32_t *P_per_instance; /* optional host array [batch] overriding P (NULL = none) */
+    int32_t max_nrhs;       /* largest nrhs passed to cyq_solve, >= 1 */
+    int32_t it_max;         /* refinement steps (CYQ_FP32_REFINE), default 10 if <= 0 */
+    double tol;             /* relative KKT residual target, default 1e-10 if <= 0 */
+    int32_t device;         /* CUDA device ordinal (the caller's current device if < 0) */
+} cyq_desc;
+
+/*
+ * Plans segments and launch shapes for every instance and allocates the
+ * handle's device workspace (factors, Schur complement blocks, coupling
+ * vectors, refinement buffers).  The only call that allocates.
+ * Errors: INVALID_ARG (sizes), CUDA (allocation), NO_DEVICE.
+ */
+cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out);
+
+/* Frees the workspace (after synchronising the device). NULL is a no-op. */
+void cyq_destroy(cyq_handle h);
+
+/*
+ * Factor K (eq. chol-fac-K-cyqlone): segment Riccati factors (Alg.
+ * fact-mod-riccati), Schur complement blocks (Alg. fact-parallel-riccati-cr,
+ * compute-schur) and their cyclic-reduction factor (factor-schur).  All data
+ * pointers are device float64 arrays in the layout above; S and Sigma may be
+ * NULL.  Asynchronous on `stream`.  A failed pivot sets the instance status
+ * to CYQ_ERR_NOT_PD.  Errors returned: INVALID_ARG (NULL Q/R/A/B), CUDA.
+ */
+cyq_status cyq_factor(cyq_handle h, const double *Q, const double *R, const double *S,
+                      const double *A, const double *B, const double *Sigma, cyq_stream stream);
+
+/*
+ * Solve K z = b for nrhs right-hand sides (1 <= nrhs <= max_nrhs) with the
+ * last factor.  b and z are device float64 arrays of nrhs * kkt_size
+ * elements (kkt_size = sum_i N_i (nu_i + 2 nx_i)); they must not overlap.
+ * CYQ_FP64: one forward/backward substitution.  CYQ_FP32_REFINE: a float32
+ * solve, then up to it_max steps of  r = b - K z (float64), dz = K^{-1} r
+ * (float32 factor), z += dz, stopping per instance once ||r||/||b|| <= tol
+ * (the loop runs on the device; no host synchronisation).
+ * Errors returned: INVALID_ARG, NO_FACTOR, CUDA.
+ */
+cyq_status cyq_solve(cyq_handle h, const double *b, double *z, int32_t nrhs, cyq_stream stream);
+
+/*
+ * b = -(r~, q, f~) for one right-hand side of the original problem
+ * (eq. opt-cond-ocp-eq: r~^0 = r^0 + S_0 x_init, f~^0 = f^0 + A_0 x_init),
+ * using the data passed to the last cyq_factor.  q, r, c, x_init are device
+ * float64 arrays in the layout above; b has kkt_size elements.
+ */
+cyq_status cyq_build_rhs(cyq_handle h, const double *q, const double *r, const double *c,
+                         const double *x_init, double *b, cyq_stream stream);
+
+/*
+ * Float64 residual  res = b - K z  and per-instance relative residual
+ * ||res||_2 / ||b||_2 (rel, device float64 array [batch], may be NULL; res may
+ * be NULL).  Uses the data of the last cyq_factor.  One right-hand side.
+ */
+cyq_status cyq_residual(cyq_handle h, const double *b, const double *z, double *res, double *rel,
+                        cyq_stream stream);
+
+/*
+ * Adjoint of z = K^{-1} b(theta) (implicit differentiation of K z = b).
+ * Given z (the solution for the right-hand side built from x_init) and
+ * dL_dz, solves K w = dL_dz with the stored factor (K is symmetric) and
+ * returns dL/dtheta:
+ *   dq_k = -w_x^k, dr_k = -w_u^k, dc_k = -w_l^k,
+ *   dQ_k = -sym(w_x^k x^k^T), dR_k = -sym(w_u^k u^k^T),
+ *   dS_k = -(w_u^k x^k^T + u^k w_x^k^T), dA_k = -(w_l^k x^k^T + lambda^k w_x^k^T),
+ *   dB_k = -(w_l^k u^k^T + lambda^k w_u^k^T), with x^0 = x_init for k = 0
+ *   (dS_0 = -w_u^0 x_init^T, dA_0 = -w_l^0 x_init^T), dx_init = -S_0^T w_u^0 - A_0^T w_l^0,
+ *   dSigma_u^k = -w_u^k .* u^k, dSigma_x^k = -w_x^k .* x^k.
+ * Every output is a device float64 array in the data layout (w: kkt_size);
+ * entries that do not enter K (dQ_0, dq_0, dSigma_x^0, dSigma_u^N) are set to
+ * zero; any output pointer may be NULL.  One right-hand side.
+ */
+cyq_status cyq_solve_adjoint(cyq_handle h, const double *x_init, const double *z, const double *dL_dz,
+                             double *w, double *dQ, double *dq, double *dR, double *dr, double *dS,
+                             double *dA, double *dB, double *dc, double *dx_init, double *dSigma,
+                             cyq_stream stream);
+
+/* Synchronises `stream` and copies the per-instance status words
+ * (cyq_status values) into host_status[batch]. Returns the first non-OK one. */
+cyq_status cyq_get_instance_status(cyq_handle h, int32_t *host_status, cyq_stream stream);
+
+/* Statistics of the last cyq_solve (host copy; synchronises `stream`). */
+typedef struct cyq_stats {
+    int32_t refine_steps;    /* refinement steps run (max over instances) */
+    double max_rel_residual; /* max over instances of ||b - Kz|| / ||b|| (refinement mode) */
+    int32_t P_min, P_max;    /* segments per instance chosen by the plan */
+    int64_t work_items;      /* (instance, segment) pairs */
+} cyq_stats;
+cyq_status cyq_get_stats(cyq_handle h, cyq_stats *out, cyq_stream stream);
+
+/* Number of float64 elements of one right-hand side (sum_i N_i (nu_i + 2 nx_i)). */
+int64_t cyq_kkt_size(cyq_handle h);
+/* Segments chosen for each instance (host array [batch]). */
+cyq_status cyq_get_segments(cyq_handle h, int32_t *P_out);
+/* Number of kernels launched by the last cyq_factor and cyq_solve calls. */
+int64_t cyq_last_launch_count(cyq_handle h);
+
+const char *cyq_status_string(cyq_status s);
+/* Text of the last CUDA error seen by this thread's calls ("" if none). */
+const char *cyq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CYQ_H */

@@ -1,0 +1,529 @@
+// Host side of the cyq C ABI: planning (segments, teams, chunks), workspace
+// allocation and the launch sequences of factor, solve, refinement and
+// adjoint.  See include/cyq.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cyq.h"
+#include "cyq_internal.cuh"
+
+using namespace cyq;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr int kSMs = 152;
+
+struct Group {
+    int team = 32;
+    size_t smem_factor = 0, smem_solve1 = 0;   // solve smem for one right-hand side
+    int max_nx = 0, max_nu = 0;
+    std::vector<Item> items;
+    Item *d_items = nullptr;
+};
+
+struct DevicePtrs {
+    std::vector<void *> all;
+    template <typename T> cudaError_t alloc(T **p, size_t count) {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+        if (e == cudaSuccess) all.push_back((void *)*p);
+        return e;
+    }
+    void free_all() {
+        for (void *p : all) cudaFree(p);
+        all.clear();
+    }
+};
+
+}  // namespace
+
+struct cyq_handle_s {
+    int device = 0;
+    int batch = 0;
+    int precision = CYQ_FP64;
+    int max_nrhs = 1, it_max = 10;
+    double tol = 1e-10;
+    std::vector<Inst> inst;
+    std::vector<Group> groups;
+    std::vector<int> cr_list;     // instances with P > 1
+    std::vector<Chunk> chunks;
+    long long kkt = 0, nL = 0, nLB = 0, nF = 0, nblk = 0, nvec = 0;
+    size_t cr_smem = 0, crs_smem1 = 0;
+    int max_nx = 0;
+    // device
+    DevicePtrs mem;
+    Inst *d_inst = nullptr;
+    int *d_cr_list = nullptr, *d_all_list = nullptr;
+    Chunk *d_chunks = nullptr;
+    void *L = nullptr, *LB = nullptr, *F = nullptr;
+    double *Mf = nullptr, *Mb = nullptr, *Kc = nullptr, *U = nullptr, *Y = nullptr;
+    double *dF = nullptr, *dB = nullptr, *lam = nullptr;
+    int *status = nullptr;
+    double *r = nullptr, *dz = nullptr, *rr = nullptr, *bb = nullptr, *rel = nullptr;
+    int *done = nullptr, *steps = nullptr;
+    Data data{};
+    bool factored = false;
+    long long launches = 0;
+    int last_refine_steps = 0;
+};
+
+namespace {
+
+cyq_status fail_cuda(cudaError_t e, const char *where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return CYQ_ERR_CUDA;
+}
+
+#define CYQ_CUDA(call)                                           \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return fail_cuda(e_, #call);      \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int choose_team(int nx, int nu) {
+    const int nux = nx + nu;
+    if (nux <= 24) return 32;
+    if (nux <= 48) return 64;
+    return 128;
+}
+
+// Segments per instance: enough (instance, segment) work items to occupy the
+// GPU when the batch is small, at least 8 stages per segment, a power of two.
+int auto_segments(int batch, int N) {
+    const int target = 2 * kSMs;
+    if (batch >= target) return 1;
+    const int want = (target + batch - 1) / batch;
+    int P = 1;
+    while (P < want) P <<= 1;
+    while (P > 1 && N / P < 8) P >>= 1;
+    return P;
+}
+
+cudaStream_t to_stream(cyq_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+SolveArgs solve_args(cyq_handle h, const Group &g, const double *b, double *z, int nrhs, const int *skip) {
+    SolveArgs a{};
+    a.inst = h->d_inst;
+    a.items = g.d_items;
+    a.n_items = (int)g.items.size();
+    a.data = h->data;
+    a.L = h->L;
+    a.LB = h->LB;
+    a.F = h->F;
+    a.Mf = h->Mf;
+    a.Kc = h->Kc;
+    a.U = h->U;
+    a.Y = h->Y;
+    a.b = b;
+    a.z = z;
+    a.kkt = h->kkt;
+    a.nrhs = nrhs;
+    a.dF = h->dF;
+    a.dB = h->dB;
+    a.lam = h->lam;
+    a.nvec = h->nvec;
+    a.skip = skip;
+    return a;
+}
+
+// One solve with the stored factor (float64 or float32 arithmetic).
+cyq_status run_solve(cyq_handle h, const double *b, double *z, int nrhs, const int *skip, cudaStream_t st) {
+    const bool fp64 = h->precision == CYQ_FP64;
+    for (const Group &g : h->groups) {
+        SolveArgs a = solve_args(h, g, b, z, nrhs, skip);
+        size_t smem = solve_smem_bytes(fp64, g.max_nx, g.max_nu, nrhs);
+        CYQ_CUDA(launch_solve_backward(fp64, g.team, smem, a, st));
+        ++h->launches;
+    }
+    {
+        SolveArgs a = solve_args(h, h->groups[0], b, z, nrhs, skip);
+        size_t smem = ((size_t)h->crs_smem1) * nrhs;
+        CYQ_CUDA(launch_cr_solve(h->batch, h->d_all_list, 128, smem, a, st));
+        ++h->launches;
+    }
+    for (const Group &g : h->groups) {
+        SolveArgs a = solve_args(h, g, b, z, nrhs, skip);
+        size_t smem = solve_smem_bytes(fp64, g.max_nx, g.max_nu, nrhs);
+        CYQ_CUDA(launch_solve_forward(fp64, g.team, smem, a, st));
+        ++h->launches;
+    }
+    return CYQ_OK;
+}
+
+ResidArgs resid_args(cyq_handle h, const double *b, const double *z, double *r, const int *skip) {
+    ResidArgs a{};
+    a.inst = h->d_inst;
+    a.chunks = h->d_chunks;
+    a.n_chunks = (int)h->chunks.size();
+    a.data = h->data;
+    a.b = b;
+    a.z = z;
+    a.r = r;
+    a.rr = h->rr;
+    a.bb = h->bb;
+    a.skip = skip;
+    return a;
+}
+
+// Float32 solve + float64 iterative refinement for one right-hand side.
+cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, cudaStream_t st) {
+    const int B = h->batch;
+    CYQ_CUDA(cudaMemsetAsync(h->done, 0, sizeof(int) * B, st));
+    CYQ_CUDA(cudaMemsetAsync(h->steps, 0, sizeof(int) * B, st));
+    CYQ_CUDA(cudaMemsetAsync(h->rr, 0, sizeof(double) * B, st));
+    CYQ_CUDA(cudaMemsetAsync(h->bb, 0, sizeof(double) * B, st));
+    cyq_status s = run_solve(h, b, z, 1, nullptr, st);
+    if (s != CYQ_OK) return s;
+    for (int it = 0; it <= h->it_max; ++it) {
+        CYQ_CUDA(launch_residual(resid_args(h, b, z, h->r, h->done), st));
+        CYQ_CUDA(launch_resid_finalize(B, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, it, h->done, st));
+        h->launches += 2;
+        if (it == h->it_max) break;
+        s = run_solve(h, h->r, h->dz, 1, h->done, st);
+        if (s != CYQ_OK) return s;
+        CYQ_CUDA(launch_ir_update(h->d_inst, B, z, h->dz, h->done, h->kkt, st));
+        ++h->launches;
+    }
+    CYQ_CUDA(launch_mark_not_converged(B, h->done, h->status, st));
+    ++h->launches;
+    return CYQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cyq_status_string(cyq_status s) {
+    switch (s) {
+        case CYQ_OK: return "ok";
+        case CYQ_ERR_INVALID_ARG: return "invalid argument";
+        case CYQ_ERR_NOT_PD: return "matrix not positive definite";
+        case CYQ_ERR_NOT_CONVERGED: return "refinement did not converge";
+        case CYQ_ERR_CUDA: return "CUDA error";
+        case CYQ_ERR_TIMEOUT: return "device wait timed out";
+        case CYQ_ERR_NO_FACTOR: return "no factorization";
+        case CYQ_ERR_UNIMPLEMENTED: return "unimplemented";
+        case CYQ_ERR_NO_DEVICE: return "no CUDA device";
+    }
+    return "unknown status";
+}
+
+const char *cyq_last_error(void) { return g_last_error.c_str(); }
+
+cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
+    if (!desc || !out) return CYQ_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (desc->batch < 1 || !desc->N || !desc->nx || !desc->nu) return CYQ_ERR_INVALID_ARG;
+    if (desc->precision != CYQ_FP64 && desc->precision != CYQ_FP32_REFINE) return CYQ_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        g_last_error = "no CUDA device";
+        return CYQ_ERR_NO_DEVICE;
+    }
+    int dev = desc->device;
+    if (dev < 0) cudaGetDevice(&dev);
+    if (dev >= ndev) return CYQ_ERR_INVALID_ARG;
+    DeviceGuard guard(dev);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+
+    cyq_handle h = new cyq_handle_s();
+    h->device = dev;
+    h->batch = desc->batch;
+    h->precision = desc->precision;
+    h->max_nrhs = desc->max_nrhs > 0 ? desc->max_nrhs : 1;
+    h->it_max = desc->it_max > 0 ? desc->it_max : 10;
+    h->tol = desc->tol > 0 ? desc->tol : 1e-10;
+    const bool fp64 = h->precision == CYQ_FP64;
+
+    long long oQ = 0, oR = 0, oS = 0, oA = 0, oB = 0, oSig = 0, oZ = 0, oL = 0, oLB = 0, oF = 0, oBlk = 0,
+              oVec = 0, oq = 0, orv = 0, oc = 0, ox0 = 0;
+    std::vector<Item> all_items;
+    int item = 0;
+    for (int i = 0; i < desc->batch; ++i) {
+        const int N = desc->N[i], nx = desc->nx[i], nu = desc->nu[i];
+        if (N < 1 || nx < 1 || nu < 1) { delete h; return CYQ_ERR_INVALID_ARG; }
+        int P = desc->P_per_instance ? desc->P_per_instance[i] : desc->P;
+        if (P <= 0) P = auto_segments(desc->batch, N);
+        if (P > N) P = N;
+        Inst in{};
+        in.N = N; in.nx = nx; in.nu = nu; in.P = P; in.item0 = item;
+        in.oQ = oQ; in.oR = oR; in.oS = oS; in.oA = oA; in.oB = oB; in.oSig = oSig; in.oZ = oZ;
+        in.oL = oL; in.oLB = oLB; in.oF = oF; in.oBlk = oBlk; in.oVec = oVec;
+        in.oq = oq; in.orv = orv; in.oc = oc; in.ox0 = ox0;
+        const long long nux = nx + nu;
+        oQ += (long long)(N + 1) * nx * nx; oR += (long long)N * nu * nu; oS += (long long)N * nu * nx;
+        oA += (long long)N * nx * nx; oB += (long long)N * nx * nu; oSig += (long long)(N + 1) * (nu + nx);
+        oZ += (long long)N * (nu + 2 * nx);
+        oL += (long long)N * nux * nux; oLB += (long long)N * nx * nu; oF += (long long)N * nx * nx;
+        oBlk += (long long)P * nx * nx; oVec += (long long)P * nx;
+        oq += (long long)(N + 1) * nx; orv += (long long)N * nu; oc += (long long)N * nx; ox0 += nx;
+        h->inst.push_back(in);
+        if (P > 1) h->cr_list.push_back(i);
+        // work items and their team class
+        const int team = choose_team(nx, nu);
+        const size_t fs = factor_smem_bytes(fp64, nx, nu);
+        if (fs > (size_t)smem_optin) { delete h; g_last_error = "stage blocks too large for shared memory"; return CYQ_ERR_INVALID_ARG; }
+        Group *g = nullptr;
+        for (Group &gg : h->groups)
+            if (gg.team == team) g = &gg;
+        if (!g) {
+            h->groups.emplace_back();
+            g = &h->groups.back();
+            g->team = team;
+        }
+        g->max_nx = std::max(g->max_nx, nx);
+        g->max_nu = std::max(g->max_nu, nu);
+        for (int c = 0; c < P; ++c) g->items.push_back(Item{i, c});
+        item += P;
+        // residual chunks of up to 64 records
+        for (int k0 = 0; k0 < N; k0 += 64) h->chunks.push_back(Chunk{i, k0, std::min(N, k0 + 64)});
+        h->max_nx = std::max(h->max_nx, nx);
+        h->crs_smem1 = std::max(h->crs_smem1, (size_t)(P + 1) * nx * sizeof(double));
+    }
+    for (Group &g : h->groups) {
+        g.smem_factor = factor_smem_bytes(fp64, g.max_nx, g.max_nu);
+        g.smem_solve1 = solve_smem_bytes(fp64, g.max_nx, g.max_nu, 1);
+        if (g.smem_factor > (size_t)smem_optin ||
+            solve_smem_bytes(fp64, g.max_nx, g.max_nu, h->max_nrhs) > (size_t)smem_optin) {
+            delete h;
+            g_last_error = "stage blocks too large for shared memory";
+            return CYQ_ERR_INVALID_ARG;
+        }
+    }
+    if (h->crs_smem1 * h->max_nrhs > (size_t)smem_optin) { delete h; return CYQ_ERR_INVALID_ARG; }
+    h->cr_smem = cr_smem_bytes(h->max_nx);
+    h->kkt = oZ; h->nL = oL; h->nLB = oLB; h->nF = oF; h->nblk = oBlk; h->nvec = oVec;
+
+    auto fail = [&](cudaError_t e, const char *what) {
+        cyq_status s = fail_cuda(e, what);
+        h->mem.free_all();
+        delete h;
+        return s;
+    };
+#define ALLOC(ptr, count)                                      \
+    do {                                                       \
+        cudaError_t e_ = h->mem.alloc(&(ptr), (count));        \
+        if (e_ != cudaSuccess) return fail(e_, "cudaMalloc");  \
+    } while (0)
+    ALLOC(h->d_inst, h->inst.size());
+    ALLOC(h->d_chunks, h->chunks.size());
+    ALLOC(h->d_cr_list, h->cr_list.size());
+    ALLOC(h->d_all_list, (size_t)h->batch);
+    for (Group &g : h->groups) ALLOC(g.d_items, g.items.size());
+    const size_t el = fp64 ? sizeof(double) : sizeof(float);
+    {
+        char *p;
+        ALLOC(p, (size_t)oL * el); h->L = p;
+        ALLOC(p, (size_t)oLB * el); h->LB = p;
+        ALLOC(p, (size_t)oF * el); h->F = p;
+    }
+    ALLOC(h->Mf, (size_t)oBlk);
+    ALLOC(h->Mb, (size_t)oBlk);
+    ALLOC(h->Kc, (size_t)oBlk);
+    ALLOC(h->U, (size_t)oBlk);
+    ALLOC(h->Y, (size_t)oBlk);
+    ALLOC(h->dF, (size_t)oVec * h->max_nrhs);
+    ALLOC(h->dB, (size_t)oVec * h->max_nrhs);
+    ALLOC(h->lam, (size_t)oVec * h->max_nrhs);
+    ALLOC(h->status, (size_t)h->batch);
+    ALLOC(h->r, (size_t)oZ);
+    ALLOC(h->dz, (size_t)oZ);
+    ALLOC(h->rr, (size_t)h->batch);
+    ALLOC(h->bb, (size_t)h->batch);
+    ALLOC(h->rel, (size_t)h->batch);
+    ALLOC(h->done, (size_t)h->batch);
+    ALLOC(h->steps, (size_t)h->batch);
+#undef ALLOC
+    std::vector<int> all(h->batch);
+    for (int i = 0; i < h->batch; ++i) all[i] = i;
+    cudaError_t e;
+    if ((e = cudaMemcpy(h->d_inst, h->inst.data(), sizeof(Inst) * h->inst.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(h->d_chunks, h->chunks.data(), sizeof(Chunk) * h->chunks.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(h->d_all_list, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemset(h->status, 0, sizeof(int) * h->batch)) ||
+        (e = cudaMemset(h->rr, 0, sizeof(double) * h->batch)) ||
+        (e = cudaMemset(h->bb, 0, sizeof(double) * h->batch)) ||
+        (e = cudaMemset(h->rel, 0, sizeof(double) * h->batch)) ||
+        (e = cudaMemset(h->steps, 0, sizeof(int) * h->batch)))
+        return fail(e, "cudaMemcpy");
+    if (!h->cr_list.empty() &&
+        (e = cudaMemcpy(h->d_cr_list, h->cr_list.data(), sizeof(int) * h->cr_list.size(), cudaMemcpyHostToDevice)))
+        return fail(e, "cudaMemcpy");
+    for (Group &g : h->groups)
+        if ((e = cudaMemcpy(g.d_items, g.items.data(), sizeof(Item) * g.items.size(), cudaMemcpyHostToDevice)))
+            return fail(e, "cudaMemcpy");
+    *out = h;
+    return CYQ_OK;
+}
+
+void cyq_destroy(cyq_handle h) {
+    if (!h) return;
+    DeviceGuard guard(h->device);
+    cudaDeviceSynchronize();
+    h->mem.free_all();
+    delete h;
+}
+
+int64_t cyq_kkt_size(cyq_handle h) { return h ? h->kkt : -1; }
+
+cyq_status cyq_get_segments(cyq_handle h, int32_t *P_out) {
+    if (!h || !P_out) return CYQ_ERR_INVALID_ARG;
+    for (int i = 0; i < h->batch; ++i) P_out[i] = h->inst[i].P;
+    return CYQ_OK;
+}
+
+int64_t cyq_last_launch_count(cyq_handle h) { return h ? h->launches : -1; }
+
+cyq_status cyq_factor(cyq_handle h, const double *Q, const double *R, const double *S, const double *A,
+                      const double *B, const double *Sigma, cyq_stream stream) {
+    if (!h || !Q || !R || !A || !B) return CYQ_ERR_INVALID_ARG;
+    DeviceGuard guard(h->device);
+    cudaStream_t st = to_stream(stream);
+    h->launches = 0;
+    h->data = Data{Q, R, S, A, B, Sigma};
+    const bool fp64 = h->precision == CYQ_FP64;
+    CYQ_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int) * h->batch, st));
+    FactorArgs a{};
+    a.inst = h->d_inst;
+    a.data = h->data;
+    a.L = h->L;
+    a.LB = h->LB;
+    a.F = h->F;
+    a.Mf = h->Mf;
+    a.Mb = h->Mb;
+    a.Kc = h->Kc;
+    a.U = h->U;
+    a.Y = h->Y;
+    a.status = h->status;
+    for (const Group &g : h->groups) {
+        a.items = g.d_items;
+        a.n_items = (int)g.items.size();
+        CYQ_CUDA(launch_factor_segments(fp64, g.team, g.smem_factor, a, st));
+        ++h->launches;
+    }
+    if (!h->cr_list.empty()) {
+        CYQ_CUDA(launch_cr_factor((int)h->cr_list.size(), h->d_cr_list, 128, h->cr_smem, a, st));
+        ++h->launches;
+    }
+    h->factored = true;
+    return CYQ_OK;
+}
+
+cyq_status cyq_solve(cyq_handle h, const double *b, double *z, int32_t nrhs, cyq_stream stream) {
+    if (!h || !b || !z || nrhs < 1 || nrhs > h->max_nrhs) return CYQ_ERR_INVALID_ARG;
+    if (!h->factored) return CYQ_ERR_NO_FACTOR;
+    DeviceGuard guard(h->device);
+    cudaStream_t st = to_stream(stream);
+    h->launches = 0;
+    if (h->precision == CYQ_FP64) return run_solve(h, b, z, nrhs, nullptr, st);
+    for (int r = 0; r < nrhs; ++r) {
+        cyq_status s = run_refined_solve(h, b + (long long)r * h->kkt, z + (long long)r * h->kkt, st);
+        if (s != CYQ_OK) return s;
+    }
+    return CYQ_OK;
+}
+
+cyq_status cyq_build_rhs(cyq_handle h, const double *q, const double *r, const double *c, const double *x_init,
+                         double *b, cyq_stream stream) {
+    if (!h || !q || !r || !c || !x_init || !b) return CYQ_ERR_INVALID_ARG;
+    if (!h->factored) return CYQ_ERR_NO_FACTOR;
+    DeviceGuard guard(h->device);
+    CYQ_CUDA(launch_build_rhs(h->d_inst, h->batch, h->data, q, r, c, x_init, b, h->kkt, to_stream(stream)));
+    return CYQ_OK;
+}
+
+cyq_status cyq_residual(cyq_handle h, const double *b, const double *z, double *res, double *rel,
+                        cyq_stream stream) {
+    if (!h || !b || !z) return CYQ_ERR_INVALID_ARG;
+    if (!h->factored) return CYQ_ERR_NO_FACTOR;
+    DeviceGuard guard(h->device);
+    cudaStream_t st = to_stream(stream);
+    CYQ_CUDA(cudaMemsetAsync(h->rr, 0, sizeof(double) * h->batch, st));
+    CYQ_CUDA(cudaMemsetAsync(h->bb, 0, sizeof(double) * h->batch, st));
+    CYQ_CUDA(launch_residual(resid_args(h, b, z, res, nullptr), st));
+    CYQ_CUDA(launch_resid_finalize(h->batch, h->rr, h->bb, rel ? rel : h->rel, nullptr, 0.0, nullptr, 0, nullptr,
+                                   st));
+    return CYQ_OK;
+}
+
+cyq_status cyq_solve_adjoint(cyq_handle h, const double *x_init, const double *z, const double *dL_dz, double *w,
+                             double *dQ, double *dq, double *dR, double *dr, double *dS, double *dA, double *dB,
+                             double *dc, double *dx_init, double *dSigma, cyq_stream stream) {
+    if (!h || !x_init || !z || !dL_dz) return CYQ_ERR_INVALID_ARG;
+    if (!h->factored) return CYQ_ERR_NO_FACTOR;
+    DeviceGuard guard(h->device);
+    cudaStream_t st = to_stream(stream);
+    double *wbuf = w ? w : h->dz;
+    if (!w && h->precision != CYQ_FP64) return CYQ_ERR_INVALID_ARG;   // dz is the refinement workspace
+    cyq_status s = cyq_solve(h, dL_dz, wbuf, 1, stream);
+    if (s != CYQ_OK) return s;
+    GradArgs g{};
+    g.inst = h->d_inst;
+    g.chunks = h->d_chunks;
+    g.x0 = x_init;
+    g.z = z;
+    g.w = wbuf;
+    g.dQ = dQ; g.dq = dq; g.dR = dR; g.dr = dr; g.dS = dS; g.dA = dA; g.dB = dB; g.dc = dc; g.dSig = dSigma;
+    CYQ_CUDA(launch_adjoint(g, (int)h->chunks.size(), h->batch, h->data, dx_init, st));
+    return CYQ_OK;
+}
+
+cyq_status cyq_get_instance_status(cyq_handle h, int32_t *host_status, cyq_stream stream) {
+    if (!h || !host_status) return CYQ_ERR_INVALID_ARG;
+    DeviceGuard guard(h->device);
+    cudaStream_t st = to_stream(stream);
+    CYQ_CUDA(cudaStreamSynchronize(st));
+    CYQ_CUDA(cudaMemcpy(host_status, h->status, sizeof(int) * h->batch, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < h->batch; ++i)
+        if (host_status[i] != 0) return (cyq_status)host_status[i];
+    return CYQ_OK;
+}
+
+cyq_status cyq_get_stats(cyq_handle h, cyq_stats *out, cyq_stream stream) {
+    if (!h || !out) return CYQ_ERR_INVALID_ARG;
+    DeviceGuard guard(h->device);
+    CYQ_CUDA(cudaStreamSynchronize(to_stream(stream)));
+    std::vector<double> rel(h->batch);
+    std::vector<int> steps(h->batch);
+    CYQ_CUDA(cudaMemcpy(rel.data(), h->rel, sizeof(double) * h->batch, cudaMemcpyDeviceToHost));
+    CYQ_CUDA(cudaMemcpy(steps.data(), h->steps, sizeof(int) * h->batch, cudaMemcpyDeviceToHost));
+    out->refine_steps = 0;
+    out->max_rel_residual = 0.0;
+    for (int i = 0; i < h->batch; ++i) {
+        out->refine_steps = std::max(out->refine_steps, steps[i]);
+        out->max_rel_residual = std::max(out->max_rel_residual, rel[i]);
+    }
+    out->P_min = 1 << 30;
+    out->P_max = 0;
+    for (const Inst &in : h->inst) {
+        out->P_min = std::min(out->P_min, in.P);
+        out->P_max = std::max(out->P_max, in.P);
+    }
+    long long items = 0;
+    for (const Group &g : h->groups) items += (long long)g.items.size();
+    out->work_items = items;
+    return CYQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,276 @@
+// Internal declarations of the cyq CUDA library: plan records, segment
+// geometry and the team-cooperative dense block primitives used by the
+// kernels.  A "team" is one CTA of TEAM threads working on one unit of work
+// (a horizon segment of one instance, or one cyclic-reduction block); all
+// matrices live in shared memory, column-major with an explicit leading
+// dimension, and have runtime sizes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cyq {
+
+// ---------------------------------------------------------------------------
+// Plan records (device copies built by cyq_create)
+// ---------------------------------------------------------------------------
+struct Inst {
+    int N, nx, nu, P;
+    int item0;       // first work item of this instance
+    int pad0;
+    long long oQ, oR, oS, oA, oB, oSig;  // offsets into the data arrays (doubles)
+    long long oZ;                        // offset into b / z (doubles)
+    long long oL, oLB, oF;               // offsets into the factor arrays (elements)
+    long long oBlk;                      // offset of the P coupling blocks (nx*nx each)
+    long long oVec;                      // offset of the P coupling vectors (nx each)
+    long long oq, orv, oc, ox0;          // offsets of q ((N+1) nx), r (N nu), c (N nx), x_init (nx)
+};
+
+struct Item {
+    int inst, seg;
+};
+
+// Data pointers of the last factor call (borrowed, float64).
+struct Data {
+    const double *Q, *R, *S, *A, *B, *Sig;
+};
+
+// Device status codes (mirror cyq_status).
+enum : int { ST_OK = 0, ST_NOT_PD = 2, ST_NOT_CONVERGED = 3 };
+
+// Segment c of an instance with horizon N split into P segments: boundaries
+// b(c) = floor(c N / P).  Segment c >= 1 holds stages b(c-1)+1 .. b(c);
+// segment 0 holds stage 0 (u^0 paired with x^N) and stages b(P-1)+1 .. N-1.
+// Stages are processed backward: s(t) = (b(c) - t) mod N, t = 0..len-1
+// (Alg. fact-mod-riccati with indices reduced modulo N).
+__host__ __device__ inline int seg_bound(int c, int N, int P) {
+    return (int)(((long long)c * N) / P);
+}
+__host__ __device__ inline int seg_len(int c, int N, int P) {
+    return c == 0 ? N - seg_bound(P - 1, N, P) : seg_bound(c, N, P) - seg_bound(c - 1, N, P);
+}
+__host__ __device__ inline int seg_stage(int c, int t, int N, int P) {
+    int s = seg_bound(c, N, P) - t;
+    return s < 0 ? s + N : s;
+}
+// Index of the state paired with stage s (x^s, or x^N for s = 0).
+__host__ __device__ inline int xstate(int s, int N) { return s == 0 ? N : s; }
+
+// ---------------------------------------------------------------------------
+// Team primitives
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void team_sync() { __syncthreads(); }
+
+template <typename T> __device__ __forceinline__ T ld_cvt(const double *p) { return (T)(*p); }
+
+// Element e of the lower triangle (diagonal included) of an n x n matrix in
+// row order: row r holds r + 1 entries.  Returns (r, c) with c <= r.
+__device__ __forceinline__ void tri_index(int e, int &r, int &c) {
+    int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+    while (rr * (rr + 1) / 2 > e) --rr;
+    r = rr;
+    c = e - rr * (rr + 1) / 2;
+}
+
+// sqrt and reciprocal used by the Cholesky pivots.
+__device__ __forceinline__ double pivot_sqrt(double d) { return sqrt(d); }
+__device__ __forceinline__ float pivot_sqrt(float d) { return sqrtf(d); }
+__device__ __forceinline__ bool finite_pos(double d) { return d > 0.0 && d < 1.0 / 0.0; }
+__device__ __forceinline__ bool finite_pos(float d) { return d > 0.0f && d < 1.0f / 0.0f; }
+
+// In-place lower Cholesky factor of the n x n matrix A (lower triangle read;
+// upper triangle set to zero).  Right-looking: per column a pivot, a scaled
+// column and a rank-1 update of the trailing lower triangle.  Every thread
+// computes the pivot redundantly (no extra barrier).  Returns false if a
+// pivot was not positive and finite (the factor then holds the first bad
+// pivot replaced by 1 so that the arithmetic stays finite).
+template <typename T, int TEAM>
+__device__ bool team_chol(T *A, int n, int ld) {
+    const int tid = threadIdx.x;
+    bool ok = true;
+    for (int k = 0; k < n; ++k) {
+        T d = A[k + k * ld];
+        if (!finite_pos(d)) { ok = false; d = T(1); }
+        const T l = pivot_sqrt(d);
+        const T il = T(1) / l;
+        team_sync();   // everyone has read A[k,k]
+        if (tid == 0) A[k + k * ld] = l;
+        for (int i = k + 1 + tid; i < n; i += TEAM) A[i + k * ld] *= il;
+        for (int i = tid; i < k; i += TEAM) A[i + k * ld] = T(0);   // upper part of column k
+        team_sync();
+        const int m = n - k - 1;                 // trailing size
+        const int cnt = m * (m + 1) / 2;
+        for (int e = tid; e < cnt; e += TEAM) {
+            int r, c;
+            tri_index(e, r, c);
+            r += k + 1;
+            c += k + 1;
+            A[r + c * ld] -= A[r + k * ld] * A[c + k * ld];
+        }
+        team_sync();
+    }
+    return ok;
+}
+
+// X (m x n, ldx) := X * L^{-T}, L lower n x n (ldl): row-wise forward substitution
+// (X L^T = Y).  One thread per row.
+template <typename T, int TEAM>
+__device__ void team_trsm_rlt(T *X, int m, int n, int ldx, const T *L, int ldl) {
+    for (int r = threadIdx.x; r < m; r += TEAM) {
+        for (int j = 0; j < n; ++j) {
+            T s = X[r + j * ldx];
+            for (int t = 0; t < j; ++t) s -= X[r + t * ldx] * L[j + t * ldl];
+            X[r + j * ldx] = s / L[j + j * ldl];
+        }
+    }
+    team_sync();
+}
+
+// Tinv (n x n, ldt) := L^{-1} for lower L (n x n, ldl); one thread per column.
+template <typename T, int TEAM>
+__device__ void team_trtri_lower(T *Tinv, int ldt, const T *L, int ldl, int n) {
+    for (int c = threadIdx.x; c < n; c += TEAM) {
+        for (int i = 0; i < c; ++i) Tinv[i + c * ldt] = T(0);
+        for (int i = c; i < n; ++i) {
+            T s = (i == c) ? T(1) : T(0);
+            for (int t = c; t < i; ++t) s -= L[i + t * ldl] * Tinv[t + c * ldt];
+            Tinv[i + c * ldt] = s / L[i + i * ldl];
+        }
+    }
+    team_sync();
+}
+
+// C (m x n, ldc) (op)= A (m x k, lda) * B (k x n, ldb).  Mode: 0 assign, 1 add, -1 subtract.
+template <typename T, int TEAM>
+__device__ void team_gemm_nn(T *C, int ldc, const T *A, int lda, const T *B, int ldb, int m, int n, int k,
+                             int mode) {
+    const int cnt = m * n;
+    for (int e = threadIdx.x; e < cnt; e += TEAM) {
+        const int r = e % m, c = e / m;
+        T s = T(0);
+        for (int t = 0; t < k; ++t) s += A[r + t * lda] * B[t + c * ldb];
+        T *o = C + r + c * ldc;
+        *o = mode == 0 ? s : (mode > 0 ? *o + s : *o - s);
+    }
+    team_sync();
+}
+
+// C (m x n) (op)= A (m x k) * B^T (B is n x k, ldb).
+template <typename T, int TEAM>
+__device__ void team_gemm_nt(T *C, int ldc, const T *A, int lda, const T *B, int ldb, int m, int n, int k,
+                             int mode) {
+    const int cnt = m * n;
+    for (int e = threadIdx.x; e < cnt; e += TEAM) {
+        const int r = e % m, c = e / m;
+        T s = T(0);
+        for (int t = 0; t < k; ++t) s += A[r + t * lda] * B[c + t * ldb];
+        T *o = C + r + c * ldc;
+        *o = mode == 0 ? s : (mode > 0 ? *o + s : *o - s);
+    }
+    team_sync();
+}
+
+// Lower triangle of C (n x n) (op)= A A^T, A is n x k.
+template <typename T, typename TC, int TEAM>
+__device__ void team_syrk_lower(TC *C, int ldc, const T *A, int lda, int n, int k, int mode) {
+    const int cnt = n * (n + 1) / 2;
+    for (int e = threadIdx.x; e < cnt; e += TEAM) {
+        int r, c;
+        tri_index(e, r, c);
+        T s = T(0);
+        for (int t = 0; t < k; ++t) s += A[r + t * lda] * A[c + t * lda];
+        TC *o = C + r + c * ldc;
+        *o = mode == 0 ? (TC)s : (mode > 0 ? *o + (TC)s : *o - (TC)s);
+    }
+    team_sync();
+}
+
+// Mirror the lower triangle of an n x n matrix into its upper triangle.
+template <typename T, int TEAM>
+__device__ void team_symmetrize(T *C, int ldc, int n) {
+    const int cnt = n * n;
+    for (int e = threadIdx.x; e < cnt; e += TEAM) {
+        const int r = e % n, c = e / n;
+        if (c > r) C[r + c * ldc] = C[c + r * ldc];
+    }
+    team_sync();
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers (defined in the kernel translation units)
+// ---------------------------------------------------------------------------
+struct Plan;   // host plan (api.cu)
+
+struct FactorArgs {
+    const Inst *inst;
+    const Item *items;
+    int n_items;
+    Data data;
+    void *L, *LB, *F;               // factor arrays (float or double)
+    double *Mf, *Mb, *Kc;           // Schur blocks (float64)
+    double *U, *Y;                  // cyclic-reduction factor blocks (float64)
+    int *status;
+};
+
+struct SolveArgs {
+    const Inst *inst;
+    const Item *items;
+    int n_items;
+    Data data;
+    const void *L, *LB, *F;
+    const double *Mf, *Kc, *U, *Y;  // coupling factor (Mf holds the CR Cholesky blocks)
+    const double *b;                // right-hand sides (float64)
+    double *z;                      // solutions (float64)
+    long long kkt;                  // elements per right-hand side
+    int nrhs;
+    double *dF, *dB, *lam;          // coupling vectors (float64), [rhs][P*nx]
+    long long nvec;                 // coupling-vector elements per right-hand side
+    const int *skip;                // optional per-instance flag: nonzero = leave this instance alone
+};
+
+cudaError_t launch_factor_segments(bool fp64, int team, size_t smem, const FactorArgs &a, cudaStream_t st);
+cudaError_t launch_cr_factor(int n_inst_cr, const int *inst_list, int team, size_t smem, const FactorArgs &a,
+                             cudaStream_t st);
+cudaError_t launch_solve_backward(bool fp64, int team, size_t smem, const SolveArgs &a, cudaStream_t st);
+cudaError_t launch_cr_solve(int n_inst_cr, const int *inst_list, int team, size_t smem, const SolveArgs &a,
+                            cudaStream_t st);
+cudaError_t launch_solve_forward(bool fp64, int team, size_t smem, const SolveArgs &a, cudaStream_t st);
+
+struct Chunk {
+    int inst, k0, k1;   // records [k0, k1) of one instance
+};
+
+struct ResidArgs {
+    const Inst *inst;
+    const Chunk *chunks;
+    int n_chunks;
+    Data data;
+    const double *b, *z;
+    double *r;          // may be null (norms only)
+    double *rr, *bb;    // per-instance accumulators (squared norms)
+    const int *skip;    // optional
+};
+
+struct GradArgs {
+    const Inst *inst;
+    const Chunk *chunks;
+    const double *x0, *z, *w;
+    double *dQ, *dq, *dR, *dr, *dS, *dA, *dB, *dc, *dSig;
+};
+
+cudaError_t launch_residual(const ResidArgs &a, cudaStream_t st);
+cudaError_t launch_resid_finalize(int batch, double *rr, double *bb, double *rel, int *done, double tol, int *steps,
+                                  int step, const int *skip_in, cudaStream_t st);
+cudaError_t launch_ir_update(const Inst *inst, int batch, double *z, const double *dz, const int *done, long long kkt,
+                             cudaStream_t st);
+cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, cudaStream_t st);
+cudaError_t launch_build_rhs(const Inst *inst, int batch, const Data &d, const double *q, const double *r,
+                             const double *c, const double *x0, double *b, long long kkt, cudaStream_t st);
+cudaError_t launch_adjoint(const GradArgs &g, int n_chunks, int batch, const Data &d, double *dx0, cudaStream_t st);
+
+size_t factor_smem_bytes(bool fp64, int nx, int nu);
+size_t cr_smem_bytes(int nx);
+size_t solve_smem_bytes(bool fp64, int nx, int nu, int nrhs);
+
+}  // namespace cyq

@@ -1,0 +1,300 @@
+// Float64 KKT residual, iterative-refinement bookkeeping, right-hand-side
+// assembly and adjoint gradient assembly.
+//
+// Residual rows (paper eq. opt-cond-ocp-eq, E_j = I), record k of z:
+//   u^k      : R_k u^k + S_k x^k + B_k^T lambda^k                       (no S_0 term)
+//   x^{k+1}  : Q_{k+1} x^{k+1} - lambda^k + S_{k+1}^T u^{k+1} + A_{k+1}^T lambda^{k+1}
+//              (the last two terms only for k+1 < N)
+//   lambda^k : B_k u^k + A_k x^k - x^{k+1}                              (no A_0 term)
+// with Sigma added to the diagonals of R and Q.  Work is split into chunks
+// of records; each chunk adds its squared norms into per-instance float64
+// accumulators.
+#include "cyq_internal.cuh"
+
+namespace cyq {
+
+
+template <int TEAM>
+__global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a) {
+    __shared__ double red_r[TEAM / 32], red_b[TEAM / 32];
+    const Chunk ch = a.chunks[blockIdx.x];
+    if (a.skip && a.skip[ch.inst]) return;
+    const Inst in = a.inst[ch.inst];
+    const int N = in.N, nx = in.nx, nu = in.nu, w = nu + 2 * nx;
+    const Data &d = a.data;
+    const double *z = a.z + in.oZ, *b = a.b + in.oZ;
+    double sr = 0.0, sb = 0.0;
+    const int rows = (ch.k1 - ch.k0) * w;
+    for (int e = threadIdx.x; e < rows; e += TEAM) {
+        const int k = ch.k0 + e / w, row = e % w;
+        const double *zk = z + (long long)k * w;
+        double acc;
+        if (row < nu) {
+            const int i = row;
+            const double *R = d.R + in.oR + (long long)k * nu * nu;
+            const double *B = d.B + in.oB + (long long)k * nx * nu;
+            acc = 0.0;
+            for (int j = 0; j < nu; ++j) acc += R[i + j * nu] * zk[j];
+            if (d.Sig) acc += d.Sig[in.oSig + (long long)k * (nu + nx) + i] * zk[i];
+            if (k > 0 && d.S) {
+                const double *S = d.S + in.oS + (long long)k * nu * nx;
+                const double *xk = zk - w + nu;
+                for (int j = 0; j < nx; ++j) acc += S[i + j * nu] * xk[j];
+            }
+            const double *lam = zk + nu + nx;
+            for (int j = 0; j < nx; ++j) acc += B[j + i * nx] * lam[j];
+        } else if (row < nu + nx) {
+            const int i = row - nu, j1 = k + 1;
+            const double *Q = d.Q + in.oQ + (long long)j1 * nx * nx;
+            const double *x = zk + nu;
+            acc = -zk[nu + nx + i];
+            for (int m = 0; m < nx; ++m) acc += Q[i + m * nx] * x[m];
+            if (d.Sig) acc += d.Sig[in.oSig + (long long)j1 * (nu + nx) + nu + i] * x[i];
+            if (j1 < N) {
+                const double *zn = zk + w;
+                const double *A = d.A + in.oA + (long long)j1 * nx * nx;
+                for (int m = 0; m < nx; ++m) acc += A[m + i * nx] * zn[nu + nx + m];
+                if (d.S) {
+                    const double *S = d.S + in.oS + (long long)j1 * nu * nx;
+                    for (int m = 0; m < nu; ++m) acc += S[m + i * nu] * zn[m];
+                }
+            }
+        } else {
+            const int i = row - nu - nx;
+            const double *B = d.B + in.oB + (long long)k * nx * nu;
+            acc = -zk[nu + i];
+            for (int m = 0; m < nu; ++m) acc += B[i + m * nx] * zk[m];
+            if (k > 0) {
+                const double *A = d.A + in.oA + (long long)k * nx * nx;
+                const double *xk = zk - w + nu;
+                for (int m = 0; m < nx; ++m) acc += A[i + m * nx] * xk[m];
+            }
+        }
+        const double bv = b[(long long)k * w + row];
+        const double rv = bv - acc;
+        if (a.r) a.r[in.oZ + (long long)k * w + row] = rv;
+        sr += rv * rv;
+        sb += bv * bv;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red_r[threadIdx.x >> 5] = sr;
+        red_b[threadIdx.x >> 5] = sb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0.0, tb = 0.0;
+        for (int i = 0; i < TEAM / 32; ++i) { tr += red_r[i]; tb += red_b[i]; }
+        atomicAdd(a.rr + ch.inst, tr);
+        atomicAdd(a.bb + ch.inst, tb);
+    }
+}
+
+// rel = ||r|| / ||b||; done = rel <= tol (refinement); clears the accumulators.
+__global__ void k_resid_finalize(int batch, double *rr, double *bb, double *rel, int *done, double tol,
+                                 int *steps, int step, const int *skip_in) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= batch) return;
+    if (skip_in && skip_in[i]) return;
+    const double r = sqrt(rr[i]), bn = sqrt(bb[i]);
+    const double v = bn > 0.0 ? r / bn : r;
+    if (rel) rel[i] = v;
+    if (done && v <= tol) done[i] = 1;
+    if (steps && (!done || !done[i])) steps[i] = step;
+    rr[i] = 0.0;
+    bb[i] = 0.0;
+}
+
+// z += dz for instances not yet converged (one thread per element).
+__global__ void k_ir_update(const Inst *inst, int batch, double *z, const double *dz, const int *done,
+                            long long kkt) {
+    // grid-stride over all elements; the instance of an element is found by binary search on oZ
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < kkt;
+         e += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = batch - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (inst[mid].oZ <= e) lo = mid; else hi = mid - 1;
+        }
+        if (!done[lo]) z[e] += dz[e];
+    }
+}
+
+__global__ void k_mark_not_converged(int batch, const int *done, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < batch && !done[i]) atomicCAS(status + i, 0, ST_NOT_CONVERGED);
+}
+
+// b = -(r~, q, f~) with r~^0 = r^0 + S_0 x_init and f~^0 = f^0 + A_0 x_init
+// (eq. opt-cond-ocp-eq); one thread per element of b.
+__device__ __forceinline__ int find_inst(const Inst *inst, int batch, long long e) {
+    int lo = 0, hi = batch - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (inst[mid].oZ <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_build_rhs(const Inst *inst, int batch, Data d, const double *q, const double *r,
+                            const double *c, const double *x0, double *b, long long kkt) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < kkt;
+         e += (long long)gridDim.x * blockDim.x) {
+        const Inst in = inst[find_inst(inst, batch, e)];
+        const int nx = in.nx, nu = in.nu, w = nu + 2 * nx;
+        const long long loc = e - in.oZ;
+        const int k = (int)(loc / w), row = (int)(loc % w);
+        const double *xi = x0 + in.ox0;
+        double v;
+        if (row < nu) {
+            v = r[in.orv + (long long)k * nu + row];
+            if (k == 0 && d.S) {
+                const double *S = d.S + in.oS;
+                for (int j = 0; j < nx; ++j) v += S[row + j * nu] * xi[j];
+            }
+        } else if (row < nu + nx) {
+            v = q[in.oq + (long long)(k + 1) * nx + (row - nu)];
+        } else {
+            const int i = row - nu - nx;
+            v = c[in.oc + (long long)k * nx + i];
+            if (k == 0) {
+                const double *A = d.A + in.oA;
+                for (int j = 0; j < nx; ++j) v += A[i + j * nx] * xi[j];
+            }
+        }
+        b[e] = -v;
+    }
+}
+
+// Adjoint gradients (implicit differentiation of K z = b), one CTA per chunk
+// of records.  w = K^{-1} dL/dz is given; with x^0 = x_init:
+//   dR_k = -sym(w_u u^T), dr_k = -w_u, dS_k = -(w_u x^{kT} + u w_x^{kT}),
+//   dA_k = -(w_l x^{kT} + lambda w_x^{kT}), dB_k = -(w_l u^T + lambda w_u^T),
+//   dc_k = -w_l, dQ_{k+1} = -sym(w_x x^T), dq_{k+1} = -w_x,
+//   dSigma_u^k = -w_u .* u, dSigma_x^{k+1} = -w_x .* x
+// (the w_x^k terms vanish for k = 0 since x^0 is fixed).
+
+template <int TEAM>
+__global__ void __launch_bounds__(TEAM) k_adjoint_grads(GradArgs g) {
+    const Chunk ch = g.chunks[blockIdx.x];
+    const Inst in = g.inst[ch.inst];
+    const int nx = in.nx, nu = in.nu, wd = nu + 2 * nx, N = in.N;
+    const double *z = g.z + in.oZ, *w = g.w + in.oZ, *xi = g.x0 + in.ox0;
+    for (int k = ch.k0; k < ch.k1; ++k) {
+        const double *u = z + (long long)k * wd, *xn = u + nu, *lam = xn + nx;
+        const double *wu = w + (long long)k * wd, *wxn = wu + nu, *wl = wxn + nx;
+        const double *xk = k > 0 ? u - wd + nu : xi;
+        const double *wxk = k > 0 ? wu - wd + nu : nullptr;
+        if (g.dR)
+            for (int e = threadIdx.x; e < nu * nu; e += TEAM) {
+                const int i = e % nu, j = e / nu;
+                g.dR[in.oR + (long long)k * nu * nu + e] = -0.5 * (wu[i] * u[j] + u[i] * wu[j]);
+            }
+        if (g.dr)
+            for (int i = threadIdx.x; i < nu; i += TEAM) g.dr[in.orv + (long long)k * nu + i] = -wu[i];
+        if (g.dS)
+            for (int e = threadIdx.x; e < nu * nx; e += TEAM) {
+                const int i = e % nu, j = e / nu;
+                g.dS[in.oS + (long long)k * nu * nx + e] = -(wu[i] * xk[j] + (wxk ? u[i] * wxk[j] : 0.0));
+            }
+        if (g.dA)
+            for (int e = threadIdx.x; e < nx * nx; e += TEAM) {
+                const int i = e % nx, j = e / nx;
+                g.dA[in.oA + (long long)k * nx * nx + e] = -(wl[i] * xk[j] + (wxk ? lam[i] * wxk[j] : 0.0));
+            }
+        if (g.dB)
+            for (int e = threadIdx.x; e < nx * nu; e += TEAM) {
+                const int i = e % nx, j = e / nx;
+                g.dB[in.oB + (long long)k * nx * nu + e] = -(wl[i] * u[j] + lam[i] * wu[j]);
+            }
+        if (g.dc)
+            for (int i = threadIdx.x; i < nx; i += TEAM) g.dc[in.oc + (long long)k * nx + i] = -wl[i];
+        if (g.dQ)
+            for (int e = threadIdx.x; e < nx * nx; e += TEAM) {
+                const int i = e % nx, j = e / nx;
+                g.dQ[in.oQ + (long long)(k + 1) * nx * nx + e] = -0.5 * (wxn[i] * xn[j] + xn[i] * wxn[j]);
+                if (k == 0) g.dQ[in.oQ + e] = 0.0;
+            }
+        if (g.dq)
+            for (int i = threadIdx.x; i < nx; i += TEAM) {
+                g.dq[in.oq + (long long)(k + 1) * nx + i] = -wxn[i];
+                if (k == 0) g.dq[in.oq + i] = 0.0;
+            }
+        if (g.dSig) {
+            double *ds = g.dSig + in.oSig;
+            for (int i = threadIdx.x; i < nu; i += TEAM) ds[(long long)k * (nu + nx) + i] = -wu[i] * u[i];
+            for (int i = threadIdx.x; i < nx; i += TEAM) ds[(long long)(k + 1) * (nu + nx) + nu + i] = -wxn[i] * xn[i];
+            if (k == 0)
+                for (int i = threadIdx.x; i < nx; i += TEAM) ds[nu + i] = 0.0;
+            if (k == N - 1)
+                for (int i = threadIdx.x; i < nu; i += TEAM) ds[(long long)N * (nu + nx) + i] = 0.0;
+        }
+    }
+}
+
+// dx_init = -S_0^T w_u^0 - A_0^T w_l^0 ; one thread per (instance, component).
+__global__ void k_adjoint_dx0(const Inst *inst, int batch, Data d, const double *w, double *dx0) {
+    const int ii = blockIdx.x;
+    if (ii >= batch) return;
+    const Inst in = inst[ii];
+    const int nx = in.nx, nu = in.nu;
+    const double *wu = w + in.oZ, *wl = wu + nu + nx;
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+        double acc = 0.0;
+        if (d.S)
+            for (int i = 0; i < nu; ++i) acc += d.S[in.oS + i + j * nu] * wu[i];
+        for (int i = 0; i < nx; ++i) acc += d.A[in.oA + i + j * nx] * wl[i];
+        dx0[in.ox0 + j] = -acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_residual(const ResidArgs &a, cudaStream_t st) {
+    if (a.n_chunks == 0) return cudaSuccess;
+    k_residual<128><<<a.n_chunks, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_finalize(int batch, double *rr, double *bb, double *rel, int *done, double tol, int *steps,
+                                  int step, const int *skip_in, cudaStream_t st) {
+    k_resid_finalize<<<(batch + 127) / 128, 128, 0, st>>>(batch, rr, bb, rel, done, tol, steps, step, skip_in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ir_update(const Inst *inst, int batch, double *z, const double *dz, const int *done, long long kkt,
+                             cudaStream_t st) {
+    long long blocks = (kkt + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_ir_update<<<(int)blocks, 256, 0, st>>>(inst, batch, z, dz, done, kkt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, cudaStream_t st) {
+    k_mark_not_converged<<<(batch + 127) / 128, 128, 0, st>>>(batch, done, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_rhs(const Inst *inst, int batch, const Data &d, const double *q, const double *r,
+                             const double *c, const double *x0, double *b, long long kkt, cudaStream_t st) {
+    long long blocks = (kkt + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_build_rhs<<<(int)blocks, 256, 0, st>>>(inst, batch, d, q, r, c, x0, b, kkt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const GradArgs &g, int n_chunks, int batch, const Data &d, double *dx0, cudaStream_t st) {
+    if (n_chunks > 0) k_adjoint_grads<128><<<n_chunks, 128, 0, st>>>(g);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (dx0) k_adjoint_dx0<<<batch, 64, 0, st>>>(g.inst, batch, d, g.w, dx0);
+    return cudaGetLastError();
+}
+
+}  // namespace cyq

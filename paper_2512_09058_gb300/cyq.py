@@ -1,0 +1,215 @@
+"""Thin ctypes binding of the cyq C ABI (include/cyq.h).
+
+Argument marshalling only: every step of factor, solve, refinement and adjoint
+runs in the CUDA library ``libcyq.so``.  PyTorch provides device memory and the
+current CUDA stream.  There is no CPU fallback: if the compiled library is
+missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcyq.so")
+
+CYQ_FP64 = 0
+CYQ_FP32_REFINE = 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "not positive definite", 3: "not converged", 4: "CUDA error",
+          5: "timeout", 6: "no factor", 7: "unimplemented", 8: "no device"}
+
+# every entry point declared in include/cyq.h
+EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual",
+           "cyq_solve_adjoint", "cyq_get_instance_status", "cyq_get_stats", "cyq_kkt_size",
+           "cyq_get_segments", "cyq_last_launch_count", "cyq_status_string", "cyq_last_error"]
+
+
+class CyqError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("cyq error %d (%s)%s" % (code, STATUS.get(code, "?"), (": " + what) if what else ""))
+
+
+class cyq_desc(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int32), ("N", ctypes.POINTER(ctypes.c_int32)),
+                ("nx", ctypes.POINTER(ctypes.c_int32)), ("nu", ctypes.POINTER(ctypes.c_int32)),
+                ("precision", ctypes.c_int32), ("P", ctypes.c_int32),
+                ("P_per_instance", ctypes.POINTER(ctypes.c_int32)), ("max_nrhs", ctypes.c_int32),
+                ("it_max", ctypes.c_int32), ("tol", ctypes.c_double), ("device", ctypes.c_int32)]
+
+
+class cyq_stats(ctypes.Structure):
+    _fields_ = [("refine_steps", ctypes.c_int32), ("max_rel_residual", ctypes.c_double),
+                ("P_min", ctypes.c_int32), ("P_max", ctypes.c_int32), ("work_items", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcyq.so (built by ``paper_2512_09058_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libcyq.so not found at %s: build it with paper_2512_09058_gb300/build.py "
+                           "(there is no CPU fallback)" % path)
+    L = ctypes.CDLL(path)
+    vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.cyq_create.argtypes = [ctypes.POINTER(cyq_desc), ctypes.POINTER(vp)]
+    L.cyq_destroy.argtypes = [vp]
+    L.cyq_destroy.restype = None
+    L.cyq_factor.argtypes = [vp] + [vp] * 6 + [vp]
+    L.cyq_solve.argtypes = [vp, vp, vp, i32, vp]
+    L.cyq_build_rhs.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.cyq_residual.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.cyq_solve_adjoint.argtypes = [vp] + [vp] * 14 + [vp]
+    L.cyq_get_instance_status.argtypes = [vp, ctypes.POINTER(i32), vp]
+    L.cyq_get_stats.argtypes = [vp, ctypes.POINTER(cyq_stats), vp]
+    L.cyq_kkt_size.argtypes = [vp]
+    L.cyq_kkt_size.restype = i64
+    L.cyq_get_segments.argtypes = [vp, ctypes.POINTER(i32)]
+    L.cyq_last_launch_count.argtypes = [vp]
+    L.cyq_last_launch_count.restype = i64
+    L.cyq_status_string.argtypes = [ctypes.c_int]
+    L.cyq_status_string.restype = ctypes.c_char_p
+    L.cyq_last_error.argtypes = []
+    L.cyq_last_error.restype = ctypes.c_char_p
+    for name in ["cyq_create", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual", "cyq_solve_adjoint",
+                 "cyq_get_instance_status", "cyq_get_stats", "cyq_get_segments"]:
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(code: int):
+    if code != 0:
+        what = _lib.cyq_last_error().decode() if code == 4 else ""
+        raise CyqError(code, what)
+
+
+def _ptr(t) -> Optional[int]:
+    """Device pointer of a torch CUDA tensor (float64, contiguous) or None."""
+    if t is None:
+        return None
+    import torch
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Solver:
+    """A planned batch of OCP KKT systems (one cyq handle)."""
+
+    def __init__(self, N: Sequence[int], nx: Sequence[int], nu: Sequence[int], precision: str = "fp64",
+                 P: int = 0, P_per_instance: Optional[Sequence[int]] = None, max_nrhs: int = 1,
+                 it_max: int = 10, tol: float = 1e-10, device: int = -1):
+        L = load()
+        self.N = np.ascontiguousarray(N, dtype=np.int32)
+        self.nx = np.ascontiguousarray(nx, dtype=np.int32)
+        self.nu = np.ascontiguousarray(nu, dtype=np.int32)
+        self.batch = len(self.N)
+        self.precision = {"fp64": CYQ_FP64, "fp32_refine": CYQ_FP32_REFINE}[precision]
+        self.max_nrhs = max_nrhs
+        pp = None
+        if P_per_instance is not None:
+            self._P = np.ascontiguousarray(P_per_instance, dtype=np.int32)
+            pp = self._P.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        desc = cyq_desc(self.batch, self.N.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                        self.nx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                        self.nu.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.precision, P, pp,
+                        max_nrhs, it_max, tol, device)
+        h = ctypes.c_void_p()
+        _check(L.cyq_create(ctypes.byref(desc), ctypes.byref(h)))
+        self._h = h
+        self.kkt_size = int(L.cyq_kkt_size(h))
+        self._data = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.cyq_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def segments(self) -> np.ndarray:
+        out = np.zeros(self.batch, np.int32)
+        _check(_lib.cyq_get_segments(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return out
+
+    def launch_count(self) -> int:
+        return int(_lib.cyq_last_launch_count(self._h))
+
+    def factor(self, Q, R, S, A, B, Sigma=None, stream=None):
+        self._data = (Q, R, S, A, B, Sigma)   # borrowed until the last solve
+        _check(_lib.cyq_factor(self._h, _ptr(Q), _ptr(R), _ptr(S), _ptr(A), _ptr(B), _ptr(Sigma),
+                               _stream(stream)))
+
+    def solve(self, b, z=None, nrhs: int = 1, stream=None):
+        import torch
+        if z is None:
+            z = torch.empty_like(b)
+        _check(_lib.cyq_solve(self._h, _ptr(b), _ptr(z), nrhs, _stream(stream)))
+        return z
+
+    def build_rhs(self, q, r, c, x0, b=None, stream=None):
+        import torch
+        if b is None:
+            b = torch.empty(self.kkt_size, dtype=torch.float64, device=q.device)
+        _check(_lib.cyq_build_rhs(self._h, _ptr(q), _ptr(r), _ptr(c), _ptr(x0), _ptr(b), _stream(stream)))
+        return b
+
+    def residual(self, b, z, res=None, stream=None):
+        import torch
+        rel = torch.empty(self.batch, dtype=torch.float64, device=b.device)
+        _check(_lib.cyq_residual(self._h, _ptr(b), _ptr(z), _ptr(res), _ptr(rel), _stream(stream)))
+        return rel
+
+    def solve_adjoint(self, x0, z, dL_dz, stream=None, want=("w", "dQ", "dq", "dR", "dr", "dS", "dA", "dB", "dc",
+                                                              "dx0", "dSigma")):
+        import torch
+        dev = z.device
+        N, nx, nu = self.N.astype(np.int64), self.nx.astype(np.int64), self.nu.astype(np.int64)
+        sizes = dict(w=self.kkt_size, dQ=int(((N + 1) * nx * nx).sum()), dq=int(((N + 1) * nx).sum()),
+                     dR=int((N * nu * nu).sum()), dr=int((N * nu).sum()), dS=int((N * nu * nx).sum()),
+                     dA=int((N * nx * nx).sum()), dB=int((N * nx * nu).sum()), dc=int((N * nx).sum()),
+                     dx0=int(nx.sum()), dSigma=int(((N + 1) * (nu + nx)).sum()))
+        out = {k: torch.empty(sizes[k], dtype=torch.float64, device=dev) for k in want}
+        g = lambda k: _ptr(out.get(k))
+        _check(_lib.cyq_solve_adjoint(self._h, _ptr(x0), _ptr(z), _ptr(dL_dz), g("w"), g("dQ"), g("dq"), g("dR"),
+                                      g("dr"), g("dS"), g("dA"), g("dB"), g("dc"), g("dx0"), g("dSigma"),
+                                      _stream(stream)))
+        return out
+
+    def instance_status(self, stream=None) -> np.ndarray:
+        out = np.zeros(self.batch, np.int32)
+        _lib.cyq_get_instance_status(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream(stream))
+        return out
+
+    def stats(self, stream=None) -> dict:
+        s = cyq_stats()
+        _check(_lib.cyq_get_stats(self._h, ctypes.byref(s), _stream(stream)))
+        return dict(refine_steps=s.refine_steps, max_rel_residual=s.max_rel_residual, P_min=s.P_min,
+                    P_max=s.P_max, work_items=s.work_items)
+
+
+def to_device(batch, device="cuda"):
+    """Copy a host Batch (float64 numpy arrays) to torch CUDA tensors (data + rhs list)."""
+    import torch
+    t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    data = dict(Q=t(batch.Q), R=t(batch.R), S=t(batch.S), A=t(batch.A), B=t(batch.B), Sigma=t(batch.Sigma))
+    rhs = [tuple(t(x) for x in r) for r in batch.rhs]
+    return data, rhs

@@ -1,0 +1,63 @@
+"""Shared helpers of the GPU tests: build/load the CUDA library, run it on a
+host Batch, and compare with the CPU oracle instance by instance."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_09058_gb300 import inputs
+
+
+def require_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    from paper_2512_09058_gb300 import build, cyq
+    build.build()
+    cyq.load()
+    return torch, cyq
+
+
+def split_instances(batch, flat):
+    """Split a concatenated KKT vector into per-instance pieces."""
+    out, off = [], 0
+    for x in batch.instances:
+        n = x.kkt_size
+        out.append(flat[off:off + n])
+        off += n
+    return out
+
+
+def oracle_rhs(batch, rhs_index=0):
+    return np.concatenate([oracle.build_rhs(x, *x.rhs[rhs_index]) for x in batch.instances])
+
+
+def gpu_solve(batch, precision="fp64", P=0, P_per_instance=None, nrhs=1, it_max=10, tol=1e-10, b_host=None):
+    """Factor + solve on the GPU through the C ABI; returns (z (nrhs, kkt), solver, device data)."""
+    torch, cyq = require_gpu()
+    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, P=P, P_per_instance=P_per_instance,
+                   max_nrhs=nrhs, it_max=it_max, tol=tol)
+    data, rhs = cyq.to_device(batch)
+    s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
+    if b_host is None:
+        b_host = np.stack([oracle_rhs(batch, j) for j in range(nrhs)])
+    b = torch.from_numpy(np.ascontiguousarray(b_host.reshape(-1))).cuda()
+    z = s.solve(b, nrhs=nrhs)
+    torch.cuda.synchronize()
+    return z.cpu().numpy().reshape(nrhs, -1), s, data, b_host.reshape(nrhs, -1)
+
+
+def rel_err(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def small_cfg(seed, S=True, sigma=(1e-2, 1e2)):
+    return dict(batch=1, N=8, nx=3, nu=2, S=S, sigma=sigma, nrhs=1, QN_equals_Q0=False, seed=seed)
+
+
+def ragged_batch(seed, dims, S=True, sigma=(1e-2, 1e2), nrhs=1):
+    insts = []
+    for i, (N, nx, nu) in enumerate(dims):
+        cfg = dict(batch=1, N=N, nx=nx, nu=nu, S=S, sigma=sigma, nrhs=nrhs, QN_equals_Q0=False, seed=seed)
+        insts.append(inputs.make_instance(cfg, i))
+    return inputs.make_batch(None, instances=insts)
