@@ -76,7 +76,7 @@ typedef enum cyq_status {
 } cyq_status;
 
 typedef enum cyq_precision {
-    CYQ_FP64 = 0,          /* factor and solve in float64 */
+    CYQ_FP64 = 0,          /* factor and solve in float64 (+ float64 refinement if it_max > 0) */
     CYQ_FP32_REFINE = 1    /* float32 factor/solve, float64 residual + iterative refinement */
 } cyq_precision;
 
@@ -95,7 +95,7 @@ typedef struct cyq_desc {
     int32_t P;              /* horizon segments per instance; 0 = automatic.  Clamped to N. */
     const int32_t *P_per_instance; /* optional host array [batch] overriding P (NULL = none) */
     int32_t max_nrhs;       /* largest nrhs passed to cyq_solve, >= 1 */
-    int32_t it_max;         /* refinement steps (CYQ_FP32_REFINE), default 10 if <= 0 */
+    int32_t it_max;         /* max refinement steps; 0 = plain solve (no residual); < 0: default 10 */
     double tol;             /* relative KKT residual target, default 1e-10 if <= 0 */
     int32_t device;         /* CUDA device ordinal (the caller's current device if < 0) */
 } cyq_desc;
@@ -126,11 +126,13 @@ cyq_status cyq_factor(cyq_handle h, const double *Q, const double *R, const doub
  * Solve K z = b for nrhs right-hand sides (1 <= nrhs <= max_nrhs) with the
  * last factor.  b and z are device float64 arrays of nrhs * kkt_size
  * elements (kkt_size = sum_i N_i (nu_i + 2 nx_i)); they must not overlap.
- * CYQ_FP64: one forward/backward substitution.  CYQ_FP32_REFINE: a float32
- * solve, then up to it_max steps of  r = b - K z (float64), dz = K^{-1} r
- * (float32 factor), z += dz, stopping per instance once ||r||/||b|| <= tol
- * (the loop runs on the device; no host synchronisation).
- * Errors returned: INVALID_ARG, NO_FACTOR, CUDA.
+ * it_max = 0: one forward/backward substitution in the factor's precision.
+ * it_max > 0: that solve, then up to it_max steps of  r = b - K z (float64),
+ * dz = K~^{-1} r (stored factor K~), z += dz, stopping per instance once
+ * ||r_j|| / ||b_j|| <= tol for every right-hand side j; an instance still
+ * above tol gets status CYQ_ERR_NOT_CONVERGED.  Every decision is taken on
+ * the device (no host synchronisation), so the call can be captured in a
+ * CUDA graph.  Errors returned: INVALID_ARG, NO_FACTOR, CUDA.
  */
 cyq_status cyq_solve(cyq_handle h, const double *b, double *z, int32_t nrhs, cyq_stream stream);
 
@@ -177,8 +179,8 @@ cyq_status cyq_get_instance_status(cyq_handle h, int32_t *host_status, cyq_strea
 
 /* Statistics of the last cyq_solve (host copy; synchronises `stream`). */
 typedef struct cyq_stats {
-    int32_t refine_steps;    /* refinement steps run (max over instances) */
-    double max_rel_residual; /* max over instances of ||b - Kz|| / ||b|| (refinement mode) */
+    int32_t refine_steps;    /* corrections applied (max over instances) */
+    double max_rel_residual; /* max over instances and rhs of ||b - Kz|| / ||b|| (-1 if it_max = 0) */
     int32_t P_min, P_max;    /* segments per instance chosen by the plan */
     int64_t work_items;      /* (instance, segment) pairs */
 } cyq_stats;

@@ -73,7 +73,7 @@ struct cyq_handle_s {
     Data data{};
     bool factored = false;
     long long launches = 0;
-    int last_refine_steps = 0;
+    int last_nrhs = 0;
 };
 
 namespace {
@@ -182,30 +182,37 @@ ResidArgs resid_args(cyq_handle h, const double *b, const double *z, double *r, 
     a.rr = h->rr;
     a.bb = h->bb;
     a.skip = skip;
+    a.kkt = h->kkt;
+    a.batch = h->batch;
     return a;
 }
 
-// Float32 solve + float64 iterative refinement for one right-hand side.
-cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, cudaStream_t st) {
+// Solve + float64 iterative refinement on all right-hand sides at once:
+//   z = K~^{-1} b;  repeat: r = b - K z (float64), stop per instance once
+//   every ||r|| / ||b|| <= tol, else z += K~^{-1} r
+// where K~ is the stored factor (float32 or float64).  All decisions are taken
+// on the device (per-instance flags), so the sequence can be graph-captured.
+cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, int nrhs, cudaStream_t st) {
     const int B = h->batch;
     CYQ_CUDA(cudaMemsetAsync(h->done, 0, sizeof(int) * B, st));
     CYQ_CUDA(cudaMemsetAsync(h->steps, 0, sizeof(int) * B, st));
-    CYQ_CUDA(cudaMemsetAsync(h->rr, 0, sizeof(double) * B, st));
-    CYQ_CUDA(cudaMemsetAsync(h->bb, 0, sizeof(double) * B, st));
-    cyq_status s = run_solve(h, b, z, 1, nullptr, st);
+    CYQ_CUDA(cudaMemsetAsync(h->rr, 0, sizeof(double) * B * h->max_nrhs, st));
+    CYQ_CUDA(cudaMemsetAsync(h->bb, 0, sizeof(double) * B * h->max_nrhs, st));
+    cyq_status s = run_solve(h, b, z, nrhs, nullptr, st);
     if (s != CYQ_OK) return s;
     for (int it = 0; it <= h->it_max; ++it) {
-        CYQ_CUDA(launch_residual(resid_args(h, b, z, h->r, h->done), st));
-        CYQ_CUDA(launch_resid_finalize(B, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, it, h->done, st));
+        CYQ_CUDA(launch_residual(resid_args(h, b, z, h->r, h->done), nrhs, st));
+        CYQ_CUDA(launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, it, st));
         h->launches += 2;
         if (it == h->it_max) break;
-        s = run_solve(h, h->r, h->dz, 1, h->done, st);
+        s = run_solve(h, h->r, h->dz, nrhs, h->done, st);
         if (s != CYQ_OK) return s;
-        CYQ_CUDA(launch_ir_update(h->d_inst, B, z, h->dz, h->done, h->kkt, st));
+        CYQ_CUDA(launch_ir_update(h->d_inst, B, z, h->dz, h->done, h->kkt, nrhs, st));
         ++h->launches;
     }
     CYQ_CUDA(launch_mark_not_converged(B, h->done, h->status, st));
     ++h->launches;
+    h->last_nrhs = nrhs;
     return CYQ_OK;
 }
 
@@ -252,7 +259,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     h->batch = desc->batch;
     h->precision = desc->precision;
     h->max_nrhs = desc->max_nrhs > 0 ? desc->max_nrhs : 1;
-    h->it_max = desc->it_max > 0 ? desc->it_max : 10;
+    h->it_max = desc->it_max >= 0 ? desc->it_max : 10;
     h->tol = desc->tol > 0 ? desc->tol : 1e-10;
     const bool fp64 = h->precision == CYQ_FP64;
 
@@ -347,11 +354,11 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     ALLOC(h->dB, (size_t)oVec * h->max_nrhs);
     ALLOC(h->lam, (size_t)oVec * h->max_nrhs);
     ALLOC(h->status, (size_t)h->batch);
-    ALLOC(h->r, (size_t)oZ);
-    ALLOC(h->dz, (size_t)oZ);
-    ALLOC(h->rr, (size_t)h->batch);
-    ALLOC(h->bb, (size_t)h->batch);
-    ALLOC(h->rel, (size_t)h->batch);
+    ALLOC(h->r, (size_t)oZ * h->max_nrhs);
+    ALLOC(h->dz, (size_t)oZ * h->max_nrhs);
+    ALLOC(h->rr, (size_t)h->batch * h->max_nrhs);
+    ALLOC(h->bb, (size_t)h->batch * h->max_nrhs);
+    ALLOC(h->rel, (size_t)h->batch * h->max_nrhs);
     ALLOC(h->done, (size_t)h->batch);
     ALLOC(h->steps, (size_t)h->batch);
 #undef ALLOC
@@ -362,9 +369,9 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         (e = cudaMemcpy(h->d_chunks, h->chunks.data(), sizeof(Chunk) * h->chunks.size(), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(h->d_all_list, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice)) ||
         (e = cudaMemset(h->status, 0, sizeof(int) * h->batch)) ||
-        (e = cudaMemset(h->rr, 0, sizeof(double) * h->batch)) ||
-        (e = cudaMemset(h->bb, 0, sizeof(double) * h->batch)) ||
-        (e = cudaMemset(h->rel, 0, sizeof(double) * h->batch)) ||
+        (e = cudaMemset(h->rr, 0, sizeof(double) * h->batch * h->max_nrhs)) ||
+        (e = cudaMemset(h->bb, 0, sizeof(double) * h->batch * h->max_nrhs)) ||
+        (e = cudaMemset(h->rel, 0, sizeof(double) * h->batch * h->max_nrhs)) ||
         (e = cudaMemset(h->steps, 0, sizeof(int) * h->batch)))
         return fail(e, "cudaMemcpy");
     if (!h->cr_list.empty() &&
@@ -436,12 +443,11 @@ cyq_status cyq_solve(cyq_handle h, const double *b, double *z, int32_t nrhs, cyq
     DeviceGuard guard(h->device);
     cudaStream_t st = to_stream(stream);
     h->launches = 0;
-    if (h->precision == CYQ_FP64) return run_solve(h, b, z, nrhs, nullptr, st);
-    for (int r = 0; r < nrhs; ++r) {
-        cyq_status s = run_refined_solve(h, b + (long long)r * h->kkt, z + (long long)r * h->kkt, st);
-        if (s != CYQ_OK) return s;
+    if (h->it_max == 0) {
+        h->last_nrhs = 0;
+        return run_solve(h, b, z, nrhs, nullptr, st);
     }
-    return CYQ_OK;
+    return run_refined_solve(h, b, z, nrhs, st);
 }
 
 cyq_status cyq_build_rhs(cyq_handle h, const double *q, const double *r, const double *c, const double *x_init,
@@ -461,9 +467,8 @@ cyq_status cyq_residual(cyq_handle h, const double *b, const double *z, double *
     cudaStream_t st = to_stream(stream);
     CYQ_CUDA(cudaMemsetAsync(h->rr, 0, sizeof(double) * h->batch, st));
     CYQ_CUDA(cudaMemsetAsync(h->bb, 0, sizeof(double) * h->batch, st));
-    CYQ_CUDA(launch_residual(resid_args(h, b, z, res, nullptr), st));
-    CYQ_CUDA(launch_resid_finalize(h->batch, h->rr, h->bb, rel ? rel : h->rel, nullptr, 0.0, nullptr, 0, nullptr,
-                                   st));
+    CYQ_CUDA(launch_residual(resid_args(h, b, z, res, nullptr), 1, st));
+    CYQ_CUDA(launch_resid_finalize(h->batch, 1, h->rr, h->bb, rel ? rel : h->rel, nullptr, 0.0, nullptr, 0, st));
     return CYQ_OK;
 }
 
@@ -504,16 +509,16 @@ cyq_status cyq_get_stats(cyq_handle h, cyq_stats *out, cyq_stream stream) {
     if (!h || !out) return CYQ_ERR_INVALID_ARG;
     DeviceGuard guard(h->device);
     CYQ_CUDA(cudaStreamSynchronize(to_stream(stream)));
-    std::vector<double> rel(h->batch);
+    const int nr = std::max(h->last_nrhs, 1);
+    std::vector<double> rel((size_t)h->batch * nr);
     std::vector<int> steps(h->batch);
-    CYQ_CUDA(cudaMemcpy(rel.data(), h->rel, sizeof(double) * h->batch, cudaMemcpyDeviceToHost));
+    CYQ_CUDA(cudaMemcpy(rel.data(), h->rel, sizeof(double) * rel.size(), cudaMemcpyDeviceToHost));
     CYQ_CUDA(cudaMemcpy(steps.data(), h->steps, sizeof(int) * h->batch, cudaMemcpyDeviceToHost));
     out->refine_steps = 0;
-    out->max_rel_residual = 0.0;
-    for (int i = 0; i < h->batch; ++i) {
-        out->refine_steps = std::max(out->refine_steps, steps[i]);
-        out->max_rel_residual = std::max(out->max_rel_residual, rel[i]);
-    }
+    out->max_rel_residual = h->last_nrhs > 0 ? 0.0 : -1.0;
+    for (int i = 0; i < h->batch; ++i) out->refine_steps = std::max(out->refine_steps, steps[i]);
+    if (h->last_nrhs > 0)
+        for (double v : rel) out->max_rel_residual = std::max(out->max_rel_residual, v);
     out->P_min = 1 << 30;
     out->P_max = 0;
     for (const Inst &in : h->inst) {

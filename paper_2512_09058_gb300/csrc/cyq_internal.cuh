@@ -248,8 +248,10 @@ struct ResidArgs {
     Data data;
     const double *b, *z;
     double *r;          // may be null (norms only)
-    double *rr, *bb;    // per-instance accumulators (squared norms)
-    const int *skip;    // optional
+    double *rr, *bb;    // accumulators of squared norms, [rhs][instance]
+    const int *skip;    // optional per-instance flag
+    long long kkt;      // elements per right-hand side
+    int batch;
 };
 
 struct GradArgs {
@@ -259,11 +261,11 @@ struct GradArgs {
     double *dQ, *dq, *dR, *dr, *dS, *dA, *dB, *dc, *dSig;
 };
 
-cudaError_t launch_residual(const ResidArgs &a, cudaStream_t st);
-cudaError_t launch_resid_finalize(int batch, double *rr, double *bb, double *rel, int *done, double tol, int *steps,
-                                  int step, const int *skip_in, cudaStream_t st);
+cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st);
+cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
+                                  int *steps, int step, cudaStream_t st);
 cudaError_t launch_ir_update(const Inst *inst, int batch, double *z, const double *dz, const int *done, long long kkt,
-                             cudaStream_t st);
+                             int nrhs, cudaStream_t st);
 cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, cudaStream_t st);
 cudaError_t launch_build_rhs(const Inst *inst, int batch, const Data &d, const double *q, const double *r,
                              const double *c, const double *x0, double *b, long long kkt, cudaStream_t st);

@@ -18,11 +18,12 @@ template <int TEAM>
 __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a) {
     __shared__ double red_r[TEAM / 32], red_b[TEAM / 32];
     const Chunk ch = a.chunks[blockIdx.x];
+    const int rhs = blockIdx.y;
     if (a.skip && a.skip[ch.inst]) return;
     const Inst in = a.inst[ch.inst];
     const int N = in.N, nx = in.nx, nu = in.nu, w = nu + 2 * nx;
     const Data &d = a.data;
-    const double *z = a.z + in.oZ, *b = a.b + in.oZ;
+    const double *z = a.z + rhs * a.kkt + in.oZ, *b = a.b + rhs * a.kkt + in.oZ;
     double sr = 0.0, sb = 0.0;
     const int rows = (ch.k1 - ch.k0) * w;
     for (int e = threadIdx.x; e < rows; e += TEAM) {
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a) {
         }
         const double bv = b[(long long)k * w + row];
         const double rv = bv - acc;
-        if (a.r) a.r[in.oZ + (long long)k * w + row] = rv;
+        if (a.r) a.r[rhs * a.kkt + in.oZ + (long long)k * w + row] = rv;
         sr += rv * rv;
         sb += bv * bv;
     }
@@ -88,38 +89,47 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a) {
     if (threadIdx.x == 0) {
         double tr = 0.0, tb = 0.0;
         for (int i = 0; i < TEAM / 32; ++i) { tr += red_r[i]; tb += red_b[i]; }
-        atomicAdd(a.rr + ch.inst, tr);
-        atomicAdd(a.bb + ch.inst, tb);
+        atomicAdd(a.rr + (long long)rhs * a.batch + ch.inst, tr);
+        atomicAdd(a.bb + (long long)rhs * a.batch + ch.inst, tb);
     }
 }
 
-// rel = ||r|| / ||b||; done = rel <= tol (refinement); clears the accumulators.
-__global__ void k_resid_finalize(int batch, double *rr, double *bb, double *rel, int *done, double tol,
-                                 int *steps, int step, const int *skip_in) {
+// Per instance: rel[r] = ||res_r|| / ||b_r|| for each right-hand side r; the
+// instance is done once every right-hand side is at or below tol (refinement
+// runs per instance).  Clears the accumulators.  steps[i] records the number
+// of corrections an instance received so far.
+__global__ void k_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
+                                 int *steps, int step) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= batch) return;
-    if (skip_in && skip_in[i]) return;
-    const double r = sqrt(rr[i]), bn = sqrt(bb[i]);
-    const double v = bn > 0.0 ? r / bn : r;
-    if (rel) rel[i] = v;
-    if (done && v <= tol) done[i] = 1;
-    if (steps && (!done || !done[i])) steps[i] = step;
-    rr[i] = 0.0;
-    bb[i] = 0.0;
+    if (done && done[i]) return;
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) {
+        const long long j = (long long)r * batch + i;
+        const double rn = sqrt(rr[j]), bn = sqrt(bb[j]);
+        const double v = bn > 0.0 ? rn / bn : rn;
+        if (rel) rel[j] = v;
+        all = all && (v <= tol);
+        rr[j] = 0.0;
+        bb[j] = 0.0;
+    }
+    if (done && all) done[i] = 1;
+    if (steps) steps[i] = step;
 }
 
-// z += dz for instances not yet converged (one thread per element).
+// z += dz for instances not yet converged (grid-stride over all elements of all right-hand sides).
 __global__ void k_ir_update(const Inst *inst, int batch, double *z, const double *dz, const int *done,
-                            long long kkt) {
-    // grid-stride over all elements; the instance of an element is found by binary search on oZ
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < kkt;
-         e += (long long)gridDim.x * blockDim.x) {
+                            long long kkt, int nrhs) {
+    const long long total = kkt * nrhs;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long e = g % kkt;
         int lo = 0, hi = batch - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (inst[mid].oZ <= e) lo = mid; else hi = mid - 1;
         }
-        if (!done[lo]) z[e] += dz[e];
+        if (!done[lo]) z[g] += dz[g];
     }
 }
 
@@ -254,24 +264,24 @@ __global__ void k_adjoint_dx0(const Inst *inst, int batch, Data d, const double 
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_residual(const ResidArgs &a, cudaStream_t st) {
+cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st) {
     if (a.n_chunks == 0) return cudaSuccess;
-    k_residual<128><<<a.n_chunks, 128, 0, st>>>(a);
+    k_residual<128><<<dim3(a.n_chunks, nrhs), 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_resid_finalize(int batch, double *rr, double *bb, double *rel, int *done, double tol, int *steps,
-                                  int step, const int *skip_in, cudaStream_t st) {
-    k_resid_finalize<<<(batch + 127) / 128, 128, 0, st>>>(batch, rr, bb, rel, done, tol, steps, step, skip_in);
+cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
+                                  int *steps, int step, cudaStream_t st) {
+    k_resid_finalize<<<(batch + 127) / 128, 128, 0, st>>>(batch, nrhs, rr, bb, rel, done, tol, steps, step);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ir_update(const Inst *inst, int batch, double *z, const double *dz, const int *done, long long kkt,
-                             cudaStream_t st) {
-    long long blocks = (kkt + 255) / 256;
+                             int nrhs, cudaStream_t st) {
+    long long blocks = (kkt * nrhs + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_ir_update<<<(int)blocks, 256, 0, st>>>(inst, batch, z, dz, done, kkt);
+    k_ir_update<<<(int)blocks, 256, 0, st>>>(inst, batch, z, dz, done, kkt, nrhs);
     return cudaGetLastError();
 }
 

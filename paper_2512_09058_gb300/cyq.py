@@ -111,7 +111,7 @@ class Solver:
 
     def __init__(self, N: Sequence[int], nx: Sequence[int], nu: Sequence[int], precision: str = "fp64",
                  P: int = 0, P_per_instance: Optional[Sequence[int]] = None, max_nrhs: int = 1,
-                 it_max: int = 10, tol: float = 1e-10, device: int = -1):
+                 it_max: int = -1, tol: float = 1e-10, device: int = -1):
         L = load()
         self.N = np.ascontiguousarray(N, dtype=np.int32)
         self.nx = np.ascontiguousarray(nx, dtype=np.int32)

@@ -31,7 +31,7 @@ def oracle_rhs(batch, rhs_index=0):
     return np.concatenate([oracle.build_rhs(x, *x.rhs[rhs_index]) for x in batch.instances])
 
 
-def gpu_solve(batch, precision="fp64", P=0, P_per_instance=None, nrhs=1, it_max=10, tol=1e-10, b_host=None):
+def gpu_solve(batch, precision="fp64", P=0, P_per_instance=None, nrhs=1, it_max=0, tol=1e-10, b_host=None):
     """Factor + solve on the GPU through the C ABI; returns (z (nrhs, kkt), solver, device data)."""
     torch, cyq = require_gpu()
     s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, P=P, P_per_instance=P_per_instance,

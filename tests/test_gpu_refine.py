@@ -1,0 +1,70 @@
+"""Iterative refinement on the GPU: float32 factor/solve + float64 residual
+(and float64 factor + float64 residual), checked with the oracle's own FP64
+residual routine on the returned z (gate: relative KKT residual <= 1e-10) and
+against the oracle's solution."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_09058_gb300 import inputs
+
+from gpu_util import gpu_solve, oracle_rhs, ragged_batch, rel_err, split_instances
+
+pytestmark = pytest.mark.gpu
+
+
+def _residuals(batch, z, b):
+    out = []
+    for j in range(z.shape[0]):
+        for inst, zi, bi in zip(batch.instances, split_instances(batch, z[j]), split_instances(batch, b[j])):
+            out.append((oracle.kkt_residual(inst, zi, bi), rel_err(zi, oracle.riccati_solve(inst, bi))))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("precision", ["fp32_refine", "fp64"])
+@pytest.mark.parametrize("P", [1, 4])
+def test_refinement_reaches_tolerance_on_ragged_batch(precision, P):
+    dims = [(8, 3, 2), (17, 6, 3), (32, 12, 4), (5, 2, 1), (40, 20, 8)]
+    batch = ragged_batch(21, dims, sigma=(1e-3, 1e3), nrhs=2)
+    z, s, _, b = gpu_solve(batch, precision=precision, nrhs=2, it_max=10,
+                           P_per_instance=[min(P, d[0]) for d in dims])
+    assert (s.instance_status() == 0).all()
+    res = _residuals(batch, z, b)
+    assert res[:, 0].max() <= 1e-10, res[:, 0].max()
+    assert res[:, 1].max() <= 1e-8
+    st = s.stats()
+    assert st["max_rel_residual"] <= 1e-10
+    assert 0 <= st["refine_steps"] <= 10
+
+
+def test_fp32_refine_on_batch1024_workload_sampled():
+    name = "batch1024_n64_nx12_nu4"
+    batch = inputs.make_batch(name)
+    z, s, _, b = gpu_solve(batch, precision="fp32_refine", nrhs=4, it_max=10)
+    assert (s.instance_status() == 0).all()
+    st = s.stats()
+    print("fp32+refinement on batch1024:", st)
+    assert st["max_rel_residual"] <= 1e-10
+    rng = np.random.default_rng(3)
+    sample = sorted(rng.choice(batch.size, size=16, replace=False))
+    for j in range(4):
+        zs, bs = split_instances(batch, z[j]), split_instances(batch, b[j])
+        for i in sample:
+            inst = batch.instances[i]
+            assert oracle.kkt_residual(inst, zs[i], bs[i]) <= 1e-10
+            assert rel_err(zs[i], oracle.riccati_solve(inst, bs[i])) <= 1e-8
+
+
+def test_fp64_one_refinement_step_on_batch1024_workload():
+    batch = inputs.make_batch("batch1024_n64_nx12_nu4", range(128))
+    z, s, _, b = gpu_solve(batch, precision="fp64", nrhs=4, it_max=10)
+    st = s.stats()
+    print("fp64+refinement on batch1024[:128]:", st)
+    assert st["max_rel_residual"] <= 1e-10 and st["refine_steps"] <= 2
+
+
+def test_no_refinement_budget_reports_not_converged():
+    # it_max = 1 with float32 on a badly scaled problem cannot reach 1e-16
+    batch = ragged_batch(22, [(12, 4, 2), (9, 3, 3)], sigma=(1e-6, 1e6))
+    z, s, _, b = gpu_solve(batch, precision="fp32_refine", it_max=1, tol=1e-16)
+    assert (s.instance_status() == 3).all()
