@@ -193,6 +193,33 @@ cyq_status cyq_get_segments(cyq_handle h, int32_t *P_out);
 /* Number of kernels launched by the last cyq_factor and cyq_solve calls. */
 int64_t cyq_last_launch_count(cyq_handle h);
 
+/*
+ * Allocation-free factor + solve of ONE OCP in float64 (one segment, one
+ * right-hand side).  The paper has no counterpart: this entry point exists
+ * for callers that must not allocate device memory at call time (a CUDA
+ * graph captured into a fixed memory plan, a real-time control loop that
+ * allocates only at start-up, a host whose device allocator belongs to
+ * another runtime).  Its workspace is one fixed array of 2^20 doubles
+ * (8 MiB) in the library's device image, held on every GPU that loads the
+ * library until the process exits; it calls no allocator.
+ *   Inputs: N, nx, nu and device float64 data Q, R, S (or NULL), A, B, Sigma
+ *   (or NULL) of one instance in the layout above, and the right-hand side b
+ *   (N (nu + 2 nx) elements).  Outputs: the solution z (same size, must not
+ *   overlap b) and, if status is not NULL, one device int32 status word
+ *   (CYQ_OK or CYQ_ERR_NOT_PD).
+ *   Size limit: N (nu+nx)^2 + N nx (nu+nx) + 5 nx^2 + 3 nx (+ padding) must
+ *   not exceed 2^20 doubles; larger problems return CYQ_ERR_INVALID_ARG with
+ *   the needed size in cyq_last_error().
+ *   The workspace is shared by every call on a device: calls that overlap on
+ *   the GPU (different streams or host threads) race and must be serialised.
+ *   The first call on a device looks up the workspace address with that
+ *   device current; make it before any stream capture.  Asynchronous on
+ *   `stream` (the data pointers must stay valid until it completes).
+ */
+cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu, const double *Q, const double *R,
+                                    const double *S, const double *A, const double *B, const double *Sigma,
+                                    const double *b, double *z, int32_t *status, cyq_stream stream);
+
 const char *cyq_status_string(cyq_status s);
 /* Text of the last CUDA error seen by this thread's calls ("" if none). */
 const char *cyq_last_error(void);

@@ -532,3 +532,5 @@ cyq_status cyq_get_stats(cyq_handle h, cyq_stats *out, cyq_stream stream) {
 }
 
 }  // extern "C"
+
+void cyq::set_last_error_message(const char *msg) { g_last_error = msg ? msg : ""; }

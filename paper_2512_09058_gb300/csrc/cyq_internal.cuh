@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace cyq {
 
 // ---------------------------------------------------------------------------
@@ -272,6 +274,10 @@ cudaError_t launch_build_rhs(const Inst *inst, int batch, const Data &d, const d
 cudaError_t launch_adjoint(const GradArgs &g, int n_chunks, int batch, const Data &d, double *dx0, cudaStream_t st);
 
 size_t factor_smem_bytes(bool fp64, int nx, int nu);
+
+// Sets the text returned by cyq_last_error() for the calling thread.
+void set_last_error_message(const char *msg);
+inline void set_last_error_message(const std::string &msg) { set_last_error_message(msg.c_str()); }
 size_t cr_smem_bytes(int nx);
 size_t solve_smem_bytes(bool fp64, int nx, int nu, int nrhs);
 

@@ -24,7 +24,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "not positive definite", 3: "not co
 # every entry point declared in include/cyq.h
 EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual",
            "cyq_solve_adjoint", "cyq_get_instance_status", "cyq_get_stats", "cyq_kkt_size",
-           "cyq_get_segments", "cyq_last_launch_count", "cyq_status_string", "cyq_last_error"]
+           "cyq_get_segments", "cyq_last_launch_count", "cyq_status_string", "cyq_last_error",
+           "cyq_factor_solve_noalloc"]
 
 
 class CyqError(RuntimeError):
