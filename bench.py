@@ -38,6 +38,9 @@ METRIC = "KKT factor+solve/sec and ns/stage at rel. residual ≤1e-10; % of roof
 UNIT = "OCP factor+solve/s"
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1258.6
 WORKLOAD = "batch1024_n64_nx12_nu4"
+# method -> (factor precision, refinement step budget).  Float64 refinement
+# converges in one step here; float32 needs ~5 at cond(K) ~ 1e11.
+METHODS = {"fp64": ("fp64", 0), "fp64_refine": ("fp64", 3), "fp32_refine": ("fp32_refine", 8)}
 
 
 def parse():
@@ -150,8 +153,7 @@ def time_oracle(batch, nrhs, min_seconds=2.0, max_instances=None):
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_method(torch, cyq, batch, data, b, method, steps, warmup, rank, world, dist):
-    precision, it_max = {"fp64": ("fp64", 0), "fp64_refine": ("fp64", 10),
-                         "fp32_refine": ("fp32_refine", 10)}[method]
+    precision, it_max = METHODS[method]
     nrhs = len(batch.rhs)
     s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, max_nrhs=nrhs, it_max=it_max)
     z = torch.empty_like(b)
@@ -210,8 +212,7 @@ def run_e2e(torch, cyq, batch, method, steps, warmup):
     """Same metric through the public API with host buffers: every step copies
     the data and (q, r, c, x_init) from pinned host memory, builds the KKT
     right-hand sides, factors, solves and copies z back to pinned memory."""
-    precision, it_max = {"fp64": ("fp64", 0), "fp64_refine": ("fp64", 10),
-                         "fp32_refine": ("fp32_refine", 10)}[method]
+    precision, it_max = METHODS[method]
     nrhs = len(batch.rhs)
     s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, max_nrhs=nrhs, it_max=it_max)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()

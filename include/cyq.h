@@ -207,7 +207,7 @@ int64_t cyq_last_launch_count(cyq_handle h);
  *   (N (nu + 2 nx) elements).  Outputs: the solution z (same size, must not
  *   overlap b) and, if status is not NULL, one device int32 status word
  *   (CYQ_OK or CYQ_ERR_NOT_PD).
- *   Size limit: N (nu+nx)^2 + N nx (nu+nx) + 5 nx^2 + 3 nx (+ padding) must
+ *   Size limit: N (nu+nx)^2 + N nx (nu+nx) + N (nu+nx) + 5 nx^2 + 3 nx (+ padding) must
  *   not exceed 2^20 doubles; larger problems return CYQ_ERR_INVALID_ARG with
  *   the needed size in cyq_last_error().
  *   The workspace is shared by every call on a device: calls that overlap on

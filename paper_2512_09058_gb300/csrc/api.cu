@@ -56,7 +56,7 @@ struct cyq_handle_s {
     std::vector<Group> groups;
     std::vector<int> cr_list;     // instances with P > 1
     std::vector<Chunk> chunks;
-    long long kkt = 0, nL = 0, nLB = 0, nF = 0, nblk = 0, nvec = 0;
+    long long kkt = 0, nL = 0, nLB = 0, nF = 0, nDI = 0, nblk = 0, nvec = 0;
     size_t cr_smem = 0, crs_smem1 = 0;
     int max_nx = 0;
     // device
@@ -64,7 +64,7 @@ struct cyq_handle_s {
     Inst *d_inst = nullptr;
     int *d_cr_list = nullptr, *d_all_list = nullptr;
     Chunk *d_chunks = nullptr;
-    void *L = nullptr, *LB = nullptr, *F = nullptr;
+    void *L = nullptr, *LB = nullptr, *F = nullptr, *DI = nullptr;
     double *Mf = nullptr, *Mb = nullptr, *Kc = nullptr, *U = nullptr, *Y = nullptr;
     double *dF = nullptr, *dB = nullptr, *lam = nullptr;
     int *status = nullptr;
@@ -121,7 +121,8 @@ int auto_segments(int batch, int N) {
 
 cudaStream_t to_stream(cyq_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
-SolveArgs solve_args(cyq_handle h, const Group &g, const double *b, double *z, int nrhs, const int *skip) {
+SolveArgs solve_args(cyq_handle h, const Group &g, const double *b, double *z, int nrhs, const int *skip,
+                     double *zacc = nullptr) {
     SolveArgs a{};
     a.inst = h->d_inst;
     a.items = g.d_items;
@@ -130,6 +131,7 @@ SolveArgs solve_args(cyq_handle h, const Group &g, const double *b, double *z, i
     a.L = h->L;
     a.LB = h->LB;
     a.F = h->F;
+    a.DI = h->DI;
     a.Mf = h->Mf;
     a.Kc = h->Kc;
     a.U = h->U;
@@ -143,26 +145,29 @@ SolveArgs solve_args(cyq_handle h, const Group &g, const double *b, double *z, i
     a.lam = h->lam;
     a.nvec = h->nvec;
     a.skip = skip;
+    a.zacc = zacc;
     return a;
 }
 
-// One solve with the stored factor (float64 or float32 arithmetic).
-cyq_status run_solve(cyq_handle h, const double *b, double *z, int nrhs, const int *skip, cudaStream_t st) {
+// One solve with the stored factor (float64 or float32 arithmetic).  With
+// zacc, the solution is added into zacc and z only holds sweep intermediates.
+cyq_status run_solve(cyq_handle h, const double *b, double *z, int nrhs, const int *skip, cudaStream_t st,
+                     double *zacc = nullptr) {
     const bool fp64 = h->precision == CYQ_FP64;
     for (const Group &g : h->groups) {
-        SolveArgs a = solve_args(h, g, b, z, nrhs, skip);
+        SolveArgs a = solve_args(h, g, b, z, nrhs, skip, zacc);
         size_t smem = solve_smem_bytes(fp64, g.max_nx, g.max_nu, nrhs);
         CYQ_CUDA(launch_solve_backward(fp64, g.team, smem, a, st));
         ++h->launches;
     }
     {
-        SolveArgs a = solve_args(h, h->groups[0], b, z, nrhs, skip);
-        size_t smem = ((size_t)h->crs_smem1) * nrhs;
+        SolveArgs a = solve_args(h, h->groups[0], b, z, nrhs, skip, zacc);
+        size_t smem = ((size_t)h->crs_smem1) * (nrhs + 1);
         CYQ_CUDA(launch_cr_solve(h->batch, h->d_all_list, 128, smem, a, st));
         ++h->launches;
     }
     for (const Group &g : h->groups) {
-        SolveArgs a = solve_args(h, g, b, z, nrhs, skip);
+        SolveArgs a = solve_args(h, g, b, z, nrhs, skip, zacc);
         size_t smem = solve_smem_bytes(fp64, g.max_nx, g.max_nu, nrhs);
         CYQ_CUDA(launch_solve_forward(fp64, g.team, smem, a, st));
         ++h->launches;
@@ -205,10 +210,9 @@ cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, int nrhs,
         CYQ_CUDA(launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, it, st));
         h->launches += 2;
         if (it == h->it_max) break;
-        s = run_solve(h, h->r, h->dz, nrhs, h->done, st);
+        // correction: z += K~^{-1} r for the instances still above tol
+        s = run_solve(h, h->r, h->dz, nrhs, h->done, st, z);
         if (s != CYQ_OK) return s;
-        CYQ_CUDA(launch_ir_update(h->d_inst, B, z, h->dz, h->done, h->kkt, nrhs, st));
-        ++h->launches;
     }
     CYQ_CUDA(launch_mark_not_converged(B, h->done, h->status, st));
     ++h->launches;
@@ -263,7 +267,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     h->tol = desc->tol > 0 ? desc->tol : 1e-10;
     const bool fp64 = h->precision == CYQ_FP64;
 
-    long long oQ = 0, oR = 0, oS = 0, oA = 0, oB = 0, oSig = 0, oZ = 0, oL = 0, oLB = 0, oF = 0, oBlk = 0,
+    long long oQ = 0, oR = 0, oS = 0, oA = 0, oB = 0, oSig = 0, oZ = 0, oL = 0, oLB = 0, oF = 0, oDI = 0, oBlk = 0,
               oVec = 0, oq = 0, orv = 0, oc = 0, ox0 = 0;
     std::vector<Item> all_items;
     int item = 0;
@@ -276,13 +280,14 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         Inst in{};
         in.N = N; in.nx = nx; in.nu = nu; in.P = P; in.item0 = item;
         in.oQ = oQ; in.oR = oR; in.oS = oS; in.oA = oA; in.oB = oB; in.oSig = oSig; in.oZ = oZ;
-        in.oL = oL; in.oLB = oLB; in.oF = oF; in.oBlk = oBlk; in.oVec = oVec;
+        in.oL = oL; in.oLB = oLB; in.oF = oF; in.oDI = oDI; in.oBlk = oBlk; in.oVec = oVec;
         in.oq = oq; in.orv = orv; in.oc = oc; in.ox0 = ox0;
         const long long nux = nx + nu;
         oQ += (long long)(N + 1) * nx * nx; oR += (long long)N * nu * nu; oS += (long long)N * nu * nx;
         oA += (long long)N * nx * nx; oB += (long long)N * nx * nu; oSig += (long long)(N + 1) * (nu + nx);
         oZ += (long long)N * (nu + 2 * nx);
         oL += (long long)N * nux * nux; oLB += (long long)N * nx * nu; oF += (long long)N * nx * nx;
+        oDI += (long long)N * nux;
         oBlk += (long long)P * nx * nx; oVec += (long long)P * nx;
         oq += (long long)(N + 1) * nx; orv += (long long)N * nu; oc += (long long)N * nx; ox0 += nx;
         h->inst.push_back(in);
@@ -306,7 +311,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         // residual chunks of up to 64 records
         for (int k0 = 0; k0 < N; k0 += 64) h->chunks.push_back(Chunk{i, k0, std::min(N, k0 + 64)});
         h->max_nx = std::max(h->max_nx, nx);
-        h->crs_smem1 = std::max(h->crs_smem1, (size_t)(P + 1) * nx * sizeof(double));
+        h->crs_smem1 = std::max(h->crs_smem1, (size_t)P * nx * sizeof(double));
     }
     for (Group &g : h->groups) {
         g.smem_factor = factor_smem_bytes(fp64, g.max_nx, g.max_nu);
@@ -318,9 +323,9 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
             return CYQ_ERR_INVALID_ARG;
         }
     }
-    if (h->crs_smem1 * h->max_nrhs > (size_t)smem_optin) { delete h; return CYQ_ERR_INVALID_ARG; }
+    if (h->crs_smem1 * (h->max_nrhs + 1) > (size_t)smem_optin) { delete h; return CYQ_ERR_INVALID_ARG; }
     h->cr_smem = cr_smem_bytes(h->max_nx);
-    h->kkt = oZ; h->nL = oL; h->nLB = oLB; h->nF = oF; h->nblk = oBlk; h->nvec = oVec;
+    h->kkt = oZ; h->nL = oL; h->nLB = oLB; h->nF = oF; h->nDI = oDI; h->nblk = oBlk; h->nvec = oVec;
 
     auto fail = [&](cudaError_t e, const char *what) {
         cyq_status s = fail_cuda(e, what);
@@ -344,6 +349,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         ALLOC(p, (size_t)oL * el); h->L = p;
         ALLOC(p, (size_t)oLB * el); h->LB = p;
         ALLOC(p, (size_t)oF * el); h->F = p;
+        ALLOC(p, (size_t)oDI * el); h->DI = p;
     }
     ALLOC(h->Mf, (size_t)oBlk);
     ALLOC(h->Mb, (size_t)oBlk);
@@ -417,6 +423,7 @@ cyq_status cyq_factor(cyq_handle h, const double *Q, const double *R, const doub
     a.L = h->L;
     a.LB = h->LB;
     a.F = h->F;
+    a.DI = h->DI;
     a.Mf = h->Mf;
     a.Mb = h->Mb;
     a.Kc = h->Kc;

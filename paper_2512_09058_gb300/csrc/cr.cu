@@ -128,8 +128,12 @@ __global__ void __launch_bounds__(TEAM) k_cr_solve(SolveArgs a, const int *inst_
     const long long nn = (long long)n * n;
     const double *L = a.Mf + in.oBlk, *U = a.U + in.oBlk, *Y = a.Y + in.oBlk;
     double *v = reinterpret_cast<double *>(smem_raw);     // P * n * nrhs (block-major per rhs)
-    double *tmp = v + (long long)P * n * nrhs;            // n * nrhs
+    double *di = v + (long long)P * n * nrhs;             // P * n reciprocal diagonals of the L_k
     const int w = nu + 2 * n;
+    for (long long e = threadIdx.x; e < (long long)P * n; e += TEAM) {
+        const int k = (int)(e / n), i = (int)(e % n);
+        di[e] = 1.0 / L[k * nn + i + i * n];
+    }
     // assemble right-hand sides
     for (long long e = threadIdx.x; e < (long long)nrhs * P * n; e += TEAM) {
         const int r = (int)(e / ((long long)P * n));
@@ -148,16 +152,15 @@ __global__ void __launch_bounds__(TEAM) k_cr_solve(SolveArgs a, const int *inst_
     for (int l = 0; l < levels; ++l) {
         const int s = 1 << l;
         // b~_k = L_k^{-1} b_k for eliminated k (one thread per (k, rhs))
-        for (int job = threadIdx.x;; job += TEAM) {
-            const int nk = (P - s + 2 * s - 1) / (2 * s);
-            if (job >= nk * nrhs) break;
+        const int nk = (P - s + 2 * s - 1) / (2 * s);
+        for (int job = threadIdx.x; job < nk * nrhs; job += TEAM) {
             const int k = s + (job % nk) * 2 * s, r = job / nk;
             double *x = v + (long long)r * P * n + (long long)k * n;
-            const double *Lk = L + k * nn;
+            const double *Lk = L + k * nn, *dk = di + (long long)k * n;
             for (int i = 0; i < n; ++i) {
                 double acc = x[i];
-                for (int t = 0; t < i; ++t) acc -= Lk[i + t * n] * x[t];
-                x[i] = acc / Lk[i + i * n];
+                for (int t = 0; t < i; ++t) acc = fma(-Lk[i + t * n], x[t], acc);
+                x[i] = acc * dk[i];
             }
         }
         team_sync();
@@ -184,13 +187,13 @@ __global__ void __launch_bounds__(TEAM) k_cr_solve(SolveArgs a, const int *inst_
         double *x = v + (long long)r * P * n;
         for (int i = 0; i < n; ++i) {
             double acc = x[i];
-            for (int t = 0; t < i; ++t) acc -= L[i + t * n] * x[t];
-            x[i] = acc / L[i + i * n];
+            for (int t = 0; t < i; ++t) acc = fma(-L[i + t * n], x[t], acc);
+            x[i] = acc * di[i];
         }
         for (int i = n - 1; i >= 0; --i) {
             double acc = x[i];
-            for (int t = i + 1; t < n; ++t) acc -= L[t + i * n] * x[t];
-            x[i] = acc / L[i + i * n];
+            for (int t = i + 1; t < n; ++t) acc = fma(-L[t + i * n], x[t], acc);
+            x[i] = acc * di[i];
         }
     }
     team_sync();
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(TEAM) k_cr_solve(SolveArgs a, const int *inst_
             const int k = s + (job % nk) * 2 * s, r = job / nk;
             double *vr = v + (long long)r * P * n;
             double *x = vr + (long long)k * n;
-            const double *Uk = U + k * nn, *Yk = Y + k * nn, *Lk = L + k * nn;
+            const double *Uk = U + k * nn, *Yk = Y + k * nn, *Lk = L + k * nn, *dk = di + (long long)k * n;
             const double *xp = vr + (long long)(k - s) * n;
             const double *xn = (k + s < P) ? vr + (long long)(k + s) * n : nullptr;
             for (int i = 0; i < n; ++i) {
@@ -215,13 +218,12 @@ __global__ void __launch_bounds__(TEAM) k_cr_solve(SolveArgs a, const int *inst_
             }
             for (int i = n - 1; i >= 0; --i) {
                 double acc = x[i];
-                for (int t = i + 1; t < n; ++t) acc -= Lk[t + i * n] * x[t];
-                x[i] = acc / Lk[i + i * n];
+                for (int t = i + 1; t < n; ++t) acc = fma(-Lk[t + i * n], x[t], acc);
+                x[i] = acc * dk[i];
             }
         }
         team_sync();
     }
-    (void)tmp;
     // scatter lambda^{b_c}
     for (long long e = threadIdx.x; e < (long long)nrhs * P * n; e += TEAM) {
         const int r = (int)(e / ((long long)P * n));
@@ -229,7 +231,8 @@ __global__ void __launch_bounds__(TEAM) k_cr_solve(SolveArgs a, const int *inst_
         const int c = rem / n, i = rem % n;
         const int bc = seg_bound(c, N, P);
         a.lam[r * a.nvec + in.oVec + rem] = v[e];
-        a.z[r * a.kkt + in.oZ + (long long)bc * w + nu + n + i] = v[e];
+        const long long o = r * a.kkt + in.oZ + (long long)bc * w + nu + n + i;
+        if (a.zacc) a.zacc[o] += v[e]; else a.z[o] = v[e];
     }
 }
 

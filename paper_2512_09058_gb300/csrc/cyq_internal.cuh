@@ -23,6 +23,7 @@ struct Inst {
     long long oQ, oR, oS, oA, oB, oSig;  // offsets into the data arrays (doubles)
     long long oZ;                        // offset into b / z (doubles)
     long long oL, oLB, oF;               // offsets into the factor arrays (elements)
+    long long oDI;                       // offset into the reciprocal-diagonal array (N*(nx+nu) elements)
     long long oBlk;                      // offset of the P coupling blocks (nx*nx each)
     long long oVec;                      // offset of the P coupling vectors (nx each)
     long long oq, orv, oc, ox0;          // offsets of q ((N+1) nx), r (N nu), c (N nx), x_init (nx)
@@ -75,29 +76,79 @@ __device__ __forceinline__ void tri_index(int e, int &r, int &c) {
     c = e - rr * (rr + 1) / 2;
 }
 
-// sqrt and reciprocal used by the Cholesky pivots.
-__device__ __forceinline__ double pivot_sqrt(double d) { return sqrt(d); }
-__device__ __forceinline__ float pivot_sqrt(float d) { return sqrtf(d); }
+// Cholesky pivots.  An FP64 instruction costs the same whether one or all 32
+// lanes run it, and the library's double sqrt and division are sequences of
+// ~10 and ~7 FP64 operations, so the pivot d -> (sqrt(d), 1/sqrt(d)) is built
+// from a single-precision estimate and a short FP64 correction:
+//   y0 = rsqrtf(d) (d truncated to float with integer operations),
+//   e  = 1 - d y0^2,   y = y0 (1 + e/2 + 3e^2/8)
+// (the series of (1-e)^{-1/2}; |e| < 2^-20 leaves a truncation error below
+// 2^-60, so y is within ~1 ulp of 1/sqrt(d)), and sqrt(d) = d y.  Pivots
+// outside [2^-120, 2^120] use the library routines.
 __device__ __forceinline__ bool finite_pos(double d) { return d > 0.0 && d < 1.0 / 0.0; }
 __device__ __forceinline__ bool finite_pos(float d) { return d > 0.0f && d < 1.0f / 0.0f; }
+
+__device__ __forceinline__ void pivot(double d, double &l, double &il) {
+    const int hi = __double2hiint(d), lo = __double2loint(d);
+    const int ex = (hi >> 20) & 0x7ff;
+    if (ex > 1023 - 120 && ex < 1023 + 120) {
+        const int fbits = ((ex - 896) << 23) | ((hi & 0xfffff) << 3) | ((unsigned)lo >> 29);
+        const float r = rsqrtf(__int_as_float(fbits));
+        const int rb = __float_as_int(r);
+        const int rex = ((rb >> 23) & 0xff) + 896;
+        const double y0 = __hiloint2double((rex << 20) | ((rb & 0x7fffff) >> 3), (rb & 0x7) << 29);
+        const double t = d * y0;
+        const double e = fma(-t, y0, 1.0);
+        const double c = fma(e, 0.375, 0.5);
+        const double y = fma(y0, e * c, y0);
+        il = y;
+        l = d * y;
+    } else {
+        l = sqrt(d);
+        il = 1.0 / l;
+    }
+}
+__device__ __forceinline__ void pivot(float d, float &l, float &il) {
+    float y = rsqrtf(d);
+    y = y * fmaf(-0.5f * d * y, y, 1.5f);   // one Newton step
+    il = y;
+    l = d * y;
+}
+
+// Asynchronous global -> shared copies (8-byte elements, any alignment of doubles).
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <int TEAM>
+__device__ __forceinline__ void async_copy_f64(double *dst, const double *src, int count) {
+    for (int e = threadIdx.x; e < count; e += TEAM) cp_async8(dst + e, src + e);
+}
 
 // In-place lower Cholesky factor of the n x n matrix A (lower triangle read;
 // upper triangle set to zero).  Right-looking: per column a pivot, a scaled
 // column and a rank-1 update of the trailing lower triangle.  Every thread
-// computes the pivot redundantly (no extra barrier).  Returns false if a
-// pivot was not positive and finite (the factor then holds the first bad
-// pivot replaced by 1 so that the arithmetic stays finite).
+// computes the pivot (an FP64 instruction costs the same on one lane as on
+// all).  dinv[k] receives 1/L_kk when dinv is not null.  Returns false if a
+// pivot was not positive and finite (that pivot is replaced by 1 so that the
+// arithmetic stays finite).
 template <typename T, int TEAM>
-__device__ bool team_chol(T *A, int n, int ld) {
+__device__ bool team_chol(T *A, int n, int ld, T *dinv = nullptr) {
     const int tid = threadIdx.x;
     bool ok = true;
     for (int k = 0; k < n; ++k) {
         T d = A[k + k * ld];
         if (!finite_pos(d)) { ok = false; d = T(1); }
-        const T l = pivot_sqrt(d);
-        const T il = T(1) / l;
+        T l, il;
+        pivot(d, l, il);
         team_sync();   // everyone has read A[k,k]
-        if (tid == 0) A[k + k * ld] = l;
+        if (tid == 0) {
+            A[k + k * ld] = l;
+            if (dinv) dinv[k] = il;
+        }
         for (int i = k + 1 + tid; i < n; i += TEAM) A[i + k * ld] *= il;
         for (int i = tid; i < k; i += TEAM) A[i + k * ld] = T(0);   // upper part of column k
         team_sync();
@@ -108,7 +159,7 @@ __device__ bool team_chol(T *A, int n, int ld) {
             tri_index(e, r, c);
             r += k + 1;
             c += k + 1;
-            A[r + c * ld] -= A[r + k * ld] * A[c + k * ld];
+            A[r + c * ld] = fma(-A[r + k * ld], A[c + k * ld], A[r + c * ld]);
         }
         team_sync();
     }
@@ -116,14 +167,14 @@ __device__ bool team_chol(T *A, int n, int ld) {
 }
 
 // X (m x n, ldx) := X * L^{-T}, L lower n x n (ldl): row-wise forward substitution
-// (X L^T = Y).  One thread per row.
+// (X L^T = Y).  One thread per row.  dinv (optional) holds 1/L_jj.
 template <typename T, int TEAM>
-__device__ void team_trsm_rlt(T *X, int m, int n, int ldx, const T *L, int ldl) {
+__device__ void team_trsm_rlt(T *X, int m, int n, int ldx, const T *L, int ldl, const T *dinv = nullptr) {
     for (int r = threadIdx.x; r < m; r += TEAM) {
         for (int j = 0; j < n; ++j) {
             T s = X[r + j * ldx];
-            for (int t = 0; t < j; ++t) s -= X[r + t * ldx] * L[j + t * ldl];
-            X[r + j * ldx] = s / L[j + j * ldl];
+            for (int t = 0; t < j; ++t) s = fma(-X[r + t * ldx], L[j + t * ldl], s);
+            X[r + j * ldx] = dinv ? s * dinv[j] : s / L[j + j * ldl];
         }
     }
     team_sync();
@@ -131,13 +182,13 @@ __device__ void team_trsm_rlt(T *X, int m, int n, int ldx, const T *L, int ldl) 
 
 // Tinv (n x n, ldt) := L^{-1} for lower L (n x n, ldl); one thread per column.
 template <typename T, int TEAM>
-__device__ void team_trtri_lower(T *Tinv, int ldt, const T *L, int ldl, int n) {
+__device__ void team_trtri_lower(T *Tinv, int ldt, const T *L, int ldl, int n, const T *dinv = nullptr) {
     for (int c = threadIdx.x; c < n; c += TEAM) {
         for (int i = 0; i < c; ++i) Tinv[i + c * ldt] = T(0);
         for (int i = c; i < n; ++i) {
             T s = (i == c) ? T(1) : T(0);
-            for (int t = c; t < i; ++t) s -= L[i + t * ldl] * Tinv[t + c * ldt];
-            Tinv[i + c * ldt] = s / L[i + i * ldl];
+            for (int t = c; t < i; ++t) s = fma(-L[i + t * ldl], Tinv[t + c * ldt], s);
+            Tinv[i + c * ldt] = dinv ? s * dinv[i] : s / L[i + i * ldl];
         }
     }
     team_sync();
@@ -210,6 +261,7 @@ struct FactorArgs {
     int n_items;
     Data data;
     void *L, *LB, *F;               // factor arrays (float or double)
+    void *DI;                       // reciprocal diagonals of the stage factors
     double *Mf, *Mb, *Kc;           // Schur blocks (float64)
     double *U, *Y;                  // cyclic-reduction factor blocks (float64)
     int *status;
@@ -220,7 +272,7 @@ struct SolveArgs {
     const Item *items;
     int n_items;
     Data data;
-    const void *L, *LB, *F;
+    const void *L, *LB, *F, *DI;
     const double *Mf, *Kc, *U, *Y;  // coupling factor (Mf holds the CR Cholesky blocks)
     const double *b;                // right-hand sides (float64)
     double *z;                      // solutions (float64)
@@ -229,6 +281,7 @@ struct SolveArgs {
     double *dF, *dB, *lam;          // coupling vectors (float64), [rhs][P*nx]
     long long nvec;                 // coupling-vector elements per right-hand side
     const int *skip;                // optional per-instance flag: nonzero = leave this instance alone
+    double *zacc;                   // optional: add the solution into zacc (z then holds intermediates only)
 };
 
 cudaError_t launch_factor_segments(bool fp64, int team, size_t smem, const FactorArgs &a, cudaStream_t st);

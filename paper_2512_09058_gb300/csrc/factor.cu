@@ -14,64 +14,68 @@
 // The Schur blocks are written in float64 whatever the factor precision.
 // With a single segment the coupling block M = M_fwd + M_bwd is also
 // Cholesky-factored here (float64), which is the whole cyclic reduction.
+//
+// The raw blocks of the next stage (R, S, Q, Sigma, B, A) are copied into a
+// double-buffered shared-memory stage while the current stage is factored
+// (cp.async), and H^ = H + V V^T is assembled directly from that copy.
 #include "cyq_internal.cuh"
 
 namespace cyq {
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+// Raw stage record in shared memory (float64): R (nu x nu) | S (nu x nx) |
+// Q (nx x nx) | Sigma_u (nu) | Sigma_x (nx) | B (nx x nu) | A (nx x nx).
+// [B A] is contiguous and column-major with leading dimension nx.
+struct StageLayout {
+    int oR, oS, oQ, oSu, oSx, oB, oA, size;
+    __device__ StageLayout(int nx, int nu) {
+        oR = 0;
+        oS = oR + nu * nu;
+        oQ = oS + nu * nx;
+        oSu = oQ + nx * nx;
+        oSx = oSu + nu;
+        oB = oSx + nx;
+        oA = oB + nx * nu;
+        size = oA + nx * nx;
+        size = (size + 1) & ~1;
+    }
+};
 
-// Lower triangle of the stage Hessian [R S; S^T Q] (+ Sigma) of stage s.
-template <typename T, int TEAM>
-__device__ void load_stage_hessian(T *H, int ld, const Data &d, const Inst &in, int s) {
-    const int nx = in.nx, nu = in.nu, N = in.N;
-    const int xq = xstate(s, N);
-    const double *R = d.R + in.oR + (long long)s * nu * nu;
-    const double *Q = d.Q + in.oQ + (long long)xq * nx * nx;
-    for (int e = threadIdx.x; e < nu * nu; e += TEAM) {
-        const int i = e % nu, j = e / nu;
-        if (i >= j) H[i + j * ld] = (T)R[e];
-    }
-    for (int e = threadIdx.x; e < nx * nx; e += TEAM) {
-        const int i = e % nx, j = e / nx;
-        if (i >= j) H[(nu + i) + (nu + j) * ld] = (T)Q[e];
-    }
-    // S_s is nu x nx (element (j,i) at j + i*nu); its transpose fills rows nu.., cols 0..nu-1
-    if (s != 0 && d.S) {
-        const double *S = d.S + in.oS + (long long)s * nu * nx;
-        for (int e = threadIdx.x; e < nu * nx; e += TEAM) {
-            const int j = e % nu, i = e / nu;
-            H[(nu + i) + j * ld] = (T)S[e];
-        }
-    } else {
-        for (int e = threadIdx.x; e < nu * nx; e += TEAM) {
-            const int j = e % nu, i = e / nu;
-            H[(nu + i) + j * ld] = T(0);
-        }
-    }
+// Issue the asynchronous copy of stage s's raw blocks.
+template <int TEAM>
+__device__ void prefetch_stage(double *buf, const StageLayout &L, const Data &d, const Inst &in, int s) {
+    const int nx = in.nx, nu = in.nu, N = in.N, xq = xstate(s, N);
+    async_copy_f64<TEAM>(buf + L.oR, d.R + in.oR + (long long)s * nu * nu, nu * nu);
+    if (s != 0 && d.S) async_copy_f64<TEAM>(buf + L.oS, d.S + in.oS + (long long)s * nu * nx, nu * nx);
+    async_copy_f64<TEAM>(buf + L.oQ, d.Q + in.oQ + (long long)xq * nx * nx, nx * nx);
     if (d.Sig) {
-        const double *su = d.Sig + in.oSig + (long long)s * (nu + nx);
-        const double *sx = d.Sig + in.oSig + (long long)xq * (nu + nx) + nu;
-        team_sync();
-        for (int i = threadIdx.x; i < nu; i += TEAM) H[i + i * ld] += (T)su[i];
-        for (int i = threadIdx.x; i < nx; i += TEAM) H[(nu + i) + (nu + i) * ld] += (T)sx[i];
+        async_copy_f64<TEAM>(buf + L.oSu, d.Sig + in.oSig + (long long)s * (nu + nx), nu);
+        async_copy_f64<TEAM>(buf + L.oSx, d.Sig + in.oSig + (long long)xq * (nu + nx) + nu, nx);
     }
+    async_copy_f64<TEAM>(buf + L.oB, d.B + in.oB + (long long)s * nx * nu, nx * nu);
+    if (s != 0) async_copy_f64<TEAM>(buf + L.oA, d.A + in.oA + (long long)s * nx * nx, nx * nx);
+    cp_async_commit();
 }
 
-// [B_s A_s] (nx x (nu+nx), ld nx); A_0 is replaced by zero (x^0 is eliminated).
-template <typename T, int TEAM>
-__device__ void load_BA(T *BA, const Data &d, const Inst &in, int s) {
+// Zero the parts of a stage record that the copy does not fill (S_0, A_0, Sigma).
+template <int TEAM>
+__device__ void stage_zero_fill(double *buf, const StageLayout &L, const Data &d, const Inst &in, int s) {
     const int nx = in.nx, nu = in.nu;
-    const double *B = d.B + in.oB + (long long)s * nx * nu;
-    for (int e = threadIdx.x; e < nx * nu; e += TEAM) BA[e] = (T)B[e];
-    if (s != 0) {
-        const double *A = d.A + in.oA + (long long)s * nx * nx;
-        for (int e = threadIdx.x; e < nx * nx; e += TEAM) BA[nx * nu + e] = (T)A[e];
-    } else {
-        for (int e = threadIdx.x; e < nx * nx; e += TEAM) BA[nx * nu + e] = T(0);
-    }
+    if (s == 0 || !d.S)
+        for (int e = threadIdx.x; e < nu * nx; e += TEAM) buf[L.oS + e] = 0.0;
+    if (!d.Sig)
+        for (int e = threadIdx.x; e < nu + nx; e += TEAM) buf[L.oSu + e] = 0.0;
+    if (s == 0)
+        for (int e = threadIdx.x; e < nx * nx; e += TEAM) buf[L.oA + e] = 0.0;
+}
+
+// Element (a, b), a >= b, of the stage Hessian [R S; S^T Q] + diag(Sigma) from a raw record.
+__device__ __forceinline__ double stage_H(const double *buf, const StageLayout &L, int nu, int nx, int a, int b) {
+    if (a < nu) return buf[L.oR + a + b * nu] + (a == b ? buf[L.oSu + a] : 0.0);
+    if (b < nu) return buf[L.oS + b + (a - nu) * nu];
+    const int i = a - nu, j = b - nu;
+    return buf[L.oQ + i + j * nx] + (i == j ? buf[L.oSx + i] : 0.0);
 }
 
 template <typename T, int TEAM>
@@ -80,8 +84,8 @@ __device__ void store_block(T *dst, const T *src, int rows, int cols, int ld) {
 }
 
 template <typename T, int TEAM>
-__device__ void store_block_f64(double *dst, const T *src, int rows, int cols, int ld, double scale) {
-    for (int e = threadIdx.x; e < rows * cols; e += TEAM) dst[e] = scale * (double)src[(e % rows) + (e / rows) * ld];
+__device__ void store_block_f64(double *dst, const T *src, int rows, int cols, int ld) {
+    for (int e = threadIdx.x; e < rows * cols; e += TEAM) dst[e] = (double)src[(e % rows) + (e / rows) * ld];
 }
 
 }  // namespace
@@ -95,99 +99,140 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
         const int N = in.N, nx = in.nx, nu = in.nu, P = in.P, c = wi.seg;
         const int nux = nx + nu;
         const int len = seg_len(c, N, P);
+        const StageLayout SL(nx, nu);
+        const bool propagate = c >= 1;   // segment 0 never carries A^cl (A_0 = 0, S_0 = 0)
 
-        T *H = reinterpret_cast<T *>(smem_raw);    // nux x nux (stage Hessian -> factor)
-        T *BA = H + nux * nux;                     // nx x nux  ([B A] of the next stage)
-        T *G = BA + nx * nux;                      // nx x nux  ([B^ A^] -> [L^B A^cl])
-        T *G2 = G + nx * nux;                      // nx x nux  (next [B^ A^])
-        T *V = G2 + nx * nux;                      // nux x nx
-        size_t off = (size_t)(V + nux * nx - H) * sizeof(T);
-        off = (off + 15) / 16 * 16;
-        double *Mf = reinterpret_cast<double *>(smem_raw + off);   // nx x nx float64 accumulator
+        double *stage[2];
+        stage[0] = reinterpret_cast<double *>(smem_raw);
+        stage[1] = stage[0] + SL.size;
+        double *Mf = stage[1] + SL.size;                        // nx x nx float64 accumulator
+        T *H = reinterpret_cast<T *>(Mf + nx * nx);             // nux x nux (stage Hessian -> factor)
+        T *V = H + nux * nux;                                   // nux x nx
+        T *G = V + nux * nx;                                    // nx x nux  ([B^ A^] -> [L^B A^cl])
+        T *G2 = G + nx * nux;                                   // nx x nux  (next [B^ A^])
+        T *BAc = G2 + nx * nux;                                 // nx x nux  ([B A] in T, float only)
+        T *dinv = BAc + (sizeof(T) == 8 ? 0 : nx * nux);        // nux
 
         T *Lg = reinterpret_cast<T *>(a.L) + in.oL;
         T *LBg = reinterpret_cast<T *>(a.LB) + in.oLB;
         T *Fg = reinterpret_cast<T *>(a.F) + in.oF;
+        T *DIg = reinterpret_cast<T *>(a.DI) + in.oDI;
 
+        // first stage: raw copy, then H^ = H and [B^ A^] = [B A]
         int s = seg_stage(c, 0, N, P);
-        load_stage_hessian<T, TEAM>(H, nux, a.data, in, s);
-        load_BA<T, TEAM>(G, a.data, in, s);
+        prefetch_stage<TEAM>(stage[0], SL, a.data, in, s);
+        stage_zero_fill<TEAM>(stage[0], SL, a.data, in, s);
         for (int e = threadIdx.x; e < nx * nx; e += TEAM) Mf[e] = 0.0;
+        cp_async_wait_all();
+        team_sync();
+        {
+            const double *buf = stage[0];
+            const int cnt = nux * (nux + 1) / 2;
+            for (int e = threadIdx.x; e < cnt; e += TEAM) {
+                int r, q;
+                tri_index(e, r, q);
+                H[r + q * nux] = (T)stage_H(buf, SL, nu, nx, r, q);
+            }
+            for (int e = threadIdx.x; e < nx * nux; e += TEAM) G[e] = (T)buf[SL.oB + e];
+        }
         team_sync();
 
         bool ok = true;
         for (int t = 0; t < len; ++t) {
             s = seg_stage(c, t, N, P);
-            const bool hasG = (t == 0) || (c >= 1);
+            const bool hasG = (t == 0) || propagate;
             const bool last = (t == len - 1);
-            ok &= team_chol<T, TEAM>(H, nux, nux);
+            double *nbuf = stage[(t + 1) & 1];
+            int s2 = 0;
+            if (!last) {
+                s2 = seg_stage(c, t + 1, N, P);
+                prefetch_stage<TEAM>(nbuf, SL, a.data, in, s2);   // overlaps with the factorization below
+            }
+            ok &= team_chol<T, TEAM>(H, nux, nux, dinv);
             store_block<T, TEAM>(Lg + (long long)s * nux * nux, H, nux, nux, nux);
+            for (int i = threadIdx.x; i < nux; i += TEAM) DIg[(long long)s * nux + i] = dinv[i];
             if (hasG) {
                 // L^B = B^ L^{R-T}
-                team_trsm_rlt<T, TEAM>(G, nx, nu, nx, H, nux);
+                team_trsm_rlt<T, TEAM>(G, nx, nu, nx, H, nux, dinv);
                 // A^cl = A^ - L^B L^{S T}   (L^S = rows nu.. of columns 0..nu-1)
                 team_gemm_nt<T, TEAM>(G + nx * nu, nx, G, nx, H + nu, nux, nx, nx, nu, -1);
                 store_block<T, TEAM>(LBg + (long long)s * nx * nu, G, nx, nu, nx);
                 team_syrk_lower<T, double, TEAM>(Mf, nx, G, nx, nx, nu, +1);
-                if (c >= 1 && !last) store_block<T, TEAM>(Fg + (long long)s * nx * nx, G + nx * nu, nx, nx, nx);
+                if (propagate && !last) store_block<T, TEAM>(Fg + (long long)s * nx * nx, G + nx * nu, nx, nx, nx);
             }
             if (!last) {
-                const int s2 = seg_stage(c, t + 1, N, P);
-                load_BA<T, TEAM>(BA, a.data, in, s2);
+                stage_zero_fill<TEAM>(nbuf, SL, a.data, in, s2);
+                cp_async_wait_all();
                 team_sync();
+                const T *BA;
+                if (sizeof(T) == 8) {
+                    BA = reinterpret_cast<const T *>(nbuf + SL.oB);
+                } else {
+                    for (int e = threadIdx.x; e < nx * nux; e += TEAM) BAc[e] = (T)nbuf[SL.oB + e];
+                    team_sync();
+                    BA = BAc;
+                }
                 // V = [B A]^T L^Q : V[a][j] = sum_{k >= j} BA[k][a] L^Q[k][j]
                 const T *LQ = H + nu + nu * nux;
                 for (int e = threadIdx.x; e < nux * nx; e += TEAM) {
                     const int aa = e % nux, j = e / nux;
                     T acc = T(0);
-                    for (int k = j; k < nx; ++k) acc += BA[k + aa * nx] * LQ[k + j * nux];
+                    for (int k = j; k < nx; ++k) acc = fma(BA[k + aa * nx], LQ[k + j * nux], acc);
                     V[aa + j * nux] = acc;
                 }
-                if (c >= 1) {
+                if (propagate) {
                     // [B^ A^]_{s2} = A^cl [B A]_{s2}
                     team_gemm_nn<T, TEAM>(G2, nx, G + nx * nu, nx, BA, nx, nx, nux, nx, 0);
                 } else {
                     team_sync();
                 }
-                load_stage_hessian<T, TEAM>(H, nux, a.data, in, s2);
+                // H^_{s2} = H_{s2} + V V^T  (lower triangle, straight from the raw record)
+                const int cnt = nux * (nux + 1) / 2;
+                for (int e = threadIdx.x; e < cnt; e += TEAM) {
+                    int r, q;
+                    tri_index(e, r, q);
+                    T acc = (T)stage_H(nbuf, SL, nu, nx, r, q);
+                    for (int k = 0; k < nx; ++k) acc = fma(V[r + k * nux], V[q + k * nux], acc);
+                    H[r + q * nux] = acc;
+                }
                 team_sync();
-                team_syrk_lower<T, T, TEAM>(H, nux, V, nux, nux, nx, +1);
                 T *tmp = G; G = G2; G2 = tmp;
             } else {
                 const T *LQ = H + nu + nu * nux;
+                const T *dq = dinv + nu;
                 T *LA = G + nx * nu;
-                if (c >= 1) {
+                if (propagate) {
                     // L^A = A^cl L^{Q-T}, stored in place of A^cl of the first stage
-                    team_trsm_rlt<T, TEAM>(LA, nx, nx, nx, LQ, nux);
+                    team_trsm_rlt<T, TEAM>(LA, nx, nx, nx, LQ, nux, dq);
                     store_block<T, TEAM>(Fg + (long long)s * nx * nx, LA, nx, nx, nx);
                     team_syrk_lower<T, double, TEAM>(Mf, nx, LA, nx, nx, nx, +1);
                 }
                 // Tinv = L^{Q -1}
                 T *Ti = V;
-                team_trtri_lower<T, TEAM>(Ti, nx, LQ, nux, nx);
-                // M_bwd = Tinv^T Tinv  -> BA (full symmetric)
-                T *Mb = BA;
+                team_trtri_lower<T, TEAM>(Ti, nx, LQ, nux, nx, dq);
+                // M_bwd = Tinv^T Tinv  (full symmetric, in G2)
+                T *Mb = G2;
                 for (int e = threadIdx.x; e < nx * nx; e += TEAM) {
                     const int i = e % nx, j = e / nx;
                     const int k0 = i > j ? i : j;
                     T acc = T(0);
-                    for (int k = k0; k < nx; ++k) acc += Ti[k + i * nx] * Ti[k + j * nx];
+                    for (int k = k0; k < nx; ++k) acc = fma(Ti[k + i * nx], Ti[k + j * nx], acc);
                     Mb[e] = acc;
                 }
                 team_sync();
                 const int cb = (c - 1 + P) % P;
-                store_block_f64<T, TEAM>(a.Mb + in.oBlk + (long long)cb * nx * nx, Mb, nx, nx, nx, 1.0);
-                if (c >= 1) {
-                    // K = -L^A Tinv (row lambda^{b_c}, column lambda^{b_{c-1}})
-                    T *Kb = G2;
+                store_block_f64<T, TEAM>(a.Mb + in.oBlk + (long long)cb * nx * nx, Mb, nx, nx, nx);
+                if (propagate) {
+                    // K = -L^A Tinv (row lambda^{b_c}, column lambda^{b_{c-1}}), in H (free now)
+                    T *Kb = H;
                     for (int e = threadIdx.x; e < nx * nx; e += TEAM) {
                         const int i = e % nx, j = e / nx;
                         T acc = T(0);
-                        for (int k = j; k < nx; ++k) acc += LA[i + k * nx] * Ti[k + j * nx];
+                        for (int k = j; k < nx; ++k) acc = fma(LA[i + k * nx], Ti[k + j * nx], acc);
                         Kb[e] = -acc;
                     }
                     team_sync();
-                    store_block_f64<T, TEAM>(a.Kc + in.oBlk + (long long)c * nx * nx, Kb, nx, nx, nx, 1.0);
+                    store_block_f64<T, TEAM>(a.Kc + in.oBlk + (long long)c * nx * nx, Kb, nx, nx, nx);
                 }
                 team_symmetrize<double, TEAM>(Mf, nx, nx);
                 if (P == 1) {
@@ -207,10 +252,12 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
 
 size_t factor_smem_bytes(bool fp64, int nx, int nu) {
     const size_t nux = (size_t)nx + nu;
+    size_t stage = (size_t)nu * nu + (size_t)nu * nx + (size_t)nx * nx + nux + (size_t)nx * nu + (size_t)nx * nx;
+    stage = (stage + 1) & ~(size_t)1;
     const size_t el = fp64 ? 8 : 4;
-    size_t off = (nux * nux + 3 * nx * nux + nux * nx) * el;
-    off = (off + 15) / 16 * 16;
-    return off + (size_t)nx * nx * 8;
+    size_t bytes = (2 * stage + (size_t)nx * nx) * 8;
+    bytes += (nux * nux + nux * nx + 2 * nx * nux + (fp64 ? 0 : nx * nux) + nux) * el;
+    return (bytes + 15) / 16 * 16;
 }
 
 template <typename T, int TEAM>

@@ -35,7 +35,7 @@ std::mutex g_mu;
 double *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Workspace layout (in doubles, each region rounded up to 32 doubles):
-//   Inst record | Item record | instance index | status | L | LB | F | Mf | Mb | Kc | U | Y | dF | dB | lam
+//   Inst record | Item record | instance index | status | L | LB | F | DI | Mf | Mb | Kc | U | Y | dF | dB | lam
 inline long long round32(long long x) { return (x + 31) / 32 * 32; }
 
 long long required_doubles(int N, int nx, int nu) {
@@ -48,6 +48,7 @@ long long required_doubles(int N, int nx, int nu) {
     n += round32((long long)N * nux * nux);   // L
     n += round32((long long)N * nx * nu);     // LB
     n += round32((long long)N * nx * nx);     // F
+    n += round32((long long)N * nux);         // DI
     n += 5 * round32((long long)nx * nx);     // Mf, Mb, Kc, U, Y
     n += 3 * round32(nx);                     // dF, dB, lam
     return n;
@@ -108,6 +109,7 @@ extern "C" cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu
     double *L = p;   p += round32((long long)N * nux * nux);
     double *LB = p;  p += round32((long long)N * nx * nu);
     double *F = p;   p += round32((long long)N * nx * nx);
+    double *DI = p;  p += round32((long long)N * nux);
     double *Mf = p;  p += round32((long long)nx * nx);
     double *Mb = p;  p += round32((long long)nx * nx);
     double *Kc = p;  p += round32((long long)nx * nx);
@@ -135,7 +137,7 @@ extern "C" cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu
     fa.items = d_item;
     fa.n_items = 1;
     fa.data = Data{Q, R, S, A, B, Sigma};
-    fa.L = L; fa.LB = LB; fa.F = F;
+    fa.L = L; fa.LB = LB; fa.F = F; fa.DI = DI;
     fa.Mf = Mf; fa.Mb = Mb; fa.Kc = Kc; fa.U = U; fa.Y = Y;
     fa.status = d_status;
     if ((e = launch_factor_segments(true, team, fs, fa, st)) != cudaSuccess)
@@ -146,7 +148,7 @@ extern "C" cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu
     sa.items = d_item;
     sa.n_items = 1;
     sa.data = fa.data;
-    sa.L = L; sa.LB = LB; sa.F = F;
+    sa.L = L; sa.LB = LB; sa.F = F; sa.DI = DI;
     sa.Mf = Mf; sa.Kc = Kc; sa.U = U; sa.Y = Y;
     sa.b = b;
     sa.z = z;

@@ -40,11 +40,12 @@ __device__ void load_BA_T(T *BA, const Data &d, const Inst &in, int s) {
 
 struct SolveSmem {
     template <typename T>
-    __device__ static void carve(unsigned char *raw, int nx, int nu, int nrhs, T *&Ls, T *&BA, T *&Fs, T *&LB,
-                                 T *&hh, T *&rho, T *&pv, T *&tv, T *&wv, T *&gmu, T *&cv, T *&xv) {
+    __device__ static void carve(unsigned char *raw, int nx, int nu, int nrhs, T *&Ls, T *&Ds, T *&BA, T *&Fs,
+                                 T *&LB, T *&hh, T *&rho, T *&pv, T *&tv, T *&wv, T *&gmu, T *&cv, T *&xv) {
         const int nux = nx + nu;
         T *p = reinterpret_cast<T *>(raw);
         Ls = p; p += nux * nux;
+        Ds = p; p += nux;
         BA = p; p += nx * nux;
         Fs = p; p += nx * nx;
         LB = p; p += nx * nu;
@@ -63,8 +64,8 @@ struct SolveSmem {
 
 size_t solve_smem_bytes(bool fp64, int nx, int nu, int nrhs) {
     const size_t nux = (size_t)nx + nu;
-    const size_t cnt = nux * nux + nx * nux + (size_t)nx * nx + (size_t)nx * nu + nux * nrhs + (size_t)nu * nrhs +
-                       6 * (size_t)nx * nrhs;
+    const size_t cnt = nux * nux + nux + nx * nux + (size_t)nx * nx + (size_t)nx * nu + nux * nrhs +
+                       (size_t)nu * nrhs + 6 * (size_t)nx * nrhs;
     return cnt * (fp64 ? 8 : 4);
 }
 
@@ -78,8 +79,10 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
         const int N = in.N, nx = in.nx, nu = in.nu, P = in.P, c = wi.seg, nrhs = a.nrhs;
         const int nux = nx + nu, w = nu + 2 * nx;
         const int len = seg_len(c, N, P);
-        T *Ls, *BA, *Fs, *LB, *hh, *rho, *pv, *tv, *wv, *gmu, *cv, *xv;
-        SolveSmem::carve<T>(smem_raw, nx, nu, nrhs, Ls, BA, Fs, LB, hh, rho, pv, tv, wv, gmu, cv, xv);
+        T *Ls, *Ds, *BA, *Fs, *LB, *hh, *rho, *pv, *tv, *wv, *gmu, *cv, *xv;
+        SolveSmem::carve<T>(smem_raw, nx, nu, nrhs, Ls, Ds, BA, Fs, LB, hh, rho, pv, tv, wv, gmu, cv, xv);
+        const T *DIg = reinterpret_cast<const T *>(a.DI) + in.oDI;
+        const T *DQ = Ds + nu;
         const T *Lg = reinterpret_cast<const T *>(a.L) + in.oL;
         const T *LBg = reinterpret_cast<const T *>(a.LB) + in.oLB;
         const T *Fg = reinterpret_cast<const T *>(a.F) + in.oF;
@@ -102,6 +105,7 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
             const bool hasG = (t == 0) || (c >= 1);
             const bool last = (t == len - 1);
             load_T<T, TEAM>(Ls, Lg + (long long)s * nux * nux, nux * nux);
+            load_T<T, TEAM>(Ds, DIg + (long long)s * nux, nux);
             if (hasG) load_T<T, TEAM>(LB, LBg + (long long)s * nx * nu, nx * nu);
             if (c >= 1) load_T<T, TEAM>(Fs, Fg + (long long)s * nx * nx, nx * nx);
             team_sync();
@@ -111,8 +115,8 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
                 T *ro = rho + r * nu;
                 for (int i = 0; i < nu; ++i) {
                     T acc = hu[i];
-                    for (int k = 0; k < i; ++k) acc -= Ls[i + k * nux] * ro[k];
-                    ro[i] = acc / Ls[i + i * nux];
+                    for (int k = 0; k < i; ++k) acc = fma(-Ls[i + k * nux], ro[k], acc);
+                    ro[i] = acc * Ds[i];
                 }
             }
             team_sync();
@@ -188,13 +192,13 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
                     T *y = wv + r * nx, *db = tv + r * nx;
                     for (int i = 0; i < nx; ++i) {
                         T acc = pr[i];
-                        for (int k = 0; k < i; ++k) acc -= LQ[i + k * nux] * y[k];
-                        y[i] = acc / LQ[i + i * nux];
+                        for (int k = 0; k < i; ++k) acc = fma(-LQ[i + k * nux], y[k], acc);
+                        y[i] = acc * DQ[i];
                     }
                     for (int i = nx - 1; i >= 0; --i) {
                         T acc = y[i];
-                        for (int k = i + 1; k < nx; ++k) acc -= LQ[k + i * nux] * db[k];
-                        db[i] = acc / LQ[i + i * nux];
+                        for (int k = i + 1; k < nx; ++k) acc = fma(-LQ[k + i * nux], db[k], acc);
+                        db[i] = acc * DQ[i];
                     }
                 }
                 team_sync();
@@ -224,14 +228,17 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
         const int N = in.N, nx = in.nx, nu = in.nu, P = in.P, c = wi.seg, nrhs = a.nrhs;
         const int nux = nx + nu, w = nu + 2 * nx;
         const int len = seg_len(c, N, P);
-        T *Ls, *BA, *Fs, *LB, *hh, *rho, *pv, *tv, *wv, *gmu, *cv, *xv;
-        SolveSmem::carve<T>(smem_raw, nx, nu, nrhs, Ls, BA, Fs, LB, hh, rho, pv, tv, wv, gmu, cv, xv);
+        T *Ls, *Ds, *BA, *Fs, *LB, *hh, *rho, *pv, *tv, *wv, *gmu, *cv, *xv;
+        SolveSmem::carve<T>(smem_raw, nx, nu, nrhs, Ls, Ds, BA, Fs, LB, hh, rho, pv, tv, wv, gmu, cv, xv);
+        const T *DIg = reinterpret_cast<const T *>(a.DI) + in.oDI;
+        const T *DQ = Ds + nu;
         T *mu = gmu, *nuv = cv;   // coupling multipliers (reuse)
         const T *Lg = reinterpret_cast<const T *>(a.L) + in.oL;
         const T *LBg = reinterpret_cast<const T *>(a.LB) + in.oLB;
         const T *Fg = reinterpret_cast<const T *>(a.F) + in.oF;
         const double *b = a.b + in.oZ;
         double *z = a.z + in.oZ;
+        double *zacc = a.zacc ? a.zacc + in.oZ : nullptr;
         const T *LQ = Ls + nu + nu * nux;
 
         for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
@@ -245,6 +252,7 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
             const bool hasG = (t == 0) || (c >= 1);
             const bool first = (t == len - 1);
             load_T<T, TEAM>(Ls, Lg + (long long)s * nux * nux, nux * nux);
+            load_T<T, TEAM>(Ds, DIg + (long long)s * nux, nux);
             if (hasG) load_T<T, TEAM>(LB, LBg + (long long)s * nx * nu, nx * nu);
             if (c >= 1) load_T<T, TEAM>(Fs, Fg + (long long)s * nx * nx, nx * nx);
             for (int e = threadIdx.x; e < nu * nrhs; e += TEAM) {
@@ -263,8 +271,8 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
                     T *y = wv + r * nx, *x = xv + r * nx;
                     for (int i = 0; i < nx; ++i) {
                         T acc = pr[i] - nr[i];
-                        for (int k = 0; k < i; ++k) acc -= LQ[i + k * nux] * y[k];
-                        y[i] = acc / LQ[i + i * nux];
+                        for (int k = 0; k < i; ++k) acc = fma(-LQ[i + k * nux], y[k], acc);
+                        y[i] = acc * DQ[i];
                     }
                     if (c >= 1)
                         for (int j = 0; j < nx; ++j) {
@@ -274,8 +282,8 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
                         }
                     for (int i = nx - 1; i >= 0; --i) {
                         T acc = y[i];
-                        for (int k = i + 1; k < nx; ++k) acc -= LQ[k + i * nux] * x[k];
-                        x[i] = acc / LQ[i + i * nux];
+                        for (int k = i + 1; k < nx; ++k) acc = fma(-LQ[k + i * nux], x[k], acc);
+                        x[i] = acc * DQ[i];
                     }
                     for (int i = 0; i < nx; ++i) x[i] = -x[i];
                 }
@@ -307,8 +315,8 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
                 T *v = hh + r * nux, *u = rho + r * nu;
                 for (int i = nu - 1; i >= 0; --i) {
                     T acc = v[i];
-                    for (int k = i + 1; k < nu; ++k) acc -= Ls[k + i * nux] * u[k];
-                    u[i] = acc / Ls[i + i * nux];
+                    for (int k = i + 1; k < nu; ++k) acc = fma(-Ls[k + i * nux], u[k], acc);
+                    u[i] = acc * Ds[i];
                 }
                 for (int i = 0; i < nu; ++i) u[i] = -u[i];
             }
@@ -321,17 +329,20 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
                     for (int j = 0; j <= i; ++j) acc += LQ[i + j * nux] * wr[j];
                     if (c >= 1)
                         for (int k = 0; k < nx; ++k) acc += Fs[k + i * nx] * mr[k];
-                    z[r * a.kkt + (long long)sp * w + nu + nx + i] = (double)acc;
+                    const long long o = r * a.kkt + (long long)sp * w + nu + nx + i;
+                    if (zacc) zacc[o] += (double)acc; else z[o] = (double)acc;
                 }
             }
             team_sync();
             for (int e = threadIdx.x; e < nu * nrhs; e += TEAM) {
                 const int i = e % nu, r = e / nu;
-                z[r * a.kkt + (long long)s * w + i] = (double)rho[e];
+                const long long o = r * a.kkt + (long long)s * w + i;
+                if (zacc) zacc[o] += (double)rho[e]; else z[o] = (double)rho[e];
             }
             for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
                 const int i = e % nx, r = e / nx;
-                z[r * a.kkt + (long long)(xq - 1) * w + nu + i] = (double)xv[e];
+                const long long o = r * a.kkt + (long long)(xq - 1) * w + nu + i;
+                if (zacc) zacc[o] += (double)xv[e]; else z[o] = (double)xv[e];
             }
             if (t > 0) {
                 // x^{s+1} = A_s x + B_s u + c_s
