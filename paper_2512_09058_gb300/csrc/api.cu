@@ -22,11 +22,19 @@ thread_local std::string g_last_error;
 constexpr int kSMs = 152;
 
 struct Group {
+    int cls = 0;
     int team = 32;
-    size_t smem_factor = 0, smem_solve1 = 0;   // solve smem for one right-hand side
+    bool need_G2 = false;                      // some item propagates A^cl (P > 1)
+    bool staged[2] = {true, true};             // factor stages copied to shared memory, [float, double]
+    size_t smem_factor[2] = {0, 0};
     int max_nx = 0, max_nu = 0;
     std::vector<Item> items;
     Item *d_items = nullptr;
+};
+
+struct FactorSet {
+    void *L = nullptr, *LB = nullptr, *F = nullptr, *DI = nullptr;
+    bool fp64 = true;
 };
 
 struct DevicePtrs {
@@ -50,21 +58,25 @@ struct cyq_handle_s {
     int device = 0;
     int batch = 0;
     int precision = CYQ_FP64;
-    int max_nrhs = 1, it_max = 10;
+    int max_nrhs = 1, it_max = 10, esc_max = 3;
     double tol = 1e-10;
     std::vector<Inst> inst;
     std::vector<Group> groups;
     std::vector<int> cr_list;     // instances with P > 1
+    std::vector<CrJob> cr_jobs;
+    CrPlan cr_plan;
+    int cr_team = 128;
     std::vector<Chunk> chunks;
     long long kkt = 0, nL = 0, nLB = 0, nF = 0, nDI = 0, nblk = 0, nvec = 0;
-    size_t cr_smem = 0, crs_smem1 = 0;
+    size_t crs_smem1 = 0;
     int max_nx = 0;
     // device
     DevicePtrs mem;
     Inst *d_inst = nullptr;
     int *d_cr_list = nullptr, *d_all_list = nullptr;
     Chunk *d_chunks = nullptr;
-    void *L = nullptr, *LB = nullptr, *F = nullptr, *DI = nullptr;
+    FactorSet fac;                // factor in the handle's precision
+    FactorSet fac64;              // float64 factor for precision escalation (float32 mode only)
     double *Mf = nullptr, *Mb = nullptr, *Kc = nullptr, *U = nullptr, *Y = nullptr;
     double *dF = nullptr, *dB = nullptr, *lam = nullptr;
     int *status = nullptr;
@@ -107,6 +119,16 @@ int choose_team(int nx, int nu) {
     return 128;
 }
 
+// Size class of an instance: work items are launched per class so that the
+// shared-memory carve-out and the team size match the blocks they hold.
+int size_class(int nx, int nu) {
+    static const int bounds[] = {8, 16, 24, 32, 48, 64, 80, 96, 128, 160, 192, 256};
+    const int nux = nx + nu;
+    for (int i = 0; i < (int)(sizeof(bounds) / sizeof(bounds[0])); ++i)
+        if (nux <= bounds[i]) return i;
+    return 99;
+}
+
 // Segments per instance: enough (instance, segment) work items to occupy the
 // GPU when the batch is small, at least 8 stages per segment, a power of two.
 int auto_segments(int batch, int N) {
@@ -121,17 +143,17 @@ int auto_segments(int batch, int N) {
 
 cudaStream_t to_stream(cyq_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
-SolveArgs solve_args(cyq_handle h, const Group &g, const double *b, double *z, int nrhs, const int *skip,
-                     double *zacc = nullptr) {
+SolveArgs solve_args(cyq_handle h, const FactorSet &fs, const Group &g, const double *b, double *z, int nrhs,
+                     const int *skip, double *zacc = nullptr) {
     SolveArgs a{};
     a.inst = h->d_inst;
     a.items = g.d_items;
     a.n_items = (int)g.items.size();
     a.data = h->data;
-    a.L = h->L;
-    a.LB = h->LB;
-    a.F = h->F;
-    a.DI = h->DI;
+    a.L = fs.L;
+    a.LB = fs.LB;
+    a.F = fs.F;
+    a.DI = fs.DI;
     a.Mf = h->Mf;
     a.Kc = h->Kc;
     a.U = h->U;
@@ -149,29 +171,58 @@ SolveArgs solve_args(cyq_handle h, const Group &g, const double *b, double *z, i
     return a;
 }
 
-// One solve with the stored factor (float64 or float32 arithmetic).  With
+// One solve with a stored factor (float64 or float32 arithmetic).  With
 // zacc, the solution is added into zacc and z only holds sweep intermediates.
-cyq_status run_solve(cyq_handle h, const double *b, double *z, int nrhs, const int *skip, cudaStream_t st,
-                     double *zacc = nullptr) {
-    const bool fp64 = h->precision == CYQ_FP64;
+cyq_status run_solve(cyq_handle h, const FactorSet &fs, const double *b, double *z, int nrhs, const int *skip,
+                     cudaStream_t st, double *zacc = nullptr) {
     for (const Group &g : h->groups) {
-        SolveArgs a = solve_args(h, g, b, z, nrhs, skip, zacc);
-        size_t smem = solve_smem_bytes(fp64, g.max_nx, g.max_nu, nrhs);
-        CYQ_CUDA(launch_solve_backward(fp64, g.team, smem, a, st));
+        SolveArgs a = solve_args(h, fs, g, b, z, nrhs, skip, zacc);
+        size_t smem = solve_smem_bytes(fs.fp64, g.max_nx, g.max_nu, nrhs);
+        CYQ_CUDA(launch_solve_backward(fs.fp64, g.team, smem, a, st));
         ++h->launches;
     }
     {
-        SolveArgs a = solve_args(h, h->groups[0], b, z, nrhs, skip, zacc);
+        SolveArgs a = solve_args(h, fs, h->groups[0], b, z, nrhs, skip, zacc);
         size_t smem = ((size_t)h->crs_smem1) * (nrhs + 1);
         CYQ_CUDA(launch_cr_solve(h->batch, h->d_all_list, 128, smem, a, st));
         ++h->launches;
     }
     for (const Group &g : h->groups) {
-        SolveArgs a = solve_args(h, g, b, z, nrhs, skip, zacc);
-        size_t smem = solve_smem_bytes(fp64, g.max_nx, g.max_nu, nrhs);
-        CYQ_CUDA(launch_solve_forward(fp64, g.team, smem, a, st));
+        SolveArgs a = solve_args(h, fs, g, b, z, nrhs, skip, zacc);
+        size_t smem = solve_smem_bytes(fs.fp64, g.max_nx, g.max_nu, nrhs);
+        CYQ_CUDA(launch_solve_forward(fs.fp64, g.team, smem, a, st));
         ++h->launches;
     }
+    return CYQ_OK;
+}
+
+// Factor all instances (or those whose skip flag is zero) into a factor set,
+// including the cyclic reduction of the coupling blocks (always float64).
+cyq_status run_factor(cyq_handle h, const FactorSet &fs, const int *skip, cudaStream_t st) {
+    FactorArgs a{};
+    a.inst = h->d_inst;
+    a.data = h->data;
+    a.L = fs.L;
+    a.LB = fs.LB;
+    a.F = fs.F;
+    a.DI = fs.DI;
+    a.Mf = h->Mf;
+    a.Mb = h->Mb;
+    a.Kc = h->Kc;
+    a.U = h->U;
+    a.Y = h->Y;
+    a.status = h->status;
+    a.skip = skip;
+    const int pi = fs.fp64 ? 1 : 0;
+    for (const Group &g : h->groups) {
+        a.items = g.d_items;
+        a.n_items = (int)g.items.size();
+        a.stage_in_smem = g.staged[pi];
+        a.need_G2 = g.need_G2;
+        CYQ_CUDA(launch_factor_segments(fs.fp64, g.team, g.smem_factor[pi], a, st));
+        ++h->launches;
+    }
+    if (!h->cr_list.empty()) CYQ_CUDA(launch_cr_factor_levels(h->cr_plan, h->cr_team, h->max_nx, a, st, &h->launches));
     return CYQ_OK;
 }
 
@@ -203,16 +254,31 @@ cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, int nrhs,
     CYQ_CUDA(cudaMemsetAsync(h->steps, 0, sizeof(int) * B, st));
     CYQ_CUDA(cudaMemsetAsync(h->rr, 0, sizeof(double) * B * h->max_nrhs, st));
     CYQ_CUDA(cudaMemsetAsync(h->bb, 0, sizeof(double) * B * h->max_nrhs, st));
-    cyq_status s = run_solve(h, b, z, nrhs, nullptr, st);
+    cyq_status s = run_solve(h, h->fac, b, z, nrhs, nullptr, st);
     if (s != CYQ_OK) return s;
-    for (int it = 0; it <= h->it_max; ++it) {
+    int step = 0;
+    for (int it = 0; it <= h->it_max; ++it, ++step) {
         CYQ_CUDA(launch_residual(resid_args(h, b, z, h->r, h->done), nrhs, st));
-        CYQ_CUDA(launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, it, st));
+        CYQ_CUDA(launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, step, st));
         h->launches += 2;
         if (it == h->it_max) break;
         // correction: z += K~^{-1} r for the instances still above tol
-        s = run_solve(h, h->r, h->dz, nrhs, h->done, st, z);
+        s = run_solve(h, h->fac, h->r, h->dz, nrhs, h->done, st, z);
         if (s != CYQ_OK) return s;
+    }
+    if (!h->fac.fp64 && h->esc_max > 0) {
+        // precision escalation: instances the float32 factor could not bring to
+        // tol get a float64 factor, and the refinement continues with it
+        s = run_factor(h, h->fac64, h->done, st);
+        if (s != CYQ_OK) return s;
+        for (int it = 0; it < h->esc_max; ++it) {
+            ++step;
+            s = run_solve(h, h->fac64, h->r, h->dz, nrhs, h->done, st, z);
+            if (s != CYQ_OK) return s;
+            CYQ_CUDA(launch_residual(resid_args(h, b, z, h->r, h->done), nrhs, st));
+            CYQ_CUDA(launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, step, st));
+            h->launches += 2;
+        }
     }
     CYQ_CUDA(launch_mark_not_converged(B, h->done, h->status, st));
     ++h->launches;
@@ -294,16 +360,17 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         if (P > 1) h->cr_list.push_back(i);
         // work items and their team class
         const int team = choose_team(nx, nu);
-        const size_t fs = factor_smem_bytes(fp64, nx, nu);
-        if (fs > (size_t)smem_optin) { delete h; g_last_error = "stage blocks too large for shared memory"; return CYQ_ERR_INVALID_ARG; }
+        const int cls = size_class(nx, nu);
         Group *g = nullptr;
         for (Group &gg : h->groups)
-            if (gg.team == team) g = &gg;
+            if (gg.cls == cls) g = &gg;
         if (!g) {
             h->groups.emplace_back();
             g = &h->groups.back();
+            g->cls = cls;
             g->team = team;
         }
+        g->team = std::max(g->team, team);
         g->max_nx = std::max(g->max_nx, nx);
         g->max_nu = std::max(g->max_nu, nu);
         for (int c = 0; c < P; ++c) g->items.push_back(Item{i, c});
@@ -313,18 +380,63 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         h->max_nx = std::max(h->max_nx, nx);
         h->crs_smem1 = std::max(h->crs_smem1, (size_t)P * nx * sizeof(double));
     }
+    // longest items first inside a class (work ~ segment length x (nx+nu)^3)
     for (Group &g : h->groups) {
-        g.smem_factor = factor_smem_bytes(fp64, g.max_nx, g.max_nu);
-        g.smem_solve1 = solve_smem_bytes(fp64, g.max_nx, g.max_nu, 1);
-        if (g.smem_factor > (size_t)smem_optin ||
-            solve_smem_bytes(fp64, g.max_nx, g.max_nu, h->max_nrhs) > (size_t)smem_optin) {
-            delete h;
-            g_last_error = "stage blocks too large for shared memory";
-            return CYQ_ERR_INVALID_ARG;
+        auto cost = [&](const Item &it) {
+            const Inst &in = h->inst[it.inst];
+            const double nux = in.nx + in.nu;
+            return (double)seg_len(it.seg, in.N, in.P) * nux * nux * nux;
+        };
+        std::stable_sort(g.items.begin(), g.items.end(),
+                         [&](const Item &x, const Item &y) { return cost(x) > cost(y); });
+    }
+    for (Group &g : h->groups) {
+        for (const Item &it : g.items) g.need_G2 |= it.seg >= 1;
+        for (int pi = 0; pi < 2; ++pi) {
+            const bool f64 = pi == 1;
+            if (!f64 && fp64) continue;   // float32 plans only in float32 mode
+            // stage the raw blocks in shared memory while two CTAs still fit on an SM
+            g.staged[pi] = factor_smem_bytes(f64, g.max_nx, g.max_nu, true, g.need_G2) <= (size_t)smem_optin / 2;
+            g.smem_factor[pi] = factor_smem_bytes(f64, g.max_nx, g.max_nu, g.staged[pi], g.need_G2);
+            if (g.smem_factor[pi] > (size_t)smem_optin ||
+                solve_smem_bytes(f64, g.max_nx, g.max_nu, h->max_nrhs) > (size_t)smem_optin) {
+                delete h;
+                g_last_error = "stage blocks too large for shared memory";
+                return CYQ_ERR_INVALID_ARG;
+            }
         }
     }
     if (h->crs_smem1 * (h->max_nrhs + 1) > (size_t)smem_optin) { delete h; return CYQ_ERR_INVALID_ARG; }
-    h->cr_smem = cr_smem_bytes(h->max_nx);
+    // level-parallel cyclic-reduction jobs
+    {
+        int maxP = 1;
+        for (int i : h->cr_list) maxP = std::max(maxP, h->inst[i].P);
+        int levels = 0;
+        while ((1 << levels) < maxP) ++levels;
+        CrPlan &cp = h->cr_plan;
+        cp.levels = levels;
+        for (int l = 0; l < levels; ++l) {
+            const int st = 1 << l;
+            cp.elim_off[l] = (int)h->cr_jobs.size();
+            for (int i : h->cr_list)
+                for (int k = st; k < h->inst[i].P; k += 2 * st) h->cr_jobs.push_back(CrJob{i, k});
+        }
+        cp.elim_off[levels] = (int)h->cr_jobs.size();
+        for (int l = 0; l < levels; ++l) {
+            const int st = 1 << l;
+            cp.upd_off[l] = (int)h->cr_jobs.size();
+            for (int i : h->cr_list)
+                for (int k = 0; k < h->inst[i].P; k += 2 * st) h->cr_jobs.push_back(CrJob{i, k});
+        }
+        cp.upd_off[levels] = (int)h->cr_jobs.size();
+        cp.n_inst = (int)h->cr_list.size();
+        h->cr_team = h->max_nx <= 8 ? 32 : 128;
+        if ((size_t)4 * h->max_nx * h->max_nx * 8 > (size_t)smem_optin) {
+            delete h;
+            g_last_error = "state dimension too large for the coupling blocks";
+            return CYQ_ERR_INVALID_ARG;
+        }
+    }
     h->kkt = oZ; h->nL = oL; h->nLB = oLB; h->nF = oF; h->nDI = oDI; h->nblk = oBlk; h->nvec = oVec;
 
     auto fail = [&](cudaError_t e, const char *what) {
@@ -341,15 +453,22 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     ALLOC(h->d_inst, h->inst.size());
     ALLOC(h->d_chunks, h->chunks.size());
     ALLOC(h->d_cr_list, h->cr_list.size());
+    {
+        CrJob *pj;
+        ALLOC(pj, h->cr_jobs.size());
+        h->cr_plan.jobs = pj;
+    }
     ALLOC(h->d_all_list, (size_t)h->batch);
     for (Group &g : h->groups) ALLOC(g.d_items, g.items.size());
-    const size_t el = fp64 ? sizeof(double) : sizeof(float);
-    {
+    for (int pass = 0; pass < (fp64 ? 1 : 2); ++pass) {
+        FactorSet &fs = pass == 0 ? h->fac : h->fac64;
+        fs.fp64 = pass == 1 || fp64;
+        const size_t el = fs.fp64 ? sizeof(double) : sizeof(float);
         char *p;
-        ALLOC(p, (size_t)oL * el); h->L = p;
-        ALLOC(p, (size_t)oLB * el); h->LB = p;
-        ALLOC(p, (size_t)oF * el); h->F = p;
-        ALLOC(p, (size_t)oDI * el); h->DI = p;
+        ALLOC(p, (size_t)oL * el); fs.L = p;
+        ALLOC(p, (size_t)oLB * el); fs.LB = p;
+        ALLOC(p, (size_t)oF * el); fs.F = p;
+        ALLOC(p, (size_t)oDI * el); fs.DI = p;
     }
     ALLOC(h->Mf, (size_t)oBlk);
     ALLOC(h->Mb, (size_t)oBlk);
@@ -381,8 +500,11 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         (e = cudaMemset(h->steps, 0, sizeof(int) * h->batch)))
         return fail(e, "cudaMemcpy");
     if (!h->cr_list.empty() &&
-        (e = cudaMemcpy(h->d_cr_list, h->cr_list.data(), sizeof(int) * h->cr_list.size(), cudaMemcpyHostToDevice)))
+        ((e = cudaMemcpy(h->d_cr_list, h->cr_list.data(), sizeof(int) * h->cr_list.size(), cudaMemcpyHostToDevice)) ||
+         (e = cudaMemcpy((void *)h->cr_plan.jobs, h->cr_jobs.data(), sizeof(CrJob) * h->cr_jobs.size(),
+                         cudaMemcpyHostToDevice))))
         return fail(e, "cudaMemcpy");
+    h->cr_plan.inst_list = h->d_cr_list;
     for (Group &g : h->groups)
         if ((e = cudaMemcpy(g.d_items, g.items.data(), sizeof(Item) * g.items.size(), cudaMemcpyHostToDevice)))
             return fail(e, "cudaMemcpy");
@@ -415,31 +537,9 @@ cyq_status cyq_factor(cyq_handle h, const double *Q, const double *R, const doub
     cudaStream_t st = to_stream(stream);
     h->launches = 0;
     h->data = Data{Q, R, S, A, B, Sigma};
-    const bool fp64 = h->precision == CYQ_FP64;
     CYQ_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int) * h->batch, st));
-    FactorArgs a{};
-    a.inst = h->d_inst;
-    a.data = h->data;
-    a.L = h->L;
-    a.LB = h->LB;
-    a.F = h->F;
-    a.DI = h->DI;
-    a.Mf = h->Mf;
-    a.Mb = h->Mb;
-    a.Kc = h->Kc;
-    a.U = h->U;
-    a.Y = h->Y;
-    a.status = h->status;
-    for (const Group &g : h->groups) {
-        a.items = g.d_items;
-        a.n_items = (int)g.items.size();
-        CYQ_CUDA(launch_factor_segments(fp64, g.team, g.smem_factor, a, st));
-        ++h->launches;
-    }
-    if (!h->cr_list.empty()) {
-        CYQ_CUDA(launch_cr_factor((int)h->cr_list.size(), h->d_cr_list, 128, h->cr_smem, a, st));
-        ++h->launches;
-    }
+    cyq_status s = run_factor(h, h->fac, nullptr, st);
+    if (s != CYQ_OK) return s;
     h->factored = true;
     return CYQ_OK;
 }
@@ -452,7 +552,7 @@ cyq_status cyq_solve(cyq_handle h, const double *b, double *z, int32_t nrhs, cyq
     h->launches = 0;
     if (h->it_max == 0) {
         h->last_nrhs = 0;
-        return run_solve(h, b, z, nrhs, nullptr, st);
+        return run_solve(h, h->fac, b, z, nrhs, nullptr, st);
     }
     return run_refined_solve(h, b, z, nrhs, st);
 }

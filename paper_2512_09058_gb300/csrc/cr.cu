@@ -34,84 +34,158 @@ __device__ void store_blk(double *dst, const double *src, int n) {
 
 }  // namespace
 
-// One CTA per instance: all levels in sequence (blocks in global memory,
-// working copies in shared memory).
-template <int TEAM>
-__global__ void __launch_bounds__(TEAM) k_cr_factor(FactorArgs a, const int *inst_list) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int ii = inst_list[blockIdx.x];
+// ---------------------------------------------------------------------------
+// Level-parallel factorization: one launch per phase of each level, one CTA
+// per block, so the O(P) eliminations of a level run on all SMs at once.
+// ---------------------------------------------------------------------------
+
+// M_c <- M_fwd,c + M_bwd,c for every block of every listed instance.
+__global__ void k_cr_assemble(FactorArgs a, const int *inst_list, int n_inst) {
+    const int ii = inst_list[blockIdx.y];
+    if (a.skip && a.skip[ii]) return;
     const Inst in = a.inst[ii];
-    const int P = in.P, n = in.nx;
+    const long long total = (long long)in.P * in.nx * in.nx;
+    double *M = a.Mf + in.oBlk;
+    const double *Mb = a.Mb + in.oBlk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        M[e] += Mb[e];
+}
+
+// Eliminate block k at stride s:  L_k = chol(M_k),  U_k = K_k^T L_k^{-T},  Y_k = K_{k+s} L_k^{-T}.
+template <int TEAM>
+__global__ void __launch_bounds__(TEAM) k_cr_eliminate(FactorArgs a, const CrJob *jobs, int s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CrJob job = jobs[blockIdx.x];
+    if (a.skip && a.skip[job.inst]) return;
+    const Inst in = a.inst[job.inst];
+    const int P = in.P, n = in.nx, k = job.k;
     const long long nn = (long long)n * n;
-    double *M = a.Mf + in.oBlk, *Mb = a.Mb + in.oBlk, *K = a.Kc + in.oBlk;
-    double *U = a.U + in.oBlk, *Y = a.Y + in.oBlk;
-    double *W0 = reinterpret_cast<double *>(smem_raw);  // n x n
-    double *W1 = W0 + nn;                               // n x n
-    double *W2 = W1 + nn;                               // n x n
-    bool ok = true;
-
-    for (long long e = threadIdx.x; e < P * nn; e += TEAM) M[e] += Mb[e];
-    __threadfence_block();
+    double *M = a.Mf + in.oBlk, *K = a.Kc + in.oBlk, *U = a.U + in.oBlk, *Y = a.Y + in.oBlk;
+    double *W0 = reinterpret_cast<double *>(smem_raw), *W1 = W0 + nn, *W2 = W1 + nn, *dinv = W2 + nn;
+    load_blk<TEAM>(W0, M + k * nn, n, false);
+    load_blk<TEAM>(W1, K + k * nn, n, true);
+    const bool hasY = k + s < P;
+    if (hasY) load_blk<TEAM>(W2, K + (k + s) * nn, n, false);
     team_sync();
-
-    for (int s = 1; s < P; s *= 2) {
-        for (int k = s; k < P; k += 2 * s) {
-            load_blk<TEAM>(W0, M + k * nn, n, false);
-            team_sync();
-            ok &= team_chol<double, TEAM>(W0, n, n);
-            store_blk<TEAM>(M + k * nn, W0, n);
-            // U_k = K_k^T L_k^{-T}
-            load_blk<TEAM>(W1, K + k * nn, n, true);
-            team_sync();
-            team_trsm_rlt<double, TEAM>(W1, n, n, n, W0, n);
-            store_blk<TEAM>(U + k * nn, W1, n);
-            // Y_k = K_{k+s} L_k^{-T}
-            if (k + s < P) {
-                load_blk<TEAM>(W2, K + (k + s) * nn, n, false);
-                team_sync();
-                team_trsm_rlt<double, TEAM>(W2, n, n, n, W0, n);
-                store_blk<TEAM>(Y + k * nn, W2, n);
-            }
-            __threadfence_block();
-            team_sync();
-        }
-        for (int i = 0; i < P; i += 2 * s) {
-            load_blk<TEAM>(W0, M + i * nn, n, false);
-            team_sync();
-            if (i - s >= 0) {
-                load_blk<TEAM>(W1, Y + (i - s) * nn, n, false);
-                team_sync();
-                team_syrk_lower<double, double, TEAM>(W0, n, W1, n, n, n, -1);
-                if (i - 2 * s >= 0) {
-                    load_blk<TEAM>(W2, U + (i - s) * nn, n, false);
-                    team_sync();
-                    // K_i <- -Y_{i-s} U_{i-s}^T
-                    double *Kn = K + i * nn;
-                    for (int e = threadIdx.x; e < n * n; e += TEAM) {
-                        const int r = e % n, c = e / n;
-                        double acc = 0.0;
-                        for (int t = 0; t < n; ++t) acc += W1[r + t * n] * W2[c + t * n];
-                        Kn[e] = -acc;
-                    }
-                    team_sync();
-                }
-            }
-            if (i + s < P) {
-                load_blk<TEAM>(W1, U + (i + s) * nn, n, false);
-                team_sync();
-                team_syrk_lower<double, double, TEAM>(W0, n, W1, n, n, n, -1);
-            }
-            team_symmetrize<double, TEAM>(W0, n, n);
-            store_blk<TEAM>(M + i * nn, W0, n);
-            __threadfence_block();
-            team_sync();
+    const bool ok = team_chol<double, TEAM>(W0, n, n, dinv);
+    store_blk<TEAM>(M + k * nn, W0, n);
+    // both triangular solves in one pass: rows of U then rows of Y
+    const int rows = hasY ? 2 * n : n;
+    for (int r = threadIdx.x; r < rows; r += TEAM) {
+        double *X = r < n ? W1 : W2;
+        const int rr = r < n ? r : r - n;
+        for (int j = 0; j < n; ++j) {
+            double acc = X[rr + j * n];
+            for (int t = 0; t < j; ++t) acc = fma(-X[rr + t * n], W0[j + t * n], acc);
+            X[rr + j * n] = acc * dinv[j];
         }
     }
+    team_sync();
+    store_blk<TEAM>(U + k * nn, W1, n);
+    if (hasY) store_blk<TEAM>(Y + k * nn, W2, n);
+    if (!ok && threadIdx.x == 0) atomicCAS(a.status + job.inst, 0, ST_NOT_PD);
+}
+
+// Update block i at stride s:  M_i -= Y_{i-s} Y_{i-s}^T + U_{i+s} U_{i+s}^T,
+// K_i <- -Y_{i-s} U_{i-s}^T (the fill coupling i and i-2s).
+template <int TEAM>
+__global__ void __launch_bounds__(TEAM) k_cr_update(FactorArgs a, const CrJob *jobs, int s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CrJob job = jobs[blockIdx.x];
+    if (a.skip && a.skip[job.inst]) return;
+    const Inst in = a.inst[job.inst];
+    const int P = in.P, n = in.nx, i = job.k;
+    const long long nn = (long long)n * n;
+    double *M = a.Mf + in.oBlk, *K = a.Kc + in.oBlk;
+    const double *U = a.U + in.oBlk, *Y = a.Y + in.oBlk;
+    double *W0 = reinterpret_cast<double *>(smem_raw), *W1 = W0 + nn, *W2 = W1 + nn, *W3 = W2 + nn;
+    const bool lo = i - s >= 0, hi = i + s < P, fill = i - 2 * s >= 0;
+    if (lo) load_blk<TEAM>(W1, Y + (i - s) * nn, n, false);
+    if (hi) load_blk<TEAM>(W2, U + (i + s) * nn, n, false);
+    if (fill) load_blk<TEAM>(W3, U + (i - s) * nn, n, false);
+    team_sync();
+    // lower triangle of M_i minus the two symmetric products, straight from global
+    const int cnt = n * (n + 1) / 2;
+    double *Mi = M + i * nn;
+    for (int e = threadIdx.x; e < cnt; e += TEAM) {
+        int r, c;
+        tri_index(e, r, c);
+        double acc = Mi[r + c * n];
+        if (lo)
+            for (int t = 0; t < n; ++t) acc = fma(-W1[r + t * n], W1[c + t * n], acc);
+        if (hi)
+            for (int t = 0; t < n; ++t) acc = fma(-W2[r + t * n], W2[c + t * n], acc);
+        W0[r + c * n] = acc;
+    }
+    if (fill) {
+        double *Ki = K + i * nn;
+        for (int e = threadIdx.x; e < n * n; e += TEAM) {
+            const int r = e % n, c = e / n;
+            double acc = 0.0;
+            for (int t = 0; t < n; ++t) acc = fma(W1[r + t * n], W3[c + t * n], acc);
+            Ki[e] = -acc;
+        }
+    }
+    team_sync();
+    for (int e = threadIdx.x; e < n * n; e += TEAM) {
+        const int r = e % n, c = e / n;
+        Mi[e] = r >= c ? W0[r + c * n] : W0[c + r * n];
+    }
+}
+
+// Last block of every instance: L_0 = chol(M_0).
+template <int TEAM>
+__global__ void __launch_bounds__(TEAM) k_cr_base(FactorArgs a, const int *inst_list) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ii = inst_list[blockIdx.x];
+    if (a.skip && a.skip[ii]) return;
+    const Inst in = a.inst[ii];
+    const int n = in.nx;
+    double *M = a.Mf + in.oBlk;
+    double *W0 = reinterpret_cast<double *>(smem_raw);
     load_blk<TEAM>(W0, M, n, false);
     team_sync();
-    ok &= team_chol<double, TEAM>(W0, n, n);
+    const bool ok = team_chol<double, TEAM>(W0, n, n);
     store_blk<TEAM>(M, W0, n);
     if (!ok && threadIdx.x == 0) atomicCAS(a.status + ii, 0, ST_NOT_PD);
+}
+
+cudaError_t launch_cr_factor_levels(const CrPlan &plan, int team, int nmax, const FactorArgs &a, cudaStream_t st,
+                                    long long *launches) {
+    if (plan.n_inst == 0) return cudaSuccess;
+    cudaError_t e;
+    const size_t nn = (size_t)nmax * nmax * sizeof(double);
+    {
+        dim3 grid(64, plan.n_inst);
+        k_cr_assemble<<<grid, 256, 0, st>>>(a, plan.inst_list, plan.n_inst);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++*launches;
+    }
+    auto elim = team == 32 ? k_cr_eliminate<32> : k_cr_eliminate<128>;
+    auto upd = team == 32 ? k_cr_update<32> : k_cr_update<128>;
+    auto base = team == 32 ? k_cr_base<32> : k_cr_base<128>;
+    const size_t se = 3 * nn + nmax * sizeof(double), su = 4 * nn;
+    if ((e = cudaFuncSetAttribute(elim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(upd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)su)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(base, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn)) != cudaSuccess) return e;
+    for (int l = 0; l < plan.levels; ++l) {
+        const int s = 1 << l;
+        const int ne = plan.elim_off[l + 1] - plan.elim_off[l], nu_ = plan.upd_off[l + 1] - plan.upd_off[l];
+        if (ne > 0) {
+            elim<<<ne, team, se, st>>>(a, plan.jobs + plan.elim_off[l], s);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            ++*launches;
+        }
+        if (nu_ > 0) {
+            upd<<<nu_, team, su, st>>>(a, plan.jobs + plan.upd_off[l], s);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            ++*launches;
+        }
+    }
+    base<<<plan.n_inst, team, nn, st>>>(a, plan.inst_list);
+    ++*launches;
+    return cudaGetLastError();
 }
 
 // Coupling right-hand side and cyclic-reduction solve, one CTA per instance:
@@ -234,24 +308,6 @@ __global__ void __launch_bounds__(TEAM) k_cr_solve(SolveArgs a, const int *inst_
         const long long o = r * a.kkt + in.oZ + (long long)bc * w + nu + n + i;
         if (a.zacc) a.zacc[o] += v[e]; else a.z[o] = v[e];
     }
-}
-
-size_t cr_smem_bytes(int nx) { return (size_t)3 * nx * nx * 8; }
-
-cudaError_t launch_cr_factor(int n_inst_cr, const int *inst_list, int team, size_t smem, const FactorArgs &a,
-                             cudaStream_t st) {
-    if (n_inst_cr == 0) return cudaSuccess;
-    cudaError_t e;
-    if (team == 32) {
-        e = cudaFuncSetAttribute(k_cr_factor<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_cr_factor<32><<<n_inst_cr, 32, smem, st>>>(a, inst_list);
-    } else {
-        e = cudaFuncSetAttribute(k_cr_factor<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_cr_factor<128><<<n_inst_cr, 128, smem, st>>>(a, inst_list);
-    }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_cr_solve(int n_inst_cr, const int *inst_list, int team, size_t smem, const SolveArgs &a,

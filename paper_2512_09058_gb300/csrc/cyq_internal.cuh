@@ -265,6 +265,9 @@ struct FactorArgs {
     double *Mf, *Mb, *Kc;           // Schur blocks (float64)
     double *U, *Y;                  // cyclic-reduction factor blocks (float64)
     int *status;
+    bool stage_in_smem;             // copy each stage's raw blocks to shared memory (cp.async)
+    bool need_G2;                   // some item propagates A^cl (P > 1): second [B^ A^] buffer
+    const int *skip;                // optional per-instance flag: nonzero = do not factor this instance
 };
 
 struct SolveArgs {
@@ -284,9 +287,24 @@ struct SolveArgs {
     double *zacc;                   // optional: add the solution into zacc (z then holds intermediates only)
 };
 
+// Level-parallel cyclic reduction plan: jobs (instance, block).  The
+// eliminations of level l are jobs[elim_off[l] .. elim_off[l+1]) and its
+// updates jobs[upd_off[l] .. upd_off[l+1]); all eliminations come first in
+// the array, then all updates.
+struct CrJob {
+    int inst, k;
+};
+struct CrPlan {
+    int n_inst = 0;                 // instances with P > 1
+    const int *inst_list = nullptr; // device
+    const CrJob *jobs = nullptr;    // device
+    int levels = 0;
+    int elim_off[33] = {0}, upd_off[33] = {0};
+};
+
 cudaError_t launch_factor_segments(bool fp64, int team, size_t smem, const FactorArgs &a, cudaStream_t st);
-cudaError_t launch_cr_factor(int n_inst_cr, const int *inst_list, int team, size_t smem, const FactorArgs &a,
-                             cudaStream_t st);
+cudaError_t launch_cr_factor_levels(const CrPlan &plan, int team, int nmax, const FactorArgs &a, cudaStream_t st,
+                                    long long *launches);
 cudaError_t launch_solve_backward(bool fp64, int team, size_t smem, const SolveArgs &a, cudaStream_t st);
 cudaError_t launch_cr_solve(int n_inst_cr, const int *inst_list, int team, size_t smem, const SolveArgs &a,
                             cudaStream_t st);
@@ -326,12 +344,12 @@ cudaError_t launch_build_rhs(const Inst *inst, int batch, const Data &d, const d
                              const double *c, const double *x0, double *b, long long kkt, cudaStream_t st);
 cudaError_t launch_adjoint(const GradArgs &g, int n_chunks, int batch, const Data &d, double *dx0, cudaStream_t st);
 
-size_t factor_smem_bytes(bool fp64, int nx, int nu);
+size_t factor_smem_bytes(bool fp64, int nx, int nu, bool staged, bool need_G2);
+size_t factor_stage_bytes(int nx, int nu);
 
 // Sets the text returned by cyq_last_error() for the calling thread.
 void set_last_error_message(const char *msg);
 inline void set_last_error_message(const std::string &msg) { set_last_error_message(msg.c_str()); }
-size_t cr_smem_bytes(int nx);
 size_t solve_smem_bytes(bool fp64, int nx, int nu, int nrhs);
 
 }  // namespace cyq

@@ -15,9 +15,11 @@
 // With a single segment the coupling block M = M_fwd + M_bwd is also
 // Cholesky-factored here (float64), which is the whole cyclic reduction.
 //
-// The raw blocks of the next stage (R, S, Q, Sigma, B, A) are copied into a
-// double-buffered shared-memory stage while the current stage is factored
-// (cp.async), and H^ = H + V V^T is assembled directly from that copy.
+// When they fit, the raw blocks of the next stage (R, S, Q, Sigma, B, A) are
+// copied into shared memory (cp.async) while the current stage is factored;
+// the current stage's copy is consumed by the end of the previous step, so
+// one buffer suffices.  H^ = H + V V^T is assembled directly from that copy,
+// or from global memory for blocks too large to stage.
 #include "cyq_internal.cuh"
 
 namespace cyq {
@@ -70,12 +72,43 @@ __device__ void stage_zero_fill(double *buf, const StageLayout &L, const Data &d
         for (int e = threadIdx.x; e < nx * nx; e += TEAM) buf[L.oA + e] = 0.0;
 }
 
-// Element (a, b), a >= b, of the stage Hessian [R S; S^T Q] + diag(Sigma) from a raw record.
-__device__ __forceinline__ double stage_H(const double *buf, const StageLayout &L, int nu, int nx, int a, int b) {
-    if (a < nu) return buf[L.oR + a + b * nu] + (a == b ? buf[L.oSu + a] : 0.0);
-    if (b < nu) return buf[L.oS + b + (a - nu) * nu];
+// Where the blocks of one stage are read from: the shared-memory copy, or
+// global memory directly when the copy would not fit.  Null S / A / Sigma
+// pointers stand for zero blocks (S_0, A_0, no regularisation).
+struct StageSrc {
+    const double *R, *S, *Q, *Su, *Sx, *B, *A;
+};
+
+__device__ __forceinline__ StageSrc stage_src_smem(const double *buf, const StageLayout &L) {
+    return StageSrc{buf + L.oR, buf + L.oS, buf + L.oQ, buf + L.oSu, buf + L.oSx, buf + L.oB, buf + L.oA};
+}
+
+__device__ __forceinline__ StageSrc stage_src_global(const Data &d, const Inst &in, int s) {
+    const int nx = in.nx, nu = in.nu, N = in.N, xq = xstate(s, N);
+    StageSrc r;
+    r.R = d.R + in.oR + (long long)s * nu * nu;
+    r.S = (s != 0 && d.S) ? d.S + in.oS + (long long)s * nu * nx : nullptr;
+    r.Q = d.Q + in.oQ + (long long)xq * nx * nx;
+    r.Su = d.Sig ? d.Sig + in.oSig + (long long)s * (nu + nx) : nullptr;
+    r.Sx = d.Sig ? d.Sig + in.oSig + (long long)xq * (nu + nx) + nu : nullptr;
+    r.B = d.B + in.oB + (long long)s * nx * nu;
+    r.A = s != 0 ? d.A + in.oA + (long long)s * nx * nx : nullptr;
+    return r;
+}
+
+// Element (a, b), a >= b, of the stage Hessian [R S; S^T Q] + diag(Sigma).
+__device__ __forceinline__ double stage_H(const StageSrc &src, int nu, int nx, int a, int b) {
+    if (a < nu) return src.R[a + b * nu] + ((a == b && src.Su) ? src.Su[a] : 0.0);
+    if (b < nu) return src.S ? src.S[b + (a - nu) * nu] : 0.0;
     const int i = a - nu, j = b - nu;
-    return buf[L.oQ + i + j * nx] + (i == j ? buf[L.oSx + i] : 0.0);
+    return src.Q[i + j * nx] + ((i == j && src.Sx) ? src.Sx[i] : 0.0);
+}
+
+// [B A] (nx x (nu+nx), ld nx) of a stage into T storage.
+template <typename T, int TEAM>
+__device__ void fill_BA(T *BA, const StageSrc &src, int nx, int nu) {
+    for (int e = threadIdx.x; e < nx * nu; e += TEAM) BA[e] = (T)src.B[e];
+    for (int e = threadIdx.x; e < nx * nx; e += TEAM) BA[nx * nu + e] = src.A ? (T)src.A[e] : T(0);
 }
 
 template <typename T, int TEAM>
@@ -95,6 +128,7 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
         const Item wi = a.items[item];
+        if (a.skip && a.skip[wi.inst]) continue;
         const Inst in = a.inst[wi.inst];
         const int N = in.N, nx = in.nx, nu = in.nu, P = in.P, c = wi.seg;
         const int nux = nx + nu;
@@ -102,38 +136,45 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
         const StageLayout SL(nx, nu);
         const bool propagate = c >= 1;   // segment 0 never carries A^cl (A_0 = 0, S_0 = 0)
 
-        double *stage[2];
-        stage[0] = reinterpret_cast<double *>(smem_raw);
-        stage[1] = stage[0] + SL.size;
-        double *Mf = stage[1] + SL.size;                        // nx x nx float64 accumulator
-        T *H = reinterpret_cast<T *>(Mf + nx * nx);             // nux x nux (stage Hessian -> factor)
-        T *V = H + nux * nux;                                   // nux x nx
-        T *G = V + nux * nx;                                    // nx x nux  ([B^ A^] -> [L^B A^cl])
-        T *G2 = G + nx * nux;                                   // nx x nux  (next [B^ A^])
-        T *BAc = G2 + nx * nux;                                 // nx x nux  ([B A] in T, float only)
-        T *dinv = BAc + (sizeof(T) == 8 ? 0 : nx * nux);        // nux
+        const bool staged = a.stage_in_smem;
+        // [B A] of the next stage: aliased to the staged copy, converted into
+        // shared memory, or read from global memory inside the V product.
+        const int ba_mode = (staged && sizeof(T) == 8) ? 0 : ((staged || a.need_G2) ? 1 : 2);
+        double *buf = reinterpret_cast<double *>(smem_raw);         // raw stage copy (staged mode)
+        double *Mf = buf + (staged ? SL.size : 0);                   // nx x nx float64 accumulator
+        T *H = reinterpret_cast<T *>(Mf + nx * nx);                  // nux x nux (stage Hessian -> factor)
+        T *V = H + nux * nux;                                        // nux x nx
+        T *G = V + nux * nx;                                         // nx x nux  ([B^ A^] -> [L^B A^cl])
+        T *G2 = G + nx * nux;                                        // nx x nux  (next [B^ A^], P > 1)
+        T *BAc = G2 + (a.need_G2 ? nx * nux : 0);                    // nx x nux  ([B A] copy, mode 1)
+        T *dinv = BAc + (ba_mode == 1 ? nx * nux : 0);               // nux
 
         T *Lg = reinterpret_cast<T *>(a.L) + in.oL;
         T *LBg = reinterpret_cast<T *>(a.LB) + in.oLB;
         T *Fg = reinterpret_cast<T *>(a.F) + in.oF;
         T *DIg = reinterpret_cast<T *>(a.DI) + in.oDI;
 
-        // first stage: raw copy, then H^ = H and [B^ A^] = [B A]
+        // first stage: H^ = H and [B^ A^] = [B A]
         int s = seg_stage(c, 0, N, P);
-        prefetch_stage<TEAM>(stage[0], SL, a.data, in, s);
-        stage_zero_fill<TEAM>(stage[0], SL, a.data, in, s);
+        StageSrc src;
+        if (staged) {
+            prefetch_stage<TEAM>(buf, SL, a.data, in, s);
+            stage_zero_fill<TEAM>(buf, SL, a.data, in, s);
+            cp_async_wait_all();
+            src = stage_src_smem(buf, SL);
+        } else {
+            src = stage_src_global(a.data, in, s);
+        }
         for (int e = threadIdx.x; e < nx * nx; e += TEAM) Mf[e] = 0.0;
-        cp_async_wait_all();
         team_sync();
         {
-            const double *buf = stage[0];
             const int cnt = nux * (nux + 1) / 2;
             for (int e = threadIdx.x; e < cnt; e += TEAM) {
                 int r, q;
                 tri_index(e, r, q);
-                H[r + q * nux] = (T)stage_H(buf, SL, nu, nx, r, q);
+                H[r + q * nux] = (T)stage_H(src, nu, nx, r, q);
             }
-            for (int e = threadIdx.x; e < nx * nux; e += TEAM) G[e] = (T)buf[SL.oB + e];
+            fill_BA<T, TEAM>(G, src, nx, nu);
         }
         team_sync();
 
@@ -142,11 +183,11 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
             s = seg_stage(c, t, N, P);
             const bool hasG = (t == 0) || propagate;
             const bool last = (t == len - 1);
-            double *nbuf = stage[(t + 1) & 1];
             int s2 = 0;
             if (!last) {
                 s2 = seg_stage(c, t + 1, N, P);
-                prefetch_stage<TEAM>(nbuf, SL, a.data, in, s2);   // overlaps with the factorization below
+                // the copy of the next stage overlaps with the factorization below
+                if (staged) prefetch_stage<TEAM>(buf, SL, a.data, in, s2);
             }
             ok &= team_chol<T, TEAM>(H, nux, nux, dinv);
             store_block<T, TEAM>(Lg + (long long)s * nux * nux, H, nux, nux, nux);
@@ -161,14 +202,19 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 if (propagate && !last) store_block<T, TEAM>(Fg + (long long)s * nx * nx, G + nx * nu, nx, nx, nx);
             }
             if (!last) {
-                stage_zero_fill<TEAM>(nbuf, SL, a.data, in, s2);
-                cp_async_wait_all();
-                team_sync();
-                const T *BA;
-                if (sizeof(T) == 8) {
-                    BA = reinterpret_cast<const T *>(nbuf + SL.oB);
+                if (staged) {
+                    stage_zero_fill<TEAM>(buf, SL, a.data, in, s2);
+                    cp_async_wait_all();
+                    team_sync();   // every thread's copies have landed
+                    src = stage_src_smem(buf, SL);
                 } else {
-                    for (int e = threadIdx.x; e < nx * nux; e += TEAM) BAc[e] = (T)nbuf[SL.oB + e];
+                    src = stage_src_global(a.data, in, s2);
+                }
+                const T *BA = nullptr;
+                if (ba_mode == 0) {
+                    BA = reinterpret_cast<const T *>(src.B);
+                } else if (ba_mode == 1) {
+                    fill_BA<T, TEAM>(BAc, src, nx, nu);
                     team_sync();
                     BA = BAc;
                 }
@@ -177,7 +223,13 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 for (int e = threadIdx.x; e < nux * nx; e += TEAM) {
                     const int aa = e % nux, j = e / nux;
                     T acc = T(0);
-                    for (int k = j; k < nx; ++k) acc = fma(BA[k + aa * nx], LQ[k + j * nux], acc);
+                    if (ba_mode != 2) {
+                        for (int k = j; k < nx; ++k) acc = fma(BA[k + aa * nx], LQ[k + j * nux], acc);
+                    } else {
+                        const double *col = aa < nu ? src.B + aa * nx : (src.A ? src.A + (aa - nu) * nx : nullptr);
+                        if (col)
+                            for (int k = j; k < nx; ++k) acc = fma((T)col[k], LQ[k + j * nux], acc);
+                    }
                     V[aa + j * nux] = acc;
                 }
                 if (propagate) {
@@ -191,12 +243,14 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 for (int e = threadIdx.x; e < cnt; e += TEAM) {
                     int r, q;
                     tri_index(e, r, q);
-                    T acc = (T)stage_H(nbuf, SL, nu, nx, r, q);
+                    T acc = (T)stage_H(src, nu, nx, r, q);
                     for (int k = 0; k < nx; ++k) acc = fma(V[r + k * nux], V[q + k * nux], acc);
                     H[r + q * nux] = acc;
                 }
                 team_sync();
-                T *tmp = G; G = G2; G2 = tmp;
+                if (a.need_G2) {
+                    T *tmp = G; G = G2; G2 = tmp;
+                }
             } else {
                 const T *LQ = H + nu + nu * nux;
                 const T *dq = dinv + nu;
@@ -207,11 +261,11 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                     store_block<T, TEAM>(Fg + (long long)s * nx * nx, LA, nx, nx, nx);
                     team_syrk_lower<T, double, TEAM>(Mf, nx, LA, nx, nx, nx, +1);
                 }
-                // Tinv = L^{Q -1}
+                // Tinv = L^{Q -1}  (in V; L^Q is not needed after this)
                 T *Ti = V;
                 team_trtri_lower<T, TEAM>(Ti, nx, LQ, nux, nx, dq);
-                // M_bwd = Tinv^T Tinv  (full symmetric, in G2)
-                T *Mb = G2;
+                // M_bwd = Tinv^T Tinv  (full symmetric, in the H buffer)
+                T *Mb = H;
                 for (int e = threadIdx.x; e < nx * nx; e += TEAM) {
                     const int i = e % nx, j = e / nx;
                     const int k0 = i > j ? i : j;
@@ -222,8 +276,18 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 team_sync();
                 const int cb = (c - 1 + P) % P;
                 store_block_f64<T, TEAM>(a.Mb + in.oBlk + (long long)cb * nx * nx, Mb, nx, nx, nx);
+                team_symmetrize<double, TEAM>(Mf, nx, nx);
+                if (P == 1) {
+                    // single coupling block: M = M_fwd + M_bwd, factor it (float64)
+                    for (int e = threadIdx.x; e < nx * nx; e += TEAM) Mf[e] += (double)Mb[e];
+                    team_sync();
+                    ok &= team_chol<double, TEAM>(Mf, nx, nx);
+                }
+                double *dst = a.Mf + in.oBlk + (long long)c * nx * nx;
+                for (int e = threadIdx.x; e < nx * nx; e += TEAM) dst[e] = Mf[e];
                 if (propagate) {
-                    // K = -L^A Tinv (row lambda^{b_c}, column lambda^{b_{c-1}}), in H (free now)
+                    // K = -L^A Tinv (row lambda^{b_c}, column lambda^{b_{c-1}}), reusing the H buffer
+                    team_sync();   // M_bwd has been read
                     T *Kb = H;
                     for (int e = threadIdx.x; e < nx * nx; e += TEAM) {
                         const int i = e % nx, j = e / nx;
@@ -234,15 +298,6 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                     team_sync();
                     store_block_f64<T, TEAM>(a.Kc + in.oBlk + (long long)c * nx * nx, Kb, nx, nx, nx);
                 }
-                team_symmetrize<double, TEAM>(Mf, nx, nx);
-                if (P == 1) {
-                    // single coupling block: M = M_fwd + M_bwd, factor it (float64)
-                    for (int e = threadIdx.x; e < nx * nx; e += TEAM) Mf[e] += (double)Mb[e];
-                    team_sync();
-                    ok &= team_chol<double, TEAM>(Mf, nx, nx);
-                }
-                double *dst = a.Mf + in.oBlk + (long long)c * nx * nx;
-                for (int e = threadIdx.x; e < nx * nx; e += TEAM) dst[e] = Mf[e];
             }
         }
         if (!ok && threadIdx.x == 0) atomicCAS(a.status + wi.inst, 0, ST_NOT_PD);
@@ -250,13 +305,19 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
     }
 }
 
-size_t factor_smem_bytes(bool fp64, int nx, int nu) {
+size_t factor_stage_bytes(int nx, int nu) {
     const size_t nux = (size_t)nx + nu;
     size_t stage = (size_t)nu * nu + (size_t)nu * nx + (size_t)nx * nx + nux + (size_t)nx * nu + (size_t)nx * nx;
     stage = (stage + 1) & ~(size_t)1;
+    return stage * 8;
+}
+
+size_t factor_smem_bytes(bool fp64, int nx, int nu, bool staged, bool need_G2) {
+    const size_t nux = (size_t)nx + nu;
     const size_t el = fp64 ? 8 : 4;
-    size_t bytes = (2 * stage + (size_t)nx * nx) * 8;
-    bytes += (nux * nux + nux * nx + 2 * nx * nux + (fp64 ? 0 : nx * nux) + nux) * el;
+    const int ba_mode = (staged && fp64) ? 0 : ((staged || need_G2) ? 1 : 2);
+    size_t bytes = (staged ? factor_stage_bytes(nx, nu) : 0) + (size_t)nx * nx * 8;
+    bytes += (nux * nux + nux * nx + nx * nux + (need_G2 ? nx * nux : 0) + (ba_mode == 1 ? nx * nux : 0) + nux) * el;
     return (bytes + 15) / 16 * 16;
 }
 

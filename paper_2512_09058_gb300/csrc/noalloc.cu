@@ -81,7 +81,8 @@ extern "C" cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return fail(CYQ_ERR_NO_DEVICE, "cyq_factor_solve_noalloc: no current CUDA device");
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t fs = factor_smem_bytes(true, nx, nu), ss = solve_smem_bytes(true, nx, nu, 1);
+    const bool staged = factor_smem_bytes(true, nx, nu, true, false) <= (size_t)smem_optin / 2;
+    const size_t fs = factor_smem_bytes(true, nx, nu, staged, false), ss = solve_smem_bytes(true, nx, nu, 1);
     if (fs > (size_t)smem_optin || ss > (size_t)smem_optin)
         return fail(CYQ_ERR_INVALID_ARG, "cyq_factor_solve_noalloc: stage blocks too large for shared memory");
 
@@ -140,6 +141,9 @@ extern "C" cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu
     fa.L = L; fa.LB = LB; fa.F = F; fa.DI = DI;
     fa.Mf = Mf; fa.Mb = Mb; fa.Kc = Kc; fa.U = U; fa.Y = Y;
     fa.status = d_status;
+    fa.stage_in_smem = staged;
+    fa.need_G2 = false;
+    fa.skip = nullptr;
     if ((e = launch_factor_segments(true, team, fs, fa, st)) != cudaSuccess)
         return fail(CYQ_ERR_CUDA, std::string("cyq_factor_solve_noalloc: ") + cudaGetErrorString(e));
 

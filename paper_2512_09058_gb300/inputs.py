@@ -241,14 +241,55 @@ def make_instance(cfg, index: int, *, N: Optional[int] = None, nx: Optional[int]
                        Sigma=Sigma, rhs=rhs)
 
 
-def make_batch(cfg, indices: Optional[Sequence[int]] = None, *, instances=None, **overrides) -> Batch:
-    """Concatenate instances (``indices`` of ``cfg``, default all) into a Batch."""
+def _make_chunk(args):
+    cfg, idx, overrides = args
+    return [make_instance(cfg, int(i), **overrides) for i in idx]
+
+
+def make_batch(cfg, indices: Optional[Sequence[int]] = None, *, instances=None, workers: int = 0,
+               **overrides) -> Batch:
+    """Concatenate instances (``indices`` of ``cfg``, default all) into a Batch.
+
+    ``workers > 1`` draws the instances in a pool of that many processes
+    (spawn context; every instance has its own seed stream, so the result is
+    identical to the serial draw).  ``workers = 0`` picks one per host core
+    for batches of more than 64 instances."""
     if instances is None:
         if isinstance(cfg, str):
             cfg = CONFIGS[cfg]
         if indices is None:
             indices = range(cfg["batch"])
-        instances = [make_instance(cfg, int(i), **overrides) for i in indices]
+        indices = [int(i) for i in indices]
+        import os
+        if workers == 0:
+            workers = min(32, os.cpu_count() or 1) if len(indices) > 64 else 1
+        if workers > 1:
+            import concurrent.futures
+            import multiprocessing
+            chunks = [indices[i::workers * 4] for i in range(workers * 4)]
+            chunks = [c for c in chunks if c]
+            ctx = multiprocessing.get_context("spawn")
+            # one BLAS thread per worker process (spawned children inherit the environment)
+            keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+            saved = {k: os.environ.get(k) for k in keys}
+            for k in keys:
+                os.environ[k] = "1"
+            try:
+                with concurrent.futures.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
+                    parts = list(ex.map(_make_chunk, [(cfg, c, overrides) for c in chunks]))
+            finally:
+                for k, v in saved.items():
+                    if v is None:
+                        os.environ.pop(k, None)
+                    else:
+                        os.environ[k] = v
+            by_index = {}
+            for c, part in zip(chunks, parts):
+                for i, inst in zip(c, part):
+                    by_index[i] = inst
+            instances = [by_index[i] for i in indices]
+        else:
+            instances = [make_instance(cfg, i, **overrides) for i in indices]
     insts = list(instances)
     cat = lambda name: np.concatenate([getattr(x, name) for x in insts]) if insts else np.zeros(0)
     has_sigma = any(x.Sigma is not None for x in insts)

@@ -68,3 +68,14 @@ def test_no_refinement_budget_reports_not_converged():
     batch = ragged_batch(22, [(12, 4, 2), (9, 3, 3)], sigma=(1e-6, 1e6))
     z, s, _, b = gpu_solve(batch, precision="fp32_refine", it_max=1, tol=1e-16)
     assert (s.instance_status() == 3).all()
+
+
+def test_float64_escalation_rescues_hard_instances():
+    # float32 with a 1-step budget cannot reach 1e-10 at Sigma in [1e-7, 1e7]; the
+    # instances left above tol get a float64 factor and converge with it
+    dims = [(30, 4, 24), (25, 5, 30), (16, 8, 8), (40, 3, 12)]
+    batch = ragged_batch(23, dims, sigma=(1e-7, 1e7))
+    z, s, _, b = gpu_solve(batch, precision="fp32_refine", it_max=1)
+    assert (s.instance_status() == 0).all()
+    res = _residuals(batch, z, b)
+    assert res[:, 0].max() <= 1e-10, res[:, 0]

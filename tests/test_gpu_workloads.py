@@ -1,0 +1,117 @@
+"""Full-size workloads in the launch configuration the benchmark uses, checked
+on sampled instances against the oracle (whole-batch properties are checked
+on the device: status words and the refinement's own float64 residuals).
+
+* long_n4096_nx32_nu16: 8 OCPs, N = 4096, P = 64 segments per OCP (cyclic
+  reduction over 64 coupling blocks); plain float64 and float32 + float64
+  refinement.
+* uneven4096: 4096 OCPs of uneven N, nx, nu; float32 + float64 refinement.
+* adjoint512_n128_nx24_nu8: 512 OCPs; float64 factor, refined solve, adjoint.
+
+Gates: refined solves <= 1e-10 relative KKT residual (float64, oracle routine
+on the GPU's z); plain float64 forward error <= 1e-9 against the oracle
+(cond(K) of these workloads reaches ~1e8, so the float64 forward error of
+either side is ~1e-16 * cond); the adjoint <= 1e-9 relative to the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_09058_gb300 import inputs
+
+from gpu_util import rel_err, require_gpu, split_instances
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(batch, precision, it_max, P=0, nrhs=1):
+    torch, cyq = require_gpu()
+    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, P=P, max_nrhs=nrhs, it_max=it_max)
+    data, rhs = cyq.to_device(batch)
+    s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
+    kk = s.kkt_size
+    b = torch.empty(nrhs * kk, dtype=torch.float64, device="cuda")
+    for j in range(nrhs):
+        s.build_rhs(*rhs[j], b=b[j * kk:(j + 1) * kk])
+    z = s.solve(b, nrhs=nrhs)
+    torch.cuda.synchronize()
+    return s, z.cpu().numpy().reshape(nrhs, -1), b.cpu().numpy().reshape(nrhs, -1), data, rhs
+
+
+@pytest.fixture(scope="module")
+def long_batch():
+    return inputs.make_batch("long_n4096_nx32_nu16")
+
+
+@pytest.mark.parametrize("precision,it_max", [("fp64", 0), ("fp32_refine", 10)])
+def test_long_horizon_segments_and_cyclic_reduction(long_batch, precision, it_max):
+    batch = long_batch
+    s, z, b, _, _ = _solve(batch, precision, it_max)
+    assert (s.segments == 64).all()
+    assert (s.instance_status() == 0).all()
+    st = s.stats()
+    if it_max:
+        assert st["max_rel_residual"] <= 1e-10
+    zs, bs = split_instances(batch, z[0]), split_instances(batch, b[0])
+    for i in (0, 5):
+        inst = batch.instances[i]
+        zo = oracle.riccati_solve(inst, bs[i])
+        res = oracle.kkt_residual(inst, zs[i], bs[i])
+        err = rel_err(zs[i], zo)
+        print(precision, "instance", i, "residual", res, "forward error", err, "oracle residual",
+              oracle.kkt_residual(inst, zo, bs[i]), st)
+        assert err <= 1e-9
+        if it_max:
+            assert res <= 1e-10
+
+
+def test_uneven_batch_fp32_refinement():
+    batch = inputs.make_batch("uneven4096")
+    s, z, b, _, _ = _solve(batch, "fp32_refine", 10)
+    assert (s.instance_status() == 0).all()
+    st = s.stats()
+    print("uneven4096", st)
+    assert st["max_rel_residual"] <= 1e-10
+    rng = np.random.default_rng(4)
+    sample = sorted(rng.choice(batch.size, size=12, replace=False))
+    zs, bs = split_instances(batch, z[0]), split_instances(batch, b[0])
+    worst = 0.0
+    for i in sample:
+        inst = batch.instances[i]
+        res = oracle.kkt_residual(inst, zs[i], bs[i])
+        worst = max(worst, res)
+        assert res <= 1e-10, (i, inst.N, inst.nx, inst.nu, res)
+        assert rel_err(zs[i], oracle.riccati_solve(inst, bs[i])) <= 1e-8
+    print("uneven4096 sampled worst residual", worst)
+
+
+def test_adjoint_workload_sampled():
+    torch, cyq = require_gpu()
+    batch = inputs.make_batch("adjoint512_n128_nx24_nu8")
+    s, z, b, data, rhs = _solve(batch, "fp64", 10)
+    assert (s.instance_status() == 0).all()
+    zt = torch.from_numpy(z[0]).cuda()
+    g = 2.0 * zt.clone()
+    # loss = sum of squared states and inputs: zero the multiplier entries of the gradient
+    off = 0
+    for x in batch.instances:
+        w = x.nu + 2 * x.nx
+        gi = g[off:off + x.kkt_size].view(x.N, w)
+        gi[:, x.nu + x.nx:] = 0.0
+        off += x.kkt_size
+    out = s.solve_adjoint(rhs[0][3], zt, g)
+    torch.cuda.synchronize()
+    G = {k: v.cpu().numpy() for k, v in out.items()}
+    gh = g.cpu().numpy()
+    offs = {k: 0 for k in G}
+    for i, inst in enumerate(batch.instances):
+        N, nx, nu = inst.N, inst.nx, inst.nu
+        sizes = dict(w=inst.kkt_size, dQ=(N + 1) * nx * nx, dq=(N + 1) * nx, dR=N * nu * nu, dr=N * nu,
+                     dS=N * nu * nx, dA=N * nx * nx, dB=N * nx * nu, dc=N * nx, dx0=nx, dSigma=(N + 1) * (nu + nx))
+        if i in (0, 77, 511):
+            zi = z[0][offs["w"]:offs["w"] + inst.kkt_size]
+            ref = oracle.adjoint(inst, inst.rhs[0][3], zi, gh[offs["w"]:offs["w"] + inst.kkt_size])
+            for k, n in sizes.items():
+                assert rel_err(G[k][offs[k]:offs[k] + n], ref[k]) <= 1e-9, (i, k)
+        for k, n in sizes.items():
+            offs[k] += n
