@@ -6,13 +6,16 @@ nx = 12, nu = 4, stage cross terms S and diagonal regularisation Sigma
 log-uniform in [1e-6, 1e6]; one factorization + 4 right-hand sides per OCP.
 One step = factor all OCPs + solve the 4 right-hand sides, with the inputs
 resident in device memory (218 MB of float64 data, larger than the 129 MB L2).
+``--workload`` selects the other workloads (single OCP, long horizon, uneven
+batch, adjoint); each has its own list of methods, the first is the headline.
 
 Methods (each timed over the same K steps):
   fp64_refine  float64 factor + solve, float64 residual and refinement until
                ||b - Kz|| / ||b|| <= 1e-10 for every OCP and right-hand side
-               (the headline: float64 arithmetic, certified at the metric's gate)
+               (float64 arithmetic, certified at the metric's gate)
   fp64         plain float64 factor + solve (no residual computed)
-  fp32_refine  float32 factor + solve, float64 residual + refinement to 1e-10
+  fp32_refine  float32 factor + solve, float64 residual + refinement to 1e-10,
+               float64 factor for the instances float32 cannot bring to 1e-10
 
 Prints ONE JSON line on rank 0.  ``--impl reference`` times the CPU oracle
 (plain FP64 C Riccati recursion) on the host instead.  Under torchrun every
@@ -36,11 +39,20 @@ from paper_2512_09058_gb300 import inputs  # noqa: E402
 
 METRIC = "KKT factor+solve/sec and ns/stage at rel. residual ≤1e-10; % of roofline"
 UNIT = "OCP factor+solve/s"
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1258.6
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07    # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1258.6
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz = 80549
 WORKLOAD = "batch1024_n64_nx12_nu4"
 # method -> (factor precision, refinement step budget).  Float64 refinement
 # converges in one step here; float32 needs ~5 at cond(K) ~ 1e11.
 METHODS = {"fp64": ("fp64", 0), "fp64_refine": ("fp64", 3), "fp32_refine": ("fp32_refine", 8)}
+# workload -> methods (first = headline), CUDA-graph replay, adjoint in the step
+WORKLOADS = {
+    "batch1024_n64_nx12_nu4": dict(methods=["fp64_refine", "fp64", "fp32_refine"], graph=False, adjoint=False),
+    "single_n32_nx8_nu4": dict(methods=["fp64", "fp64_refine"], graph=True, adjoint=False),
+    "long_n4096_nx32_nu16": dict(methods=["fp32_refine", "fp64", "fp64_refine"], graph=False, adjoint=False),
+    "uneven4096": dict(methods=["fp32_refine", "fp64_refine"], graph=True, adjoint=False),
+    "adjoint512_n128_nx24_nu8": dict(methods=["fp64_refine"], graph=False, adjoint=True),
+}
 
 
 def parse():
@@ -50,7 +62,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="cyq", choices=["cyq", "reference"])
     p.add_argument("--workload", default=WORKLOAD, choices=sorted(inputs.CONFIGS))
-    p.add_argument("--methods", default="fp64_refine,fp64,fp32_refine")
+    p.add_argument("--methods", default="", help="comma list; default: the workload's methods")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -62,15 +74,57 @@ def riccati_fma_per_stage(nx, nu):
     return 0.5 * nux * nx * nx + 0.5 * nux * nux * nx + nux ** 3 / 6.0
 
 
-def solve_fma_per_stage(nx, nu):
-    """Segment solve sweeps per right-hand side (backward + forward, P = 1):
-    nu^2 + 2 nx nu + 2 nx^2 + 2 nux nx."""
-    return nu * nu + 2 * nx * nu + 2 * nx * nx + 2 * (nx + nu) * nx
+def _seg_len(c, N, P):
+    b = lambda k: (k * N) // P
+    return N - b(P - 1) if c == 0 else b(c) - b(c - 1)
 
 
-def residual_fma_per_stage(nx, nu):
-    """Float64 residual rows per right-hand side: R, S (twice), B (twice), Q, A (twice)."""
-    return nu * nu + 2 * nu * nx + 2 * nx * nu + nx * nx + 2 * nx * nx
+def factor_fma(N, nx, nu, P):
+    """Algorithmic FMAs (FMA = 1, leading terms as in paper Sec. 4.5) of the
+    factorization as scheduled: P segments of the modified Riccati recursion
+    (Alg. fact-mod-riccati), the Schur blocks (compute-schur) and the cyclic
+    reduction of the P coupling blocks."""
+    nux = nx + nu
+    total = 0.0
+    for c in range(P):
+        L = _seg_len(c, N, P)
+        prop = c >= 1
+        for t in range(L):
+            total += nux ** 3 / 6.0                                        # potrf
+            if t == 0 or prop:
+                total += 0.5 * nx * nu * nu + nx * nx * nu + 0.5 * nx * nx * nu   # trsm L^B, gemm A^cl, syrk M_fwd
+            if t < L - 1:
+                total += 0.5 * nux * nx * nx + 0.5 * nux * nux * nx          # trmm V, syrk H + V V^T
+                if prop:
+                    total += nux * nx * nx                                     # gemm [B^ A^] = A^cl [B A]
+        if prop:
+            total += 1.5 * nx ** 3                                             # trsm L^A, syrk L^A L^A^T, trmm K
+        total += nx ** 3 / 3.0                                                 # trtri, lauum (M_bwd)
+    n3 = float(nx) ** 3
+    if P == 1:
+        total += n3 / 6.0
+    else:
+        s = 1
+        while s < P:
+            for k in range(s, P, 2 * s):
+                total += n3 / 6.0 + 0.5 * n3 + (0.5 * n3 if k + s < P else 0.0)
+            for i in range(0, P, 2 * s):
+                total += (0.5 * n3 if i - s >= 0 else 0.0) + (0.5 * n3 if i + s < P else 0.0) \
+                    + (n3 if i - 2 * s >= 0 else 0.0)
+            s *= 2
+        total += n3 / 6.0
+    return total
+
+
+def batch_factor_fma(batch, segments):
+    cache = {}
+    tot = 0.0
+    for N, nx, nu, P in zip(batch.N, batch.nx, batch.nu, segments):
+        key = (int(N), int(nx), int(nu), int(P))
+        if key not in cache:
+            cache[key] = factor_fma(*key)
+        tot += cache[key]
+    return tot
 
 
 # ---------------------------------------------------------------------------
@@ -134,17 +188,21 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and the cpu_baseline)
 # ---------------------------------------------------------------------------
-def time_oracle(batch, nrhs, min_seconds=2.0, max_instances=None):
+def time_oracle(batch, nrhs, budget_s=2.0, max_instances=None):
+    """Oracle (FP64 C, textbook Riccati; one factorization shared by the nrhs
+    right-hand sides) over the batch's instances in order, until ``budget_s``
+    seconds of CPU work or ``max_instances`` instances.  Returns (OCP/s, count, s)."""
     import oracle   # CPU-baseline / reference leg only
     insts = batch.instances if max_instances is None else batch.instances[:max_instances]
-    bs = [np.stack([oracle.build_rhs(x, *x.rhs[j]) for j in range(nrhs)]) for x in insts]
-    done, t0 = 0, time.perf_counter()
-    while True:
-        for x, b in zip(insts, bs):
-            oracle.riccati_solve(x, b)
-        done += len(insts)
-        el = time.perf_counter() - t0
-        if el >= min_seconds:
+    done, el = 0, 0.0
+    t0 = time.perf_counter()
+    for x in insts:
+        b = np.stack([oracle.build_rhs(x, *x.rhs[j]) for j in range(nrhs)])
+        t = time.perf_counter()
+        oracle.riccati_solve(x, b)
+        el += time.perf_counter() - t
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
             break
     return done / el, done, el
 
@@ -152,24 +210,62 @@ def time_oracle(batch, nrhs, min_seconds=2.0, max_instances=None):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def run_method(torch, cyq, batch, data, b, method, steps, warmup, rank, world, dist):
+def _loss_grad(torch, batch, z):
+    """dL/dz of L = sum of squared states and inputs (multiplier entries zero)."""
+    g = 2.0 * z
+    off = 0
+    for x in batch.instances:
+        w = x.nu + 2 * x.nx
+        g[off:off + x.kkt_size].view(x.N, w)[:, x.nu + x.nx:] = 0.0
+        off += x.kkt_size
+    return g
+
+
+def run_method(torch, cyq, batch, data, b, x0, method, steps, warmup, dist, graph=False, adjoint=False):
     precision, it_max = METHODS[method]
     nrhs = len(batch.rhs)
     s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, max_nrhs=nrhs, it_max=it_max)
     z = torch.empty_like(b)
-    stream = torch.cuda.current_stream()
+    mask = _loss_grad(torch, batch, torch.ones_like(b[:s.kkt_size])) / 2.0 if adjoint else None
 
-    def step():
+    def factor():
         s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
-        s.solve(b, z, nrhs=nrhs)
 
-    s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
+    def solve():
+        s.solve(b, z, nrhs=nrhs)
+        if adjoint:
+            g = 2.0 * z[:s.kkt_size] * mask
+            s.solve_adjoint(x0, z[:s.kkt_size], g)
+
+    factor()
     launches_factor = s.launch_count()
     s.solve(b, z, nrhs=nrhs)
-    launches_solve = s.launch_count()
+    launches_solve = s.launch_count() + (1 + 2 * 3 + 1 if adjoint else 0)   # adjoint: solve + grads
     for _ in range(warmup):
-        step()
+        factor()
+        solve()
     torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    g_factor = g_solve = None
+    if graph:
+        # one step captured as two graphs (factor, solve): every launch and memset of
+        # the library is stream-ordered, so the whole refinement loop replays
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            factor()
+            solve()
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        g_factor, g_solve = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_factor):
+            factor()
+        with torch.cuda.graph(g_solve):
+            solve()
+        for _ in range(max(1, warmup)):
+            g_factor.replay()
+            g_solve.replay()
+        torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
@@ -179,9 +275,15 @@ def run_method(torch, cyq, batch, data, b, method, steps, warmup, rank, world, d
     t_start.record(stream)
     for i in range(steps):
         ev[i][0].record(stream)
-        s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
+        if graph:
+            g_factor.replay()
+        else:
+            factor()
         ev[i][1].record(stream)
-        s.solve(b, z, nrhs=nrhs)
+        if graph:
+            g_solve.replay()
+        else:
+            solve()
         ev[i][2].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -202,13 +304,14 @@ def run_method(torch, cyq, batch, data, b, method, steps, warmup, rank, world, d
             rel = s.residual(b[j * kk:(j + 1) * kk], z[j * kk:(j + 1) * kk])
             worst = max(worst, float(rel.max().item()))
         st["max_rel_residual"] = worst
+    segments = s.segments
     s.close()
     return dict(total_ms=total_ms, factor_ms=float(np.mean(factor_ms)), solve_ms=float(np.mean(solve_ms)),
-                status_ok=bool((status == 0).all()), stats=st,
+                status_ok=bool((status == 0).all()), stats=st, segments=segments,
                 launches_per_step=launches_factor + launches_solve)
 
 
-def run_e2e(torch, cyq, batch, method, steps, warmup):
+def run_e2e(torch, cyq, batch, method, steps, warmup, adjoint=False):
     """Same metric through the public API with host buffers: every step copies
     the data and (q, r, c, x_init) from pinned host memory, builds the KKT
     right-hand sides, factors, solves and copies z back to pinned memory."""
@@ -224,9 +327,11 @@ def run_e2e(torch, cyq, batch, method, steps, warmup):
     kk = s.kkt_size
     b = torch.empty(nrhs * kk, dtype=torch.float64, device="cuda")
     z = torch.empty_like(b)
-    z_host = torch.empty(nrhs * kk, dtype=torch.float64).pin_memory()
+    nout = nrhs * kk
+    mask = _loss_grad(torch, batch, torch.ones(kk, dtype=torch.float64, device="cuda")) / 2.0 if adjoint else None
+    out_host = torch.empty(nout + (int(batch.A.size) if adjoint else 0), dtype=torch.float64).pin_memory()
     h2d = sum(v.numel() * 8 for v in host.values() if v is not None) + sum(x.numel() * 8 for r in host_rhs for x in r)
-    d2h = z_host.numel() * 8
+    d2h = out_host.numel() * 8
 
     def step():
         for k, v in host.items():
@@ -239,7 +344,10 @@ def run_e2e(torch, cyq, batch, method, steps, warmup):
         for j in range(nrhs):
             s.build_rhs(*dev_rhs[j], b=b[j * kk:(j + 1) * kk])
         s.solve(b, z, nrhs=nrhs)
-        z_host.copy_(z, non_blocking=True)
+        out_host[:nout].copy_(z, non_blocking=True)
+        if adjoint:
+            gr = s.solve_adjoint(dev_rhs[0][3], z[:kk], 2.0 * z[:kk] * mask, want=("w", "dA"))
+            out_host[nout:].copy_(gr["dA"], non_blocking=True)
 
     for _ in range(warmup):
         step()
@@ -261,30 +369,34 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     cfg = inputs.CONFIGS[args.workload]
+    prof = WORKLOADS[args.workload]
+    nominal = lambda key: cfg[key] if not isinstance(cfg[key], tuple) else "U%s" % (cfg[key],)
 
     if args.impl == "reference":
         if rank != 0:
             return 0
         batch = inputs.make_batch(args.workload)
         nrhs = len(batch.rhs)
-        stages = int(batch.N.sum())
         for _ in range(args.warmup):
-            time_oracle(batch, nrhs, min_seconds=0.0, max_instances=16)
-        rate, done, el = time_oracle(batch, nrhs, min_seconds=0.0)   # one pass per step
-        t_steps = []
+            time_oracle(batch, nrhs, budget_s=0.05)
+        rates, samples = [], []
         for _ in range(args.steps):
-            r, d, e = time_oracle(batch, nrhs, min_seconds=0.0)
-            t_steps.append(e)
-        ms = 1e3 * float(np.mean(t_steps))
-        value = batch.size / (ms / 1e3)
-        sample = "the full workload (%d OCPs x %d rhs) per step, one host core" % (batch.size, nrhs)
+            r, d, e = time_oracle(batch, nrhs, budget_s=1.0)
+            rates.append(r)
+            samples.append(d)
+        value = float(np.mean(rates))
+        per_stage = float(np.mean(batch.N))
+        ms = batch.size / value * 1e3
+        sample = ("per step the first OCPs of the workload in order for ~1 s of one host core "
+                  "(%d OCPs x %d rhs per step on average)" % (int(np.mean(samples)), nrhs))
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "ns_per_stage": ms * 1e6 / stages,
-            "config": {"workload": args.workload, "global_batch": batch.size, "stages_per_ocp": int(cfg["N"]),
-                       "nx": cfg["nx"], "nu": cfg["nu"], "nrhs": nrhs, "method": "cpu oracle (textbook Riccati, FP64)"},
+            "ns_per_stage": 1e9 / (value * per_stage),
+            "config": {"workload": args.workload, "global_batch": batch.size, "stages_per_ocp": nominal("N"),
+                       "nx": nominal("nx"), "nu": nominal("nu"), "nrhs": nrhs,
+                       "method": "cpu oracle (textbook Riccati, FP64)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return 0
@@ -318,12 +430,13 @@ def main():
         s0.build_rhs(*rhs_dev[j], b=b[j * s0.kkt_size:(j + 1) * s0.kkt_size])
     torch.cuda.synchronize()
     s0.close()
+    x0 = rhs_dev[0][3]
 
-    methods = [m for m in args.methods.split(",") if m]
+    methods = [m for m in (args.methods.split(",") if args.methods else prof["methods"]) if m]
     clocks = ClockSampler(local_rank)
     clocks.start()
-    results = {m: run_method(torch, cyq, batch, data, b, m, args.steps, args.warmup, rank, world, dist)
-               for m in methods}
+    results = {m: run_method(torch, cyq, batch, data, b, x0, m, args.steps, args.warmup, dist,
+                             graph=prof["graph"], adjoint=prof["adjoint"]) for m in methods}
     clk = clocks.stop()
     head = methods[0]
     R = results[head]
@@ -332,7 +445,8 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e2e_ms, h2d, d2h = run_e2e(torch, cyq, batch, head, max(3, args.steps // 4), args.warmup)
+        e2e_ms, h2d, d2h = run_e2e(torch, cyq, batch, head, max(3, args.steps // 4), args.warmup,
+                                   adjoint=prof["adjoint"])
         if dist is not None:
             t = torch.tensor([e2e_ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -342,39 +456,49 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, done, el = time_oracle(batch, nrhs, min_seconds=2.0)
+        rate, done, el = time_oracle(batch, nrhs, budget_s=3.0)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "whole %d-OCP workload x %d rhs, repeated for %.1f s (%d OCPs), one host core"
-                         % (batch.size, nrhs, el, done)}
+               "sample": "first %d OCPs of the workload x %d rhs (%.1f s of one host core), scaled to OCP/s"
+                         % (done, nrhs, el)}
 
-    nx, nu = int(cfg["nx"]), int(cfg["nu"])
-    fl_factor = 2.0 * riccati_fma_per_stage(nx, nu) * stages
-    achieved = fl_factor / (R["factor_ms"] / 1e3) / 1e9
     variants = {}
     for m, r in results.items():
         msm = r["total_ms"] / args.steps
+        fl = 2.0 * batch_factor_fma(batch, r["segments"])
+        f64 = METHODS[m][0] == "fp64"
+        peak = FP64_PEAK_GFLOPS if f64 else FP32_PEAK_GFLOPS
         variants[m] = {"value": world * batch.size / (msm / 1e3), "ms_per_step": msm,
                        "factor_ms": r["factor_ms"], "solve_ms": r["solve_ms"],
                        "ns_per_stage": msm * 1e6 / stages,
                        "max_rel_residual": r["stats"]["max_rel_residual"],
                        "refine_steps": r["stats"]["refine_steps"], "status_ok": r["status_ok"],
-                       "factor_gflops": (fl_factor / (r["factor_ms"] / 1e3) / 1e9)}
+                       "segments_per_ocp": [int(r["segments"].min()), int(r["segments"].max())],
+                       "factor_gflops": fl / (r["factor_ms"] / 1e3) / 1e9,
+                       "factor_frac_of_pipe_peak": fl / (r["factor_ms"] / 1e3) / 1e9 / peak}
+    fl = 2.0 * batch_factor_fma(batch, R["segments"])
+    f64 = METHODS[head][0] == "fp64"
+    peak = FP64_PEAK_GFLOPS if f64 else FP32_PEAK_GFLOPS
+    achieved = fl / (R["factor_ms"] / 1e3) / 1e9
+    sbytes = (batch.Q.nbytes + batch.R.nbytes + batch.S.nbytes + batch.A.nbytes + batch.B.nbytes
+              + (batch.Sigma.nbytes if batch.Sigma is not None else 0))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if f64 else "f32+f64", "data": "synthetic",
         "ns_per_stage": ms * 1e6 / stages,
-        "config": {"workload": args.workload, "global_batch": world * batch.size, "stages_per_ocp": int(cfg["N"]),
-                   "nx": nx, "nu": nu, "nrhs": nrhs, "method": head, "parallelism": "dp%d" % world,
-                   "l2": "inputs larger than L2 (%.0f MB float64 data per GPU)"
-                         % ((batch.Q.nbytes + batch.R.nbytes + batch.S.nbytes + batch.A.nbytes + batch.B.nbytes
-                             + (batch.Sigma.nbytes if batch.Sigma is not None else 0)) / 1e6)},
+        "config": {"workload": args.workload, "global_batch": world * batch.size,
+                   "stages_per_ocp": nominal("N"), "nx": nominal("nx"), "nu": nominal("nu"), "nrhs": nrhs,
+                   "method": head, "cuda_graph": prof["graph"], "adjoint": prof["adjoint"],
+                   "parallelism": "dp%d" % world,
+                   "l2": ("inputs larger than L2 (%.0f MB float64 data per GPU)" % (sbytes / 1e6))
+                   if sbytes > 129e6 else "inputs smaller than L2 (%.1f MB): no flush, L2-resident" % (sbytes / 1e6)},
         "max_rel_residual": R["stats"]["max_rel_residual"],
         "refine_steps": R["stats"]["refine_steps"],
-        "roofline": {"kernel": "k_factor_segments<double,32>", "bound": "alu", "achieved": achieved,
-                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
-                     "traffic": None,
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (recipe's 1.25 TF nominal)"},
+        "roofline": {"kernel": "k_factor_segments<%s> (+ cyclic reduction when P > 1)" % ("double" if f64 else "float"),
+                     "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz" if f64 else
+                                     "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz")},
         "variants": variants,
         "gpu_launches": R["launches_per_step"] * args.steps,
         "clocks": clk,

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -641,3 +644,16 @@ cyq_status cyq_get_stats(cyq_handle h, cyq_stats *out, cyq_stream stream) {
 }  // extern "C"
 
 void cyq::set_last_error_message(const char *msg) { g_last_error = msg ? msg : ""; }
+
+cudaError_t cyq::ensure_smem(const void *kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> set;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = set[std::make_pair(dev, kernel)];
+    if (bytes <= cur) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}

@@ -166,9 +166,9 @@ cudaError_t launch_cr_factor_levels(const CrPlan &plan, int team, int nmax, cons
     auto upd = team == 32 ? k_cr_update<32> : k_cr_update<128>;
     auto base = team == 32 ? k_cr_base<32> : k_cr_base<128>;
     const size_t se = 3 * nn + nmax * sizeof(double), su = 4 * nn;
-    if ((e = cudaFuncSetAttribute(elim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(upd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)su)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(base, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn)) != cudaSuccess) return e;
+    if ((e = ensure_smem((const void *)elim, se)) != cudaSuccess) return e;
+    if ((e = ensure_smem((const void *)upd, su)) != cudaSuccess) return e;
+    if ((e = ensure_smem((const void *)base, nn)) != cudaSuccess) return e;
     for (int l = 0; l < plan.levels; ++l) {
         const int s = 1 << l;
         const int ne = plan.elim_off[l + 1] - plan.elim_off[l], nu_ = plan.upd_off[l + 1] - plan.upd_off[l];
@@ -315,11 +315,11 @@ cudaError_t launch_cr_solve(int n_inst_cr, const int *inst_list, int team, size_
     if (n_inst_cr == 0) return cudaSuccess;
     cudaError_t e;
     if (team == 32) {
-        e = cudaFuncSetAttribute(k_cr_solve<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_smem((const void *)k_cr_solve<32>, smem);
         if (e != cudaSuccess) return e;
         k_cr_solve<32><<<n_inst_cr, 32, smem, st>>>(a, inst_list);
     } else {
-        e = cudaFuncSetAttribute(k_cr_solve<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_smem((const void *)k_cr_solve<128>, smem);
         if (e != cudaSuccess) return e;
         k_cr_solve<128><<<n_inst_cr, 128, smem, st>>>(a, inst_list);
     }

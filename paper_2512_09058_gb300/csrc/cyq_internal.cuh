@@ -347,6 +347,11 @@ cudaError_t launch_adjoint(const GradArgs &g, int n_chunks, int batch, const Dat
 size_t factor_smem_bytes(bool fp64, int nx, int nu, bool staged, bool need_G2);
 size_t factor_stage_bytes(int nx, int nu);
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device (cached per kernel and device, so repeated launches -- and
+// launches recorded into a CUDA graph -- make no attribute calls).
+cudaError_t ensure_smem(const void *kernel, size_t bytes);
+
 // Sets the text returned by cyq_last_error() for the calling thread.
 void set_last_error_message(const char *msg);
 inline void set_last_error_message(const std::string &msg) { set_last_error_message(msg.c_str()); }

@@ -324,7 +324,7 @@ size_t factor_smem_bytes(bool fp64, int nx, int nu, bool staged, bool need_G2) {
 template <typename T, int TEAM>
 static cudaError_t launch_factor_t(size_t smem, const FactorArgs &a, cudaStream_t st) {
     auto k = k_factor_segments<T, TEAM>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem((const void *)k, smem);
     if (e != cudaSuccess) return e;
     k<<<a.n_items, TEAM, smem, st>>>(a);
     return cudaGetLastError();

@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
 template <typename T, int TEAM>
 static cudaError_t launch_sweep(bool backward, size_t smem, const SolveArgs &a, cudaStream_t st) {
     auto k = backward ? k_solve_backward<T, TEAM> : k_solve_forward<T, TEAM>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem((const void *)k, smem);
     if (e != cudaSuccess) return e;
     k<<<a.n_items, TEAM, smem, st>>>(a);
     return cudaGetLastError();
