@@ -76,6 +76,17 @@ __device__ __forceinline__ void tri_index(int e, int &r, int &c) {
     c = e - rr * (rr + 1) / 2;
 }
 
+// Move (r, c) forward by `step` elements in that row order.  Threads start
+// at tri_index(threadIdx.x) and step by the team size, so the mapping is
+// computed once instead of once per element.
+__device__ __forceinline__ void tri_advance(int &r, int &c, int step) {
+    c += step;
+    while (c > r) {
+        c -= r + 1;
+        ++r;
+    }
+}
+
 // Cholesky pivots.  An FP64 instruction costs the same whether one or all 32
 // lanes run it, and the library's double sqrt and division are sequences of
 // ~10 and ~7 FP64 operations, so the pivot d -> (sqrt(d), 1/sqrt(d)) is built
@@ -138,6 +149,8 @@ __device__ __forceinline__ void async_copy_f64(double *dst, const double *src, i
 template <typename T, int TEAM>
 __device__ bool team_chol(T *A, int n, int ld, T *dinv = nullptr) {
     const int tid = threadIdx.x;
+    int r0, c0;
+    tri_index(tid, r0, c0);
     bool ok = true;
     for (int k = 0; k < n; ++k) {
         T d = A[k + k * ld];
@@ -153,13 +166,9 @@ __device__ bool team_chol(T *A, int n, int ld, T *dinv = nullptr) {
         for (int i = tid; i < k; i += TEAM) A[i + k * ld] = T(0);   // upper part of column k
         team_sync();
         const int m = n - k - 1;                 // trailing size
-        const int cnt = m * (m + 1) / 2;
-        for (int e = tid; e < cnt; e += TEAM) {
-            int r, c;
-            tri_index(e, r, c);
-            r += k + 1;
-            c += k + 1;
-            A[r + c * ld] = fma(-A[r + k * ld], A[c + k * ld], A[r + c * ld]);
+        for (int r = r0, c = c0; r < m; tri_advance(r, c, TEAM)) {
+            const int rr = r + k + 1, cc = c + k + 1;
+            A[rr + cc * ld] = fma(-A[rr + k * ld], A[cc + k * ld], A[rr + cc * ld]);
         }
         team_sync();
     }
@@ -227,10 +236,9 @@ __device__ void team_gemm_nt(T *C, int ldc, const T *A, int lda, const T *B, int
 // Lower triangle of C (n x n) (op)= A A^T, A is n x k.
 template <typename T, typename TC, int TEAM>
 __device__ void team_syrk_lower(TC *C, int ldc, const T *A, int lda, int n, int k, int mode) {
-    const int cnt = n * (n + 1) / 2;
-    for (int e = threadIdx.x; e < cnt; e += TEAM) {
-        int r, c;
-        tri_index(e, r, c);
+    int r, c;
+    tri_index(threadIdx.x, r, c);
+    for (; r < n; tri_advance(r, c, TEAM)) {
         T s = T(0);
         for (int t = 0; t < k; ++t) s += A[r + t * lda] * A[c + t * lda];
         TC *o = C + r + c * ldc;

@@ -137,17 +137,19 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
         const bool propagate = c >= 1;   // segment 0 never carries A^cl (A_0 = 0, S_0 = 0)
 
         const bool staged = a.stage_in_smem;
-        // [B A] of the next stage: aliased to the staged copy, converted into
-        // shared memory, or read from global memory inside the V product.
-        const int ba_mode = (staged && sizeof(T) == 8) ? 0 : ((staged || a.need_G2) ? 1 : 2);
+        // [B A] of the next stage: aliased to the staged float64 copy, or
+        // converted into its own shared-memory tile.
+        const bool ba_alias = staged && sizeof(T) == 8;
         double *buf = reinterpret_cast<double *>(smem_raw);         // raw stage copy (staged mode)
         double *Mf = buf + (staged ? SL.size : 0);                   // nx x nx float64 accumulator
         T *H = reinterpret_cast<T *>(Mf + nx * nx);                  // nux x nux (stage Hessian -> factor)
         T *V = H + nux * nux;                                        // nux x nx
-        T *G = V + nux * nx;                                         // nx x nux  ([B^ A^] -> [L^B A^cl])
+        // [B^ A^] -> [L^B A^cl]: without A^cl propagation it is only used at the
+        // first stage, before V is formed, so it shares V's tile
+        T *G = a.need_G2 ? V + nux * nx : V;                         // nx x nux
         T *G2 = G + nx * nux;                                        // nx x nux  (next [B^ A^], P > 1)
-        T *BAc = G2 + (a.need_G2 ? nx * nux : 0);                    // nx x nux  ([B A] copy, mode 1)
-        T *dinv = BAc + (ba_mode == 1 ? nx * nux : 0);               // nux
+        T *BAc = a.need_G2 ? G2 + nx * nux : V + nux * nx;           // nx x nux  ([B A] tile)
+        T *dinv = BAc + (ba_alias ? 0 : nx * nux);                   // nux
 
         T *Lg = reinterpret_cast<T *>(a.L) + in.oL;
         T *LBg = reinterpret_cast<T *>(a.LB) + in.oLB;
@@ -168,12 +170,9 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
         for (int e = threadIdx.x; e < nx * nx; e += TEAM) Mf[e] = 0.0;
         team_sync();
         {
-            const int cnt = nux * (nux + 1) / 2;
-            for (int e = threadIdx.x; e < cnt; e += TEAM) {
-                int r, q;
-                tri_index(e, r, q);
-                H[r + q * nux] = (T)stage_H(src, nu, nx, r, q);
-            }
+            int r, q;
+            tri_index(threadIdx.x, r, q);
+            for (; r < nux; tri_advance(r, q, TEAM)) H[r + q * nux] = (T)stage_H(src, nu, nx, r, q);
             fill_BA<T, TEAM>(G, src, nx, nu);
         }
         team_sync();
@@ -210,10 +209,10 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 } else {
                     src = stage_src_global(a.data, in, s2);
                 }
-                const T *BA = nullptr;
-                if (ba_mode == 0) {
+                const T *BA;
+                if (ba_alias) {
                     BA = reinterpret_cast<const T *>(src.B);
-                } else if (ba_mode == 1) {
+                } else {
                     fill_BA<T, TEAM>(BAc, src, nx, nu);
                     team_sync();
                     BA = BAc;
@@ -223,13 +222,7 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 for (int e = threadIdx.x; e < nux * nx; e += TEAM) {
                     const int aa = e % nux, j = e / nux;
                     T acc = T(0);
-                    if (ba_mode != 2) {
-                        for (int k = j; k < nx; ++k) acc = fma(BA[k + aa * nx], LQ[k + j * nux], acc);
-                    } else {
-                        const double *col = aa < nu ? src.B + aa * nx : (src.A ? src.A + (aa - nu) * nx : nullptr);
-                        if (col)
-                            for (int k = j; k < nx; ++k) acc = fma((T)col[k], LQ[k + j * nux], acc);
-                    }
+                    for (int k = j; k < nx; ++k) acc = fma(BA[k + aa * nx], LQ[k + j * nux], acc);
                     V[aa + j * nux] = acc;
                 }
                 if (propagate) {
@@ -239,10 +232,9 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                     team_sync();
                 }
                 // H^_{s2} = H_{s2} + V V^T  (lower triangle, straight from the raw record)
-                const int cnt = nux * (nux + 1) / 2;
-                for (int e = threadIdx.x; e < cnt; e += TEAM) {
-                    int r, q;
-                    tri_index(e, r, q);
+                int r, q;
+                tri_index(threadIdx.x, r, q);
+                for (; r < nux; tri_advance(r, q, TEAM)) {
                     T acc = (T)stage_H(src, nu, nx, r, q);
                     for (int k = 0; k < nx; ++k) acc = fma(V[r + k * nux], V[q + k * nux], acc);
                     H[r + q * nux] = acc;
@@ -315,9 +307,9 @@ size_t factor_stage_bytes(int nx, int nu) {
 size_t factor_smem_bytes(bool fp64, int nx, int nu, bool staged, bool need_G2) {
     const size_t nux = (size_t)nx + nu;
     const size_t el = fp64 ? 8 : 4;
-    const int ba_mode = (staged && fp64) ? 0 : ((staged || need_G2) ? 1 : 2);
+    const bool ba_alias = staged && fp64;
     size_t bytes = (staged ? factor_stage_bytes(nx, nu) : 0) + (size_t)nx * nx * 8;
-    bytes += (nux * nux + nux * nx + nx * nux + (need_G2 ? nx * nux : 0) + (ba_mode == 1 ? nx * nux : 0) + nux) * el;
+    bytes += (nux * nux + nux * nx + (need_G2 ? 2 * nx * nux : 0) + (ba_alias ? 0 : nx * nux) + nux) * el;
     return (bytes + 15) / 16 * 16;
 }
 
