@@ -35,7 +35,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2512_09058_gb300 import inputs  # noqa: E402
+from paper_2512_09058_gb300 import inputs, shard  # noqa: E402
 
 METRIC = "KKT factor+solve/sec and ns/stage at rel. residual ≤1e-10; % of roofline"
 UNIT = "OCP factor+solve/s"
@@ -301,10 +301,8 @@ def run_method(torch, cyq, batch, data, b, x0, method, steps, warmup, dist, grap
     total_ms = t_start.elapsed_time(t_end)
     if flush is not None:
         total_ms = sum(e[0].elapsed_time(e[2]) for e in ev)
+    total_ms = shard.reduce_time_ms(total_ms, dist, device="cuda")
     if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     factor_ms = [e[0].elapsed_time(e[1]) for e in ev]
     solve_ms = [e[1].elapsed_time(e[2]) for e in ev]
@@ -432,7 +430,7 @@ def main():
     n = cfg["batch"]
     if args.instances:
         n = min(n, args.instances)
-    batch = inputs.make_batch(args.workload, range(rank * n, (rank + 1) * n))
+    batch = inputs.make_batch(args.workload, shard.shard_indices(n, rank))
     nrhs = len(batch.rhs)
     stages = int(batch.N.sum())
     # KKT right-hand sides of the original problem, built on the device by the library
@@ -458,16 +456,13 @@ def main():
     head = methods[0]
     R = results[head]
     ms = R["total_ms"] / args.steps
-    value = world * batch.size / (ms / 1e3)
+    value = shard.job_throughput(batch.size, world, ms)
 
     e2e = None
     if not args.no_e2e:
         e2e_ms, h2d, d2h = run_e2e(torch, cyq, batch, head, max(3, args.steps // 4), args.warmup,
                                    adjoint=prof["adjoint"])
-        if dist is not None:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = shard.reduce_time_ms(e2e_ms, dist, device="cuda")
         e2e = {"value": world * batch.size / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 

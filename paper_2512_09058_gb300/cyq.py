@@ -133,6 +133,7 @@ class Solver:
         self._h = h
         self.kkt_size = int(L.cyq_kkt_size(h))
         self._data = None
+        self.factor_version = 0
 
     def close(self):
         if getattr(self, "_h", None):
@@ -158,6 +159,7 @@ class Solver:
         self._data = (Q, R, S, A, B, Sigma)   # borrowed until the last solve
         _check(_lib.cyq_factor(self._h, _ptr(Q), _ptr(R), _ptr(S), _ptr(A), _ptr(B), _ptr(Sigma),
                                _stream(stream)))
+        self.factor_version += 1
 
     def solve(self, b, z=None, nrhs: int = 1, stream=None):
         import torch

@@ -38,7 +38,7 @@ import numpy as np
 
 __all__ = [
     "OCPInstance", "Batch", "CONFIGS", "make_instance", "make_batch",
-    "config_dims", "blocks_to_flat", "flat_to_blocks",
+    "config_dims", "instance_dims", "blocks_to_flat", "flat_to_blocks",
 ]
 
 
@@ -159,17 +159,24 @@ CONFIGS = {
 _DIMS_STREAM = 0x5EED_D135
 
 
-def config_dims(cfg: dict, batch: Optional[int] = None):
-    """Per-instance (N, nx, nu) arrays of a config (uniform or drawn)."""
-    b = cfg["batch"] if batch is None else batch
+def instance_dims(cfg: dict, index: int):
+    """(N, nx, nu) of instance ``index``: fixed, or drawn from the instance's own
+    dimension stream (config seed, dims, index) for uneven workloads."""
     if isinstance(cfg["N"], tuple):
-        g = np.random.Generator(np.random.PCG64([cfg["seed"], _DIMS_STREAM]))
-        N = g.integers(cfg["N"][0], cfg["N"][1], size=cfg["batch"], endpoint=True)
-        nx = g.integers(cfg["nx"][0], cfg["nx"][1], size=cfg["batch"], endpoint=True)
-        nu = g.integers(cfg["nu"][0], cfg["nu"][1], size=cfg["batch"], endpoint=True)
-        return (N[:b].astype(np.int32), nx[:b].astype(np.int32), nu[:b].astype(np.int32))
-    return (np.full(b, cfg["N"], np.int32), np.full(b, cfg["nx"], np.int32),
-            np.full(b, cfg["nu"], np.int32))
+        g = np.random.Generator(np.random.PCG64([cfg["seed"], _DIMS_STREAM, index]))
+        N = int(g.integers(cfg["N"][0], cfg["N"][1], endpoint=True))
+        nx = int(g.integers(cfg["nx"][0], cfg["nx"][1], endpoint=True))
+        nu = int(g.integers(cfg["nu"][0], cfg["nu"][1], endpoint=True))
+        return N, nx, nu
+    return int(cfg["N"]), int(cfg["nx"]), int(cfg["nu"])
+
+
+def config_dims(cfg: dict, batch: Optional[int] = None, indices: Optional[Sequence[int]] = None):
+    """Per-instance (N, nx, nu) arrays of a config (instances 0..batch-1 or ``indices``)."""
+    if indices is None:
+        indices = range(cfg["batch"] if batch is None else batch)
+    d = np.array([instance_dims(cfg, int(i)) for i in indices], dtype=np.int32).reshape(-1, 3)
+    return d[:, 0].copy(), d[:, 1].copy(), d[:, 2].copy()
 
 
 def _spd(g, count, n):
@@ -188,11 +195,7 @@ def make_instance(cfg, index: int, *, N: Optional[int] = None, nx: Optional[int]
     """
     if isinstance(cfg, str):
         cfg = CONFIGS[cfg]
-    if isinstance(cfg["N"], tuple):
-        Ns, nxs, nus = config_dims(cfg)
-        dN, dnx, dnu = int(Ns[index]), int(nxs[index]), int(nus[index])
-    else:
-        dN, dnx, dnu = cfg["N"], cfg["nx"], cfg["nu"]
+    dN, dnx, dnu = instance_dims(cfg, index)
     N = dN if N is None else int(N)
     nx = dnx if nx is None else int(nx)
     nu = dnu if nu is None else int(nu)
