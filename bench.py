@@ -45,6 +45,9 @@ WORKLOAD = "batch1024_n64_nx12_nu4"
 # method -> (factor precision, refinement step budget).  Float64 refinement
 # converges in one step here; float32 needs ~5 at cond(K) ~ 1e11.
 METHODS = {"fp64": ("fp64", 0), "fp64_refine": ("fp64", 3), "fp32_refine": ("fp32_refine", 8)}
+# refinement target: the metric's gate, as evaluated by the library's float64
+# residual kernel
+REFINE_TOL = 1e-10
 # workload -> methods (first = headline), CUDA-graph replay, adjoint in the step
 WORKLOADS = {
     "batch1024_n64_nx12_nu4": dict(methods=["fp64_refine", "fp64", "fp32_refine"], graph=False, adjoint=False),
@@ -233,7 +236,8 @@ def run_method(torch, cyq, batch, data, b, x0, method, steps, warmup, dist, grap
     the step time is the sum of the per-step event intervals."""
     precision, it_max = METHODS[method]
     nrhs = len(batch.rhs)
-    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, max_nrhs=nrhs, it_max=it_max)
+    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, max_nrhs=nrhs, it_max=it_max,
+                   tol=REFINE_TOL)
     z = torch.empty_like(b)
     mask = _loss_grad(torch, batch, torch.ones_like(b[:s.kkt_size])) / 2.0 if adjoint else None
 
@@ -328,7 +332,8 @@ def run_e2e(torch, cyq, batch, method, steps, warmup, adjoint=False):
     right-hand sides, factors, solves and copies z back to pinned memory."""
     precision, it_max = METHODS[method]
     nrhs = len(batch.rhs)
-    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, max_nrhs=nrhs, it_max=it_max)
+    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, max_nrhs=nrhs, it_max=it_max,
+                   tol=REFINE_TOL)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     host = {k: pin(getattr(batch, k)) for k in ("Q", "R", "S", "A", "B")}
     host["Sigma"] = pin(batch.Sigma) if batch.Sigma is not None else None

@@ -76,6 +76,24 @@ __device__ __forceinline__ void tri_index(int e, int &r, int &c) {
     c = e - rr * (rr + 1) / 2;
 }
 
+// Leading dimension of a shared-memory tile with `rows` rows: rounded up to an
+// odd number, so that threads walking a row (stride = ld) hit distinct banks.
+__host__ __device__ __forceinline__ int pad_ld(int rows) { return rows | 1; }
+
+// Column-major walk of an m x n grid: element e = threadIdx.x, then steps of
+// `step`; (r, c) advance without integer division.
+__device__ __forceinline__ void rect_start(int e, int m, int &r, int &c) {
+    c = e / m;
+    r = e - c * m;
+}
+__device__ __forceinline__ void rect_advance(int &r, int &c, int m, int step) {
+    r += step;
+    while (r >= m) {
+        r -= m;
+        ++c;
+    }
+}
+
 // Move (r, c) forward by `step` elements in that row order.  Threads start
 // at tri_index(threadIdx.x) and step by the team size, so the mapping is
 // computed once instead of once per element.
@@ -207,13 +225,19 @@ __device__ void team_trtri_lower(T *Tinv, int ldt, const T *L, int ldl, int n, c
 template <typename T, int TEAM>
 __device__ void team_gemm_nn(T *C, int ldc, const T *A, int lda, const T *B, int ldb, int m, int n, int k,
                              int mode) {
-    const int cnt = m * n;
-    for (int e = threadIdx.x; e < cnt; e += TEAM) {
-        const int r = e % m, c = e / m;
-        T s = T(0);
-        for (int t = 0; t < k; ++t) s += A[r + t * lda] * B[t + c * ldb];
-        T *o = C + r + c * ldc;
-        *o = mode == 0 ? s : (mode > 0 ? *o + s : *o - s);
+    int r, c;
+    rect_start(threadIdx.x, m, r, c);
+    for (; c < n; rect_advance(r, c, m, TEAM)) {
+        T s = mode == 0 ? T(0) : C[r + c * ldc];
+        const T *a = A + r, *b = B + c * ldb;
+        if (mode >= 0) {
+#pragma unroll 4
+            for (int t = 0; t < k; ++t) s = fma(a[t * lda], b[t], s);
+        } else {
+#pragma unroll 4
+            for (int t = 0; t < k; ++t) s = fma(-a[t * lda], b[t], s);
+        }
+        C[r + c * ldc] = s;
     }
     team_sync();
 }
@@ -222,13 +246,19 @@ __device__ void team_gemm_nn(T *C, int ldc, const T *A, int lda, const T *B, int
 template <typename T, int TEAM>
 __device__ void team_gemm_nt(T *C, int ldc, const T *A, int lda, const T *B, int ldb, int m, int n, int k,
                              int mode) {
-    const int cnt = m * n;
-    for (int e = threadIdx.x; e < cnt; e += TEAM) {
-        const int r = e % m, c = e / m;
-        T s = T(0);
-        for (int t = 0; t < k; ++t) s += A[r + t * lda] * B[c + t * ldb];
-        T *o = C + r + c * ldc;
-        *o = mode == 0 ? s : (mode > 0 ? *o + s : *o - s);
+    int r, c;
+    rect_start(threadIdx.x, m, r, c);
+    for (; c < n; rect_advance(r, c, m, TEAM)) {
+        T s = mode == 0 ? T(0) : C[r + c * ldc];
+        const T *a = A + r, *b = B + c;
+        if (mode >= 0) {
+#pragma unroll 4
+            for (int t = 0; t < k; ++t) s = fma(a[t * lda], b[t * ldb], s);
+        } else {
+#pragma unroll 4
+            for (int t = 0; t < k; ++t) s = fma(-a[t * lda], b[t * ldb], s);
+        }
+        C[r + c * ldc] = s;
     }
     team_sync();
 }
@@ -240,7 +270,9 @@ __device__ void team_syrk_lower(TC *C, int ldc, const T *A, int lda, int n, int 
     tri_index(threadIdx.x, r, c);
     for (; r < n; tri_advance(r, c, TEAM)) {
         T s = T(0);
-        for (int t = 0; t < k; ++t) s += A[r + t * lda] * A[c + t * lda];
+        const T *a = A + r, *b = A + c;
+#pragma unroll 4
+        for (int t = 0; t < k; ++t) s = fma(a[t * lda], b[t * lda], s);
         TC *o = C + r + c * ldc;
         *o = mode == 0 ? (TC)s : (mode > 0 ? *o + (TC)s : *o - (TC)s);
     }

@@ -104,24 +104,51 @@ __device__ __forceinline__ double stage_H(const StageSrc &src, int nu, int nx, i
     return src.Q[i + j * nx] + ((i == j && src.Sx) ? src.Sx[i] : 0.0);
 }
 
-// [B A] (nx x (nu+nx), ld nx) of a stage into T storage.
+// [B A] (nx x (nu+nx)) of a stage into T storage with leading dimension ld.
 template <typename T, int TEAM>
-__device__ void fill_BA(T *BA, const StageSrc &src, int nx, int nu) {
-    for (int e = threadIdx.x; e < nx * nu; e += TEAM) BA[e] = (T)src.B[e];
-    for (int e = threadIdx.x; e < nx * nx; e += TEAM) BA[nx * nu + e] = src.A ? (T)src.A[e] : T(0);
+__device__ void fill_BA(T *BA, int ld, const StageSrc &src, int nx, int nu) {
+    int r, c;
+    rect_start(threadIdx.x, nx, r, c);
+    for (; c < nu; rect_advance(r, c, nx, TEAM)) BA[r + c * ld] = (T)src.B[r + c * nx];
+    rect_start(threadIdx.x, nx, r, c);
+    for (; c < nx; rect_advance(r, c, nx, TEAM)) BA[r + (nu + c) * ld] = src.A ? (T)src.A[r + c * nx] : T(0);
 }
 
 template <typename T, int TEAM>
 __device__ void store_block(T *dst, const T *src, int rows, int cols, int ld) {
-    for (int e = threadIdx.x; e < rows * cols; e += TEAM) dst[e] = src[(e % rows) + (e / rows) * ld];
+    int r, c;
+    rect_start(threadIdx.x, rows, r, c);
+    for (; c < cols; rect_advance(r, c, rows, TEAM)) dst[r + c * rows] = src[r + c * ld];
 }
 
 template <typename T, int TEAM>
 __device__ void store_block_f64(double *dst, const T *src, int rows, int cols, int ld) {
-    for (int e = threadIdx.x; e < rows * cols; e += TEAM) dst[e] = (double)src[(e % rows) + (e / rows) * ld];
+    int r, c;
+    rect_start(threadIdx.x, rows, r, c);
+    for (; c < cols; rect_advance(r, c, rows, TEAM)) dst[r + c * rows] = (double)src[r + c * ld];
 }
 
 }  // namespace
+
+// Shared-memory tiles of one work item (T = factor precision).  Every tile
+// has an odd leading dimension (pad_ld) except the aliased raw [B A] copy.
+struct FactorTiles {
+    int ldH, ldV, ldG, ldT;
+    size_t nH, nVG, nG, nBA;   // elements
+    __host__ __device__ FactorTiles(int nx, int nu, bool need_G2, bool ba_alias) {
+        const int nux = nx + nu;
+        ldH = pad_ld(nux);
+        ldV = pad_ld(nux);
+        ldG = pad_ld(nx);
+        ldT = pad_ld(nx);
+        nH = (size_t)ldH * nux;
+        const size_t nV = (size_t)ldV * nx, nGg = (size_t)ldG * nux;
+        // without A^cl propagation [B^ A^] lives only until V is formed: one shared tile
+        nVG = need_G2 ? nV : (nV > nGg ? nV : nGg);
+        nG = need_G2 ? 2 * nGg : 0;
+        nBA = ba_alias ? 0 : nGg;
+    }
+};
 
 template <typename T, int TEAM>
 __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
@@ -140,16 +167,18 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
         // [B A] of the next stage: aliased to the staged float64 copy, or
         // converted into its own shared-memory tile.
         const bool ba_alias = staged && sizeof(T) == 8;
+        const FactorTiles TL(nx, nu, a.need_G2, ba_alias);
+        const int ldH = TL.ldH, ldV = TL.ldV, ldG = TL.ldG, ldT = TL.ldT;
         double *buf = reinterpret_cast<double *>(smem_raw);         // raw stage copy (staged mode)
         double *Mf = buf + (staged ? SL.size : 0);                   // nx x nx float64 accumulator
         T *H = reinterpret_cast<T *>(Mf + nx * nx);                  // nux x nux (stage Hessian -> factor)
-        T *V = H + nux * nux;                                        // nux x nx
-        // [B^ A^] -> [L^B A^cl]: without A^cl propagation it is only used at the
-        // first stage, before V is formed, so it shares V's tile
-        T *G = a.need_G2 ? V + nux * nx : V;                         // nx x nux
-        T *G2 = G + nx * nux;                                        // nx x nux  (next [B^ A^], P > 1)
-        T *BAc = a.need_G2 ? G2 + nx * nux : V + nux * nx;           // nx x nux  ([B A] tile)
-        T *dinv = BAc + (ba_alias ? 0 : nx * nux);                   // nux
+        T *V = H + TL.nH;                                            // nux x nx
+        // [B^ A^] -> [L^B A^cl]; without propagation it shares V's tile (used before V is formed)
+        T *G = a.need_G2 ? V + TL.nVG : V;                           // nx x nux
+        T *G2 = G + (a.need_G2 ? TL.nG / 2 : 0);                     // nx x nux  (next [B^ A^], P > 1)
+        T *BAc = V + TL.nVG + TL.nG;                                 // nx x nux  ([B A] tile)
+        T *dinv = BAc + TL.nBA;                                      // nux
+        const int ldBA = ba_alias ? nx : ldG;
 
         T *Lg = reinterpret_cast<T *>(a.L) + in.oL;
         T *LBg = reinterpret_cast<T *>(a.LB) + in.oLB;
@@ -172,8 +201,8 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
         {
             int r, q;
             tri_index(threadIdx.x, r, q);
-            for (; r < nux; tri_advance(r, q, TEAM)) H[r + q * nux] = (T)stage_H(src, nu, nx, r, q);
-            fill_BA<T, TEAM>(G, src, nx, nu);
+            for (; r < nux; tri_advance(r, q, TEAM)) H[r + q * ldH] = (T)stage_H(src, nu, nx, r, q);
+            fill_BA<T, TEAM>(G, ldG, src, nx, nu);
         }
         team_sync();
 
@@ -188,17 +217,17 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 // the copy of the next stage overlaps with the factorization below
                 if (staged) prefetch_stage<TEAM>(buf, SL, a.data, in, s2);
             }
-            ok &= team_chol<T, TEAM>(H, nux, nux, dinv);
-            store_block<T, TEAM>(Lg + (long long)s * nux * nux, H, nux, nux, nux);
+            ok &= team_chol<T, TEAM>(H, nux, ldH, dinv);
+            store_block<T, TEAM>(Lg + (long long)s * nux * nux, H, nux, nux, ldH);
             for (int i = threadIdx.x; i < nux; i += TEAM) DIg[(long long)s * nux + i] = dinv[i];
             if (hasG) {
                 // L^B = B^ L^{R-T}
-                team_trsm_rlt<T, TEAM>(G, nx, nu, nx, H, nux, dinv);
+                team_trsm_rlt<T, TEAM>(G, nx, nu, ldG, H, ldH, dinv);
                 // A^cl = A^ - L^B L^{S T}   (L^S = rows nu.. of columns 0..nu-1)
-                team_gemm_nt<T, TEAM>(G + nx * nu, nx, G, nx, H + nu, nux, nx, nx, nu, -1);
-                store_block<T, TEAM>(LBg + (long long)s * nx * nu, G, nx, nu, nx);
-                team_syrk_lower<T, double, TEAM>(Mf, nx, G, nx, nx, nu, +1);
-                if (propagate && !last) store_block<T, TEAM>(Fg + (long long)s * nx * nx, G + nx * nu, nx, nx, nx);
+                team_gemm_nt<T, TEAM>(G + ldG * nu, ldG, G, ldG, H + nu, ldH, nx, nx, nu, -1);
+                store_block<T, TEAM>(LBg + (long long)s * nx * nu, G, nx, nu, ldG);
+                team_syrk_lower<T, double, TEAM>(Mf, nx, G, ldG, nx, nu, +1);
+                if (propagate && !last) store_block<T, TEAM>(Fg + (long long)s * nx * nx, G + ldG * nu, nx, nx, ldG);
             }
             if (!last) {
                 if (staged) {
@@ -213,82 +242,97 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 if (ba_alias) {
                     BA = reinterpret_cast<const T *>(src.B);
                 } else {
-                    fill_BA<T, TEAM>(BAc, src, nx, nu);
+                    fill_BA<T, TEAM>(BAc, ldBA, src, nx, nu);
                     team_sync();
                     BA = BAc;
                 }
                 // V = [B A]^T L^Q : V[a][j] = sum_{k >= j} BA[k][a] L^Q[k][j]
-                const T *LQ = H + nu + nu * nux;
-                for (int e = threadIdx.x; e < nux * nx; e += TEAM) {
-                    const int aa = e % nux, j = e / nux;
-                    T acc = T(0);
-                    for (int k = j; k < nx; ++k) acc = fma(BA[k + aa * nx], LQ[k + j * nux], acc);
-                    V[aa + j * nux] = acc;
+                const T *LQ = H + nu + nu * ldH;
+                {
+                    int aa, j;
+                    rect_start(threadIdx.x, nux, aa, j);
+                    for (; j < nx; rect_advance(aa, j, nux, TEAM)) {
+                        const T *ba = BA + aa * ldBA, *lq = LQ + j * ldH;
+                        T acc = T(0);
+#pragma unroll 4
+                        for (int k = j; k < nx; ++k) acc = fma(ba[k], lq[k], acc);
+                        V[aa + j * ldV] = acc;
+                    }
                 }
                 if (propagate) {
                     // [B^ A^]_{s2} = A^cl [B A]_{s2}
-                    team_gemm_nn<T, TEAM>(G2, nx, G + nx * nu, nx, BA, nx, nx, nux, nx, 0);
+                    team_gemm_nn<T, TEAM>(G2, ldG, G + ldG * nu, ldG, BA, ldBA, nx, nux, nx, 0);
                 } else {
                     team_sync();
                 }
                 // H^_{s2} = H_{s2} + V V^T  (lower triangle, straight from the raw record)
-                int r, q;
-                tri_index(threadIdx.x, r, q);
-                for (; r < nux; tri_advance(r, q, TEAM)) {
-                    T acc = (T)stage_H(src, nu, nx, r, q);
-                    for (int k = 0; k < nx; ++k) acc = fma(V[r + k * nux], V[q + k * nux], acc);
-                    H[r + q * nux] = acc;
+                {
+                    int r, q;
+                    tri_index(threadIdx.x, r, q);
+                    for (; r < nux; tri_advance(r, q, TEAM)) {
+                        T acc = (T)stage_H(src, nu, nx, r, q);
+                        const T *vr = V + r, *vq = V + q;
+#pragma unroll 4
+                        for (int k = 0; k < nx; ++k) acc = fma(vr[k * ldV], vq[k * ldV], acc);
+                        H[r + q * ldH] = acc;
+                    }
                 }
                 team_sync();
                 if (a.need_G2) {
                     T *tmp = G; G = G2; G2 = tmp;
                 }
             } else {
-                const T *LQ = H + nu + nu * nux;
+                const T *LQ = H + nu + nu * ldH;
                 const T *dq = dinv + nu;
-                T *LA = G + nx * nu;
+                T *LA = G + ldG * nu;
                 if (propagate) {
                     // L^A = A^cl L^{Q-T}, stored in place of A^cl of the first stage
-                    team_trsm_rlt<T, TEAM>(LA, nx, nx, nx, LQ, nux, dq);
-                    store_block<T, TEAM>(Fg + (long long)s * nx * nx, LA, nx, nx, nx);
-                    team_syrk_lower<T, double, TEAM>(Mf, nx, LA, nx, nx, nx, +1);
+                    team_trsm_rlt<T, TEAM>(LA, nx, nx, ldG, LQ, ldH, dq);
+                    store_block<T, TEAM>(Fg + (long long)s * nx * nx, LA, nx, nx, ldG);
+                    team_syrk_lower<T, double, TEAM>(Mf, nx, LA, ldG, nx, nx, +1);
                 }
-                // Tinv = L^{Q -1}  (in V; L^Q is not needed after this)
+                // Tinv = L^{Q -1}  (in V's tile; L^Q is not needed after this)
                 T *Ti = V;
-                team_trtri_lower<T, TEAM>(Ti, nx, LQ, nux, nx, dq);
-                // M_bwd = Tinv^T Tinv  (full symmetric, in the H buffer)
+                team_trtri_lower<T, TEAM>(Ti, ldT, LQ, ldH, nx, dq);
+                // M_bwd = Tinv^T Tinv  (full symmetric, in the H tile, leading dimension ldT)
                 T *Mb = H;
-                for (int e = threadIdx.x; e < nx * nx; e += TEAM) {
-                    const int i = e % nx, j = e / nx;
-                    const int k0 = i > j ? i : j;
-                    T acc = T(0);
-                    for (int k = k0; k < nx; ++k) acc = fma(Ti[k + i * nx], Ti[k + j * nx], acc);
-                    Mb[e] = acc;
+                {
+                    int i, j;
+                    rect_start(threadIdx.x, nx, i, j);
+                    for (; j < nx; rect_advance(i, j, nx, TEAM)) {
+                        const int k0 = i > j ? i : j;
+                        T acc = T(0);
+                        for (int k = k0; k < nx; ++k) acc = fma(Ti[k + i * ldT], Ti[k + j * ldT], acc);
+                        Mb[i + j * ldT] = acc;
+                    }
                 }
                 team_sync();
                 const int cb = (c - 1 + P) % P;
-                store_block_f64<T, TEAM>(a.Mb + in.oBlk + (long long)cb * nx * nx, Mb, nx, nx, nx);
+                store_block_f64<T, TEAM>(a.Mb + in.oBlk + (long long)cb * nx * nx, Mb, nx, nx, ldT);
                 team_symmetrize<double, TEAM>(Mf, nx, nx);
                 if (P == 1) {
                     // single coupling block: M = M_fwd + M_bwd, factor it (float64)
-                    for (int e = threadIdx.x; e < nx * nx; e += TEAM) Mf[e] += (double)Mb[e];
+                    int i, j;
+                    rect_start(threadIdx.x, nx, i, j);
+                    for (; j < nx; rect_advance(i, j, nx, TEAM)) Mf[i + j * nx] += (double)Mb[i + j * ldT];
                     team_sync();
                     ok &= team_chol<double, TEAM>(Mf, nx, nx);
                 }
                 double *dst = a.Mf + in.oBlk + (long long)c * nx * nx;
                 for (int e = threadIdx.x; e < nx * nx; e += TEAM) dst[e] = Mf[e];
                 if (propagate) {
-                    // K = -L^A Tinv (row lambda^{b_c}, column lambda^{b_{c-1}}), reusing the H buffer
+                    // K = -L^A Tinv (row lambda^{b_c}, column lambda^{b_{c-1}}), reusing the H tile
                     team_sync();   // M_bwd has been read
                     T *Kb = H;
-                    for (int e = threadIdx.x; e < nx * nx; e += TEAM) {
-                        const int i = e % nx, j = e / nx;
+                    int i, j;
+                    rect_start(threadIdx.x, nx, i, j);
+                    for (; j < nx; rect_advance(i, j, nx, TEAM)) {
                         T acc = T(0);
-                        for (int k = j; k < nx; ++k) acc = fma(LA[i + k * nx], Ti[k + j * nx], acc);
-                        Kb[e] = -acc;
+                        for (int k = j; k < nx; ++k) acc = fma(LA[i + k * ldG], Ti[k + j * ldT], acc);
+                        Kb[i + j * ldT] = -acc;
                     }
                     team_sync();
-                    store_block_f64<T, TEAM>(a.Kc + in.oBlk + (long long)c * nx * nx, Kb, nx, nx, nx);
+                    store_block_f64<T, TEAM>(a.Kc + in.oBlk + (long long)c * nx * nx, Kb, nx, nx, ldT);
                 }
             }
         }
@@ -307,9 +351,9 @@ size_t factor_stage_bytes(int nx, int nu) {
 size_t factor_smem_bytes(bool fp64, int nx, int nu, bool staged, bool need_G2) {
     const size_t nux = (size_t)nx + nu;
     const size_t el = fp64 ? 8 : 4;
-    const bool ba_alias = staged && fp64;
+    const FactorTiles TL(nx, nu, need_G2, staged && fp64);
     size_t bytes = (staged ? factor_stage_bytes(nx, nu) : 0) + (size_t)nx * nx * 8;
-    bytes += (nux * nux + nux * nx + (need_G2 ? 2 * nx * nux : 0) + (ba_alias ? 0 : nx * nux) + nux) * el;
+    bytes += (TL.nH + TL.nVG + TL.nG + TL.nBA + nux) * el;
     return (bytes + 15) / 16 * 16;
 }
 

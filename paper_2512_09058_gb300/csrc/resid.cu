@@ -14,83 +14,168 @@
 namespace cyq {
 
 
+// Rows are processed one kind at a time (u rows, then x rows, then lambda rows)
+// so that a warp runs one code path: a divergent FP64 instruction costs a
+// full warp slot per path.  Up to RG right-hand sides share every matrix load.
+constexpr int RG = 4;
+
 template <int TEAM>
-__global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a) {
-    __shared__ double red_r[TEAM / 32], red_b[TEAM / 32];
+__global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
+    __shared__ double red[2 * RG][TEAM / 32];
     const Chunk ch = a.chunks[blockIdx.x];
-    const int rhs = blockIdx.y;
     if (a.skip && a.skip[ch.inst]) return;
+    const int r0 = blockIdx.y * RG;
+    const int nr = min(RG, nrhs - r0);
     const Inst in = a.inst[ch.inst];
     const int N = in.N, nx = in.nx, nu = in.nu, w = nu + 2 * nx;
     const Data &d = a.data;
-    const double *z = a.z + rhs * a.kkt + in.oZ, *b = a.b + rhs * a.kkt + in.oZ;
-    double sr = 0.0, sb = 0.0;
-    const int rows = (ch.k1 - ch.k0) * w;
-    for (int e = threadIdx.x; e < rows; e += TEAM) {
-        const int k = ch.k0 + e / w, row = e % w;
-        const double *zk = z + (long long)k * w;
-        double acc;
-        if (row < nu) {
-            const int i = row;
-            const double *R = d.R + in.oR + (long long)k * nu * nu;
-            const double *B = d.B + in.oB + (long long)k * nx * nu;
-            acc = 0.0;
-            for (int j = 0; j < nu; ++j) acc += R[i + j * nu] * zk[j];
-            if (d.Sig) acc += d.Sig[in.oSig + (long long)k * (nu + nx) + i] * zk[i];
-            if (k > 0 && d.S) {
-                const double *S = d.S + in.oS + (long long)k * nu * nx;
-                const double *xk = zk - w + nu;
-                for (int j = 0; j < nx; ++j) acc += S[i + j * nu] * xk[j];
-            }
-            const double *lam = zk + nu + nx;
-            for (int j = 0; j < nx; ++j) acc += B[j + i * nx] * lam[j];
-        } else if (row < nu + nx) {
-            const int i = row - nu, j1 = k + 1;
-            const double *Q = d.Q + in.oQ + (long long)j1 * nx * nx;
-            const double *x = zk + nu;
-            acc = -zk[nu + nx + i];
-            for (int m = 0; m < nx; ++m) acc += Q[i + m * nx] * x[m];
-            if (d.Sig) acc += d.Sig[in.oSig + (long long)j1 * (nu + nx) + nu + i] * x[i];
-            if (j1 < N) {
-                const double *zn = zk + w;
-                const double *A = d.A + in.oA + (long long)j1 * nx * nx;
-                for (int m = 0; m < nx; ++m) acc += A[m + i * nx] * zn[nu + nx + m];
-                if (d.S) {
-                    const double *S = d.S + in.oS + (long long)j1 * nu * nx;
-                    for (int m = 0; m < nu; ++m) acc += S[m + i * nu] * zn[m];
-                }
-            }
-        } else {
-            const int i = row - nu - nx;
-            const double *B = d.B + in.oB + (long long)k * nx * nu;
-            acc = -zk[nu + i];
-            for (int m = 0; m < nu; ++m) acc += B[i + m * nx] * zk[m];
-            if (k > 0) {
-                const double *A = d.A + in.oA + (long long)k * nx * nx;
-                const double *xk = zk - w + nu;
-                for (int m = 0; m < nx; ++m) acc += A[i + m * nx] * xk[m];
+    const double *zb = a.z + in.oZ, *bb = a.b + in.oZ;
+    const long long kk = a.kkt;
+    const int nrec = ch.k1 - ch.k0;
+    double sr[RG], sb[RG];
+#pragma unroll
+    for (int r = 0; r < RG; ++r) sr[r] = sb[r] = 0.0;
+
+    auto finish_row = [&](int k, int row, const double *acc) {
+#pragma unroll
+        for (int r = 0; r < RG; ++r) {
+            if (r < nr) {
+                const long long o = (long long)(r0 + r) * kk + (long long)k * w + row;
+                const double bv = bb[o];
+                const double rv = bv - acc[r];
+                if (a.r) a.r[in.oZ + o] = rv;
+                sr[r] = fma(rv, rv, sr[r]);
+                sb[r] = fma(bv, bv, sb[r]);
             }
         }
-        const double bv = b[(long long)k * w + row];
-        const double rv = bv - acc;
-        if (a.r) a.r[rhs * a.kkt + in.oZ + (long long)k * w + row] = rv;
-        sr += rv * rv;
-        sb += bv * bv;
+    };
+
+    // u^k rows: R_k u^k + Sigma_u u^k + S_k x^k + B_k^T lambda^k
+    {
+        int i, q;
+        rect_start(threadIdx.x, nu, i, q);
+        for (; q < nrec; rect_advance(i, q, nu, TEAM)) {
+            const int k = ch.k0 + q;
+            const double *R = d.R + in.oR + (long long)k * nu * nu;
+            const double *B = d.B + in.oB + (long long)k * nx * nu;
+            double acc[RG];
+#pragma unroll
+            for (int r = 0; r < RG; ++r) acc[r] = 0.0;
+            const double sg = d.Sig ? d.Sig[in.oSig + (long long)k * (nu + nx) + i] : 0.0;
+            for (int j = 0; j < nu; ++j) {
+                const double m = R[i + j * nu] + (j == i ? sg : 0.0);
+#pragma unroll
+                for (int r = 0; r < RG; ++r)
+                    if (r < nr) acc[r] = fma(m, zb[(r0 + r) * kk + (long long)k * w + j], acc[r]);
+            }
+            if (k > 0 && d.S) {
+                const double *S = d.S + in.oS + (long long)k * nu * nx;
+                for (int j = 0; j < nx; ++j) {
+                    const double m = S[i + j * nu];
+#pragma unroll
+                    for (int r = 0; r < RG; ++r)
+                        if (r < nr) acc[r] = fma(m, zb[(r0 + r) * kk + (long long)(k - 1) * w + nu + j], acc[r]);
+                }
+            }
+            for (int j = 0; j < nx; ++j) {
+                const double m = B[j + i * nx];
+#pragma unroll
+                for (int r = 0; r < RG; ++r)
+                    if (r < nr) acc[r] = fma(m, zb[(r0 + r) * kk + (long long)k * w + nu + nx + j], acc[r]);
+            }
+            finish_row(k, i, acc);
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        sr += __shfl_xor_sync(0xffffffffu, sr, o);
-        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    // x^{k+1} rows: Q x - lambda^k (+ S_{k+1}^T u^{k+1} + A_{k+1}^T lambda^{k+1} when k+1 < N)
+    {
+        int i, q;
+        rect_start(threadIdx.x, nx, i, q);
+        for (; q < nrec; rect_advance(i, q, nx, TEAM)) {
+            const int k = ch.k0 + q, j1 = k + 1;
+            const double *Q = d.Q + in.oQ + (long long)j1 * nx * nx;
+            double acc[RG];
+#pragma unroll
+            for (int r = 0; r < RG; ++r)
+                acc[r] = r < nr ? -zb[(r0 + r) * kk + (long long)k * w + nu + nx + i] : 0.0;
+            const double sg = d.Sig ? d.Sig[in.oSig + (long long)j1 * (nu + nx) + nu + i] : 0.0;
+            for (int m = 0; m < nx; ++m) {
+                const double v = Q[i + m * nx] + (m == i ? sg : 0.0);
+#pragma unroll
+                for (int r = 0; r < RG; ++r)
+                    if (r < nr) acc[r] = fma(v, zb[(r0 + r) * kk + (long long)k * w + nu + m], acc[r]);
+            }
+            if (j1 < N) {
+                const double *A = d.A + in.oA + (long long)j1 * nx * nx;
+                for (int m = 0; m < nx; ++m) {
+                    const double v = A[m + i * nx];
+#pragma unroll
+                    for (int r = 0; r < RG; ++r)
+                        if (r < nr) acc[r] = fma(v, zb[(r0 + r) * kk + (long long)j1 * w + nu + nx + m], acc[r]);
+                }
+                if (d.S) {
+                    const double *S = d.S + in.oS + (long long)j1 * nu * nx;
+                    for (int m = 0; m < nu; ++m) {
+                        const double v = S[m + i * nu];
+#pragma unroll
+                        for (int r = 0; r < RG; ++r)
+                            if (r < nr) acc[r] = fma(v, zb[(r0 + r) * kk + (long long)j1 * w + m], acc[r]);
+                    }
+                }
+            }
+            finish_row(k, nu + i, acc);
+        }
     }
-    if ((threadIdx.x & 31) == 0) {
-        red_r[threadIdx.x >> 5] = sr;
-        red_b[threadIdx.x >> 5] = sb;
+    // lambda^k rows: B_k u^k + A_k x^k - x^{k+1}  (no A_0 x^0 term)
+    {
+        int i, q;
+        rect_start(threadIdx.x, nx, i, q);
+        for (; q < nrec; rect_advance(i, q, nx, TEAM)) {
+            const int k = ch.k0 + q;
+            const double *B = d.B + in.oB + (long long)k * nx * nu;
+            double acc[RG];
+#pragma unroll
+            for (int r = 0; r < RG; ++r) acc[r] = r < nr ? -zb[(r0 + r) * kk + (long long)k * w + nu + i] : 0.0;
+            for (int m = 0; m < nu; ++m) {
+                const double v = B[i + m * nx];
+#pragma unroll
+                for (int r = 0; r < RG; ++r)
+                    if (r < nr) acc[r] = fma(v, zb[(r0 + r) * kk + (long long)k * w + m], acc[r]);
+            }
+            if (k > 0) {
+                const double *A = d.A + in.oA + (long long)k * nx * nx;
+                for (int m = 0; m < nx; ++m) {
+                    const double v = A[i + m * nx];
+#pragma unroll
+                    for (int r = 0; r < RG; ++r)
+                        if (r < nr) acc[r] = fma(v, zb[(r0 + r) * kk + (long long)(k - 1) * w + nu + m], acc[r]);
+                }
+            }
+            finish_row(k, nu + nx + i, acc);
+        }
+    }
+    // per right-hand side block reduction of ||r||^2 and ||b||^2
+#pragma unroll
+    for (int r = 0; r < RG; ++r) {
+        double x = sr[r], y = sb[r];
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[2 * r][threadIdx.x >> 5] = x;
+            red[2 * r + 1][threadIdx.x >> 5] = y;
+        }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < nr) {
+        const int r = threadIdx.x;
         double tr = 0.0, tb = 0.0;
-        for (int i = 0; i < TEAM / 32; ++i) { tr += red_r[i]; tb += red_b[i]; }
-        atomicAdd(a.rr + (long long)rhs * a.batch + ch.inst, tr);
-        atomicAdd(a.bb + (long long)rhs * a.batch + ch.inst, tb);
+        for (int i = 0; i < TEAM / 32; ++i) {
+            tr += red[2 * r][i];
+            tb += red[2 * r + 1][i];
+        }
+        atomicAdd(a.rr + (long long)(r0 + r) * a.batch + ch.inst, tr);
+        atomicAdd(a.bb + (long long)(r0 + r) * a.batch + ch.inst, tb);
     }
 }
 
@@ -266,7 +351,7 @@ __global__ void k_adjoint_dx0(const Inst *inst, int batch, Data d, const double 
 // ---------------------------------------------------------------------------
 cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st) {
     if (a.n_chunks == 0) return cudaSuccess;
-    k_residual<128><<<dim3(a.n_chunks, nrhs), 128, 0, st>>>(a);
+    k_residual<128><<<dim3(a.n_chunks, (nrhs + RG - 1) / RG), 128, 0, st>>>(a, nrhs);
     return cudaGetLastError();
 }
 
