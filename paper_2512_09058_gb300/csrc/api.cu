@@ -30,6 +30,7 @@ struct Group {
     bool need_G2 = false;                      // some item propagates A^cl (P > 1)
     bool staged[2] = {true, true};             // factor stages copied to shared memory, [float, double]
     size_t smem_factor[2] = {0, 0};
+    int solve_nbuf[2] = {2, 2};                // solve stage packages in shared memory, [float, double]
     int max_nx = 0, max_nu = 0;
     std::vector<Item> items;
     Item *d_items = nullptr;
@@ -171,6 +172,7 @@ SolveArgs solve_args(cyq_handle h, const FactorSet &fs, const Group &g, const do
     a.nvec = h->nvec;
     a.skip = skip;
     a.zacc = zacc;
+    a.nbuf = g.solve_nbuf[fs.fp64 ? 1 : 0];
     return a;
 }
 
@@ -180,7 +182,7 @@ cyq_status run_solve(cyq_handle h, const FactorSet &fs, const double *b, double 
                      cudaStream_t st, double *zacc = nullptr) {
     for (const Group &g : h->groups) {
         SolveArgs a = solve_args(h, fs, g, b, z, nrhs, skip, zacc);
-        size_t smem = solve_smem_bytes(fs.fp64, g.max_nx, g.max_nu, nrhs);
+        size_t smem = solve_smem_bytes(fs.fp64, g.max_nx, g.max_nu, nrhs, a.nbuf);
         CYQ_CUDA(launch_solve_backward(fs.fp64, g.team, smem, a, st));
         ++h->launches;
     }
@@ -192,7 +194,7 @@ cyq_status run_solve(cyq_handle h, const FactorSet &fs, const double *b, double 
     }
     for (const Group &g : h->groups) {
         SolveArgs a = solve_args(h, fs, g, b, z, nrhs, skip, zacc);
-        size_t smem = solve_smem_bytes(fs.fp64, g.max_nx, g.max_nu, nrhs);
+        size_t smem = solve_smem_bytes(fs.fp64, g.max_nx, g.max_nu, nrhs, a.nbuf);
         CYQ_CUDA(launch_solve_forward(fs.fp64, g.team, smem, a, st));
         ++h->launches;
     }
@@ -401,8 +403,10 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
             // stage the raw blocks in shared memory while two CTAs still fit on an SM
             g.staged[pi] = factor_smem_bytes(f64, g.max_nx, g.max_nu, true, g.need_G2) <= (size_t)smem_optin / 2;
             g.smem_factor[pi] = factor_smem_bytes(f64, g.max_nx, g.max_nu, g.staged[pi], g.need_G2);
+            // solve: prefetch the next stage while two packages fit, else fetch after use
+            g.solve_nbuf[pi] = solve_smem_bytes(f64, g.max_nx, g.max_nu, h->max_nrhs, 2) <= (size_t)smem_optin ? 2 : 1;
             if (g.smem_factor[pi] > (size_t)smem_optin ||
-                solve_smem_bytes(f64, g.max_nx, g.max_nu, h->max_nrhs) > (size_t)smem_optin) {
+                solve_smem_bytes(f64, g.max_nx, g.max_nu, h->max_nrhs, g.solve_nbuf[pi]) > (size_t)smem_optin) {
                 delete h;
                 g_last_error = "stage blocks too large for shared memory";
                 return CYQ_ERR_INVALID_ARG;

@@ -325,6 +325,7 @@ struct SolveArgs {
     long long nvec;                 // coupling-vector elements per right-hand side
     const int *skip;                // optional per-instance flag: nonzero = leave this instance alone
     double *zacc;                   // optional: add the solution into zacc (z then holds intermediates only)
+    int nbuf;                       // stage packages in shared memory: 2 = prefetch the next stage, 1 = fetch after use
 };
 
 // Level-parallel cyclic reduction plan: jobs (instance, block).  The
@@ -395,6 +396,6 @@ cudaError_t ensure_smem(const void *kernel, size_t bytes);
 // Sets the text returned by cyq_last_error() for the calling thread.
 void set_last_error_message(const char *msg);
 inline void set_last_error_message(const std::string &msg) { set_last_error_message(msg.c_str()); }
-size_t solve_smem_bytes(bool fp64, int nx, int nu, int nrhs);
+size_t solve_smem_bytes(bool fp64, int nx, int nu, int nrhs, int nbuf);
 
 }  // namespace cyq

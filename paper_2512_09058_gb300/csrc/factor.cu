@@ -218,6 +218,17 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 if (staged) prefetch_stage<TEAM>(buf, SL, a.data, in, s2);
             }
             ok &= team_chol<T, TEAM>(H, nux, ldH, dinv);
+            // L^{R-1} (strictly lower part) into the free upper triangle of the R block,
+            // transposed: entry (k, i), k < i, holds (L^{R-1})_{ik}.  The solve sweeps
+            // then apply L^{R-1} and L^{R-T} as parallel matrix-vector products.
+            for (int cc = threadIdx.x; cc < nu; cc += TEAM)
+                for (int i = cc + 1; i < nu; ++i) {
+                    T acc = T(0);
+                    for (int k = cc; k < i; ++k)
+                        acc = fma(-H[i + k * ldH], k == cc ? dinv[cc] : H[cc + k * ldH], acc);
+                    H[cc + i * ldH] = acc * dinv[i];
+                }
+            team_sync();
             store_block<T, TEAM>(Lg + (long long)s * nux * nux, H, nux, nux, ldH);
             for (int i = threadIdx.x; i < nux; i += TEAM) DIg[(long long)s * nux + i] = dinv[i];
             if (hasG) {
@@ -294,6 +305,15 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 // Tinv = L^{Q -1}  (in V's tile; L^Q is not needed after this)
                 T *Ti = V;
                 team_trtri_lower<T, TEAM>(Ti, ldT, LQ, ldH, nx, dq);
+                // and its strictly lower part, transposed, into the upper triangle of the
+                // stored Q block of this (first) stage, for the sweeps' end-of-segment solves
+                {
+                    T *Lq = Lg + (long long)s * nux * nux + nu + nu * nux;
+                    int i, cc;
+                    rect_start(threadIdx.x, nx, i, cc);
+                    for (; cc < nx; rect_advance(i, cc, nx, TEAM))
+                        if (i > cc) Lq[cc + i * nux] = Ti[i + cc * ldT];
+                }
                 // M_bwd = Tinv^T Tinv  (full symmetric, in the H tile, leading dimension ldT)
                 T *Mb = H;
                 {

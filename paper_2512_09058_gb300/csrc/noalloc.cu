@@ -82,8 +82,10 @@ extern "C" cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu
         return fail(CYQ_ERR_NO_DEVICE, "cyq_factor_solve_noalloc: no current CUDA device");
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const bool staged = factor_smem_bytes(true, nx, nu, true, false) <= (size_t)smem_optin / 2;
-    const size_t fs = factor_smem_bytes(true, nx, nu, staged, false), ss = solve_smem_bytes(true, nx, nu, 1);
-    if (fs > (size_t)smem_optin || ss > (size_t)smem_optin)
+    const size_t fs = factor_smem_bytes(true, nx, nu, staged, false), ss1 = solve_smem_bytes(true, nx, nu, 1, 1);
+    const int nbuf = solve_smem_bytes(true, nx, nu, 1, 2) <= (size_t)smem_optin ? 2 : 1;
+    const size_t ss = solve_smem_bytes(true, nx, nu, 1, nbuf);
+    if (fs > (size_t)smem_optin || ss1 > (size_t)smem_optin)
         return fail(CYQ_ERR_INVALID_ARG, "cyq_factor_solve_noalloc: stage blocks too large for shared memory");
 
     // per-device set-up: the device address of the workspace array
@@ -161,6 +163,7 @@ extern "C" cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu
     sa.dF = dF; sa.dB = dB; sa.lam = lam;
     sa.nvec = nx;
     sa.skip = nullptr;
+    sa.nbuf = nbuf;
     if ((e = launch_solve_backward(true, team, ss, sa, st)) != cudaSuccess ||
         (e = launch_cr_solve(1, d_list, 128, (size_t)2 * nx * sizeof(double), sa, st)) != cudaSuccess ||
         (e = launch_solve_forward(true, team, ss, sa, st)) != cudaSuccess)

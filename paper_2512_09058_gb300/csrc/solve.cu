@@ -17,56 +17,117 @@
 //   lambda^{j-1} = L^Q_j L^Q_j^T x^j + p_j + A^{cl T}_j mu   (interior stages),
 //   x^{j+1} = A_j x^j + B_j u^j + c_j.
 // rho_j and p_j are parked in the u / x slots of z between the two sweeps.
-// One CTA per (instance, segment); nrhs right-hand sides share each factor load.
+//
+// The factor stores L^{R-1} (every stage) and L^{Q-1} (first stage of each
+// segment) in the free upper triangle of L, so every triangular solve here is
+// a parallel matrix-vector product.  One CTA per (instance, segment); the
+// next stage's blocks are copied to shared memory (cp.async) while the
+// current stage is processed (or, when two packages do not fit in shared
+// memory, right after it); nrhs right-hand sides share each block.
 #include "cyq_internal.cuh"
 
 namespace cyq {
 
 namespace {
 
-template <typename T, int TEAM>
-__device__ void load_T(T *dst, const T *src, int count) {
-    for (int e = threadIdx.x; e < count; e += TEAM) dst[e] = src[e];
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
 template <typename T, int TEAM>
-__device__ void load_BA_T(T *BA, const Data &d, const Inst &in, int s) {
-    const int nx = in.nx, nu = in.nu;
-    const double *B = d.B + in.oB + (long long)s * nx * nu;
-    const double *A = d.A + in.oA + (long long)s * nx * nx;
-    for (int e = threadIdx.x; e < nx * nu; e += TEAM) BA[e] = (T)B[e];
-    for (int e = threadIdx.x; e < nx * nx; e += TEAM) BA[nx * nu + e] = (s != 0) ? (T)A[e] : T(0);
-}
-
-struct SolveSmem {
-    template <typename T>
-    __device__ static void carve(unsigned char *raw, int nx, int nu, int nrhs, T *&Ls, T *&Ds, T *&BA, T *&Fs,
-                                 T *&LB, T *&hh, T *&rho, T *&pv, T *&tv, T *&wv, T *&gmu, T *&cv, T *&xv) {
-        const int nux = nx + nu;
-        T *p = reinterpret_cast<T *>(raw);
-        Ls = p; p += nux * nux;
-        Ds = p; p += nux;
-        BA = p; p += nx * nux;
-        Fs = p; p += nx * nx;
-        LB = p; p += nx * nu;
-        hh = p; p += nux * nrhs;
-        rho = p; p += nu * nrhs;
-        pv = p; p += nx * nrhs;
-        tv = p; p += nx * nrhs;
-        wv = p; p += nx * nrhs;
-        gmu = p; p += nx * nrhs;
-        cv = p; p += nx * nrhs;
-        xv = p; p += nx * nrhs;
+__device__ void async_copy(T *dst, const T *src, int count) {
+    for (int e = threadIdx.x; e < count; e += TEAM) {
+        if (sizeof(T) == 8)
+            cp_async8(dst + e, src + e);
+        else
+            cp_async4(dst + e, src + e);
     }
+}
+
+// Per-stage package in shared memory: factor blocks of stage s and the raw
+// float64 [B A] of the stage whose dynamics the sweep needs next.
+template <typename T>
+struct Package {
+    T *L, *D, *LB, *F;   // (nu+nx)^2 (ld nu+nx), nu+nx, nx*nu, nx*nx
+    double *BA;          // nx x (nu+nx), ld nx (raw [B A])
 };
+
+template <typename T>
+__device__ Package<T> carve_package(unsigned char *&p, int nx, int nu) {
+    const int nux = nx + nu;
+    Package<T> k;
+    k.BA = reinterpret_cast<double *>(p);
+    p += ((size_t)nx * nux * 8 + 15) / 16 * 16;
+    k.L = reinterpret_cast<T *>(p);
+    k.D = k.L + nux * nux;
+    k.LB = k.D + nux;
+    k.F = k.LB + nx * nu;
+    p += (((size_t)nux * nux + nux + (size_t)nx * nu + (size_t)nx * nx) * sizeof(T) + 15) / 16 * 16;
+    return k;
+}
+
+size_t package_bytes(bool fp64, int nx, int nu) {
+    const size_t nux = (size_t)nx + nu;
+    const size_t el = fp64 ? 8 : 4;
+    return ((size_t)nx * nux * 8 + 15) / 16 * 16 +
+           ((nux * nux + nux + (size_t)nx * nu + (size_t)nx * nx) * el + 15) / 16 * 16;
+}
+
+// Issue the copies of a package: factor blocks of stage s (LB/F when needed),
+// and [B A] of stage sba (skipped when sba < 0; A_0 is replaced by zero).
+template <typename T, int TEAM>
+__device__ void fetch_package(const Package<T> &k, const SolveArgs &a, const Inst &in, int s, bool wantLB,
+                              bool wantF, int sba) {
+    const int nx = in.nx, nu = in.nu, nux = nx + nu;
+    const T *Lg = reinterpret_cast<const T *>(a.L) + in.oL;
+    const T *LBg = reinterpret_cast<const T *>(a.LB) + in.oLB;
+    const T *Fg = reinterpret_cast<const T *>(a.F) + in.oF;
+    const T *DIg = reinterpret_cast<const T *>(a.DI) + in.oDI;
+    async_copy<T, TEAM>(k.L, Lg + (long long)s * nux * nux, nux * nux);
+    async_copy<T, TEAM>(k.D, DIg + (long long)s * nux, nux);
+    if (wantLB) async_copy<T, TEAM>(k.LB, LBg + (long long)s * nx * nu, nx * nu);
+    if (wantF) async_copy<T, TEAM>(k.F, Fg + (long long)s * nx * nx, nx * nx);
+    if (sba >= 0) {
+        async_copy<double, TEAM>(k.BA, a.data.B + in.oB + (long long)sba * nx * nu, nx * nu);
+        if (sba != 0)
+            async_copy<double, TEAM>(k.BA + nx * nu, a.data.A + in.oA + (long long)sba * nx * nx, nx * nx);
+        else
+            for (int e = threadIdx.x; e < nx * nx; e += TEAM) k.BA[nx * nu + e] = 0.0;
+    }
+    cp_async_commit();
+}
+
+// Vectors of one work item (T), each nrhs copies.
+template <typename T>
+struct Vecs {
+    T *hh, *rho, *pv, *tv, *wv, *gmu, *cv, *xv;
+};
+
+template <typename T>
+__device__ Vecs<T> carve_vecs(unsigned char *p, int nx, int nu, int nrhs) {
+    const int nux = nx + nu;
+    T *q = reinterpret_cast<T *>(p);
+    Vecs<T> v;
+    v.hh = q; q += nux * nrhs;
+    v.rho = q; q += nu * nrhs;
+    v.pv = q; q += nx * nrhs;
+    v.tv = q; q += nx * nrhs;
+    v.wv = q; q += nx * nrhs;
+    v.gmu = q; q += nx * nrhs;
+    v.cv = q; q += nx * nrhs;
+    v.xv = q; q += nx * nrhs;
+    return v;
+}
+
+size_t vecs_bytes(bool fp64, int nx, int nu, int nrhs) {
+    return ((size_t)(nx + nu) * nrhs + (size_t)nu * nrhs + 6 * (size_t)nx * nrhs) * (fp64 ? 8 : 4);
+}
 
 }  // namespace
 
-size_t solve_smem_bytes(bool fp64, int nx, int nu, int nrhs) {
-    const size_t nux = (size_t)nx + nu;
-    const size_t cnt = nux * nux + nux + nx * nux + (size_t)nx * nx + (size_t)nx * nu + nux * nrhs +
-                       (size_t)nu * nrhs + 6 * (size_t)nx * nrhs;
-    return cnt * (fp64 ? 8 : 4);
+size_t solve_smem_bytes(bool fp64, int nx, int nu, int nrhs, int nbuf) {
+    return nbuf * package_bytes(fp64, nx, nu) + vecs_bytes(fp64, nx, nu, nrhs);
 }
 
 template <typename T, int TEAM>
@@ -79,141 +140,161 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
         const int N = in.N, nx = in.nx, nu = in.nu, P = in.P, c = wi.seg, nrhs = a.nrhs;
         const int nux = nx + nu, w = nu + 2 * nx;
         const int len = seg_len(c, N, P);
-        T *Ls, *Ds, *BA, *Fs, *LB, *hh, *rho, *pv, *tv, *wv, *gmu, *cv, *xv;
-        SolveSmem::carve<T>(smem_raw, nx, nu, nrhs, Ls, Ds, BA, Fs, LB, hh, rho, pv, tv, wv, gmu, cv, xv);
-        const T *DIg = reinterpret_cast<const T *>(a.DI) + in.oDI;
-        const T *DQ = Ds + nu;
-        const T *Lg = reinterpret_cast<const T *>(a.L) + in.oL;
-        const T *LBg = reinterpret_cast<const T *>(a.LB) + in.oLB;
-        const T *Fg = reinterpret_cast<const T *>(a.F) + in.oF;
+        unsigned char *p = smem_raw;
+        Package<T> pk[2];
+        pk[0] = carve_package<T>(p, nx, nu);
+        pk[1] = a.nbuf == 2 ? carve_package<T>(p, nx, nu) : pk[0];
+        const Vecs<T> v = carve_vecs<T>(p, nx, nu, nrhs);
         const double *b = a.b + in.oZ;
         double *z = a.z + in.oZ;
-        const T *LQ = Ls + nu + nu * nux;
 
-        // right-hand side of the first processed stage
+        // package t: factor blocks of stage s(t) and [B A] of stage s(t+1)
+        auto fetch = [&](int t) {
+            const int s = seg_stage(c, t, N, P);
+            const bool last = t == len - 1;
+            fetch_package<T, TEAM>(pk[t & 1], a, in, s, (t == 0) || (c >= 1), c >= 1,
+                                   last ? -1 : seg_stage(c, t + 1, N, P));
+        };
+        fetch(0);
         {
             const int s = seg_stage(c, 0, N, P), xq = xstate(s, N);
             for (int e = threadIdx.x; e < nux * nrhs; e += TEAM) {
                 const int aa = e % nux, r = e / nux;
                 const double *br = b + r * a.kkt;
-                hh[e] = aa < nu ? -(T)br[(long long)s * w + aa] : -(T)br[(long long)(xq - 1) * w + nu + (aa - nu)];
+                v.hh[e] = aa < nu ? -(T)br[(long long)s * w + aa] : -(T)br[(long long)(xq - 1) * w + nu + (aa - nu)];
             }
-            for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) gmu[e] = T(0);
+            for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) v.gmu[e] = T(0);
         }
         for (int t = 0; t < len; ++t) {
             const int s = seg_stage(c, t, N, P), xq = xstate(s, N);
             const bool hasG = (t == 0) || (c >= 1);
             const bool last = (t == len - 1);
-            load_T<T, TEAM>(Ls, Lg + (long long)s * nux * nux, nux * nux);
-            load_T<T, TEAM>(Ds, DIg + (long long)s * nux, nux);
-            if (hasG) load_T<T, TEAM>(LB, LBg + (long long)s * nx * nu, nx * nu);
-            if (c >= 1) load_T<T, TEAM>(Fs, Fg + (long long)s * nx * nx, nx * nx);
+            const Package<T> &K = pk[t & 1];
+            cp_async_wait_all();
             team_sync();
-            // rho = L^{R-1} h_u
-            for (int r = threadIdx.x; r < nrhs; r += TEAM) {
-                const T *hu = hh + r * nux;
-                T *ro = rho + r * nu;
-                for (int i = 0; i < nu; ++i) {
-                    T acc = hu[i];
-                    for (int k = 0; k < i; ++k) acc = fma(-Ls[i + k * nux], ro[k], acc);
-                    ro[i] = acc * Ds[i];
+            if (!last && a.nbuf == 2) fetch(t + 1);   // overlaps with this stage
+            const T *Ls = K.L, *Ds = K.D;
+            const T *LQ = Ls + nu + nu * nux, *DQ = Ds + nu;
+            // rho = L^{R-1} h_u  (stored inverse: diagonal Ds, strictly lower part transposed above)
+            {
+                int i, r;
+                rect_start(threadIdx.x, nu, i, r);
+                for (; r < nrhs; rect_advance(i, r, nu, TEAM)) {
+                    const T *hu = v.hh + r * nux;
+                    T acc = Ds[i] * hu[i];
+                    for (int k = 0; k < i; ++k) acc = fma(Ls[k + i * nux], hu[k], acc);
+                    v.rho[i + r * nu] = acc;
                 }
             }
-            team_sync();
-            // p = h_x - L^S rho ;  g -= L^B rho
-            for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
-                const int i = e % nx, r = e / nx;
-                const T *ro = rho + r * nu;
-                T acc = hh[r * nux + nu + i];
-                for (int k = 0; k < nu; ++k) acc -= Ls[(nu + i) + k * nux] * ro[k];
-                pv[e] = acc;
-                if (hasG) {
-                    T g = T(0);
-                    for (int k = 0; k < nu; ++k) g += LB[i + k * nx] * ro[k];
-                    gmu[e] -= g;
-                }
-            }
-            team_sync();
-            for (int e = threadIdx.x; e < nu * nrhs; e += TEAM) {
-                const int i = e % nu, r = e / nu;
-                z[r * a.kkt + (long long)s * w + i] = (double)rho[e];
-            }
-            for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
-                const int i = e % nx, r = e / nx;
-                z[r * a.kkt + (long long)(xq - 1) * w + nu + i] = (double)pv[e];
-            }
+            // next stage's constant terms (independent of rho)
+            int s2 = 0, xq2 = 0;
             if (!last) {
-                const int s2 = seg_stage(c, t + 1, N, P), xq2 = xstate(s2, N);
-                load_BA_T<T, TEAM>(BA, a.data, in, s2);
+                s2 = seg_stage(c, t + 1, N, P);
+                xq2 = xstate(s2, N);
                 for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
                     const int i = e % nx, r = e / nx;
-                    cv[e] = -(T)b[r * a.kkt + (long long)s2 * w + nu + nx + i];
+                    v.cv[e] = -(T)b[r * a.kkt + (long long)s2 * w + nu + nx + i];
                 }
-                team_sync();
+            }
+            team_sync();
+            // p = h_x - L^S rho ;  g -= L^B rho ; park rho, p
+            {
+                int i, r;
+                rect_start(threadIdx.x, nx, i, r);
+                for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
+                    const T *ro = v.rho + r * nu;
+                    T acc = v.hh[r * nux + nu + i];
+                    for (int k = 0; k < nu; ++k) acc = fma(-Ls[(nu + i) + k * nux], ro[k], acc);
+                    v.pv[i + r * nx] = acc;
+                    z[r * a.kkt + (long long)(xq - 1) * w + nu + i] = (double)acc;
+                    if (hasG) {
+                        T g = v.gmu[i + r * nx];
+                        for (int k = 0; k < nu; ++k) g = fma(-K.LB[i + k * nx], ro[k], g);
+                        v.gmu[i + r * nx] = g;
+                    }
+                }
+                for (int e = threadIdx.x; e < nu * nrhs; e += TEAM) {
+                    const int i = e % nu, r = e / nu;
+                    z[r * a.kkt + (long long)s * w + i] = (double)v.rho[e];
+                }
+            }
+            if (!last) {
                 // w = L^{Q T} c
-                for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
-                    const int j = e % nx, r = e / nx;
-                    const T *cr = cv + r * nx;
-                    T acc = T(0);
-                    for (int k = j; k < nx; ++k) acc += LQ[k + j * nux] * cr[k];
-                    wv[e] = acc;
+                {
+                    int j, r;
+                    rect_start(threadIdx.x, nx, j, r);
+                    for (; r < nrhs; rect_advance(j, r, nx, TEAM)) {
+                        const T *cr = v.cv + r * nx;
+                        T acc = T(0);
+                        for (int k = j; k < nx; ++k) acc = fma(LQ[k + j * nux], cr[k], acc);
+                        v.wv[j + r * nx] = acc;
+                    }
                 }
                 team_sync();
                 // t = L^Q w + p ;  g += A^cl c
-                for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
-                    const int i = e % nx, r = e / nx;
-                    const T *wr = wv + r * nx;
-                    T acc = pv[e];
-                    for (int j = 0; j <= i; ++j) acc += LQ[i + j * nux] * wr[j];
-                    tv[e] = acc;
-                    if (c >= 1) {
-                        const T *cr = cv + r * nx;
-                        T g = T(0);
-                        for (int k = 0; k < nx; ++k) g += Fs[i + k * nx] * cr[k];
-                        gmu[e] += g;
+                {
+                    int i, r;
+                    rect_start(threadIdx.x, nx, i, r);
+                    for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
+                        const T *wr = v.wv + r * nx;
+                        T acc = v.pv[i + r * nx];
+                        for (int j = 0; j <= i; ++j) acc = fma(LQ[i + j * nux], wr[j], acc);
+                        v.tv[i + r * nx] = acc;
+                        if (c >= 1) {
+                            const T *cr = v.cv + r * nx;
+                            T g = v.gmu[i + r * nx];
+                            for (int k = 0; k < nx; ++k) g = fma(K.F[i + k * nx], cr[k], g);
+                            v.gmu[i + r * nx] = g;
+                        }
                     }
                 }
                 team_sync();
                 // h^_{s2} = h_{s2} + [B A]^T t
-                for (int e = threadIdx.x; e < nux * nrhs; e += TEAM) {
-                    const int aa = e % nux, r = e / nux;
-                    const double *br = b + r * a.kkt;
-                    const T *tr = tv + r * nx;
-                    T acc = aa < nu ? -(T)br[(long long)s2 * w + aa]
-                                    : -(T)br[(long long)(xq2 - 1) * w + nu + (aa - nu)];
-                    for (int k = 0; k < nx; ++k) acc += BA[k + aa * nx] * tr[k];
-                    hh[e] = acc;
+                {
+                    int aa, r;
+                    rect_start(threadIdx.x, nux, aa, r);
+                    for (; r < nrhs; rect_advance(aa, r, nux, TEAM)) {
+                        const double *br = b + r * a.kkt;
+                        const T *tr = v.tv + r * nx;
+                        const double *col = K.BA + aa * nx;
+                        T acc = aa < nu ? -(T)br[(long long)s2 * w + aa]
+                                        : -(T)br[(long long)(xq2 - 1) * w + nu + (aa - nu)];
+                        for (int k = 0; k < nx; ++k) acc = fma((T)col[k], tr[k], acc);
+                        v.hh[aa + r * nux] = acc;
+                    }
                 }
-                team_sync();
             } else {
-                // y = L^{Q-1} p ;  d_bwd = L^{Q-T} y ;  d_fwd = g - L^A y
-                for (int r = threadIdx.x; r < nrhs; r += TEAM) {
-                    const T *pr = pv + r * nx;
-                    T *y = wv + r * nx, *db = tv + r * nx;
-                    for (int i = 0; i < nx; ++i) {
-                        T acc = pr[i];
-                        for (int k = 0; k < i; ++k) acc = fma(-LQ[i + k * nux], y[k], acc);
-                        y[i] = acc * DQ[i];
-                    }
-                    for (int i = nx - 1; i >= 0; --i) {
-                        T acc = y[i];
-                        for (int k = i + 1; k < nx; ++k) acc = fma(-LQ[k + i * nux], db[k], acc);
-                        db[i] = acc * DQ[i];
+                team_sync();
+                // y = L^{Q-1} p  (inverse stored above the diagonal of this first stage's Q block)
+                {
+                    int i, r;
+                    rect_start(threadIdx.x, nx, i, r);
+                    for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
+                        const T *pr = v.pv + r * nx;
+                        T acc = DQ[i] * pr[i];
+                        for (int k = 0; k < i; ++k) acc = fma(LQ[k + i * nux], pr[k], acc);
+                        v.wv[i + r * nx] = acc;
                     }
                 }
                 team_sync();
-                for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
-                    const int i = e % nx, r = e / nx;
-                    T df = gmu[e];
-                    if (c >= 1) {
-                        const T *y = wv + r * nx;
-                        for (int k = 0; k < nx; ++k) df -= Fs[i + k * nx] * y[k];
+                // d_bwd = L^{Q-T} y ;  d_fwd = g - L^A y
+                {
+                    int i, r;
+                    rect_start(threadIdx.x, nx, i, r);
+                    for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
+                        const T *y = v.wv + r * nx;
+                        T db = DQ[i] * y[i];
+                        for (int k = i + 1; k < nx; ++k) db = fma(LQ[i + k * nux], y[k], db);
+                        T df = v.gmu[i + r * nx];
+                        if (c >= 1)
+                            for (int k = 0; k < nx; ++k) df = fma(-K.F[i + k * nx], y[k], df);
+                        a.dF[r * a.nvec + in.oVec + (long long)c * nx + i] = (double)df;
+                        a.dB[r * a.nvec + in.oVec + (long long)c * nx + i] = (double)db;
                     }
-                    a.dF[r * a.nvec + in.oVec + (long long)c * nx + i] = (double)df;
-                    a.dB[r * a.nvec + in.oVec + (long long)c * nx + i] = (double)tv[e];
                 }
             }
             team_sync();
+            if (!last && a.nbuf == 1) fetch(t + 1);   // the single package is free again
         }
     }
 }
@@ -228,19 +309,23 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
         const int N = in.N, nx = in.nx, nu = in.nu, P = in.P, c = wi.seg, nrhs = a.nrhs;
         const int nux = nx + nu, w = nu + 2 * nx;
         const int len = seg_len(c, N, P);
-        T *Ls, *Ds, *BA, *Fs, *LB, *hh, *rho, *pv, *tv, *wv, *gmu, *cv, *xv;
-        SolveSmem::carve<T>(smem_raw, nx, nu, nrhs, Ls, Ds, BA, Fs, LB, hh, rho, pv, tv, wv, gmu, cv, xv);
-        const T *DIg = reinterpret_cast<const T *>(a.DI) + in.oDI;
-        const T *DQ = Ds + nu;
-        T *mu = gmu, *nuv = cv;   // coupling multipliers (reuse)
-        const T *Lg = reinterpret_cast<const T *>(a.L) + in.oL;
-        const T *LBg = reinterpret_cast<const T *>(a.LB) + in.oLB;
-        const T *Fg = reinterpret_cast<const T *>(a.F) + in.oF;
+        unsigned char *p = smem_raw;
+        Package<T> pk[2];
+        pk[0] = carve_package<T>(p, nx, nu);
+        pk[1] = a.nbuf == 2 ? carve_package<T>(p, nx, nu) : pk[0];
+        const Vecs<T> v = carve_vecs<T>(p, nx, nu, nrhs);
+        T *mu = v.gmu, *nuv = v.cv;   // coupling multipliers
         const double *b = a.b + in.oZ;
         double *z = a.z + in.oZ;
         double *zacc = a.zacc ? a.zacc + in.oZ : nullptr;
-        const T *LQ = Ls + nu + nu * nux;
 
+        // package for processing step t (time order: t = len-1 .. 0): factor blocks
+        // of stage s(t) and [B A] of that same stage (its outgoing dynamics)
+        auto fetch = [&](int t) {
+            const int s = seg_stage(c, t, N, P);
+            fetch_package<T, TEAM>(pk[t & 1], a, in, s, (t == 0) || (c >= 1), c >= 1, t > 0 ? s : -1);
+        };
+        fetch(len - 1);
         for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
             const int i = e % nx, r = e / nx;
             const double *lr = a.lam + r * a.nvec + in.oVec;
@@ -251,84 +336,94 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
             const int s = seg_stage(c, t, N, P), xq = xstate(s, N);
             const bool hasG = (t == 0) || (c >= 1);
             const bool first = (t == len - 1);
-            load_T<T, TEAM>(Ls, Lg + (long long)s * nux * nux, nux * nux);
-            load_T<T, TEAM>(Ds, DIg + (long long)s * nux, nux);
-            if (hasG) load_T<T, TEAM>(LB, LBg + (long long)s * nx * nu, nx * nu);
-            if (c >= 1) load_T<T, TEAM>(Fs, Fg + (long long)s * nx * nx, nx * nx);
+            const Package<T> &K = pk[t & 1];
+            // parked rho / p of this stage
             for (int e = threadIdx.x; e < nu * nrhs; e += TEAM) {
                 const int i = e % nu, r = e / nu;
-                rho[e] = (T)z[r * a.kkt + (long long)s * w + i];
+                v.rho[e] = (T)z[r * a.kkt + (long long)s * w + i];
             }
             for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
                 const int i = e % nx, r = e / nx;
-                pv[e] = (T)z[r * a.kkt + (long long)(xq - 1) * w + nu + i];
+                v.pv[e] = (T)z[r * a.kkt + (long long)(xq - 1) * w + nu + i];
             }
+            cp_async_wait_all();
             team_sync();
+            if (t > 0 && a.nbuf == 2) fetch(t - 1);   // overlaps with this stage
+            const T *Ls = K.L, *Ds = K.D;
+            const T *LQ = Ls + nu + nu * nux, *DQ = Ds + nu;
             if (first) {
                 // x^{j1} = -L^{Q-T} (L^{Q-1}(p - nu) + L^{A T} mu)
-                for (int r = threadIdx.x; r < nrhs; r += TEAM) {
-                    const T *pr = pv + r * nx, *nr = nuv + r * nx, *mr = mu + r * nx;
-                    T *y = wv + r * nx, *x = xv + r * nx;
-                    for (int i = 0; i < nx; ++i) {
-                        T acc = pr[i] - nr[i];
-                        for (int k = 0; k < i; ++k) acc = fma(-LQ[i + k * nux], y[k], acc);
-                        y[i] = acc * DQ[i];
+                {
+                    int i, r;
+                    rect_start(threadIdx.x, nx, i, r);
+                    for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
+                        const T *pr = v.pv + r * nx, *nr = nuv + r * nx, *mr = mu + r * nx;
+                        T acc = DQ[i] * (pr[i] - nr[i]);
+                        for (int k = 0; k < i; ++k) acc = fma(LQ[k + i * nux], pr[k] - nr[k], acc);
+                        if (c >= 1)
+                            for (int k = 0; k < nx; ++k) acc = fma(K.F[k + i * nx], mr[k], acc);
+                        v.wv[i + r * nx] = acc;
                     }
-                    if (c >= 1)
-                        for (int j = 0; j < nx; ++j) {
-                            T acc = T(0);
-                            for (int i = 0; i < nx; ++i) acc += Fs[i + j * nx] * mr[i];
-                            y[j] += acc;
-                        }
-                    for (int i = nx - 1; i >= 0; --i) {
-                        T acc = y[i];
-                        for (int k = i + 1; k < nx; ++k) acc = fma(-LQ[k + i * nux], x[k], acc);
-                        x[i] = acc * DQ[i];
+                }
+                team_sync();
+                {
+                    int i, r;
+                    rect_start(threadIdx.x, nx, i, r);
+                    for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
+                        const T *y = v.wv + r * nx;
+                        T acc = DQ[i] * y[i];
+                        for (int k = i + 1; k < nx; ++k) acc = fma(LQ[i + k * nux], y[k], acc);
+                        v.xv[i + r * nx] = -acc;
                     }
-                    for (int i = 0; i < nx; ++i) x[i] = -x[i];
                 }
                 team_sync();
             }
-            // v = L^{S T} x + rho + L^{B T} mu  ->  hh[0..nu)
-            for (int e = threadIdx.x; e < nu * nrhs; e += TEAM) {
-                const int k = e % nu, r = e / nu;
-                const T *x = xv + r * nx, *mr = mu + r * nx;
-                T acc = rho[e];
-                for (int i = 0; i < nx; ++i) acc += Ls[(nu + i) + k * nux] * x[i];
-                if (hasG)
-                    for (int i = 0; i < nx; ++i) acc += LB[i + k * nx] * mr[i];
-                hh[r * nux + k] = acc;
+            // v = L^{S T} x + rho + L^{B T} mu  ->  hh[0..nu) ;  w = L^{Q T} x (interior stages)
+            {
+                int k, r;
+                rect_start(threadIdx.x, nu, k, r);
+                for (; r < nrhs; rect_advance(k, r, nu, TEAM)) {
+                    const T *x = v.xv + r * nx, *mr = mu + r * nx;
+                    T acc = v.rho[k + r * nu];
+                    for (int i = 0; i < nx; ++i) acc = fma(Ls[(nu + i) + k * nux], x[i], acc);
+                    if (hasG)
+                        for (int i = 0; i < nx; ++i) acc = fma(K.LB[i + k * nx], mr[i], acc);
+                    v.hh[k + r * nux] = acc;
+                }
             }
-            // interior multiplier lambda^{s-1} = L^Q L^{Q T} x + p + A^{cl T} mu
             if (!first) {
-                for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
-                    const int j = e % nx, r = e / nx;
-                    const T *x = xv + r * nx;
+                int j, r;
+                rect_start(threadIdx.x, nx, j, r);
+                for (; r < nrhs; rect_advance(j, r, nx, TEAM)) {
+                    const T *x = v.xv + r * nx;
                     T acc = T(0);
-                    for (int k = j; k < nx; ++k) acc += LQ[k + j * nux] * x[k];
-                    wv[e] = acc;
+                    for (int k = j; k < nx; ++k) acc = fma(LQ[k + j * nux], x[k], acc);
+                    v.wv[j + r * nx] = acc;
                 }
             }
             team_sync();
-            // u = -L^{R-T} v
-            for (int r = threadIdx.x; r < nrhs; r += TEAM) {
-                T *v = hh + r * nux, *u = rho + r * nu;
-                for (int i = nu - 1; i >= 0; --i) {
-                    T acc = v[i];
-                    for (int k = i + 1; k < nu; ++k) acc = fma(-Ls[k + i * nux], u[k], acc);
-                    u[i] = acc * Ds[i];
+            // u = -L^{R-T} v  (stored inverse)
+            {
+                int i, r;
+                rect_start(threadIdx.x, nu, i, r);
+                for (; r < nrhs; rect_advance(i, r, nu, TEAM)) {
+                    const T *vv = v.hh + r * nux;
+                    T acc = Ds[i] * vv[i];
+                    for (int k = i + 1; k < nu; ++k) acc = fma(Ls[i + k * nux], vv[k], acc);
+                    v.rho[i + r * nu] = -acc;
                 }
-                for (int i = 0; i < nu; ++i) u[i] = -u[i];
             }
+            // interior multiplier lambda^{s-1} = L^Q L^{Q T} x + p + A^{cl T} mu
             if (!first) {
                 const int sp = (s - 1 + N) % N;
-                for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
-                    const int i = e % nx, r = e / nx;
-                    const T *wr = wv + r * nx, *mr = mu + r * nx;
-                    T acc = pv[e];
-                    for (int j = 0; j <= i; ++j) acc += LQ[i + j * nux] * wr[j];
+                int i, r;
+                rect_start(threadIdx.x, nx, i, r);
+                for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
+                    const T *wr = v.wv + r * nx, *mr = mu + r * nx;
+                    T acc = v.pv[i + r * nx];
+                    for (int j = 0; j <= i; ++j) acc = fma(LQ[i + j * nux], wr[j], acc);
                     if (c >= 1)
-                        for (int k = 0; k < nx; ++k) acc += Fs[k + i * nx] * mr[k];
+                        for (int k = 0; k < nx; ++k) acc = fma(K.F[k + i * nx], mr[k], acc);
                     const long long o = r * a.kkt + (long long)sp * w + nu + nx + i;
                     if (zacc) zacc[o] += (double)acc; else z[o] = (double)acc;
                 }
@@ -337,29 +432,29 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
             for (int e = threadIdx.x; e < nu * nrhs; e += TEAM) {
                 const int i = e % nu, r = e / nu;
                 const long long o = r * a.kkt + (long long)s * w + i;
-                if (zacc) zacc[o] += (double)rho[e]; else z[o] = (double)rho[e];
+                if (zacc) zacc[o] += (double)v.rho[e]; else z[o] = (double)v.rho[e];
             }
             for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
                 const int i = e % nx, r = e / nx;
                 const long long o = r * a.kkt + (long long)(xq - 1) * w + nu + i;
-                if (zacc) zacc[o] += (double)xv[e]; else z[o] = (double)xv[e];
+                if (zacc) zacc[o] += (double)v.xv[e]; else z[o] = (double)v.xv[e];
             }
             if (t > 0) {
                 // x^{s+1} = A_s x + B_s u + c_s
-                load_BA_T<T, TEAM>(BA, a.data, in, s);
-                team_sync();
-                for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
-                    const int i = e % nx, r = e / nx;
-                    const T *x = xv + r * nx, *u = rho + r * nu;
+                int i, r;
+                rect_start(threadIdx.x, nx, i, r);
+                for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
+                    const T *x = v.xv + r * nx, *u = v.rho + r * nu;
                     T acc = -(T)b[r * a.kkt + (long long)s * w + nu + nx + i];
-                    for (int k = 0; k < nu; ++k) acc += BA[i + k * nx] * u[k];
-                    for (int k = 0; k < nx; ++k) acc += BA[i + (nu + k) * nx] * x[k];
-                    tv[e] = acc;
+                    for (int k = 0; k < nu; ++k) acc = fma((T)K.BA[i + k * nx], u[k], acc);
+                    for (int k = 0; k < nx; ++k) acc = fma((T)K.BA[i + (nu + k) * nx], x[k], acc);
+                    v.tv[i + r * nx] = acc;
                 }
                 team_sync();
-                for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) xv[e] = tv[e];
+                for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) v.xv[e] = v.tv[e];
             }
             team_sync();
+            if (t > 0 && a.nbuf == 1) fetch(t - 1);   // the single package is free again
         }
     }
 }
