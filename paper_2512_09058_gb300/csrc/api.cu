@@ -38,6 +38,7 @@ struct Group {
 
 struct FactorSet {
     void *L = nullptr, *LB = nullptr, *F = nullptr, *DI = nullptr;
+    void *BA = nullptr;   // float32 [B A] copies (float32 sets only)
     bool fp64 = true;
 };
 
@@ -123,6 +124,16 @@ int choose_team(int nx, int nu) {
     return 128;
 }
 
+// Solve sweeps: enough threads for one pass over the (row, right-hand side)
+// pairs of a stage block, up to 256.
+int solve_team(int nux, int nrhs) {
+    const int need = nux * nrhs;
+    if (need <= 32) return 32;
+    if (need <= 64) return 64;
+    if (need <= 128) return 128;
+    return 256;
+}
+
 // Size class of an instance: work items are launched per class so that the
 // shared-memory carve-out and the team size match the blocks they hold.
 int size_class(int nx, int nu) {
@@ -172,6 +183,7 @@ SolveArgs solve_args(cyq_handle h, const FactorSet &fs, const Group &g, const do
     a.nvec = h->nvec;
     a.skip = skip;
     a.zacc = zacc;
+    a.BA = fs.fp64 ? nullptr : fs.BA;
     a.nbuf = g.solve_nbuf[fs.fp64 ? 1 : 0];
     return a;
 }
@@ -183,7 +195,7 @@ cyq_status run_solve(cyq_handle h, const FactorSet &fs, const double *b, double 
     for (const Group &g : h->groups) {
         SolveArgs a = solve_args(h, fs, g, b, z, nrhs, skip, zacc);
         size_t smem = solve_smem_bytes(fs.fp64, g.max_nx, g.max_nu, nrhs, a.nbuf);
-        CYQ_CUDA(launch_solve_backward(fs.fp64, g.team, smem, a, st));
+        CYQ_CUDA(launch_solve_backward(fs.fp64, solve_team(g.max_nx + g.max_nu, nrhs), smem, a, st));
         ++h->launches;
     }
     {
@@ -195,7 +207,7 @@ cyq_status run_solve(cyq_handle h, const FactorSet &fs, const double *b, double 
     for (const Group &g : h->groups) {
         SolveArgs a = solve_args(h, fs, g, b, z, nrhs, skip, zacc);
         size_t smem = solve_smem_bytes(fs.fp64, g.max_nx, g.max_nu, nrhs, a.nbuf);
-        CYQ_CUDA(launch_solve_forward(fs.fp64, g.team, smem, a, st));
+        CYQ_CUDA(launch_solve_forward(fs.fp64, solve_team(g.max_nx + g.max_nu, nrhs), smem, a, st));
         ++h->launches;
     }
     return CYQ_OK;
@@ -211,6 +223,7 @@ cyq_status run_factor(cyq_handle h, const FactorSet &fs, const int *skip, cudaSt
     a.LB = fs.LB;
     a.F = fs.F;
     a.DI = fs.DI;
+    a.BAf = fs.fp64 ? nullptr : fs.BA;
     a.Mf = h->Mf;
     a.Mb = h->Mb;
     a.Kc = h->Kc;
@@ -338,7 +351,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     h->tol = desc->tol > 0 ? desc->tol : 1e-10;
     const bool fp64 = h->precision == CYQ_FP64;
 
-    long long oQ = 0, oR = 0, oS = 0, oA = 0, oB = 0, oSig = 0, oZ = 0, oL = 0, oLB = 0, oF = 0, oDI = 0, oBlk = 0,
+    long long oQ = 0, oR = 0, oS = 0, oA = 0, oB = 0, oSig = 0, oZ = 0, oL = 0, oLB = 0, oF = 0, oDI = 0, oBA = 0, oBlk = 0,
               oVec = 0, oq = 0, orv = 0, oc = 0, ox0 = 0;
     std::vector<Item> all_items;
     int item = 0;
@@ -351,7 +364,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         Inst in{};
         in.N = N; in.nx = nx; in.nu = nu; in.P = P; in.item0 = item;
         in.oQ = oQ; in.oR = oR; in.oS = oS; in.oA = oA; in.oB = oB; in.oSig = oSig; in.oZ = oZ;
-        in.oL = oL; in.oLB = oLB; in.oF = oF; in.oDI = oDI; in.oBlk = oBlk; in.oVec = oVec;
+        in.oL = oL; in.oLB = oLB; in.oF = oF; in.oDI = oDI; in.oBA = oBA; in.oBlk = oBlk; in.oVec = oVec;
         in.oq = oq; in.orv = orv; in.oc = oc; in.ox0 = ox0;
         const long long nux = nx + nu;
         oQ += (long long)(N + 1) * nx * nx; oR += (long long)N * nu * nu; oS += (long long)N * nu * nx;
@@ -359,6 +372,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         oZ += (long long)N * (nu + 2 * nx);
         oL += (long long)N * nux * nux; oLB += (long long)N * nx * nu; oF += (long long)N * nx * nx;
         oDI += (long long)N * nux;
+        oBA += (long long)N * nx * nux;
         oBlk += (long long)P * nx * nx; oVec += (long long)P * nx;
         oq += (long long)(N + 1) * nx; orv += (long long)N * nu; oc += (long long)N * nx; ox0 += nx;
         h->inst.push_back(in);
@@ -476,6 +490,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         ALLOC(p, (size_t)oLB * el); fs.LB = p;
         ALLOC(p, (size_t)oF * el); fs.F = p;
         ALLOC(p, (size_t)oDI * el); fs.DI = p;
+        if (!fs.fp64) { ALLOC(p, (size_t)oBA * el); fs.BA = p; }
     }
     ALLOC(h->Mf, (size_t)oBlk);
     ALLOC(h->Mb, (size_t)oBlk);

@@ -24,6 +24,7 @@ struct Inst {
     long long oZ;                        // offset into b / z (doubles)
     long long oL, oLB, oF;               // offsets into the factor arrays (elements)
     long long oDI;                       // offset into the reciprocal-diagonal array (N*(nx+nu) elements)
+    long long oBA;                       // offset into the float32 [B A] copy (N*nx*(nx+nu) elements)
     long long oBlk;                      // offset of the P coupling blocks (nx*nx each)
     long long oVec;                      // offset of the P coupling vectors (nx each)
     long long oq, orv, oc, ox0;          // offsets of q ((N+1) nx), r (N nu), c (N nx), x_init (nx)
@@ -302,6 +303,7 @@ struct FactorArgs {
     Data data;
     void *L, *LB, *F;               // factor arrays (float or double)
     void *DI;                       // reciprocal diagonals of the stage factors
+    void *BAf;                      // optional float32 copy of every stage's [B A] (float32 factors only)
     double *Mf, *Mb, *Kc;           // Schur blocks (float64)
     double *U, *Y;                  // cyclic-reduction factor blocks (float64)
     int *status;
@@ -316,6 +318,7 @@ struct SolveArgs {
     int n_items;
     Data data;
     const void *L, *LB, *F, *DI;
+    const void *BA;                 // float32 [B A] copies (float32 factors); float64 sweeps read the data
     const double *Mf, *Kc, *U, *Y;  // coupling factor (Mf holds the CR Cholesky blocks)
     const double *b;                // right-hand sides (float64)
     double *z;                      // solutions (float64)

@@ -256,6 +256,10 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                     fill_BA<T, TEAM>(BAc, ldBA, src, nx, nu);
                     team_sync();
                     BA = BAc;
+                    // float32 copy for the solve sweeps (no conversions there)
+                    if (a.BAf)
+                        store_block<T, TEAM>(reinterpret_cast<T *>(a.BAf) + in.oBA + (long long)s2 * nx * nux, BAc,
+                                             nx, nux, ldBA);
                 }
                 // V = [B A]^T L^Q : V[a][j] = sum_{k >= j} BA[k][a] L^Q[k][j]
                 const T *LQ = H + nu + nu * ldH;

@@ -20,10 +20,17 @@
 //
 // The factor stores L^{R-1} (every stage) and L^{Q-1} (first stage of each
 // segment) in the free upper triangle of L, so every triangular solve here is
-// a parallel matrix-vector product.  One CTA per (instance, segment); the
-// next stage's blocks are copied to shared memory (cp.async) while the
-// current stage is processed (or, when two packages do not fit in shared
-// memory, right after it); nrhs right-hand sides share each block.
+// a parallel matrix-vector product.
+//
+// Work per stage is split into three barrier-separated phases; products
+// whose rows are independent of each other share a phase.  Each stage's
+// package (factor blocks, [B A], and the right-hand-side / parked vector
+// entries the stage reads) is copied to shared memory with cp.async while the
+// previous stage is processed (or, when two packages do not fit in shared
+// memory, right after it).  The float32 sweeps read a float32 copy of [B A]
+// written by the factorization and convert the package's float64 vector
+// entries once on arrival, so no conversion sits inside a dot product.
+// One CTA per (instance, segment); nrhs right-hand sides share each block.
 #include "cyq_internal.cuh"
 
 namespace cyq {
@@ -35,8 +42,23 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// count elements global -> shared; 16-byte copies when both ends and the
+// length allow it.
 template <typename T, int TEAM>
 __device__ void async_copy(T *dst, const T *src, int count) {
+    const int bytes = count * (int)sizeof(T);
+    if (((reinterpret_cast<unsigned long long>(src) | reinterpret_cast<unsigned long long>(dst)) & 15) == 0 &&
+        (bytes & 15) == 0) {
+        char *d = reinterpret_cast<char *>(dst);
+        const char *g = reinterpret_cast<const char *>(src);
+        for (int e = threadIdx.x; e < bytes / 16; e += TEAM) cp_async16(d + 16 * e, g + 16 * e);
+        return;
+    }
     for (int e = threadIdx.x; e < count; e += TEAM) {
         if (sizeof(T) == 8)
             cp_async8(dst + e, src + e);
@@ -45,89 +67,128 @@ __device__ void async_copy(T *dst, const T *src, int count) {
     }
 }
 
-// Per-stage package in shared memory: factor blocks of stage s and the raw
-// float64 [B A] of the stage whose dynamics the sweep needs next.
+// Column-major walk over the (row, right-hand side) pairs of an n x nrhs
+// grid: the thread's first pair and the step, computed once per work item.
+struct Walk {
+    int i0, r0, di, dr, n;
+    __device__ __forceinline__ void init(int n_, int team) {
+        n = n_;
+        r0 = threadIdx.x / n;
+        i0 = threadIdx.x - r0 * n;
+        dr = team / n;
+        di = team - dr * n;
+    }
+    __device__ __forceinline__ void next(int &i, int &r) const {
+        i += di;
+        r += dr;
+        if (i >= n) {
+            i -= n;
+            ++r;
+        }
+    }
+};
+
+__host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+
+// Per-stage package in shared memory.
 template <typename T>
 struct Package {
+    double *vb;          // nrhs records of nux + nx float64 vector entries
     T *L, *D, *LB, *F;   // (nu+nx)^2 (ld nu+nx), nu+nx, nx*nu, nx*nx
-    double *BA;          // nx x (nu+nx), ld nx (raw [B A])
+    T *BA;               // nx x (nu+nx), ld nx ([B A])
 };
 
 template <typename T>
-__device__ Package<T> carve_package(unsigned char *&p, int nx, int nu) {
-    const int nux = nx + nu;
+__device__ Package<T> carve_package(unsigned char *&p, int nx, int nu, int nrhs) {
+    const size_t nux = nx + nu;
     Package<T> k;
-    k.BA = reinterpret_cast<double *>(p);
-    p += ((size_t)nx * nux * 8 + 15) / 16 * 16;
-    k.L = reinterpret_cast<T *>(p);
-    k.D = k.L + nux * nux;
-    k.LB = k.D + nux;
-    k.F = k.LB + nx * nu;
-    p += (((size_t)nux * nux + nux + (size_t)nx * nu + (size_t)nx * nx) * sizeof(T) + 15) / 16 * 16;
+    k.vb = reinterpret_cast<double *>(p); p += align16((nux + nx) * nrhs * 8);
+    k.L = reinterpret_cast<T *>(p);       p += align16(nux * nux * sizeof(T));
+    k.D = reinterpret_cast<T *>(p);       p += align16(nux * sizeof(T));
+    k.LB = reinterpret_cast<T *>(p);      p += align16((size_t)nx * nu * sizeof(T));
+    k.F = reinterpret_cast<T *>(p);       p += align16((size_t)nx * nx * sizeof(T));
+    k.BA = reinterpret_cast<T *>(p);      p += align16((size_t)nx * nux * sizeof(T));
     return k;
 }
 
-size_t package_bytes(bool fp64, int nx, int nu) {
-    const size_t nux = (size_t)nx + nu;
-    const size_t el = fp64 ? 8 : 4;
-    return ((size_t)nx * nux * 8 + 15) / 16 * 16 +
-           ((nux * nux + nux + (size_t)nx * nu + (size_t)nx * nx) * el + 15) / 16 * 16;
+__host__ __device__ size_t package_bytes(bool fp64, int nx, int nu, int nrhs) {
+    const size_t nux = (size_t)nx + nu, el = fp64 ? 8 : 4;
+    return align16((nux + nx) * nrhs * 8) + align16(nux * nux * el) + align16(nux * el) +
+           align16((size_t)nx * nu * el) + align16((size_t)nx * nx * el) + align16((size_t)nx * nux * el);
 }
 
-// Issue the copies of a package: factor blocks of stage s (LB/F when needed),
-// and [B A] of stage sba (skipped when sba < 0; A_0 is replaced by zero).
+// Factor blocks of stage s (L^B / the A^cl block only where the sweep uses them).
 template <typename T, int TEAM>
-__device__ void fetch_package(const Package<T> &k, const SolveArgs &a, const Inst &in, int s, bool wantLB,
-                              bool wantF, int sba) {
+__device__ void fetch_factor(const Package<T> &k, const SolveArgs &a, const Inst &in, int s, bool wantLB,
+                             bool wantF) {
     const int nx = in.nx, nu = in.nu, nux = nx + nu;
-    const T *Lg = reinterpret_cast<const T *>(a.L) + in.oL;
-    const T *LBg = reinterpret_cast<const T *>(a.LB) + in.oLB;
-    const T *Fg = reinterpret_cast<const T *>(a.F) + in.oF;
-    const T *DIg = reinterpret_cast<const T *>(a.DI) + in.oDI;
-    async_copy<T, TEAM>(k.L, Lg + (long long)s * nux * nux, nux * nux);
-    async_copy<T, TEAM>(k.D, DIg + (long long)s * nux, nux);
-    if (wantLB) async_copy<T, TEAM>(k.LB, LBg + (long long)s * nx * nu, nx * nu);
-    if (wantF) async_copy<T, TEAM>(k.F, Fg + (long long)s * nx * nx, nx * nx);
-    if (sba >= 0) {
-        async_copy<double, TEAM>(k.BA, a.data.B + in.oB + (long long)sba * nx * nu, nx * nu);
-        if (sba != 0)
-            async_copy<double, TEAM>(k.BA + nx * nu, a.data.A + in.oA + (long long)sba * nx * nx, nx * nx);
-        else
-            for (int e = threadIdx.x; e < nx * nx; e += TEAM) k.BA[nx * nu + e] = 0.0;
+    async_copy<T, TEAM>(k.L, reinterpret_cast<const T *>(a.L) + in.oL + (long long)s * nux * nux, nux * nux);
+    async_copy<T, TEAM>(k.D, reinterpret_cast<const T *>(a.DI) + in.oDI + (long long)s * nux, nux);
+    if (wantLB) async_copy<T, TEAM>(k.LB, reinterpret_cast<const T *>(a.LB) + in.oLB + (long long)s * nx * nu, nx * nu);
+    if (wantF) async_copy<T, TEAM>(k.F, reinterpret_cast<const T *>(a.F) + in.oF + (long long)s * nx * nx, nx * nx);
+}
+
+// [B A] of stage s (s > 0): the float32 copy, or the float64 data itself.
+template <typename T, int TEAM>
+__device__ void fetch_BA(const Package<T> &k, const SolveArgs &a, const Inst &in, int s) {
+    const int nx = in.nx, nu = in.nu, nux = nx + nu;
+    if (sizeof(T) == 4) {
+        async_copy<T, TEAM>(k.BA, reinterpret_cast<const T *>(a.BA) + in.oBA + (long long)s * nx * nux, nx * nux);
+    } else {
+        double *d = reinterpret_cast<double *>(k.BA);
+        async_copy<double, TEAM>(d, a.data.B + in.oB + (long long)s * nx * nu, nx * nu);
+        async_copy<double, TEAM>(d + nx * nu, a.data.A + in.oA + (long long)s * nx * nx, nx * nx);
     }
-    cp_async_commit();
 }
 
 // Vectors of one work item (T), each nrhs copies.
 template <typename T>
 struct Vecs {
-    T *hh, *rho, *pv, *tv, *wv, *gmu, *cv, *xv;
+    T *hh, *rho, *wv, *tv, *pv, *gmu, *cv, *xa, *xb;
+    T *nb;      // float32: the package's vector entries after conversion (two buffers of nbs)
+    int nbs;
 };
 
 template <typename T>
 __device__ Vecs<T> carve_vecs(unsigned char *p, int nx, int nu, int nrhs) {
-    const int nux = nx + nu;
+    const int nux = nx + nu, nv = nux + nx;
     T *q = reinterpret_cast<T *>(p);
     Vecs<T> v;
-    v.hh = q; q += nux * nrhs;
+    v.hh = q;  q += nux * nrhs;
     v.rho = q; q += nu * nrhs;
-    v.pv = q; q += nx * nrhs;
-    v.tv = q; q += nx * nrhs;
-    v.wv = q; q += nx * nrhs;
+    v.wv = q;  q += nx * nrhs;
+    v.tv = q;  q += nx * nrhs;
+    v.pv = q;  q += nx * nrhs;
     v.gmu = q; q += nx * nrhs;
-    v.cv = q; q += nx * nrhs;
-    v.xv = q; q += nx * nrhs;
+    v.cv = q;  q += nx * nrhs;
+    v.xa = q;  q += nx * nrhs;
+    v.xb = q;  q += nx * nrhs;
+    v.nb = q;
+    v.nbs = nv * nrhs;
     return v;
 }
 
 size_t vecs_bytes(bool fp64, int nx, int nu, int nrhs) {
-    return ((size_t)(nx + nu) * nrhs + (size_t)nu * nrhs + 6 * (size_t)nx * nrhs) * (fp64 ? 8 : 4);
+    const size_t nux = (size_t)nx + nu;
+    return (nux + nu + 7 * (size_t)nx + 2 * (nux + nx)) * nrhs * (fp64 ? 8 : 4);
+}
+
+// Vector entries of the package as T: float64 reads them in place; float32
+// converts the entries this thread copied itself (visible to it after its own
+// cp.async wait) into nb; the barrier that follows publishes them.
+template <typename T>
+__device__ __forceinline__ const T *package_vectors(const Package<T> &K, const Vecs<T> &v, int buf, const Walk &Wv,
+                                                    int nrhs, int nv) {
+    if (sizeof(T) == 8) return reinterpret_cast<const T *>(K.vb);
+    T *nb = v.nb + buf * v.nbs;
+    for (int i = Wv.i0, r = Wv.r0; r < nrhs; Wv.next(i, r)) nb[i + r * nv] = (T)K.vb[i + r * nv];
+    return nb;
 }
 
 }  // namespace
 
 size_t solve_smem_bytes(bool fp64, int nx, int nu, int nrhs, int nbuf) {
-    return nbuf * package_bytes(fp64, nx, nu) + vecs_bytes(fp64, nx, nu, nrhs);
+    return align16(nbuf * package_bytes(fp64, nx, nu, nrhs)) + vecs_bytes(fp64, nx, nu, nrhs);
 }
 
 template <typename T, int TEAM>
@@ -138,163 +199,153 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
         if (a.skip && a.skip[wi.inst]) continue;
         const Inst in = a.inst[wi.inst];
         const int N = in.N, nx = in.nx, nu = in.nu, P = in.P, c = wi.seg, nrhs = a.nrhs;
-        const int nux = nx + nu, w = nu + 2 * nx;
+        const int nux = nx + nu, nv = nux + nx, w = nu + 2 * nx;
         const int len = seg_len(c, N, P);
-        unsigned char *p = smem_raw;
-        Package<T> pk[2];
-        pk[0] = carve_package<T>(p, nx, nu);
-        pk[1] = a.nbuf == 2 ? carve_package<T>(p, nx, nu) : pk[0];
-        const Vecs<T> v = carve_vecs<T>(p, nx, nu, nrhs);
+        Walk Wu, Wx, Wux, Wv;
+        Wu.init(nu, TEAM);
+        Wx.init(nx, TEAM);
+        Wux.init(nux, TEAM);
+        Wv.init(nv, TEAM);
+        // package t at smem_raw + (t & 1) * pstride (one package when nbuf == 1)
+        const size_t pbytes = package_bytes(sizeof(T) == 8, nx, nu, nrhs);
+        const size_t pstride = a.nbuf == 2 ? pbytes : 0;
+        auto package = [&](int t) {
+            unsigned char *q = smem_raw + (size_t)(t & 1) * pstride;
+            return carve_package<T>(q, nx, nu, nrhs);
+        };
+        const Vecs<T> v = carve_vecs<T>(smem_raw + align16(a.nbuf * pbytes), nx, nu, nrhs);
         const double *b = a.b + in.oZ;
         double *z = a.z + in.oZ;
 
-        // package t: factor blocks of stage s(t) and [B A] of stage s(t+1)
+        // package t: factor blocks of stage s(t); [B A] of stage s(t+1) and its
+        // right-hand-side entries (b_u, b_x of h_{s(t+1)}, then b_lambda = -c)
         auto fetch = [&](int t) {
             const int s = seg_stage(c, t, N, P);
-            const bool last = t == len - 1;
-            fetch_package<T, TEAM>(pk[t & 1], a, in, s, (t == 0) || (c >= 1), c >= 1,
-                                   last ? -1 : seg_stage(c, t + 1, N, P));
+            const Package<T> K = package(t);
+            fetch_factor<T, TEAM>(K, a, in, s, (t == 0) || (c >= 1), c >= 1);
+            if (t < len - 1) {
+                const int s2 = seg_stage(c, t + 1, N, P), xq2 = xstate(s2, N);
+                fetch_BA<T, TEAM>(K, a, in, s2);
+                for (int i = Wv.i0, r = Wv.r0; r < nrhs; Wv.next(i, r)) {
+                    const double *br = b + r * a.kkt;
+                    const double *src = i < nu    ? br + (long long)s2 * w + i
+                                        : i < nux ? br + (long long)(xq2 - 1) * w + i
+                                                  : br + (long long)s2 * w + nu + (i - nu);
+                    cp_async8(K.vb + i + r * nv, src);
+                }
+            }
+            cp_async_commit();
         };
         fetch(0);
         {
             const int s = seg_stage(c, 0, N, P), xq = xstate(s, N);
-            for (int e = threadIdx.x; e < nux * nrhs; e += TEAM) {
-                const int aa = e % nux, r = e / nux;
+            for (int i = Wux.i0, r = Wux.r0; r < nrhs; Wux.next(i, r)) {
                 const double *br = b + r * a.kkt;
-                v.hh[e] = aa < nu ? -(T)br[(long long)s * w + aa] : -(T)br[(long long)(xq - 1) * w + nu + (aa - nu)];
+                v.hh[i + r * nux] = -(T)(i < nu ? br[(long long)s * w + i] : br[(long long)(xq - 1) * w + i]);
             }
             for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) v.gmu[e] = T(0);
         }
         for (int t = 0; t < len; ++t) {
             const int s = seg_stage(c, t, N, P), xq = xstate(s, N);
             const bool hasG = (t == 0) || (c >= 1);
-            const bool last = (t == len - 1);
-            const Package<T> &K = pk[t & 1];
+            const bool last = t == len - 1;
+            const Package<T> K = package(t);
             cp_async_wait_all();
+            const T *nb = last ? nullptr : package_vectors<T>(K, v, t & 1, Wv, nrhs, nv);
             team_sync();
             if (!last && a.nbuf == 2) fetch(t + 1);   // overlaps with this stage
             const T *Ls = K.L, *Ds = K.D;
             const T *LQ = Ls + nu + nu * nux, *DQ = Ds + nu;
-            // rho = L^{R-1} h_u  (stored inverse: diagonal Ds, strictly lower part transposed above)
-            {
-                int i, r;
-                rect_start(threadIdx.x, nu, i, r);
-                for (; r < nrhs; rect_advance(i, r, nu, TEAM)) {
-                    const T *hu = v.hh + r * nux;
-                    T acc = Ds[i] * hu[i];
-                    for (int k = 0; k < i; ++k) acc = fma(Ls[k + i * nux], hu[k], acc);
-                    v.rho[i + r * nu] = acc;
-                }
+
+            // phase 1: rho = L^{R-1} h_u (stored inverse);  w = L^{Q T} c
+            for (int i = Wu.i0, r = Wu.r0; r < nrhs; Wu.next(i, r)) {
+                const T *hu = v.hh + r * nux;
+                T acc = Ds[i] * hu[i];
+#pragma unroll 4
+                for (int k = 0; k < i; ++k) acc = fma(Ls[k + i * nux], hu[k], acc);
+                v.rho[i + r * nu] = acc;
             }
-            // next stage's constant terms (independent of rho)
-            int s2 = 0, xq2 = 0;
             if (!last) {
-                s2 = seg_stage(c, t + 1, N, P);
-                xq2 = xstate(s2, N);
-                for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
-                    const int i = e % nx, r = e / nx;
-                    v.cv[e] = -(T)b[r * a.kkt + (long long)s2 * w + nu + nx + i];
+                for (int j = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(j, r)) {
+                    const T *cr = nb + r * nv + nux;   // b_lambda = -c
+                    T acc = T(0);
+#pragma unroll 4
+                    for (int k = j; k < nx; ++k) acc = fma(LQ[k + j * nux], cr[k], acc);
+                    v.wv[j + r * nx] = -acc;
                 }
             }
             team_sync();
-            // p = h_x - L^S rho ;  g -= L^B rho ; park rho, p
-            {
-                int i, r;
-                rect_start(threadIdx.x, nx, i, r);
-                for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
-                    const T *ro = v.rho + r * nu;
-                    T acc = v.hh[r * nux + nu + i];
-                    for (int k = 0; k < nu; ++k) acc = fma(-Ls[(nu + i) + k * nux], ro[k], acc);
-                    v.pv[i + r * nx] = acc;
-                    z[r * a.kkt + (long long)(xq - 1) * w + nu + i] = (double)acc;
-                    if (hasG) {
-                        T g = v.gmu[i + r * nx];
-                        for (int k = 0; k < nu; ++k) g = fma(-K.LB[i + k * nx], ro[k], g);
-                        v.gmu[i + r * nx] = g;
+            // phase 2: p = h_x - L^S rho (parked);  g -= L^B rho;  t = L^Q w + p;  g += A^cl c
+            for (int i = Wu.i0, r = Wu.r0; r < nrhs; Wu.next(i, r))
+                z[r * a.kkt + (long long)s * w + i] = (double)v.rho[i + r * nu];
+            for (int i = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(i, r)) {
+                const T *ro = v.rho + r * nu;
+                T pacc = v.hh[r * nux + nu + i];
+#pragma unroll 4
+                for (int k = 0; k < nu; ++k) pacc = fma(-Ls[(nu + i) + k * nux], ro[k], pacc);
+                z[r * a.kkt + (long long)(xq - 1) * w + nu + i] = (double)pacc;
+                T g = v.gmu[i + r * nx];
+                if (hasG) {
+#pragma unroll 4
+                    for (int k = 0; k < nu; ++k) g = fma(-K.LB[i + k * nx], ro[k], g);
+                }
+                if (!last) {
+                    const T *wr = v.wv + r * nx;
+                    T acc = pacc;
+#pragma unroll 4
+                    for (int j = 0; j <= i; ++j) acc = fma(LQ[i + j * nux], wr[j], acc);
+                    v.tv[i + r * nx] = acc;
+                    if (c >= 1) {
+                        const T *cr = nb + r * nv + nux;
+#pragma unroll 4
+                        for (int k = 0; k < nx; ++k) g = fma(-K.F[i + k * nx], cr[k], g);
                     }
+                } else {
+                    v.pv[i + r * nx] = pacc;
                 }
-                for (int e = threadIdx.x; e < nu * nrhs; e += TEAM) {
-                    const int i = e % nu, r = e / nu;
-                    z[r * a.kkt + (long long)s * w + i] = (double)v.rho[e];
-                }
+                v.gmu[i + r * nx] = g;
             }
+            team_sync();
             if (!last) {
-                // w = L^{Q T} c
-                {
-                    int j, r;
-                    rect_start(threadIdx.x, nx, j, r);
-                    for (; r < nrhs; rect_advance(j, r, nx, TEAM)) {
-                        const T *cr = v.cv + r * nx;
-                        T acc = T(0);
-                        for (int k = j; k < nx; ++k) acc = fma(LQ[k + j * nux], cr[k], acc);
-                        v.wv[j + r * nx] = acc;
-                    }
+                // phase 3: h^_{s2} = h_{s2} + [B A]^T t
+                for (int aa = Wux.i0, r = Wux.r0; r < nrhs; Wux.next(aa, r)) {
+                    const T *tr = v.tv + r * nx;
+                    const T *col = K.BA + aa * nx;
+                    T acc = -nb[aa + r * nv];
+#pragma unroll 4
+                    for (int k = 0; k < nx; ++k) acc = fma(col[k], tr[k], acc);
+                    v.hh[aa + r * nux] = acc;
                 }
-                team_sync();
-                // t = L^Q w + p ;  g += A^cl c
-                {
-                    int i, r;
-                    rect_start(threadIdx.x, nx, i, r);
-                    for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
-                        const T *wr = v.wv + r * nx;
-                        T acc = v.pv[i + r * nx];
-                        for (int j = 0; j <= i; ++j) acc = fma(LQ[i + j * nux], wr[j], acc);
-                        v.tv[i + r * nx] = acc;
-                        if (c >= 1) {
-                            const T *cr = v.cv + r * nx;
-                            T g = v.gmu[i + r * nx];
-                            for (int k = 0; k < nx; ++k) g = fma(K.F[i + k * nx], cr[k], g);
-                            v.gmu[i + r * nx] = g;
-                        }
-                    }
-                }
-                team_sync();
-                // h^_{s2} = h_{s2} + [B A]^T t
-                {
-                    int aa, r;
-                    rect_start(threadIdx.x, nux, aa, r);
-                    for (; r < nrhs; rect_advance(aa, r, nux, TEAM)) {
-                        const double *br = b + r * a.kkt;
-                        const T *tr = v.tv + r * nx;
-                        const double *col = K.BA + aa * nx;
-                        T acc = aa < nu ? -(T)br[(long long)s2 * w + aa]
-                                        : -(T)br[(long long)(xq2 - 1) * w + nu + (aa - nu)];
-                        for (int k = 0; k < nx; ++k) acc = fma((T)col[k], tr[k], acc);
-                        v.hh[aa + r * nux] = acc;
-                    }
+                if (a.nbuf == 1) {
+                    team_sync();   // the single package is free again
+                    fetch(t + 1);
                 }
             } else {
-                team_sync();
-                // y = L^{Q-1} p  (inverse stored above the diagonal of this first stage's Q block)
-                {
-                    int i, r;
-                    rect_start(threadIdx.x, nx, i, r);
-                    for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
-                        const T *pr = v.pv + r * nx;
-                        T acc = DQ[i] * pr[i];
-                        for (int k = 0; k < i; ++k) acc = fma(LQ[k + i * nux], pr[k], acc);
-                        v.wv[i + r * nx] = acc;
-                    }
+                // y = L^{Q-1} p  (inverse stored above the diagonal of the segment's first Q block)
+                for (int i = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(i, r)) {
+                    const T *pr = v.pv + r * nx;
+                    T acc = DQ[i] * pr[i];
+#pragma unroll 4
+                    for (int k = 0; k < i; ++k) acc = fma(LQ[k + i * nux], pr[k], acc);
+                    v.wv[i + r * nx] = acc;
                 }
                 team_sync();
                 // d_bwd = L^{Q-T} y ;  d_fwd = g - L^A y
-                {
-                    int i, r;
-                    rect_start(threadIdx.x, nx, i, r);
-                    for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
-                        const T *y = v.wv + r * nx;
-                        T db = DQ[i] * y[i];
-                        for (int k = i + 1; k < nx; ++k) db = fma(LQ[i + k * nux], y[k], db);
-                        T df = v.gmu[i + r * nx];
-                        if (c >= 1)
-                            for (int k = 0; k < nx; ++k) df = fma(-K.F[i + k * nx], y[k], df);
-                        a.dF[r * a.nvec + in.oVec + (long long)c * nx + i] = (double)df;
-                        a.dB[r * a.nvec + in.oVec + (long long)c * nx + i] = (double)db;
+                for (int i = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(i, r)) {
+                    const T *y = v.wv + r * nx;
+                    T db = DQ[i] * y[i];
+#pragma unroll 4
+                    for (int k = i + 1; k < nx; ++k) db = fma(LQ[i + k * nux], y[k], db);
+                    T df = v.gmu[i + r * nx];
+                    if (c >= 1) {
+#pragma unroll 4
+                        for (int k = 0; k < nx; ++k) df = fma(-K.F[i + k * nx], y[k], df);
                     }
+                    a.dF[r * a.nvec + in.oVec + (long long)c * nx + i] = (double)df;
+                    a.dB[r * a.nvec + in.oVec + (long long)c * nx + i] = (double)db;
                 }
+                team_sync();   // shared memory is reused by the next work item
             }
-            team_sync();
-            if (!last && a.nbuf == 1) fetch(t + 1);   // the single package is free again
         }
     }
 }
@@ -307,23 +358,40 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
         if (a.skip && a.skip[wi.inst]) continue;
         const Inst in = a.inst[wi.inst];
         const int N = in.N, nx = in.nx, nu = in.nu, P = in.P, c = wi.seg, nrhs = a.nrhs;
-        const int nux = nx + nu, w = nu + 2 * nx;
+        const int nux = nx + nu, nv = nux + nx, w = nu + 2 * nx;
         const int len = seg_len(c, N, P);
-        unsigned char *p = smem_raw;
-        Package<T> pk[2];
-        pk[0] = carve_package<T>(p, nx, nu);
-        pk[1] = a.nbuf == 2 ? carve_package<T>(p, nx, nu) : pk[0];
-        const Vecs<T> v = carve_vecs<T>(p, nx, nu, nrhs);
+        Walk Wu, Wx, Wv;
+        Wu.init(nu, TEAM);
+        Wx.init(nx, TEAM);
+        Wv.init(nv, TEAM);
+        // package t at smem_raw + (t & 1) * pstride (one package when nbuf == 1)
+        const size_t pbytes = package_bytes(sizeof(T) == 8, nx, nu, nrhs);
+        const size_t pstride = a.nbuf == 2 ? pbytes : 0;
+        auto package = [&](int t) {
+            unsigned char *q = smem_raw + (size_t)(t & 1) * pstride;
+            return carve_package<T>(q, nx, nu, nrhs);
+        };
+        const Vecs<T> v = carve_vecs<T>(smem_raw + align16(a.nbuf * pbytes), nx, nu, nrhs);
         T *mu = v.gmu, *nuv = v.cv;   // coupling multipliers
         const double *b = a.b + in.oZ;
         double *z = a.z + in.oZ;
         double *zacc = a.zacc ? a.zacc + in.oZ : nullptr;
 
         // package for processing step t (time order: t = len-1 .. 0): factor blocks
-        // of stage s(t) and [B A] of that same stage (its outgoing dynamics)
+        // and [B A] of stage s(t), its parked rho / p and b_lambda = -c
         auto fetch = [&](int t) {
-            const int s = seg_stage(c, t, N, P);
-            fetch_package<T, TEAM>(pk[t & 1], a, in, s, (t == 0) || (c >= 1), c >= 1, t > 0 ? s : -1);
+            const int s = seg_stage(c, t, N, P), xq = xstate(s, N);
+            const Package<T> K = package(t);
+            fetch_factor<T, TEAM>(K, a, in, s, (t == 0) || (c >= 1), c >= 1);
+            if (t > 0) fetch_BA<T, TEAM>(K, a, in, s);
+            for (int i = Wv.i0, r = Wv.r0; r < nrhs; Wv.next(i, r)) {
+                if (i >= nux && t == 0) continue;
+                const double *src = i < nu    ? z + r * a.kkt + (long long)s * w + i
+                                    : i < nux ? z + r * a.kkt + (long long)(xq - 1) * w + i
+                                              : b + r * a.kkt + (long long)s * w + nu + (i - nu);
+                cp_async8(K.vb + i + r * nv, src);
+            }
+            cp_async_commit();
         };
         fetch(len - 1);
         for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
@@ -332,130 +400,109 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
             mu[e] = (T)lr[(long long)c * nx + i];
             nuv[e] = (T)lr[(long long)((c - 1 + P) % P) * nx + i];
         }
+        T *xv = v.xa, *xn = v.xb;
         for (int t = len - 1; t >= 0; --t) {
             const int s = seg_stage(c, t, N, P), xq = xstate(s, N);
             const bool hasG = (t == 0) || (c >= 1);
-            const bool first = (t == len - 1);
-            const Package<T> &K = pk[t & 1];
-            // parked rho / p of this stage
-            for (int e = threadIdx.x; e < nu * nrhs; e += TEAM) {
-                const int i = e % nu, r = e / nu;
-                v.rho[e] = (T)z[r * a.kkt + (long long)s * w + i];
-            }
-            for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
-                const int i = e % nx, r = e / nx;
-                v.pv[e] = (T)z[r * a.kkt + (long long)(xq - 1) * w + nu + i];
-            }
+            const bool first = t == len - 1;
+            const Package<T> K = package(t);
             cp_async_wait_all();
+            const T *nb = package_vectors<T>(K, v, t & 1, Wv, nrhs, nv);
             team_sync();
             if (t > 0 && a.nbuf == 2) fetch(t - 1);   // overlaps with this stage
             const T *Ls = K.L, *Ds = K.D;
             const T *LQ = Ls + nu + nu * nux, *DQ = Ds + nu;
             if (first) {
                 // x^{j1} = -L^{Q-T} (L^{Q-1}(p - nu) + L^{A T} mu)
-                {
-                    int i, r;
-                    rect_start(threadIdx.x, nx, i, r);
-                    for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
-                        const T *pr = v.pv + r * nx, *nr = nuv + r * nx, *mr = mu + r * nx;
-                        T acc = DQ[i] * (pr[i] - nr[i]);
-                        for (int k = 0; k < i; ++k) acc = fma(LQ[k + i * nux], pr[k] - nr[k], acc);
-                        if (c >= 1)
-                            for (int k = 0; k < nx; ++k) acc = fma(K.F[k + i * nx], mr[k], acc);
-                        v.wv[i + r * nx] = acc;
+                for (int i = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(i, r)) {
+                    const T *pr = nb + r * nv + nu, *nr = nuv + r * nx, *mr = mu + r * nx;
+                    T acc = DQ[i] * (pr[i] - nr[i]);
+                    for (int k = 0; k < i; ++k) acc = fma(LQ[k + i * nux], pr[k] - nr[k], acc);
+                    if (c >= 1) {
+#pragma unroll 4
+                        for (int k = 0; k < nx; ++k) acc = fma(K.F[k + i * nx], mr[k], acc);
                     }
+                    v.wv[i + r * nx] = acc;
                 }
                 team_sync();
-                {
-                    int i, r;
-                    rect_start(threadIdx.x, nx, i, r);
-                    for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
-                        const T *y = v.wv + r * nx;
-                        T acc = DQ[i] * y[i];
-                        for (int k = i + 1; k < nx; ++k) acc = fma(LQ[i + k * nux], y[k], acc);
-                        v.xv[i + r * nx] = -acc;
-                    }
+                for (int i = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(i, r)) {
+                    const T *y = v.wv + r * nx;
+                    T acc = DQ[i] * y[i];
+#pragma unroll 4
+                    for (int k = i + 1; k < nx; ++k) acc = fma(LQ[i + k * nux], y[k], acc);
+                    xv[i + r * nx] = -acc;
                 }
                 team_sync();
             }
-            // v = L^{S T} x + rho + L^{B T} mu  ->  hh[0..nu) ;  w = L^{Q T} x (interior stages)
-            {
-                int k, r;
-                rect_start(threadIdx.x, nu, k, r);
-                for (; r < nrhs; rect_advance(k, r, nu, TEAM)) {
-                    const T *x = v.xv + r * nx, *mr = mu + r * nx;
-                    T acc = v.rho[k + r * nu];
-                    for (int i = 0; i < nx; ++i) acc = fma(Ls[(nu + i) + k * nux], x[i], acc);
-                    if (hasG)
-                        for (int i = 0; i < nx; ++i) acc = fma(K.LB[i + k * nx], mr[i], acc);
-                    v.hh[k + r * nux] = acc;
+            // phase 1: v = L^{S T} x + rho + L^{B T} mu ;  w = L^{Q T} x (interior stages) ;  x out
+            for (int k = Wu.i0, r = Wu.r0; r < nrhs; Wu.next(k, r)) {
+                const T *x = xv + r * nx, *mr = mu + r * nx;
+                T acc = nb[k + r * nv];
+#pragma unroll 4
+                for (int i = 0; i < nx; ++i) acc = fma(Ls[(nu + i) + k * nux], x[i], acc);
+                if (hasG) {
+#pragma unroll 4
+                    for (int i = 0; i < nx; ++i) acc = fma(K.LB[i + k * nx], mr[i], acc);
                 }
+                v.hh[k + r * nux] = acc;
             }
-            if (!first) {
-                int j, r;
-                rect_start(threadIdx.x, nx, j, r);
-                for (; r < nrhs; rect_advance(j, r, nx, TEAM)) {
-                    const T *x = v.xv + r * nx;
+            for (int j = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(j, r)) {
+                const T *x = xv + r * nx;
+                if (!first) {
                     T acc = T(0);
+#pragma unroll 4
                     for (int k = j; k < nx; ++k) acc = fma(LQ[k + j * nux], x[k], acc);
                     v.wv[j + r * nx] = acc;
                 }
+                const long long o = r * a.kkt + (long long)(xq - 1) * w + nu + j;
+                if (zacc) atomicAdd(zacc + o, (double)x[j]); else z[o] = (double)x[j];
             }
             team_sync();
-            // u = -L^{R-T} v  (stored inverse)
-            {
-                int i, r;
-                rect_start(threadIdx.x, nu, i, r);
-                for (; r < nrhs; rect_advance(i, r, nu, TEAM)) {
-                    const T *vv = v.hh + r * nux;
-                    T acc = Ds[i] * vv[i];
-                    for (int k = i + 1; k < nu; ++k) acc = fma(Ls[i + k * nux], vv[k], acc);
-                    v.rho[i + r * nu] = -acc;
-                }
+            // phase 2: u = -L^{R-T} v (stored inverse) ;  lambda^{s-1} = L^Q w + p + A^{cl T} mu
+            for (int i = Wu.i0, r = Wu.r0; r < nrhs; Wu.next(i, r)) {
+                const T *vv = v.hh + r * nux;
+                T acc = Ds[i] * vv[i];
+#pragma unroll 4
+                for (int k = i + 1; k < nu; ++k) acc = fma(Ls[i + k * nux], vv[k], acc);
+                v.rho[i + r * nu] = -acc;
+                const long long o = r * a.kkt + (long long)s * w + i;
+                if (zacc) atomicAdd(zacc + o, (double)(-acc)); else z[o] = (double)(-acc);
             }
-            // interior multiplier lambda^{s-1} = L^Q L^{Q T} x + p + A^{cl T} mu
             if (!first) {
                 const int sp = (s - 1 + N) % N;
-                int i, r;
-                rect_start(threadIdx.x, nx, i, r);
-                for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
+                for (int i = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(i, r)) {
                     const T *wr = v.wv + r * nx, *mr = mu + r * nx;
-                    T acc = v.pv[i + r * nx];
+                    T acc = nb[r * nv + nu + i];
+#pragma unroll 4
                     for (int j = 0; j <= i; ++j) acc = fma(LQ[i + j * nux], wr[j], acc);
-                    if (c >= 1)
+                    if (c >= 1) {
+#pragma unroll 4
                         for (int k = 0; k < nx; ++k) acc = fma(K.F[k + i * nx], mr[k], acc);
+                    }
                     const long long o = r * a.kkt + (long long)sp * w + nu + nx + i;
-                    if (zacc) zacc[o] += (double)acc; else z[o] = (double)acc;
+                    if (zacc) atomicAdd(zacc + o, (double)acc); else z[o] = (double)acc;
                 }
             }
             team_sync();
-            for (int e = threadIdx.x; e < nu * nrhs; e += TEAM) {
-                const int i = e % nu, r = e / nu;
-                const long long o = r * a.kkt + (long long)s * w + i;
-                if (zacc) zacc[o] += (double)v.rho[e]; else z[o] = (double)v.rho[e];
-            }
-            for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
-                const int i = e % nx, r = e / nx;
-                const long long o = r * a.kkt + (long long)(xq - 1) * w + nu + i;
-                if (zacc) zacc[o] += (double)v.xv[e]; else z[o] = (double)v.xv[e];
-            }
             if (t > 0) {
-                // x^{s+1} = A_s x + B_s u + c_s
-                int i, r;
-                rect_start(threadIdx.x, nx, i, r);
-                for (; r < nrhs; rect_advance(i, r, nx, TEAM)) {
-                    const T *x = v.xv + r * nx, *u = v.rho + r * nu;
-                    T acc = -(T)b[r * a.kkt + (long long)s * w + nu + nx + i];
-                    for (int k = 0; k < nu; ++k) acc = fma((T)K.BA[i + k * nx], u[k], acc);
-                    for (int k = 0; k < nx; ++k) acc = fma((T)K.BA[i + (nu + k) * nx], x[k], acc);
-                    v.tv[i + r * nx] = acc;
+                // phase 3: x^{s+1} = A_s x + B_s u + c_s
+                for (int i = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(i, r)) {
+                    const T *x = xv + r * nx, *u = v.rho + r * nu;
+                    T acc = -nb[r * nv + nux + i];
+#pragma unroll 4
+                    for (int k = 0; k < nu; ++k) acc = fma(K.BA[i + k * nx], u[k], acc);
+#pragma unroll 4
+                    for (int k = 0; k < nx; ++k) acc = fma(K.BA[i + (nu + k) * nx], x[k], acc);
+                    xn[i + r * nx] = acc;
                 }
-                team_sync();
-                for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) v.xv[e] = v.tv[e];
+                T *tmp = xv; xv = xn; xn = tmp;
+                if (a.nbuf == 1) {
+                    team_sync();   // the single package is free again
+                    fetch(t - 1);
+                }
             }
-            team_sync();
-            if (t > 0 && a.nbuf == 1) fetch(t - 1);   // the single package is free again
         }
+        team_sync();   // shared memory is reused by the next work item
     }
 }
 
@@ -468,17 +515,19 @@ static cudaError_t launch_sweep(bool backward, size_t smem, const SolveArgs &a, 
     return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t launch_sweep_team(bool backward, int team, size_t smem, const SolveArgs &a, cudaStream_t st) {
+    if (team == 32) return launch_sweep<T, 32>(backward, smem, a, st);
+    if (team == 64) return launch_sweep<T, 64>(backward, smem, a, st);
+    if (team == 128) return launch_sweep<T, 128>(backward, smem, a, st);
+    return launch_sweep<T, 256>(backward, smem, a, st);
+}
+
 static cudaError_t launch_sweep_any(bool backward, bool fp64, int team, size_t smem, const SolveArgs &a,
                                     cudaStream_t st) {
     if (a.n_items == 0) return cudaSuccess;
-    if (fp64) {
-        if (team == 32) return launch_sweep<double, 32>(backward, smem, a, st);
-        if (team == 64) return launch_sweep<double, 64>(backward, smem, a, st);
-        return launch_sweep<double, 128>(backward, smem, a, st);
-    }
-    if (team == 32) return launch_sweep<float, 32>(backward, smem, a, st);
-    if (team == 64) return launch_sweep<float, 64>(backward, smem, a, st);
-    return launch_sweep<float, 128>(backward, smem, a, st);
+    return fp64 ? launch_sweep_team<double>(backward, team, smem, a, st)
+                : launch_sweep_team<float>(backward, team, smem, a, st);
 }
 
 cudaError_t launch_solve_backward(bool fp64, int team, size_t smem, const SolveArgs &a, cudaStream_t st) {
