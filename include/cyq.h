@@ -98,6 +98,9 @@ typedef struct cyq_desc {
     int32_t it_max;         /* max refinement steps; 0 = plain solve (no residual); < 0: default 10 */
     double tol;             /* relative KKT residual target, default 1e-10 if <= 0 */
     int32_t device;         /* CUDA device ordinal (the caller's current device if < 0) */
+    int32_t esc_max;        /* float32 mode: float64 corrections after re-factoring, in float64,
+                               the instances still above tol after it_max steps; 0 = none,
+                               < 0: default 3 */
 } cyq_desc;
 
 /*

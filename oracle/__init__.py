@@ -31,6 +31,8 @@ def lib():
         L.oracle_build_rhs.restype = None
         L.oracle_kkt_matvec.argtypes = [i, i, i, d, d, d, d, d, d, d, d]
         L.oracle_kkt_matvec.restype = None
+        L.oracle_kkt_abs_matvec.argtypes = [i, i, i, d, d, d, d, d, d, d, d]
+        L.oracle_kkt_abs_matvec.restype = None
         L.oracle_kkt_residual.argtypes = [i, i, i, d, d, d, d, d, d, d, d, d]
         L.oracle_kkt_residual.restype = ctypes.c_double
         L.oracle_kkt_dense.argtypes = [i, i, i, d, d, d, d, d, d, d]
@@ -80,6 +82,26 @@ def kkt_matvec(inst, z) -> np.ndarray:
     y = np.zeros(kkt_size(inst))
     lib().oracle_kkt_matvec(N, nx, nu, _p(Q), _p(R), _p(S), _p(A), _p(B), _p(Sg), _p(z), _p(y))
     return y
+
+
+def kkt_abs_matvec(inst, z) -> np.ndarray:
+    """|K| |z| (absolute values of every coefficient and entry)."""
+    N, nx, nu, Q, R, S, A, B, Sg = _data(inst)
+    z = _f(z)
+    y = np.zeros(kkt_size(inst))
+    lib().oracle_kkt_abs_matvec(N, nx, nu, _p(Q), _p(R), _p(S), _p(A), _p(B), _p(Sg), _p(z), _p(y))
+    return y
+
+
+def residual_eval_bound(inst, z, b) -> float:
+    """Bound on the error of any float64 evaluation of ||b - K z|| / ||b||:
+    gamma_m || |b| + |K| |z| ||_2 / ||b||_2 with m = 2 nx + nu + 2 terms per row
+    (componentwise bound of a float64 sum of m products, Higham Sec. 3.1)."""
+    u = 2.0 ** -53
+    m = 2 * inst.nx + inst.nu + 2
+    gamma = m * u / (1.0 - m * u)
+    b = _f(b)
+    return float(gamma * np.linalg.norm(np.abs(b) + kkt_abs_matvec(inst, z)) / np.linalg.norm(b))
 
 
 def kkt_residual(inst, z, b) -> float:

@@ -227,6 +227,61 @@ void oracle_kkt_matvec(int N, int nx, int nu, const double *Q, const double *R, 
     free(t);
 }
 
+/* y += |A| |x| (A m x n) and y += |A|^T |x| */
+static void abs_mat_vec_add(int m, int n, const double *A, const double *x, double *y) {
+    for (int i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s += fabs(A[IX(i, j, m)]) * fabs(x[j]);
+        y[i] += s;
+    }
+}
+static void abs_mat_tvec_add(int m, int n, const double *A, const double *x, double *y) {
+    for (int j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += fabs(A[IX(i, j, m)]) * fabs(x[i]);
+        y[j] += s;
+    }
+}
+
+/* y = |K| |z|: the rows of oracle_kkt_matvec with every coefficient and every
+ * entry of z replaced by its absolute value (the identity couplings of the
+ * dynamics count +1).  Componentwise, an evaluation of b - K z in float64 with
+ * any summation order is within gamma_m (|b| + |K| |z|) of the exact value,
+ * gamma_m = m u / (1 - m u), m the number of terms of a row plus one
+ * (Higham, Accuracy and Stability of Numerical Algorithms, Sec. 3.1). */
+void oracle_kkt_abs_matvec(int N, int nx, int nu, const double *Q, const double *R, const double *S,
+                           const double *A, const double *B, const double *Sigma, const double *z, double *y) {
+    ocp_t p = {N, nx, nu, Q, R, S, A, B, Sigma};
+    size_t w = rec(&p);
+    double *M = malloc(sizeof(double) * (size_t)(nx > nu ? nx : nu) * (nx > nu ? nx : nu));
+    memset(y, 0, sizeof(double) * (size_t)N * w);
+    for (int k = 0; k < N; ++k) {
+        const double *u = z + k * w;
+        const double *xn = u + nu;
+        const double *lam = xn + nx;
+        const double *xk = k > 0 ? z + (k - 1) * w + nu : NULL;
+        double *yu = y + k * w, *yx = yu + nu, *yl = yx + nx;
+        effR(&p, k, M);
+        abs_mat_vec_add(nu, nu, M, u, yu);
+        if (xk && S) abs_mat_vec_add(nu, nx, blkS(&p, k), xk, yu);
+        abs_mat_tvec_add(nx, nu, blkB(&p, k), lam, yu);
+        int j = k + 1;
+        effQ(&p, j, M);
+        abs_mat_vec_add(nx, nx, M, xn, yx);
+        for (int i = 0; i < nx; ++i) yx[i] += fabs(lam[i]);
+        if (j < N) {
+            const double *un = z + j * w;
+            const double *ln = un + nu + nx;
+            if (S) abs_mat_tvec_add(nu, nx, blkS(&p, j), un, yx);
+            abs_mat_tvec_add(nx, nx, blkA(&p, j), ln, yx);
+        }
+        abs_mat_vec_add(nx, nu, blkB(&p, k), u, yl);
+        if (xk) abs_mat_vec_add(nx, nx, blkA(&p, k), xk, yl);
+        for (int i = 0; i < nx; ++i) yl[i] += fabs(xn[i]);
+    }
+    free(M);
+}
+
 /* relative residual ||b - K z||_2 / ||b||_2 (returns ||b - Kz|| if b = 0) */
 double oracle_kkt_residual(int N, int nx, int nu, const double *Q, const double *R, const double *S,
                            const double *A, const double *B, const double *Sigma,

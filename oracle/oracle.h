@@ -9,6 +9,8 @@ void oracle_build_rhs(int N, int nx, int nu, const double *S, const double *A,
 void oracle_kkt_matvec(int N, int nx, int nu, const double *Q, const double *R, const double *S,
                        const double *A, const double *B, const double *Sigma,
                        const double *z, double *y);
+void oracle_kkt_abs_matvec(int N, int nx, int nu, const double *Q, const double *R, const double *S,
+                           const double *A, const double *B, const double *Sigma, const double *z, double *y);
 double oracle_kkt_residual(int N, int nx, int nu, const double *Q, const double *R, const double *S,
                            const double *A, const double *B, const double *Sigma,
                            const double *z, const double *b, double *r_out);

@@ -244,8 +244,10 @@ cyq_status run_factor(cyq_handle h, const FactorSet &fs, const int *skip, cudaSt
     return CYQ_OK;
 }
 
-ResidArgs resid_args(cyq_handle h, const double *b, const double *z, double *r, const int *skip) {
+ResidArgs resid_args(cyq_handle h, const double *b, const double *z, double *r, const int *skip,
+                     bool need_bb = true) {
     ResidArgs a{};
+    a.need_bb = need_bb;
     a.inst = h->d_inst;
     a.chunks = h->d_chunks;
     a.n_chunks = (int)h->chunks.size();
@@ -276,8 +278,9 @@ cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, int nrhs,
     if (s != CYQ_OK) return s;
     int step = 0;
     for (int it = 0; it <= h->it_max; ++it, ++step) {
-        CYQ_CUDA(launch_residual(resid_args(h, b, z, h->r, h->done), nrhs, st));
-        CYQ_CUDA(launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, step, st));
+        // ||b||^2 once (first residual); later steps reuse it
+        CYQ_CUDA(launch_residual(resid_args(h, b, z, h->r, h->done, it == 0), nrhs, st));
+        CYQ_CUDA(launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, step, true, st));
         h->launches += 2;
         if (it == h->it_max) break;
         // correction: z += K~^{-1} r for the instances still above tol
@@ -293,8 +296,8 @@ cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, int nrhs,
             ++step;
             s = run_solve(h, h->fac64, h->r, h->dz, nrhs, h->done, st, z);
             if (s != CYQ_OK) return s;
-            CYQ_CUDA(launch_residual(resid_args(h, b, z, h->r, h->done), nrhs, st));
-            CYQ_CUDA(launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, step, st));
+            CYQ_CUDA(launch_residual(resid_args(h, b, z, h->r, h->done, false), nrhs, st));
+            CYQ_CUDA(launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, step, true, st));
             h->launches += 2;
         }
     }
@@ -348,6 +351,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     h->precision = desc->precision;
     h->max_nrhs = desc->max_nrhs > 0 ? desc->max_nrhs : 1;
     h->it_max = desc->it_max >= 0 ? desc->it_max : 10;
+    h->esc_max = desc->esc_max >= 0 ? desc->esc_max : 3;
     h->tol = desc->tol > 0 ? desc->tol : 1e-10;
     const bool fp64 = h->precision == CYQ_FP64;
 
@@ -597,7 +601,7 @@ cyq_status cyq_residual(cyq_handle h, const double *b, const double *z, double *
     CYQ_CUDA(cudaMemsetAsync(h->rr, 0, sizeof(double) * h->batch, st));
     CYQ_CUDA(cudaMemsetAsync(h->bb, 0, sizeof(double) * h->batch, st));
     CYQ_CUDA(launch_residual(resid_args(h, b, z, res, nullptr), 1, st));
-    CYQ_CUDA(launch_resid_finalize(h->batch, 1, h->rr, h->bb, rel ? rel : h->rel, nullptr, 0.0, nullptr, 0, st));
+    CYQ_CUDA(launch_resid_finalize(h->batch, 1, h->rr, h->bb, rel ? rel : h->rel, nullptr, 0.0, nullptr, 0, false, st));
     return CYQ_OK;
 }
 

@@ -369,6 +369,7 @@ struct ResidArgs {
     const int *skip;    // optional per-instance flag
     long long kkt;      // elements per right-hand side
     int batch;
+    bool need_bb;       // accumulate ||b||^2 too (false: bb already holds it)
 };
 
 struct GradArgs {
@@ -380,7 +381,7 @@ struct GradArgs {
 
 cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st);
 cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
-                                  int *steps, int step, cudaStream_t st);
+                                  int *steps, int step, bool keep_bb, cudaStream_t st);
 cudaError_t launch_ir_update(const Inst *inst, int batch, double *z, const double *dz, const int *done, long long kkt,
                              int nrhs, cudaStream_t st);
 cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, cudaStream_t st);

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
                 const double rv = bv - acc[r];
                 if (a.r) a.r[in.oZ + o] = rv;
                 sr[r] = fma(rv, rv, sr[r]);
-                sb[r] = fma(bv, bv, sb[r]);
+                if (a.need_bb) sb[r] = fma(bv, bv, sb[r]);
             }
         }
     };
@@ -61,12 +61,17 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
             double acc[RG];
 #pragma unroll
             for (int r = 0; r < RG; ++r) acc[r] = 0.0;
-            const double sg = d.Sig ? d.Sig[in.oSig + (long long)k * (nu + nx) + i] : 0.0;
             for (int j = 0; j < nu; ++j) {
-                const double m = R[i + j * nu] + (j == i ? sg : 0.0);
+                const double m = R[i + j * nu];
 #pragma unroll
                 for (int r = 0; r < RG; ++r)
                     if (r < nr) acc[r] = fma(m, zb[(r0 + r) * kk + (long long)k * w + j], acc[r]);
+            }
+            if (d.Sig) {
+                const double sg = d.Sig[in.oSig + (long long)k * (nu + nx) + i];
+#pragma unroll
+                for (int r = 0; r < RG; ++r)
+                    if (r < nr) acc[r] = fma(sg, zb[(r0 + r) * kk + (long long)k * w + i], acc[r]);
             }
             if (k > 0 && d.S) {
                 const double *S = d.S + in.oS + (long long)k * nu * nx;
@@ -97,12 +102,17 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
 #pragma unroll
             for (int r = 0; r < RG; ++r)
                 acc[r] = r < nr ? -zb[(r0 + r) * kk + (long long)k * w + nu + nx + i] : 0.0;
-            const double sg = d.Sig ? d.Sig[in.oSig + (long long)j1 * (nu + nx) + nu + i] : 0.0;
             for (int m = 0; m < nx; ++m) {
-                const double v = Q[i + m * nx] + (m == i ? sg : 0.0);
+                const double v = Q[i + m * nx];
 #pragma unroll
                 for (int r = 0; r < RG; ++r)
                     if (r < nr) acc[r] = fma(v, zb[(r0 + r) * kk + (long long)k * w + nu + m], acc[r]);
+            }
+            if (d.Sig) {
+                const double sg = d.Sig[in.oSig + (long long)j1 * (nu + nx) + nu + i];
+#pragma unroll
+                for (int r = 0; r < RG; ++r)
+                    if (r < nr) acc[r] = fma(sg, zb[(r0 + r) * kk + (long long)k * w + nu + i], acc[r]);
             }
             if (j1 < N) {
                 const double *A = d.A + in.oA + (long long)j1 * nx * nx;
@@ -159,7 +169,7 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
         double x = sr[r], y = sb[r];
         for (int o = 16; o > 0; o >>= 1) {
             x += __shfl_xor_sync(0xffffffffu, x, o);
-            y += __shfl_xor_sync(0xffffffffu, y, o);
+            if (a.need_bb) y += __shfl_xor_sync(0xffffffffu, y, o);
         }
         if ((threadIdx.x & 31) == 0) {
             red[2 * r][threadIdx.x >> 5] = x;
@@ -175,16 +185,17 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
             tb += red[2 * r + 1][i];
         }
         atomicAdd(a.rr + (long long)(r0 + r) * a.batch + ch.inst, tr);
-        atomicAdd(a.bb + (long long)(r0 + r) * a.batch + ch.inst, tb);
+        if (a.need_bb) atomicAdd(a.bb + (long long)(r0 + r) * a.batch + ch.inst, tb);
     }
 }
 
 // Per instance: rel[r] = ||res_r|| / ||b_r|| for each right-hand side r; the
 // instance is done once every right-hand side is at or below tol (refinement
-// runs per instance).  Clears the accumulators.  steps[i] records the number
+// runs per instance).  Clears the accumulators (||b||^2 stays when keep_bb:
+// b does not change between the refinement steps of one solve).  steps[i] records the number
 // of corrections an instance received so far.
 __global__ void k_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
-                                 int *steps, int step) {
+                                 int *steps, int step, bool keep_bb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= batch) return;
     if (done && done[i]) return;
@@ -196,7 +207,7 @@ __global__ void k_resid_finalize(int batch, int nrhs, double *rr, double *bb, do
         if (rel) rel[j] = v;
         all = all && (v <= tol);
         rr[j] = 0.0;
-        bb[j] = 0.0;
+        if (!keep_bb) bb[j] = 0.0;
     }
     if (done && all) done[i] = 1;
     if (steps) steps[i] = step;
@@ -356,8 +367,8 @@ cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st) {
 }
 
 cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
-                                  int *steps, int step, cudaStream_t st) {
-    k_resid_finalize<<<(batch + 127) / 128, 128, 0, st>>>(batch, nrhs, rr, bb, rel, done, tol, steps, step);
+                                  int *steps, int step, bool keep_bb, cudaStream_t st) {
+    k_resid_finalize<<<(batch + 127) / 128, 128, 0, st>>>(batch, nrhs, rr, bb, rel, done, tol, steps, step, keep_bb);
     return cudaGetLastError();
 }
 

@@ -39,7 +39,8 @@ class cyq_desc(ctypes.Structure):
                 ("nx", ctypes.POINTER(ctypes.c_int32)), ("nu", ctypes.POINTER(ctypes.c_int32)),
                 ("precision", ctypes.c_int32), ("P", ctypes.c_int32),
                 ("P_per_instance", ctypes.POINTER(ctypes.c_int32)), ("max_nrhs", ctypes.c_int32),
-                ("it_max", ctypes.c_int32), ("tol", ctypes.c_double), ("device", ctypes.c_int32)]
+                ("it_max", ctypes.c_int32), ("tol", ctypes.c_double), ("device", ctypes.c_int32),
+                ("esc_max", ctypes.c_int32)]
 
 
 class cyq_stats(ctypes.Structure):
@@ -112,7 +113,7 @@ class Solver:
 
     def __init__(self, N: Sequence[int], nx: Sequence[int], nu: Sequence[int], precision: str = "fp64",
                  P: int = 0, P_per_instance: Optional[Sequence[int]] = None, max_nrhs: int = 1,
-                 it_max: int = -1, tol: float = 1e-10, device: int = -1):
+                 it_max: int = -1, tol: float = 1e-10, device: int = -1, esc_max: int = -1):
         L = load()
         self.N = np.ascontiguousarray(N, dtype=np.int32)
         self.nx = np.ascontiguousarray(nx, dtype=np.int32)
@@ -127,7 +128,7 @@ class Solver:
         desc = cyq_desc(self.batch, self.N.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                         self.nx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                         self.nu.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.precision, P, pp,
-                        max_nrhs, it_max, tol, device)
+                        max_nrhs, it_max, tol, device, esc_max)
         h = ctypes.c_void_p()
         _check(L.cyq_create(ctypes.byref(desc), ctypes.byref(h)))
         self._h = h

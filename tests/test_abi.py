@@ -40,8 +40,8 @@ def test_host_logic_without_device():
     L = cyq.load()
     assert L.cyq_status_string(2) == b"matrix not positive definite"
     N = (ctypes.c_int32 * 1)(4)
-    d = cyq.cyq_desc(1, N, N, N, 0, 0, None, 1, 0, 0.0, -1)
+    d = cyq.cyq_desc(1, N, N, N, 0, 0, None, 1, 0, 0.0, -1, -1)
     h = ctypes.c_void_p()
     assert L.cyq_create(ctypes.byref(d), ctypes.byref(h)) == 8     # CYQ_ERR_NO_DEVICE
-    bad = cyq.cyq_desc(0, N, N, N, 0, 0, None, 1, 0, 0.0, -1)
+    bad = cyq.cyq_desc(0, N, N, N, 0, 0, None, 1, 0, 0.0, -1, -1)
     assert L.cyq_create(ctypes.byref(bad), ctypes.byref(h)) == 1   # CYQ_ERR_INVALID_ARG

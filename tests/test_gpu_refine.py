@@ -12,16 +12,19 @@ from gpu_util import gpu_solve, oracle_rhs, ragged_batch, rel_err, split_instanc
 
 pytestmark = pytest.mark.gpu
 
-# the oracle's float64 re-evaluation of a residual certified <= 1e-10 on the
-# device may differ by a few % (different summation order); see test_gpu_workloads
-EVAL_TOL = 1.05e-10
+# The oracle's float64 re-evaluation of a residual certified <= 1e-10 on the
+# device may differ from the device's by up to twice the rounding bound of a
+# float64 evaluation (oracle.residual_eval_bound); column 0 below is the
+# oracle residual minus that allowance.
+TOL = 1e-10
 
 
 def _residuals(batch, z, b):
     out = []
     for j in range(z.shape[0]):
         for inst, zi, bi in zip(batch.instances, split_instances(batch, z[j]), split_instances(batch, b[j])):
-            out.append((oracle.kkt_residual(inst, zi, bi), rel_err(zi, oracle.riccati_solve(inst, bi))))
+            res = oracle.kkt_residual(inst, zi, bi) - 2.0 * oracle.residual_eval_bound(inst, zi, bi)
+            out.append((res, rel_err(zi, oracle.riccati_solve(inst, bi))))
     return np.array(out)
 
 
@@ -34,7 +37,7 @@ def test_refinement_reaches_tolerance_on_ragged_batch(precision, P):
                            P_per_instance=[min(P, d[0]) for d in dims])
     assert (s.instance_status() == 0).all()
     res = _residuals(batch, z, b)
-    assert res[:, 0].max() <= EVAL_TOL, res[:, 0].max()
+    assert res[:, 0].max() <= TOL, res[:, 0].max()
     assert res[:, 1].max() <= 1e-8
     st = s.stats()
     assert st["max_rel_residual"] <= 1e-10
@@ -55,7 +58,8 @@ def test_fp32_refine_on_batch1024_workload_sampled():
         zs, bs = split_instances(batch, z[j]), split_instances(batch, b[j])
         for i in sample:
             inst = batch.instances[i]
-            assert oracle.kkt_residual(inst, zs[i], bs[i]) <= EVAL_TOL
+            assert (oracle.kkt_residual(inst, zs[i], bs[i]) <=
+                    TOL + 2.0 * oracle.residual_eval_bound(inst, zs[i], bs[i]))
             assert rel_err(zs[i], oracle.riccati_solve(inst, bs[i])) <= 1e-8
 
 
@@ -82,4 +86,4 @@ def test_float64_escalation_rescues_hard_instances():
     z, s, _, b = gpu_solve(batch, precision="fp32_refine", it_max=1)
     assert (s.instance_status() == 0).all()
     res = _residuals(batch, z, b)
-    assert res[:, 0].max() <= EVAL_TOL, res[:, 0]
+    assert res[:, 0].max() <= TOL, res[:, 0]

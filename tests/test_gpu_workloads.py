@@ -10,12 +10,11 @@ on the device: status words and the refinement's own float64 residuals).
 
 Gates: refined solves reach <= 1e-10 relative KKT residual as evaluated by the
 library's float64 residual (device statistics), and the oracle's independent
-float64 evaluation on the same z agrees within EVAL_TOL: two float64
-evaluations of ||b - K z|| with different summation orders differ by up to
-2.5 % (measured) near 1e-10 on the hardest instances of the uneven workload
-(cond(K) ~ 1e11: the rounding of each row sum is ~ u sum_j |K_ij z_j|, the
-same order as the residual itself); plain float64 forward error <= 1e-9 against
-the oracle;
+float64 evaluation on the same z is at most 1e-10 plus twice the rounding
+bound of a float64 evaluation (gamma_m || |b| + |K| |z| || / ||b||, computed by
+the oracle): near 1e-10 on the hardest instances of the uneven workload that
+bound is a few percent of the residual itself, so the two evaluations can
+straddle the target; plain float64 forward error <= 1e-9 against the oracle;
 the adjoint <= 1e-9 relative to the oracle's.
 """
 import numpy as np
@@ -28,7 +27,12 @@ from gpu_util import rel_err, require_gpu, split_instances
 
 pytestmark = pytest.mark.gpu
 
-EVAL_TOL = 1.05e-10
+TOL = 1e-10
+
+
+def eval_gate(inst, z, b):
+    """Largest oracle-evaluated residual consistent with a device-certified TOL."""
+    return TOL + 2.0 * oracle.residual_eval_bound(inst, z, b)
 
 
 def _solve(batch, precision, it_max, P=0, nrhs=1):
@@ -69,7 +73,7 @@ def test_long_horizon_segments_and_cyclic_reduction(long_batch, precision, it_ma
               oracle.kkt_residual(inst, zo, bs[i]), st)
         assert err <= 1e-9
         if it_max:
-            assert res <= EVAL_TOL
+            assert res <= eval_gate(inst, zs[i], bs[i])
 
 
 def test_uneven_batch_fp32_refinement():
@@ -87,7 +91,8 @@ def test_uneven_batch_fp32_refinement():
         inst = batch.instances[i]
         res = oracle.kkt_residual(inst, zs[i], bs[i])
         worst = max(worst, res)
-        assert res <= EVAL_TOL, (i, inst.N, inst.nx, inst.nu, res)
+        assert res <= eval_gate(inst, zs[i], bs[i]), (i, inst.N, inst.nx, inst.nu, res,
+                                                       oracle.residual_eval_bound(inst, zs[i], bs[i]))
         assert rel_err(zs[i], oracle.riccati_solve(inst, bs[i])) <= 1e-8
     print("uneven4096 sampled worst residual", worst)
 

@@ -78,6 +78,34 @@ def test_dense_matrix_equals_structured_matvec_and_is_symmetric(N, nx, nu):
 
 
 @pytest.mark.parametrize("N,nx,nu", CASES)
+def test_abs_matvec_equals_dense_abs_product(N, nx, nu):
+    inst = _small(150 + N, N, nx, nu, sigma=(1e-3, 1e3))
+    K = oracle.kkt_dense(inst)
+    rng = np.random.default_rng(7 + N)
+    v = rng.standard_normal(K.shape[0])
+    assert np.allclose(np.abs(K) @ np.abs(v), oracle.kkt_abs_matvec(inst, v), rtol=1e-13, atol=0.0)
+
+
+def test_residual_evaluation_bound_holds():
+    """The float64 residual of a near-solution differs from the residual computed
+    in extended precision (dense K, numpy longdouble) by at most the stated bound."""
+    for seed, (N, nx, nu) in enumerate([(6, 5, 2), (8, 4, 3), (5, 6, 4)]):
+        inst = _small(300 + seed, N, nx, nu, sigma=(1e-6, 1e6))
+        q, r, c, x0 = inst.rhs[0]
+        b = oracle.build_rhs(inst, q, r, c, x0)
+        z0 = oracle.riccati_solve(inst, b)
+        rng = np.random.default_rng(seed)
+        K = oracle.kkt_dense(inst).astype(np.longdouble)
+        # the solution itself (residual near the float64 floor) and a perturbed one
+        for z in (z0, z0 * (1.0 + 1e-9 * rng.standard_normal(z0.size))):
+            exact = np.linalg.norm((b.astype(np.longdouble) - K @ z.astype(np.longdouble)).astype(np.float64))
+            rel_exact = exact / np.linalg.norm(b)
+            bound = oracle.residual_eval_bound(inst, z, b)
+            assert abs(oracle.kkt_residual(inst, z, b) - rel_exact) <= bound
+            assert bound < 1e-10   # informative at the 1e-10 refinement target
+
+
+@pytest.mark.parametrize("N,nx,nu", CASES)
 def test_inertia_of_kkt_matrix(N, nx, nu):
     inst = _small(200 + N, N, nx, nu)
     ev = np.linalg.eigvalsh(oracle.kkt_dense(inst))
