@@ -49,13 +49,32 @@ METHODS = {"fp64": ("fp64", 0), "fp64_refine": ("fp64", 3), "fp32_refine": ("fp3
 # residual kernel
 REFINE_TOL = 1e-10
 # workload -> methods (first = headline), CUDA-graph replay, adjoint in the step
+# workload -> methods (first = headline), CUDA-graph replay, adjoint in the step,
+# segment counts tuned by timing (cyq_tune_segments); launch shapes are always
+# tuned by timing (cyq_autotune) before the timed region
 WORKLOADS = {
-    "batch1024_n64_nx12_nu4": dict(methods=["fp64_refine", "fp64", "fp32_refine"], graph=False, adjoint=False),
-    "single_n32_nx8_nu4": dict(methods=["fp64", "fp64_refine"], graph=True, adjoint=False),
-    "long_n4096_nx32_nu16": dict(methods=["fp32_refine", "fp64", "fp64_refine"], graph=False, adjoint=False),
-    "uneven4096": dict(methods=["fp32_refine", "fp64_refine"], graph=True, adjoint=False),
-    "adjoint512_n128_nx24_nu8": dict(methods=["fp64_refine"], graph=False, adjoint=True),
+    "batch1024_n64_nx12_nu4": dict(methods=["fp64_refine", "fp64", "fp32_refine"], graph=False, adjoint=False,
+                                   tune_segments=False),
+    "single_n32_nx8_nu4": dict(methods=["fp64", "fp64_refine"], graph=True, adjoint=False, tune_segments=True),
+    "long_n4096_nx32_nu16": dict(methods=["fp32_refine", "fp64", "fp64_refine"], graph=False, adjoint=False,
+                                 tune_segments=True),
+    "uneven4096": dict(methods=["fp32_refine", "fp64_refine"], graph=True, adjoint=False, tune_segments=True),
+    "adjoint512_n128_nx24_nu8": dict(methods=["fp64_refine"], graph=False, adjoint=True, tune_segments=False),
 }
+
+
+def tuned_solver(torch, cyq, batch, data, b, method, tune_segments, P=None):
+    """A solver for `method` with timed-autotuned segment counts (when asked, or
+    the given P) and launch shapes; returns (solver, P).  Untimed setup."""
+    precision, it_max = METHODS[method]
+    nrhs = len(batch.rhs)
+    if P is None and tune_segments:
+        P = cyq.tune_segments(batch.N, batch.nx, batch.nu, data, b, nrhs=nrhs, reps=2, precision=precision,
+                              it_max=it_max, tol=REFINE_TOL)
+    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, max_nrhs=nrhs, it_max=it_max,
+                   tol=REFINE_TOL, P_per_instance=P)
+    s.autotune(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"], b, nrhs=nrhs, reps=3)
+    return s, P
 
 
 def parse():
@@ -230,14 +249,14 @@ L2_BYTES = 129e6
 
 
 def run_method(torch, cyq, batch, data, b, x0, method, steps, warmup, dist, graph=False, adjoint=False,
-               flush=None):
+               flush=None, tune_segments=False):
     """Time `steps` factor+solve steps.  With `flush` (a device buffer larger than
     L2), the buffer is rewritten between steps, outside the per-step events, and
     the step time is the sum of the per-step event intervals."""
     precision, it_max = METHODS[method]
     nrhs = len(batch.rhs)
-    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, max_nrhs=nrhs, it_max=it_max,
-                   tol=REFINE_TOL)
+    s, P = tuned_solver(torch, cyq, batch, data, b, method, tune_segments)
+    shapes = s.launch_shapes(nrhs=nrhs)
     z = torch.empty_like(b)
     mask = _loss_grad(torch, batch, torch.ones_like(b[:s.kkt_size])) / 2.0 if adjoint else None
 
@@ -323,17 +342,17 @@ def run_method(torch, cyq, batch, data, b, x0, method, steps, warmup, dist, grap
     s.close()
     return dict(total_ms=total_ms, factor_ms=float(np.mean(factor_ms)), solve_ms=float(np.mean(solve_ms)),
                 status_ok=bool((status == 0).all()), stats=st, segments=segments,
-                launches_per_step=launches_factor + launches_solve)
+                launches_per_step=launches_factor + launches_solve, P=P, shapes=shapes)
 
 
-def run_e2e(torch, cyq, batch, method, steps, warmup, adjoint=False):
+def run_e2e(torch, cyq, batch, method, steps, warmup, data, b, P=None, adjoint=False):
     """Same metric through the public API with host buffers: every step copies
     the data and (q, r, c, x_init) from pinned host memory, builds the KKT
-    right-hand sides, factors, solves and copies z back to pinned memory."""
+    right-hand sides, factors, solves and copies z back to pinned memory.  The
+    solver is tuned like the device-resident one (same segment counts)."""
     precision, it_max = METHODS[method]
     nrhs = len(batch.rhs)
-    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, max_nrhs=nrhs, it_max=it_max,
-                   tol=REFINE_TOL)
+    s, _ = tuned_solver(torch, cyq, batch, data, b, method, False, P=P)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     host = {k: pin(getattr(batch, k)) for k in ("Q", "R", "S", "A", "B")}
     host["Sigma"] = pin(batch.Sigma) if batch.Sigma is not None else None
@@ -456,7 +475,8 @@ def main():
     clocks = ClockSampler(local_rank)
     clocks.start()
     results = {m: run_method(torch, cyq, batch, data, b, x0, m, args.steps, args.warmup, dist,
-                             graph=prof["graph"], adjoint=prof["adjoint"], flush=flush) for m in methods}
+                             graph=prof["graph"], adjoint=prof["adjoint"], flush=flush,
+                             tune_segments=prof["tune_segments"]) for m in methods}
     clk = clocks.stop()
     head = methods[0]
     R = results[head]
@@ -465,8 +485,8 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e2e_ms, h2d, d2h = run_e2e(torch, cyq, batch, head, max(3, args.steps // 4), args.warmup,
-                                   adjoint=prof["adjoint"])
+        e2e_ms, h2d, d2h = run_e2e(torch, cyq, batch, head, max(3, args.steps // 4), args.warmup, data, b,
+                                   P=R["P"], adjoint=prof["adjoint"])
         e2e_ms = shard.reduce_time_ms(e2e_ms, dist, device="cuda")
         e2e = {"value": world * batch.size / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
@@ -490,6 +510,8 @@ def main():
                        "max_rel_residual": r["stats"]["max_rel_residual"],
                        "refine_steps": r["stats"]["refine_steps"], "status_ok": r["status_ok"],
                        "segments_per_ocp": [int(r["segments"].min()), int(r["segments"].max())],
+                       "segments_tuned": r["P"] is not None,
+                       "threads_per_item": r["shapes"],
                        "factor_gflops": fl / (r["factor_ms"] / 1e3) / 1e9,
                        "factor_frac_of_pipe_peak": fl / (r["factor_ms"] / 1e3) / 1e9 / peak}
     fl = 2.0 * batch_factor_fma(batch, R["segments"])

@@ -197,6 +197,44 @@ cyq_status cyq_get_segments(cyq_handle h, int32_t *P_out);
 int64_t cyq_last_launch_count(cyq_handle h);
 
 /*
+ * Launch-shape autotuner (the paper tunes its SIMD width and segment count
+ * per problem size, Sec. 5; here the GPU analogue).  For every size class of
+ * the handle, times the stage factorization with 32, 64 and 128 threads per
+ * work item and the two solve sweeps with 32 to 256 threads per work item
+ * (nrhs right-hand sides b), `reps` launches each (default 3 if < 1), with
+ * CUDA events on `stream`, and keeps the fastest shapes in the handle: the
+ * stage factor's for every later cyq_factor, the sweeps' for every later
+ * cyq_solve with this nrhs.  Binds and factors the data like cyq_factor and
+ * leaves the handle factored; z (nrhs * kkt_size) is scratch.  Synchronises
+ * the stream.  Results do not depend on the shapes (the same arithmetic in
+ * the same order per work item).  Errors: INVALID_ARG, CUDA.
+ */
+cyq_status cyq_autotune(cyq_handle h, const double *Q, const double *R, const double *S,
+                        const double *A, const double *B, const double *Sigma, const double *b,
+                        double *z, int32_t nrhs, int32_t reps, cyq_stream stream);
+
+/* Launch shapes in use: threads per work item of the stage factor and of the
+ * sweeps (for nrhs right-hand sides) per size class; arrays of *n_groups
+ * entries (either may be NULL; call with both NULL to get *n_groups). */
+cyq_status cyq_get_launch_shapes(cyq_handle h, int32_t *n_groups, int32_t *factor_team,
+                                 int32_t *sweep_team, int32_t nrhs);
+
+/*
+ * Segment-count tuner.  Starting from desc's segment counts (automatic where
+ * desc->P = 0 and no P_per_instance), tries the counts scaled by 1/4, 1/2, 1,
+ * 2 and 4 (clamped to [1, N_i]), each in a temporary handle: one untimed
+ * factor + solve, then `reps` (default 2 if < 1) timed factor + solve with
+ * nrhs right-hand sides b (refinement as set in desc).  Writes the fastest
+ * counts to P_out (host array [batch]) for use as desc->P_per_instance.
+ * Allocates and frees a handle per candidate (a candidate whose workspace
+ * cannot be allocated is skipped); z is scratch; synchronises the stream.
+ * Errors: INVALID_ARG, CUDA and the errors of cyq_create / cyq_solve.
+ */
+cyq_status cyq_tune_segments(const cyq_desc *desc, const double *Q, const double *R, const double *S,
+                             const double *A, const double *B, const double *Sigma, const double *b,
+                             double *z, int32_t nrhs, int32_t reps, cyq_stream stream, int32_t *P_out);
+
+/*
  * Allocation-free factor + solve of ONE OCP in float64 (one segment, one
  * right-hand side).  The paper has no counterpart: this entry point exists
  * for callers that must not allocate device memory at call time (a CUDA

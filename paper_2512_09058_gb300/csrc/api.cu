@@ -31,6 +31,9 @@ struct Group {
     bool staged[2] = {true, true};             // factor stages copied to shared memory, [float, double]
     size_t smem_factor[2] = {0, 0};
     int solve_nbuf[2] = {2, 2};                // solve stage packages in shared memory, [float, double]
+    int team_factor[2] = {0, 0};               // tuned threads per item of the stage factor (0: heuristic)
+    int team_solve[2] = {0, 0};                // tuned threads per item of the sweeps, for team_solve_nrhs
+    int team_solve_nrhs = 0;
     int max_nx = 0, max_nu = 0;
     std::vector<Item> items;
     Item *d_items = nullptr;
@@ -134,6 +137,16 @@ int solve_team(int nux, int nrhs) {
     return 256;
 }
 
+int factor_team_of(const Group &g, bool fp64) {
+    const int t = g.team_factor[fp64 ? 1 : 0];
+    return t ? t : g.team;
+}
+
+int sweep_team_of(const Group &g, bool fp64, int nrhs) {
+    const int t = g.team_solve[fp64 ? 1 : 0];
+    return (t && g.team_solve_nrhs == nrhs) ? t : solve_team(g.max_nx + g.max_nu, nrhs);
+}
+
 // Size class of an instance: work items are launched per class so that the
 // shared-memory carve-out and the team size match the blocks they hold.
 int size_class(int nx, int nu) {
@@ -188,14 +201,21 @@ SolveArgs solve_args(cyq_handle h, const FactorSet &fs, const Group &g, const do
     return a;
 }
 
+// One sweep (backward or forward) over the work items of one size class.
+cudaError_t launch_group_sweep(cyq_handle h, const FactorSet &fs, const Group &g, bool backward, const double *b,
+                               double *z, int nrhs, const int *skip, double *zacc, cudaStream_t st) {
+    SolveArgs a = solve_args(h, fs, g, b, z, nrhs, skip, zacc);
+    const size_t smem = solve_smem_bytes(fs.fp64, g.max_nx, g.max_nu, nrhs, a.nbuf);
+    const int team = sweep_team_of(g, fs.fp64, nrhs);
+    return backward ? launch_solve_backward(fs.fp64, team, smem, a, st) : launch_solve_forward(fs.fp64, team, smem, a, st);
+}
+
 // One solve with a stored factor (float64 or float32 arithmetic).  With
 // zacc, the solution is added into zacc and z only holds sweep intermediates.
 cyq_status run_solve(cyq_handle h, const FactorSet &fs, const double *b, double *z, int nrhs, const int *skip,
                      cudaStream_t st, double *zacc = nullptr) {
     for (const Group &g : h->groups) {
-        SolveArgs a = solve_args(h, fs, g, b, z, nrhs, skip, zacc);
-        size_t smem = solve_smem_bytes(fs.fp64, g.max_nx, g.max_nu, nrhs, a.nbuf);
-        CYQ_CUDA(launch_solve_backward(fs.fp64, solve_team(g.max_nx + g.max_nu, nrhs), smem, a, st));
+        CYQ_CUDA(launch_group_sweep(h, fs, g, true, b, z, nrhs, skip, zacc, st));
         ++h->launches;
     }
     {
@@ -205,9 +225,7 @@ cyq_status run_solve(cyq_handle h, const FactorSet &fs, const double *b, double 
         ++h->launches;
     }
     for (const Group &g : h->groups) {
-        SolveArgs a = solve_args(h, fs, g, b, z, nrhs, skip, zacc);
-        size_t smem = solve_smem_bytes(fs.fp64, g.max_nx, g.max_nu, nrhs, a.nbuf);
-        CYQ_CUDA(launch_solve_forward(fs.fp64, solve_team(g.max_nx + g.max_nu, nrhs), smem, a, st));
+        CYQ_CUDA(launch_group_sweep(h, fs, g, false, b, z, nrhs, skip, zacc, st));
         ++h->launches;
     }
     return CYQ_OK;
@@ -215,7 +233,7 @@ cyq_status run_solve(cyq_handle h, const FactorSet &fs, const double *b, double 
 
 // Factor all instances (or those whose skip flag is zero) into a factor set,
 // including the cyclic reduction of the coupling blocks (always float64).
-cyq_status run_factor(cyq_handle h, const FactorSet &fs, const int *skip, cudaStream_t st) {
+FactorArgs factor_args(cyq_handle h, const FactorSet &fs, const int *skip) {
     FactorArgs a{};
     a.inst = h->d_inst;
     a.data = h->data;
@@ -231,13 +249,23 @@ cyq_status run_factor(cyq_handle h, const FactorSet &fs, const int *skip, cudaSt
     a.Y = h->Y;
     a.status = h->status;
     a.skip = skip;
+    return a;
+}
+
+// The stage factor over the work items of one size class.
+cudaError_t launch_group_factor(const FactorSet &fs, const Group &g, FactorArgs a, cudaStream_t st) {
     const int pi = fs.fp64 ? 1 : 0;
+    a.items = g.d_items;
+    a.n_items = (int)g.items.size();
+    a.stage_in_smem = g.staged[pi];
+    a.need_G2 = g.need_G2;
+    return launch_factor_segments(fs.fp64, factor_team_of(g, fs.fp64), g.smem_factor[pi], a, st);
+}
+
+cyq_status run_factor(cyq_handle h, const FactorSet &fs, const int *skip, cudaStream_t st) {
+    FactorArgs a = factor_args(h, fs, skip);
     for (const Group &g : h->groups) {
-        a.items = g.d_items;
-        a.n_items = (int)g.items.size();
-        a.stage_in_smem = g.staged[pi];
-        a.need_G2 = g.need_G2;
-        CYQ_CUDA(launch_factor_segments(fs.fp64, g.team, g.smem_factor[pi], a, st));
+        CYQ_CUDA(launch_group_factor(fs, g, a, st));
         ++h->launches;
     }
     if (!h->cr_list.empty()) CYQ_CUDA(launch_cr_factor_levels(h->cr_plan, h->cr_team, h->max_nx, a, st, &h->launches));
@@ -661,6 +689,158 @@ cyq_status cyq_get_stats(cyq_handle h, cyq_stats *out, cyq_stream stream) {
     long long items = 0;
     for (const Group &g : h->groups) items += (long long)g.items.size();
     out->work_items = items;
+    return CYQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning (host-timed with CUDA events on the caller's stream)
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+// Mean time in ms of `reps` calls of fn (each returns a cudaError_t) on st.
+template <typename F>
+cyq_status time_ms(cudaStream_t st, int reps, F &&fn, float *ms) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail_cuda(cudaGetLastError(), "cudaEventCreate");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail_cuda(cudaGetLastError(), "cudaEventCreate");
+    }
+    cudaError_t e = cudaEventRecord(e0, st);
+    for (int i = 0; i < reps && e == cudaSuccess; ++i) e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail_cuda(e, "autotune");
+    *ms = t / reps;
+    return CYQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cyq_status cyq_autotune(cyq_handle h, const double *Q, const double *R, const double *S, const double *A,
+                        const double *B, const double *Sigma, const double *b, double *z, int32_t nrhs,
+                        int32_t reps, cyq_stream stream) {
+    if (!h || !b || !z || nrhs < 1 || nrhs > h->max_nrhs) return CYQ_ERR_INVALID_ARG;
+    if (reps < 1) reps = 3;
+    cyq_status s = cyq_factor(h, Q, R, S, A, B, Sigma, stream);   // binds the data
+    if (s != CYQ_OK) return s;
+    DeviceGuard guard(h->device);
+    cudaStream_t st = to_stream(stream);
+    const FactorSet &fs = h->fac;
+    const int pi = fs.fp64 ? 1 : 0;
+    // a plain solve fills the coupling multipliers that the forward sweep reads
+    s = run_solve(h, fs, b, z, nrhs, nullptr, st);
+    if (s != CYQ_OK) return s;
+    const FactorArgs fa = factor_args(h, fs, nullptr);
+    static const int cand_factor[] = {32, 64, 128};
+    static const int cand_sweep[] = {32, 64, 128, 256};
+    for (Group &g : h->groups) {
+        float best = 3.0e38f;
+        int pick = 0;
+        for (int t : cand_factor) {
+            g.team_factor[pi] = t;
+            float ms = 0.0f;
+            s = time_ms(st, reps, [&] { return launch_group_factor(fs, g, fa, st); }, &ms);
+            if (s != CYQ_OK) { g.team_factor[pi] = 0; return s; }
+            if (ms < best) { best = ms; pick = t; }
+        }
+        g.team_factor[pi] = pick;
+        best = 3.0e38f;
+        pick = 0;
+        g.team_solve_nrhs = nrhs;
+        for (int t : cand_sweep) {
+            g.team_solve[pi] = t;
+            float ms = 0.0f;
+            s = time_ms(st, reps, [&] {
+                cudaError_t e = launch_group_sweep(h, fs, g, true, b, z, nrhs, nullptr, nullptr, st);
+                return e != cudaSuccess ? e : launch_group_sweep(h, fs, g, false, b, z, nrhs, nullptr, nullptr, st);
+            }, &ms);
+            if (s != CYQ_OK) { g.team_solve[pi] = 0; return s; }
+            if (ms < best) { best = ms; pick = t; }
+        }
+        g.team_solve[pi] = pick;
+    }
+    // the timed launches left the factor intact (same data); refresh it as a whole
+    s = run_factor(h, fs, nullptr, st);
+    if (s != CYQ_OK) return s;
+    CYQ_CUDA(cudaStreamSynchronize(st));
+    return CYQ_OK;
+}
+
+cyq_status cyq_get_launch_shapes(cyq_handle h, int32_t *n_groups, int32_t *factor_team, int32_t *sweep_team,
+                                 int32_t nrhs) {
+    if (!h || !n_groups) return CYQ_ERR_INVALID_ARG;
+    *n_groups = (int32_t)h->groups.size();
+    const bool f64 = h->fac.fp64;
+    for (size_t i = 0; i < h->groups.size(); ++i) {
+        if (factor_team) factor_team[i] = factor_team_of(h->groups[i], f64);
+        if (sweep_team) sweep_team[i] = sweep_team_of(h->groups[i], f64, nrhs > 0 ? nrhs : 1);
+    }
+    return CYQ_OK;
+}
+
+cyq_status cyq_tune_segments(const cyq_desc *desc, const double *Q, const double *R, const double *S,
+                             const double *A, const double *B, const double *Sigma, const double *b, double *z,
+                             int32_t nrhs, int32_t reps, cyq_stream stream, int32_t *P_out) {
+    if (!desc || !P_out || desc->batch < 1 || !desc->N || !b || !z || nrhs < 1) return CYQ_ERR_INVALID_ARG;
+    if (reps < 1) reps = 2;
+    const int batch = desc->batch;
+    std::vector<int> base(batch);
+    for (int i = 0; i < batch; ++i) {
+        const int N = desc->N[i];
+        if (N < 1) return CYQ_ERR_INVALID_ARG;
+        int P = desc->P_per_instance ? desc->P_per_instance[i] : desc->P;
+        if (P <= 0) P = auto_segments(batch, N);
+        base[i] = std::min(P, N);
+    }
+    cudaStream_t st = to_stream(stream);
+    std::vector<std::vector<int>> tried;
+    std::vector<int> best_P = base;
+    float best = 3.0e38f;
+    for (int shift = -2; shift <= 2; ++shift) {
+        std::vector<int> P(batch);
+        for (int i = 0; i < batch; ++i) {
+            long long p = shift >= 0 ? (long long)base[i] << shift : base[i] >> -shift;
+            P[i] = (int)std::max(1LL, std::min<long long>(p, desc->N[i]));
+        }
+        if (std::find(tried.begin(), tried.end(), P) != tried.end()) continue;
+        tried.push_back(P);
+        cyq_desc d = *desc;
+        d.P = 0;
+        d.P_per_instance = P.data();
+        if (d.max_nrhs < nrhs) d.max_nrhs = nrhs;
+        cyq_handle h = nullptr;
+        if (cyq_create(&d, &h) != CYQ_OK) {
+            if (shift == 0) return CYQ_ERR_INVALID_ARG;
+            continue;   // e.g. the workspace of this candidate does not fit
+        }
+        // warm-up, then factor + solve timed together
+        cyq_status s = cyq_factor(h, Q, R, S, A, B, Sigma, stream);
+        if (s == CYQ_OK) s = cyq_solve(h, b, z, nrhs, stream);
+        float ms = 0.0f;
+        if (s == CYQ_OK)
+            s = time_ms(st, reps, [&] {
+                cyq_status q = cyq_factor(h, Q, R, S, A, B, Sigma, stream);
+                if (q == CYQ_OK) q = cyq_solve(h, b, z, nrhs, stream);
+                return q == CYQ_OK ? cudaSuccess : cudaErrorUnknown;
+            }, &ms);
+        cyq_destroy(h);
+        if (s != CYQ_OK) return s;
+        if (ms < best) {
+            best = ms;
+            best_P = P;
+        }
+    }
+    for (int i = 0; i < batch; ++i) P_out[i] = best_P[i];
     return CYQ_OK;
 }
 

@@ -25,7 +25,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "not positive definite", 3: "not co
 EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual",
            "cyq_solve_adjoint", "cyq_get_instance_status", "cyq_get_stats", "cyq_kkt_size",
            "cyq_get_segments", "cyq_last_launch_count", "cyq_status_string", "cyq_last_error",
-           "cyq_factor_solve_noalloc"]
+           "cyq_factor_solve_noalloc", "cyq_autotune", "cyq_get_launch_shapes", "cyq_tune_segments"]
 
 
 class CyqError(RuntimeError):
@@ -80,8 +80,13 @@ def load(path: str = LIB_PATH):
     L.cyq_status_string.restype = ctypes.c_char_p
     L.cyq_last_error.argtypes = []
     L.cyq_last_error.restype = ctypes.c_char_p
+    pi32 = ctypes.POINTER(i32)
+    L.cyq_autotune.argtypes = [vp] + [vp] * 6 + [vp, vp, i32, i32, vp]
+    L.cyq_get_launch_shapes.argtypes = [vp, pi32, pi32, pi32, i32]
+    L.cyq_tune_segments.argtypes = [ctypes.POINTER(cyq_desc)] + [vp] * 6 + [vp, vp, i32, i32, vp, pi32]
     for name in ["cyq_create", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual", "cyq_solve_adjoint",
-                 "cyq_get_instance_status", "cyq_get_stats", "cyq_get_segments"]:
+                 "cyq_get_instance_status", "cyq_get_stats", "cyq_get_segments", "cyq_autotune",
+                 "cyq_get_launch_shapes", "cyq_tune_segments"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -108,6 +113,40 @@ def _stream(stream=None) -> int:
     return s.cuda_stream
 
 
+class _Desc:
+    """A cyq_desc with the host arrays it points to kept alive."""
+
+    def __init__(self, N, nx, nu, precision="fp64", P=0, P_per_instance=None, max_nrhs=1, it_max=-1,
+                 tol=1e-10, device=-1, esc_max=-1):
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        self.N = np.ascontiguousarray(N, dtype=np.int32)
+        self.nx = np.ascontiguousarray(nx, dtype=np.int32)
+        self.nu = np.ascontiguousarray(nu, dtype=np.int32)
+        self.precision = {"fp64": CYQ_FP64, "fp32_refine": CYQ_FP32_REFINE}[precision]
+        pp = None
+        if P_per_instance is not None:
+            self.P = np.ascontiguousarray(P_per_instance, dtype=np.int32)
+            pp = self.P.ctypes.data_as(i32p)
+        self.desc = cyq_desc(len(self.N), self.N.ctypes.data_as(i32p), self.nx.ctypes.data_as(i32p),
+                             self.nu.ctypes.data_as(i32p), self.precision, P, pp, max_nrhs, it_max, tol, device,
+                             esc_max)
+
+
+def tune_segments(N, nx, nu, data, b, nrhs: int = 1, reps: int = 2, stream=None, **desc_kw) -> np.ndarray:
+    """Segment counts per instance chosen by timing (cyq_tune_segments); pass the
+    result as ``P_per_instance`` to :class:`Solver`.  ``data`` holds the device
+    arrays Q, R, S, A, B, Sigma; ``b`` the nrhs right-hand sides."""
+    import torch
+    L = load()
+    d = _Desc(N, nx, nu, max_nrhs=nrhs, **desc_kw)
+    z = torch.empty_like(b)
+    out = np.zeros(len(d.N), np.int32)
+    _check(L.cyq_tune_segments(ctypes.byref(d.desc), _ptr(data["Q"]), _ptr(data["R"]), _ptr(data.get("S")),
+                               _ptr(data["A"]), _ptr(data["B"]), _ptr(data.get("Sigma")), _ptr(b), _ptr(z), nrhs,
+                               reps, _stream(stream), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return out
+
+
 class Solver:
     """A planned batch of OCP KKT systems (one cyq handle)."""
 
@@ -115,20 +154,13 @@ class Solver:
                  P: int = 0, P_per_instance: Optional[Sequence[int]] = None, max_nrhs: int = 1,
                  it_max: int = -1, tol: float = 1e-10, device: int = -1, esc_max: int = -1):
         L = load()
-        self.N = np.ascontiguousarray(N, dtype=np.int32)
-        self.nx = np.ascontiguousarray(nx, dtype=np.int32)
-        self.nu = np.ascontiguousarray(nu, dtype=np.int32)
+        d = _Desc(N, nx, nu, precision, P, P_per_instance, max_nrhs, it_max, tol, device, esc_max)
+        self._desc = d
+        self.N, self.nx, self.nu = d.N, d.nx, d.nu
         self.batch = len(self.N)
-        self.precision = {"fp64": CYQ_FP64, "fp32_refine": CYQ_FP32_REFINE}[precision]
+        self.precision = d.precision
         self.max_nrhs = max_nrhs
-        pp = None
-        if P_per_instance is not None:
-            self._P = np.ascontiguousarray(P_per_instance, dtype=np.int32)
-            pp = self._P.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-        desc = cyq_desc(self.batch, self.N.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                        self.nx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                        self.nu.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.precision, P, pp,
-                        max_nrhs, it_max, tol, device, esc_max)
+        desc = d.desc
         h = ctypes.c_void_p()
         _check(L.cyq_create(ctypes.byref(desc), ctypes.byref(h)))
         self._h = h
@@ -155,6 +187,25 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(_lib.cyq_last_launch_count(self._h))
+
+    def autotune(self, Q, R, S, A, B, Sigma, b, nrhs: int = 1, reps: int = 3, stream=None):
+        """Pick launch shapes by timing (cyq_autotune); leaves the solver factored."""
+        import torch
+        z = torch.empty_like(b)
+        self._data = (Q, R, S, A, B, Sigma)
+        _check(_lib.cyq_autotune(self._h, _ptr(Q), _ptr(R), _ptr(S), _ptr(A), _ptr(B), _ptr(Sigma), _ptr(b),
+                                 _ptr(z), nrhs, reps, _stream(stream)))
+        self.factor_version += 1
+
+    def launch_shapes(self, nrhs: int = 1) -> dict:
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        n = ctypes.c_int32(0)
+        _check(_lib.cyq_get_launch_shapes(self._h, ctypes.byref(n), None, None, nrhs))
+        f = np.zeros(n.value, np.int32)
+        w = np.zeros(n.value, np.int32)
+        _check(_lib.cyq_get_launch_shapes(self._h, ctypes.byref(n), f.ctypes.data_as(i32p), w.ctypes.data_as(i32p),
+                                          nrhs))
+        return dict(factor=f.tolist(), sweep=w.tolist())
 
     def factor(self, Q, R, S, A, B, Sigma=None, stream=None):
         self._data = (Q, R, S, A, B, Sigma)   # borrowed until the last solve

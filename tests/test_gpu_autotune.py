@@ -1,0 +1,66 @@
+"""Launch-shape and segment-count autotuners (cyq_autotune, cyq_tune_segments).
+
+Every output element of the stage factor and of the sweeps is computed by one
+thread with the same arithmetic whatever the number of threads per work item,
+so tuned and default launch shapes give the same solution (compared to 1e-12);
+the tuned segment counts are valid and the solve with them matches the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+from gpu_util import oracle_rhs, ragged_batch, rel_err, require_gpu, split_instances
+
+pytestmark = pytest.mark.gpu
+
+DIMS = [(24, 3, 2), (40, 12, 4), (33, 12, 4), (16, 30, 10), (50, 6, 1), (20, 52, 20)]
+
+
+def _run(batch, precision, nrhs, tune, P=0, P_per_instance=None):
+    torch, cyq = require_gpu()
+    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, P=P, P_per_instance=P_per_instance,
+                   max_nrhs=nrhs, it_max=0 if precision == "fp64" else 10)
+    data, _ = cyq.to_device(batch)
+    b_host = np.stack([oracle_rhs(batch, j) for j in range(nrhs)])
+    b = torch.from_numpy(np.ascontiguousarray(b_host.reshape(-1))).cuda()
+    if tune:
+        s.autotune(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"], b, nrhs=nrhs, reps=2)
+    else:
+        s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
+    z = s.solve(b, nrhs=nrhs)
+    torch.cuda.synchronize()
+    return s, z.cpu().numpy().reshape(nrhs, -1), b_host
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("P", [1, 4])
+def test_autotuned_shapes_give_the_same_solution(precision, P):
+    batch = ragged_batch(41, DIMS, nrhs=2)
+    s0, z0, b = _run(batch, precision, 2, False, P=P)
+    s1, z1, _ = _run(batch, precision, 2, True, P=P)
+    shapes = s1.launch_shapes(nrhs=2)
+    print(precision, "default", s0.launch_shapes(nrhs=2), "tuned", shapes)
+    assert len(shapes["factor"]) >= 2
+    assert all(t in (32, 64, 128) for t in shapes["factor"])
+    assert all(t in (32, 64, 128, 256) for t in shapes["sweep"])
+    assert (s1.instance_status() == 0).all()
+    assert rel_err(z1, z0) <= 1e-12
+    for inst, zi, bi in zip(batch.instances, split_instances(batch, z1[0]), split_instances(batch, b[0])):
+        assert rel_err(zi, oracle.riccati_solve(inst, bi)) <= 1e-8
+
+
+def test_tuned_segment_counts_are_valid_and_solve_correctly():
+    torch, cyq = require_gpu()
+    batch = ragged_batch(42, [(512, 8, 4), (300, 6, 3), (128, 10, 2)])
+    data, _ = cyq.to_device(batch)
+    b_host = oracle_rhs(batch)
+    b = torch.from_numpy(b_host).cuda()
+    P = cyq.tune_segments(batch.N, batch.nx, batch.nu, data, b, nrhs=1, reps=2, it_max=0)
+    print("tuned segments", P)
+    assert P.shape == (batch.size,)
+    assert ((P >= 1) & (P <= np.asarray(batch.N))).all()
+    s, z, _ = _run(batch, "fp64", 1, False, P_per_instance=P)
+    assert (s.segments == P).all()
+    for inst, zi, bi in zip(batch.instances, split_instances(batch, z[0]), split_instances(batch, b_host)):
+        assert rel_err(zi, oracle.riccati_solve(inst, bi)) <= 1e-9
