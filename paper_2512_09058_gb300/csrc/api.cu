@@ -34,6 +34,7 @@ struct Group {
     int team_factor[2] = {0, 0};               // tuned threads per item of the stage factor (0: heuristic)
     int team_solve[2] = {0, 0};                // tuned threads per item of the sweeps, for team_solve_nrhs
     int team_solve_nrhs = 0;
+    int shape = -1;                            // kStageShapes index shared by all items (0: mixed / other)
     int max_nx = 0, max_nu = 0;
     std::vector<Item> items;
     Item *d_items = nullptr;
@@ -207,7 +208,9 @@ cudaError_t launch_group_sweep(cyq_handle h, const FactorSet &fs, const Group &g
     SolveArgs a = solve_args(h, fs, g, b, z, nrhs, skip, zacc);
     const size_t smem = solve_smem_bytes(fs.fp64, g.max_nx, g.max_nu, nrhs, a.nbuf);
     const int team = sweep_team_of(g, fs.fp64, nrhs);
-    return backward ? launch_solve_backward(fs.fp64, team, smem, a, st) : launch_solve_forward(fs.fp64, team, smem, a, st);
+    const int shape = g.shape > 0 ? g.shape : 0;
+    return backward ? launch_solve_backward(fs.fp64, team, shape, smem, a, st)
+                    : launch_solve_forward(fs.fp64, team, shape, smem, a, st);
 }
 
 // One solve with a stored factor (float64 or float32 arithmetic).  With
@@ -422,6 +425,10 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
             g->team = team;
         }
         g->team = std::max(g->team, team);
+        {
+            const int sh = stage_shape_index(nx, nu);
+            g->shape = g->shape < 0 ? sh : (g->shape == sh ? sh : 0);
+        }
         g->max_nx = std::max(g->max_nx, nx);
         g->max_nu = std::max(g->max_nu, nu);
         for (int c = 0; c < P; ++c) g->items.push_back(Item{i, c});

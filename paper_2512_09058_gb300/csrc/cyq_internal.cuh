@@ -30,6 +30,20 @@ struct Inst {
     long long oq, orv, oc, ox0;          // offsets of q ((N+1) nx), r (N nu), c (N nx), x_init (nx)
 };
 
+// Stage shapes (nx, nu) for which float32 kernels are also compiled with fixed
+// dimensions (loops unrolled, index arithmetic folded); a launch whose work
+// items all have one of these shapes uses them.  Entry 0 stands for any shape.
+struct StageShape {
+    int nx, nu;
+};
+constexpr StageShape kStageShapes[] = {{0, 0}, {8, 4}, {12, 4}, {24, 8}, {32, 16}};
+constexpr int kNumStageShapes = sizeof(kStageShapes) / sizeof(kStageShapes[0]);
+inline int stage_shape_index(int nx, int nu) {
+    for (int i = 1; i < kNumStageShapes; ++i)
+        if (kStageShapes[i].nx == nx && kStageShapes[i].nu == nu) return i;
+    return 0;
+}
+
 struct Item {
     int inst, seg;
 };
@@ -349,10 +363,10 @@ struct CrPlan {
 cudaError_t launch_factor_segments(bool fp64, int team, size_t smem, const FactorArgs &a, cudaStream_t st);
 cudaError_t launch_cr_factor_levels(const CrPlan &plan, int team, int nmax, const FactorArgs &a, cudaStream_t st,
                                     long long *launches);
-cudaError_t launch_solve_backward(bool fp64, int team, size_t smem, const SolveArgs &a, cudaStream_t st);
+cudaError_t launch_solve_backward(bool fp64, int team, int shape, size_t smem, const SolveArgs &a, cudaStream_t st);
 cudaError_t launch_cr_solve(int n_inst_cr, const int *inst_list, int team, size_t smem, const SolveArgs &a,
                             cudaStream_t st);
-cudaError_t launch_solve_forward(bool fp64, int team, size_t smem, const SolveArgs &a, cudaStream_t st);
+cudaError_t launch_solve_forward(bool fp64, int team, int shape, size_t smem, const SolveArgs &a, cudaStream_t st);
 
 struct Chunk {
     int inst, k0, k1;   // records [k0, k1) of one instance

@@ -164,9 +164,9 @@ extern "C" cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu
     sa.nvec = nx;
     sa.skip = nullptr;
     sa.nbuf = nbuf;
-    if ((e = launch_solve_backward(true, team, ss, sa, st)) != cudaSuccess ||
+    if ((e = launch_solve_backward(true, team, 0, ss, sa, st)) != cudaSuccess ||
         (e = launch_cr_solve(1, d_list, 128, (size_t)2 * nx * sizeof(double), sa, st)) != cudaSuccess ||
-        (e = launch_solve_forward(true, team, ss, sa, st)) != cudaSuccess)
+        (e = launch_solve_forward(true, team, 0, ss, sa, st)) != cudaSuccess)
         return fail(CYQ_ERR_CUDA, std::string("cyq_factor_solve_noalloc: ") + cudaGetErrorString(e));
     if (status_out &&
         (e = cudaMemcpyAsync(status_out, d_status, sizeof(int), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)

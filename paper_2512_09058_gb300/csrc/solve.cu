@@ -191,14 +191,16 @@ size_t solve_smem_bytes(bool fp64, int nx, int nu, int nrhs, int nbuf) {
     return align16(nbuf * package_bytes(fp64, nx, nu, nrhs)) + vecs_bytes(fp64, nx, nu, nrhs);
 }
 
-template <typename T, int TEAM>
+template <typename T, int TEAM, int NXC, int NUC>
 __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
         const Item wi = a.items[item];
         if (a.skip && a.skip[wi.inst]) continue;
         const Inst in = a.inst[wi.inst];
-        const int N = in.N, nx = in.nx, nu = in.nu, P = in.P, c = wi.seg, nrhs = a.nrhs;
+        // NXC / NUC > 0: kernel compiled for that stage shape (every item of the launch has it)
+        const int nx = NXC > 0 ? NXC : in.nx, nu = NUC > 0 ? NUC : in.nu;
+        const int N = in.N, P = in.P, c = wi.seg, nrhs = a.nrhs;
         const int nux = nx + nu, nv = nux + nx, w = nu + 2 * nx;
         const int len = seg_len(c, N, P);
         Walk Wu, Wx, Wux, Wv;
@@ -350,14 +352,16 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
     }
 }
 
-template <typename T, int TEAM>
+template <typename T, int TEAM, int NXC, int NUC>
 __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
         const Item wi = a.items[item];
         if (a.skip && a.skip[wi.inst]) continue;
         const Inst in = a.inst[wi.inst];
-        const int N = in.N, nx = in.nx, nu = in.nu, P = in.P, c = wi.seg, nrhs = a.nrhs;
+        // NXC / NUC > 0: kernel compiled for that stage shape (every item of the launch has it)
+        const int nx = NXC > 0 ? NXC : in.nx, nu = NUC > 0 ? NUC : in.nu;
+        const int N = in.N, P = in.P, c = wi.seg, nrhs = a.nrhs;
         const int nux = nx + nu, nv = nux + nx, w = nu + 2 * nx;
         const int len = seg_len(c, N, P);
         Walk Wu, Wx, Wv;
@@ -506,35 +510,41 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
     }
 }
 
-template <typename T, int TEAM>
+template <typename T, int TEAM, int NXC, int NUC>
 static cudaError_t launch_sweep(bool backward, size_t smem, const SolveArgs &a, cudaStream_t st) {
-    auto k = backward ? k_solve_backward<T, TEAM> : k_solve_forward<T, TEAM>;
+    auto k = backward ? k_solve_backward<T, TEAM, NXC, NUC> : k_solve_forward<T, TEAM, NXC, NUC>;
     cudaError_t e = ensure_smem((const void *)k, smem);
     if (e != cudaSuccess) return e;
     k<<<a.n_items, TEAM, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, int NXC, int NUC>
 static cudaError_t launch_sweep_team(bool backward, int team, size_t smem, const SolveArgs &a, cudaStream_t st) {
-    if (team == 32) return launch_sweep<T, 32>(backward, smem, a, st);
-    if (team == 64) return launch_sweep<T, 64>(backward, smem, a, st);
-    if (team == 128) return launch_sweep<T, 128>(backward, smem, a, st);
-    return launch_sweep<T, 256>(backward, smem, a, st);
+    if (team == 32) return launch_sweep<T, 32, NXC, NUC>(backward, smem, a, st);
+    if (team == 64) return launch_sweep<T, 64, NXC, NUC>(backward, smem, a, st);
+    if (team == 128) return launch_sweep<T, 128, NXC, NUC>(backward, smem, a, st);
+    return launch_sweep<T, 256, NXC, NUC>(backward, smem, a, st);
 }
 
-static cudaError_t launch_sweep_any(bool backward, bool fp64, int team, size_t smem, const SolveArgs &a,
+static cudaError_t launch_sweep_any(bool backward, bool fp64, int team, int shape, size_t smem, const SolveArgs &a,
                                     cudaStream_t st) {
     if (a.n_items == 0) return cudaSuccess;
-    return fp64 ? launch_sweep_team<double>(backward, team, smem, a, st)
-                : launch_sweep_team<float>(backward, team, smem, a, st);
+    if (fp64) return launch_sweep_team<double, 0, 0>(backward, team, smem, a, st);
+    switch (shape) {   // float32 kernels compiled for the listed stage shapes (kStageShapes)
+        case 1: return launch_sweep_team<float, kStageShapes[1].nx, kStageShapes[1].nu>(backward, team, smem, a, st);
+        case 2: return launch_sweep_team<float, kStageShapes[2].nx, kStageShapes[2].nu>(backward, team, smem, a, st);
+        case 3: return launch_sweep_team<float, kStageShapes[3].nx, kStageShapes[3].nu>(backward, team, smem, a, st);
+        case 4: return launch_sweep_team<float, kStageShapes[4].nx, kStageShapes[4].nu>(backward, team, smem, a, st);
+        default: return launch_sweep_team<float, 0, 0>(backward, team, smem, a, st);
+    }
 }
 
-cudaError_t launch_solve_backward(bool fp64, int team, size_t smem, const SolveArgs &a, cudaStream_t st) {
-    return launch_sweep_any(true, fp64, team, smem, a, st);
+cudaError_t launch_solve_backward(bool fp64, int team, int shape, size_t smem, const SolveArgs &a, cudaStream_t st) {
+    return launch_sweep_any(true, fp64, team, shape, smem, a, st);
 }
-cudaError_t launch_solve_forward(bool fp64, int team, size_t smem, const SolveArgs &a, cudaStream_t st) {
-    return launch_sweep_any(false, fp64, team, smem, a, st);
+cudaError_t launch_solve_forward(bool fp64, int team, int shape, size_t smem, const SolveArgs &a, cudaStream_t st) {
+    return launch_sweep_any(false, fp64, team, shape, smem, a, st);
 }
 
 }  // namespace cyq
