@@ -219,6 +219,15 @@ cyq_status cyq_autotune(cyq_handle h, const double *Q, const double *R, const do
 cyq_status cyq_get_launch_shapes(cyq_handle h, int32_t *n_groups, int32_t *factor_team,
                                  int32_t *sweep_team, int32_t nrhs);
 
+/* Set the launch shapes explicitly (e.g. ones tuned earlier): arrays of one
+ * entry per size class (cyq_get_launch_shapes gives the count); 0 restores
+ * the default of that class; the sweep shapes apply to cyq_solve calls with
+ * nrhs right-hand sides.  Either array may be NULL (left unchanged).
+ * Allowed values: factor 32, 64, 128; sweeps 32, 64, 128, 256.
+ * Errors: INVALID_ARG. */
+cyq_status cyq_set_launch_shapes(cyq_handle h, const int32_t *factor_team, const int32_t *sweep_team,
+                                 int32_t nrhs);
+
 /*
  * Segment-count tuner.  Starting from desc's segment counts (automatic where
  * desc->P = 0 and no P_per_instance), tries the counts scaled by 1/4, 1/2, 1,

@@ -262,7 +262,8 @@ cudaError_t launch_group_factor(const FactorSet &fs, const Group &g, FactorArgs 
     a.n_items = (int)g.items.size();
     a.stage_in_smem = g.staged[pi];
     a.need_G2 = g.need_G2;
-    return launch_factor_segments(fs.fp64, factor_team_of(g, fs.fp64), g.smem_factor[pi], a, st);
+    return launch_factor_segments(fs.fp64, factor_team_of(g, fs.fp64), g.shape > 0 ? g.shape : 0, g.smem_factor[pi], a,
+                                  st);
 }
 
 cyq_status run_factor(cyq_handle h, const FactorSet &fs, const int *skip, cudaStream_t st) {
@@ -791,6 +792,26 @@ cyq_status cyq_get_launch_shapes(cyq_handle h, int32_t *n_groups, int32_t *facto
     for (size_t i = 0; i < h->groups.size(); ++i) {
         if (factor_team) factor_team[i] = factor_team_of(h->groups[i], f64);
         if (sweep_team) sweep_team[i] = sweep_team_of(h->groups[i], f64, nrhs > 0 ? nrhs : 1);
+    }
+    return CYQ_OK;
+}
+
+cyq_status cyq_set_launch_shapes(cyq_handle h, const int32_t *factor_team, const int32_t *sweep_team, int32_t nrhs) {
+    if (!h) return CYQ_ERR_INVALID_ARG;
+    const int pi = h->fac.fp64 ? 1 : 0;
+    for (size_t i = 0; i < h->groups.size(); ++i) {
+        const int f = factor_team ? factor_team[i] : 0, w = sweep_team ? sweep_team[i] : 0;
+        if (!(f == 0 || f == 32 || f == 64 || f == 128)) return CYQ_ERR_INVALID_ARG;
+        if (!(w == 0 || w == 32 || w == 64 || w == 128 || w == 256)) return CYQ_ERR_INVALID_ARG;
+    }
+    if (sweep_team && nrhs < 1) return CYQ_ERR_INVALID_ARG;
+    for (size_t i = 0; i < h->groups.size(); ++i) {
+        Group &g = h->groups[i];
+        if (factor_team) g.team_factor[pi] = factor_team[i];
+        if (sweep_team) {
+            g.team_solve[pi] = sweep_team[i];
+            g.team_solve_nrhs = nrhs;
+        }
     }
     return CYQ_OK;
 }

@@ -360,7 +360,7 @@ struct CrPlan {
     int elim_off[33] = {0}, upd_off[33] = {0};
 };
 
-cudaError_t launch_factor_segments(bool fp64, int team, size_t smem, const FactorArgs &a, cudaStream_t st);
+cudaError_t launch_factor_segments(bool fp64, int team, int shape, size_t smem, const FactorArgs &a, cudaStream_t st);
 cudaError_t launch_cr_factor_levels(const CrPlan &plan, int team, int nmax, const FactorArgs &a, cudaStream_t st,
                                     long long *launches);
 cudaError_t launch_solve_backward(bool fp64, int team, int shape, size_t smem, const SolveArgs &a, cudaStream_t st);

@@ -20,6 +20,8 @@
 // the current stage's copy is consumed by the end of the previous step, so
 // one buffer suffices.  H^ = H + V V^T is assembled directly from that copy,
 // or from global memory for blocks too large to stage.
+#include <type_traits>
+
 #include "cyq_internal.cuh"
 
 namespace cyq {
@@ -150,14 +152,190 @@ struct FactorTiles {
     }
 };
 
-template <typename T, int TEAM>
+
+// Interior stages t0 <= t < t1 of a segment that carries no A^cl (segment 0):
+// float32, one warp, a stage shape fixed at compile time with NU + NX <= 32.
+// Lane i holds row i of the current stage matrix in registers, and columns
+// reach the other lanes through shuffles, so a stage needs no shared-memory
+// round trips and no block barriers.  Entered with H^_{s(t0)} in the H tile
+// (leading dimension ldH); leaves H^_{s(t1)} there.  Every value is formed by
+// the same operations in the same order as in the shared-memory path below
+// (potrf, L^{R-1}, V = [B A]^T L^Q, H^ = H + V V^T), so the results agree.
+// Largest nu + nx of the register path (a 32-row matrix and V no longer fit in
+// the registers of one thread without spilling).
+constexpr int kRegisterRows = 24;
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1, so
+// that register arrays are only ever indexed by constants.
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// Interior stages t0 <= t < t1 of a segment that carries no A^cl (segment 0):
+// float32, one warp, a stage shape fixed at compile time with NU + NX <= 32.
+// Lane i holds row i of the current stage matrix in registers, and columns
+// reach the other lanes through shuffles, so a stage needs no shared-memory
+// round trips and no block barriers.  Entered with H^_{s(t0)} in the H tile
+// (leading dimension ldH); leaves H^_{s(t1)} there.  Every value is formed by
+// the same operations in the same order as in the shared-memory path below
+// (potrf, L^{R-1}, V = [B A]^T L^Q, H^ = H + V V^T), so the results agree.
+template <int NX, int NU>
+__device__ __forceinline__ bool stages_in_registers(float *H, int ldH, float *Vs, double *buf, const StageLayout &SL,
+                                                    const FactorArgs &a, const Inst &in, int c, int t0, int t1,
+                                                    float *Lg, float *DIg, float *BAg) {
+    constexpr int NUX = NX + NU;
+    constexpr unsigned FULL = 0xffffffffu;
+    static_assert(NUX <= 32, "one row per lane");
+    static_assert(NX % 4 == 0, "rows of V as 16-byte vectors");
+    const int lane = threadIdx.x;
+    const int N = in.N, P = in.P;
+    float h[NUX];
+    static_for<0, NUX>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        h[j] = (lane < NUX && j <= lane) ? H[lane + j * ldH] : 0.0f;
+    });
+    bool ok = true;
+    for (int t = t0; t < t1; ++t) {
+        const int s = seg_stage(c, t, N, P), s2 = seg_stage(c, t + 1, N, P);
+        prefetch_stage<32>(buf, SL, a.data, in, s2);   // lands while this stage is factored
+        // Cholesky, right-looking: column k is scaled by the lanes that own its rows,
+        // then row j of column k is broadcast for the rank-1 update of column j
+        float dl = 1.0f;
+        static_for<0, NUX>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            float d = __shfl_sync(FULL, h[k], k);
+            if (!finite_pos(d)) {
+                ok = false;
+                d = 1.0f;
+            }
+            float l, il;
+            pivot(d, l, il);
+            if (lane == k) {
+                h[k] = l;
+                dl = il;
+            } else if (lane > k) {
+                h[k] *= il;
+            }
+            static_for<k + 1, NUX>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                const float ljk = __shfl_sync(FULL, h[k], j);
+                if (lane >= j) h[j] = fmaf(-h[k], ljk, h[j]);
+            });
+        });
+        // X = L^{R-1}, row m of X in lane m: X[m][k] = -1/L_mm sum_{q=k}^{m-1} L[m][q] X[q][k]
+        float x[NU], acc[NU];
+        static_for<0, NU>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            x[k] = acc[k] = 0.0f;
+        });
+        static_for<0, NU>([&](auto mc) {
+            constexpr int m = decltype(mc)::value;
+            if (lane == m) {
+                static_for<0, m>([&](auto kc) {
+                    constexpr int k = decltype(kc)::value;
+                    x[k] = -acc[k] * dl;
+                });
+                x[m] = dl;
+            }
+            static_for<0, m + 1>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                const float xm = __shfl_sync(FULL, x[k], m);
+                if (lane > m) acc[k] = fmaf(h[m], xm, acc[k]);
+            });
+        });
+        // stored factor: lower triangle, X transposed above the diagonal of the R block, zeros elsewhere
+        float *Ls = Lg + (long long)s * NUX * NUX;
+        if (lane < NUX) {
+            static_for<0, NUX>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                if (j <= lane)
+                    Ls[lane + j * NUX] = h[j];
+                else if (!(lane < NU && j < NU))
+                    Ls[lane + j * NUX] = 0.0f;
+            });
+            DIg[(long long)s * NUX + lane] = dl;
+        }
+        if (lane < NU) {
+            static_for<0, NU>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                if (k < lane) Ls[k + lane * NUX] = x[k];
+            });
+        }
+        // raw blocks of stage s2
+        stage_zero_fill<32>(buf, SL, a.data, in, s2);
+        cp_async_wait_all();
+        __syncwarp();
+        const StageSrc src = stage_src_smem(buf, SL);
+        // V = [B A]^T L^Q, row `lane`: v[j] = sum_{k >= j} BA[k][lane] L^Q[k][j]
+        float v[NX];
+        static_for<0, NX>([&](auto jc) { v[decltype(jc)::value] = 0.0f; });
+        const double *bacol = lane < NU ? src.B + lane * NX : src.A + (lane - NU) * NX;   // column `lane` of [B A]
+        float *badst = (BAg && lane < NUX) ? BAg + (long long)s2 * NX * NUX + lane * NX : nullptr;
+        static_for<0, NX>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            const float ba = lane < NUX ? (float)bacol[k] : 0.0f;
+            if (badst) badst[k] = ba;
+            static_for<0, k + 1>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                const float lq = __shfl_sync(FULL, h[NU + j], NU + k);
+                v[j] = fmaf(ba, lq, v[j]);
+            });
+        });
+        // H^_{s2} = H_{s2} + V V^T, row `lane`; rows of V are read back from shared
+        // memory as 16-byte broadcasts
+        if (lane < NUX) {
+            static_for<0, NX / 4>([&](auto qc) {
+                constexpr int j = 4 * decltype(qc)::value;
+                *reinterpret_cast<float4 *>(Vs + lane * NX + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            });
+        }
+        __syncwarp();
+        const int ra = lane < NU ? lane : 0, qa = lane >= NU && lane < NUX ? lane - NU : 0;
+        static_for<0, NUX>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            // raw entry (lane, b), lane >= b: R, S^T or Q, plus Sigma on the diagonal (float64, as stage_H)
+            double raw;
+            if constexpr (b < NU)
+                raw = lane < NU ? src.R[ra + b * NU] + (lane == b ? src.Su[b] : 0.0) : src.S[b + qa * NU];
+            else
+                raw = src.Q[qa + (b - NU) * NX] + (lane == b ? src.Sx[b - NU] : 0.0);
+            float hb = (lane < NUX && b <= lane) ? (float)raw : 0.0f;
+            static_for<0, NX / 4>([&](auto qc) {
+                constexpr int j = 4 * decltype(qc)::value;
+                const float4 vb = *reinterpret_cast<const float4 *>(Vs + b * NX + j);
+                hb = fmaf(v[j], vb.x, hb);
+                hb = fmaf(v[j + 1], vb.y, hb);
+                hb = fmaf(v[j + 2], vb.z, hb);
+                hb = fmaf(v[j + 3], vb.w, hb);
+            });
+            h[b] = b <= lane ? hb : 0.0f;
+        });
+        __syncwarp();   // every lane has read the stage copy and V before they are overwritten
+    }
+    if (lane < NUX) {
+        static_for<0, NUX>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            if (j <= lane) H[lane + j * ldH] = h[j];
+        });
+    }
+    __syncwarp();
+    return ok;
+}
+
+template <typename T, int TEAM, int NXC, int NUC>
 __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
         const Item wi = a.items[item];
         if (a.skip && a.skip[wi.inst]) continue;
         const Inst in = a.inst[wi.inst];
-        const int N = in.N, nx = in.nx, nu = in.nu, P = in.P, c = wi.seg;
+        // NXC / NUC > 0: kernel compiled for that stage shape (every item of the launch has it)
+        const int nx = NXC > 0 ? NXC : in.nx, nu = NUC > 0 ? NUC : in.nu;
+        const int N = in.N, P = in.P, c = wi.seg;
         const int nux = nx + nu;
         const int len = seg_len(c, N, P);
         const StageLayout SL(nx, nu);
@@ -208,6 +386,17 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
 
         bool ok = true;
         for (int t = 0; t < len; ++t) {
+            if constexpr (sizeof(T) == 4 && TEAM == 32 && NXC > 0 && NXC % 4 == 0 && NXC + NUC <= kRegisterRows) {
+                // V's tile (>= nux * nx floats) holds the rows of V; it must be 16-byte aligned
+                if (t == 1 && !propagate && staged && len > 2 && (reinterpret_cast<size_t>(V) & 15) == 0) {
+                    ok &= stages_in_registers<NXC, NUC>(reinterpret_cast<float *>(H), ldH,
+                                                        reinterpret_cast<float *>(V), buf, SL, a, in, c, 1,
+                                                        len - 1, reinterpret_cast<float *>(Lg),
+                                                        reinterpret_cast<float *>(DIg),
+                                                        reinterpret_cast<float *>(a.BAf) + (a.BAf ? in.oBA : 0));
+                    t = len - 1;   // the last stage closes the segment below
+                }
+            }
             s = seg_stage(c, t, N, P);
             const bool hasG = (t == 0) || propagate;
             const bool last = (t == len - 1);
@@ -381,23 +570,31 @@ size_t factor_smem_bytes(bool fp64, int nx, int nu, bool staged, bool need_G2) {
     return (bytes + 15) / 16 * 16;
 }
 
-template <typename T, int TEAM>
+template <typename T, int TEAM, int NXC = 0, int NUC = 0>
 static cudaError_t launch_factor_t(size_t smem, const FactorArgs &a, cudaStream_t st) {
-    auto k = k_factor_segments<T, TEAM>;
+    auto k = k_factor_segments<T, TEAM, NXC, NUC>;
     cudaError_t e = ensure_smem((const void *)k, smem);
     if (e != cudaSuccess) return e;
     k<<<a.n_items, TEAM, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_factor_segments(bool fp64, int team, size_t smem, const FactorArgs &a, cudaStream_t st) {
+cudaError_t launch_factor_segments(bool fp64, int team, int shape, size_t smem, const FactorArgs &a, cudaStream_t st) {
     if (a.n_items == 0) return cudaSuccess;
     if (fp64) {
         if (team == 32) return launch_factor_t<double, 32>(smem, a, st);
         if (team == 64) return launch_factor_t<double, 64>(smem, a, st);
         return launch_factor_t<double, 128>(smem, a, st);
     }
-    if (team == 32) return launch_factor_t<float, 32>(smem, a, st);
+    if (team == 32) {
+        switch (shape) {   // float32, one warp: kernels compiled for the listed stage shapes (kStageShapes)
+            case 1: return launch_factor_t<float, 32, kStageShapes[1].nx, kStageShapes[1].nu>(smem, a, st);
+            case 2: return launch_factor_t<float, 32, kStageShapes[2].nx, kStageShapes[2].nu>(smem, a, st);
+            case 3: return launch_factor_t<float, 32, kStageShapes[3].nx, kStageShapes[3].nu>(smem, a, st);
+            case 4: return launch_factor_t<float, 32, kStageShapes[4].nx, kStageShapes[4].nu>(smem, a, st);
+            default: return launch_factor_t<float, 32>(smem, a, st);
+        }
+    }
     if (team == 64) return launch_factor_t<float, 64>(smem, a, st);
     return launch_factor_t<float, 128>(smem, a, st);
 }

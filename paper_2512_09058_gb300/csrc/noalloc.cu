@@ -146,7 +146,7 @@ extern "C" cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu
     fa.stage_in_smem = staged;
     fa.need_G2 = false;
     fa.skip = nullptr;
-    if ((e = launch_factor_segments(true, team, fs, fa, st)) != cudaSuccess)
+    if ((e = launch_factor_segments(true, team, 0, fs, fa, st)) != cudaSuccess)
         return fail(CYQ_ERR_CUDA, std::string("cyq_factor_solve_noalloc: ") + cudaGetErrorString(e));
 
     SolveArgs sa{};

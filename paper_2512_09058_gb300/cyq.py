@@ -25,7 +25,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "not positive definite", 3: "not co
 EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual",
            "cyq_solve_adjoint", "cyq_get_instance_status", "cyq_get_stats", "cyq_kkt_size",
            "cyq_get_segments", "cyq_last_launch_count", "cyq_status_string", "cyq_last_error",
-           "cyq_factor_solve_noalloc", "cyq_autotune", "cyq_get_launch_shapes", "cyq_tune_segments"]
+           "cyq_factor_solve_noalloc", "cyq_autotune", "cyq_get_launch_shapes", "cyq_tune_segments",
+           "cyq_set_launch_shapes"]
 
 
 class CyqError(RuntimeError):
@@ -84,9 +85,10 @@ def load(path: str = LIB_PATH):
     L.cyq_autotune.argtypes = [vp] + [vp] * 6 + [vp, vp, i32, i32, vp]
     L.cyq_get_launch_shapes.argtypes = [vp, pi32, pi32, pi32, i32]
     L.cyq_tune_segments.argtypes = [ctypes.POINTER(cyq_desc)] + [vp] * 6 + [vp, vp, i32, i32, vp, pi32]
+    L.cyq_set_launch_shapes.argtypes = [vp, pi32, pi32, i32]
     for name in ["cyq_create", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual", "cyq_solve_adjoint",
                  "cyq_get_instance_status", "cyq_get_stats", "cyq_get_segments", "cyq_autotune",
-                 "cyq_get_launch_shapes", "cyq_tune_segments"]:
+                 "cyq_get_launch_shapes", "cyq_tune_segments", "cyq_set_launch_shapes"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -206,6 +208,14 @@ class Solver:
         _check(_lib.cyq_get_launch_shapes(self._h, ctypes.byref(n), f.ctypes.data_as(i32p), w.ctypes.data_as(i32p),
                                           nrhs))
         return dict(factor=f.tolist(), sweep=w.tolist())
+
+    def set_launch_shapes(self, factor=None, sweep=None, nrhs: int = 1):
+        """Threads per work item per size class (0 = default); None leaves a kind unchanged."""
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        f = None if factor is None else np.ascontiguousarray(factor, dtype=np.int32)
+        w = None if sweep is None else np.ascontiguousarray(sweep, dtype=np.int32)
+        _check(_lib.cyq_set_launch_shapes(self._h, None if f is None else f.ctypes.data_as(i32p),
+                                          None if w is None else w.ctypes.data_as(i32p), nrhs))
 
     def factor(self, Q, R, S, A, B, Sigma=None, stream=None):
         self._data = (Q, R, S, A, B, Sigma)   # borrowed until the last solve

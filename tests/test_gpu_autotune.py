@@ -64,3 +64,28 @@ def test_tuned_segment_counts_are_valid_and_solve_correctly():
     assert (s.segments == P).all()
     for inst, zi, bi in zip(batch.instances, split_instances(batch, z[0]), split_instances(batch, b_host)):
         assert rel_err(zi, oracle.riccati_solve(inst, bi)) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp32_refine", "fp64"])
+def test_launch_shapes_agree_on_a_fixed_shape_batch(precision):
+    """Stage shapes with compiled float32 kernels (nx = 12, nu = 4 and nx = 8,
+    nu = 4): the one-warp path (registers and shuffles for interior stages in
+    float32) and the multi-warp shared-memory path give the same solution."""
+    torch, cyq = require_gpu()
+    for dims, P in [((40, 12, 4), 1), ((33, 8, 4), 1), ((64, 12, 4), 4)]:
+        batch = ragged_batch(43, [dims] * 6, sigma=None, nrhs=1)
+        data, _ = cyq.to_device(batch)
+        b_host = oracle_rhs(batch)
+        b = torch.from_numpy(b_host).cuda()
+        zs = []
+        for team in (32, 64, 128):
+            s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, P=P, it_max=0)
+            s.set_launch_shapes(factor=[team] * len(s.launch_shapes()["factor"]))
+            assert s.launch_shapes()["factor"][0] == team
+            s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
+            zs.append(s.solve(b).cpu().numpy())
+            s.close()
+        assert np.array_equal(zs[0], zs[1]) and np.array_equal(zs[0], zs[2]), (dims, P, rel_err(zs[0], zs[1]))
+        tol = 1e-3 if precision == "fp32_refine" else 1e-9
+        for inst, zi, bi in zip(batch.instances, split_instances(batch, zs[0]), split_instances(batch, b_host)):
+            assert rel_err(zi, oracle.riccati_solve(inst, bi)) <= tol
