@@ -121,6 +121,10 @@ struct DeviceGuard {
     }
 };
 
+// Records per residual work item: small enough that the last refinement steps,
+// with few instances left, still spread over many SMs.
+constexpr int kResidChunk = 32;
+
 int choose_team(int nx, int nu) {
     const int nux = nx + nu;
     if (nux <= 24) return 32;
@@ -434,8 +438,8 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         g->max_nu = std::max(g->max_nu, nu);
         for (int c = 0; c < P; ++c) g->items.push_back(Item{i, c});
         item += P;
-        // residual chunks of up to 64 records
-        for (int k0 = 0; k0 < N; k0 += 64) h->chunks.push_back(Chunk{i, k0, std::min(N, k0 + 64)});
+        // residual chunks of up to kResidChunk records
+        for (int k0 = 0; k0 < N; k0 += kResidChunk) h->chunks.push_back(Chunk{i, k0, std::min(N, k0 + kResidChunk)});
         h->max_nx = std::max(h->max_nx, nx);
         h->crs_smem1 = std::max(h->crs_smem1, (size_t)P * nx * sizeof(double));
     }
@@ -457,8 +461,21 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
             // stage the raw blocks in shared memory while two CTAs still fit on an SM
             g.staged[pi] = factor_smem_bytes(f64, g.max_nx, g.max_nu, true, g.need_G2) <= (size_t)smem_optin / 2;
             g.smem_factor[pi] = factor_smem_bytes(f64, g.max_nx, g.max_nu, g.staged[pi], g.need_G2);
-            // solve: prefetch the next stage while two packages fit, else fetch after use
-            g.solve_nbuf[pi] = solve_smem_bytes(f64, g.max_nx, g.max_nu, h->max_nrhs, 2) <= (size_t)smem_optin ? 2 : 1;
+            // solve: a ring of up to 4 stage packages (prefetch depth 3) within the shared
+            // memory one CTA may take while all of the class's items stay resident
+            {
+                const long long per_sm = std::max<long long>(1, ((long long)g.items.size() + kSMs - 1) / kSMs);
+                const size_t budget = std::max<size_t>(48 * 1024, (size_t)228 * 1024 / per_sm);
+                int nb = 1;
+                for (int cand = 4; cand >= 2; --cand) {
+                    const size_t need = solve_smem_bytes(f64, g.max_nx, g.max_nu, h->max_nrhs, cand);
+                    if (need <= (size_t)smem_optin && need <= budget) {
+                        nb = cand;
+                        break;
+                    }
+                }
+                g.solve_nbuf[pi] = nb;
+            }
             if (g.smem_factor[pi] > (size_t)smem_optin ||
                 solve_smem_bytes(f64, g.max_nx, g.max_nu, h->max_nrhs, g.solve_nbuf[pi]) > (size_t)smem_optin) {
                 delete h;

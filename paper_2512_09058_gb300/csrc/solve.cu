@@ -25,9 +25,9 @@
 // Work per stage is split into three barrier-separated phases; products
 // whose rows are independent of each other share a phase.  Each stage's
 // package (factor blocks, [B A], and the right-hand-side / parked vector
-// entries the stage reads) is copied to shared memory with cp.async while the
-// previous stage is processed (or, when two packages do not fit in shared
-// memory, right after it).  The float32 sweeps read a float32 copy of [B A]
+// entries the stage reads) is copied to shared memory with cp.async up to
+// three stages ahead, in a ring of up to four packages (or right after use
+// when a single package is all that fits).  The float32 sweeps read a float32 copy of [B A]
 // written by the factorization and convert the package's float64 vector
 // entries once on arrival, so no conversion sits inside a dot product.
 // One CTA per (instance, segment); nrhs right-hand sides share each block.
@@ -89,6 +89,16 @@ struct Walk {
 };
 
 __host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+
+// Wait until at most n of this thread's committed cp.async groups are pending.
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+    if (n <= 0)
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    else if (n == 1)
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    else
+        asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+}
 
 // Per-stage package in shared memory.
 template <typename T>
@@ -208,11 +218,12 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
         Wx.init(nx, TEAM);
         Wux.init(nux, TEAM);
         Wv.init(nv, TEAM);
-        // package t at smem_raw + (t & 1) * pstride (one package when nbuf == 1)
+        // ring of nbuf packages: the package of processing step u sits in slot u % nbuf
+        // and is fetched D = nbuf - 1 steps ahead (right after use when nbuf == 1)
         const size_t pbytes = package_bytes(sizeof(T) == 8, nx, nu, nrhs);
-        const size_t pstride = a.nbuf == 2 ? pbytes : 0;
-        auto package = [&](int t) {
-            unsigned char *q = smem_raw + (size_t)(t & 1) * pstride;
+        const int nbuf = a.nbuf, D = a.nbuf - 1;
+        auto package = [&](int u) {
+            unsigned char *q = smem_raw + (size_t)(u % nbuf) * pbytes;
             return carve_package<T>(q, nx, nu, nrhs);
         };
         const Vecs<T> v = carve_vecs<T>(smem_raw + align16(a.nbuf * pbytes), nx, nu, nrhs);
@@ -222,6 +233,10 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
         // package t: factor blocks of stage s(t); [B A] of stage s(t+1) and its
         // right-hand-side entries (b_u, b_x of h_{s(t+1)}, then b_lambda = -c)
         auto fetch = [&](int t) {
+            if (t >= len) {   // an empty group keeps the count of groups in flight uniform
+                cp_async_commit();
+                return;
+            }
             const int s = seg_stage(c, t, N, P);
             const Package<T> K = package(t);
             fetch_factor<T, TEAM>(K, a, in, s, (t == 0) || (c >= 1), c >= 1);
@@ -238,7 +253,7 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
             }
             cp_async_commit();
         };
-        fetch(0);
+        for (int u = 0; u < (D > 0 ? D : 1); ++u) fetch(u);
         {
             const int s = seg_stage(c, 0, N, P), xq = xstate(s, N);
             for (int i = Wux.i0, r = Wux.r0; r < nrhs; Wux.next(i, r)) {
@@ -252,10 +267,10 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
             const bool hasG = (t == 0) || (c >= 1);
             const bool last = t == len - 1;
             const Package<T> K = package(t);
-            cp_async_wait_all();
+            cp_async_wait_pending(D > 0 ? D - 1 : 0);   // this step's package has landed
             const T *nb = last ? nullptr : package_vectors<T>(K, v, t & 1, Wv, nrhs, nv);
             team_sync();
-            if (!last && a.nbuf == 2) fetch(t + 1);   // overlaps with this stage
+            if (D > 0) fetch(t + D);   // into the slot read by the previous step
             const T *Ls = K.L, *Ds = K.D;
             const T *LQ = Ls + nu + nu * nux, *DQ = Ds + nu;
 
@@ -318,7 +333,7 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
                     for (int k = 0; k < nx; ++k) acc = fma(col[k], tr[k], acc);
                     v.hh[aa + r * nux] = acc;
                 }
-                if (a.nbuf == 1) {
+                if (D == 0) {
                     team_sync();   // the single package is free again
                     fetch(t + 1);
                 }
@@ -368,11 +383,12 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
         Wu.init(nu, TEAM);
         Wx.init(nx, TEAM);
         Wv.init(nv, TEAM);
-        // package t at smem_raw + (t & 1) * pstride (one package when nbuf == 1)
+        // ring of nbuf packages: the package of processing step u sits in slot u % nbuf
+        // and is fetched D = nbuf - 1 steps ahead (right after use when nbuf == 1)
         const size_t pbytes = package_bytes(sizeof(T) == 8, nx, nu, nrhs);
-        const size_t pstride = a.nbuf == 2 ? pbytes : 0;
-        auto package = [&](int t) {
-            unsigned char *q = smem_raw + (size_t)(t & 1) * pstride;
+        const int nbuf = a.nbuf, D = a.nbuf - 1;
+        auto package = [&](int u) {
+            unsigned char *q = smem_raw + (size_t)(u % nbuf) * pbytes;
             return carve_package<T>(q, nx, nu, nrhs);
         };
         const Vecs<T> v = carve_vecs<T>(smem_raw + align16(a.nbuf * pbytes), nx, nu, nrhs);
@@ -383,9 +399,14 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
 
         // package for processing step t (time order: t = len-1 .. 0): factor blocks
         // and [B A] of stage s(t), its parked rho / p and b_lambda = -c
-        auto fetch = [&](int t) {
+        auto fetch = [&](int u) {
+            const int t = len - 1 - u;
+            if (t < 0) {   // an empty group keeps the count of groups in flight uniform
+                cp_async_commit();
+                return;
+            }
             const int s = seg_stage(c, t, N, P), xq = xstate(s, N);
-            const Package<T> K = package(t);
+            const Package<T> K = package(u);
             fetch_factor<T, TEAM>(K, a, in, s, (t == 0) || (c >= 1), c >= 1);
             if (t > 0) fetch_BA<T, TEAM>(K, a, in, s);
             for (int i = Wv.i0, r = Wv.r0; r < nrhs; Wv.next(i, r)) {
@@ -397,7 +418,7 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
             }
             cp_async_commit();
         };
-        fetch(len - 1);
+        for (int u = 0; u < (D > 0 ? D : 1); ++u) fetch(u);
         for (int e = threadIdx.x; e < nx * nrhs; e += TEAM) {
             const int i = e % nx, r = e / nx;
             const double *lr = a.lam + r * a.nvec + in.oVec;
@@ -409,11 +430,12 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
             const int s = seg_stage(c, t, N, P), xq = xstate(s, N);
             const bool hasG = (t == 0) || (c >= 1);
             const bool first = t == len - 1;
-            const Package<T> K = package(t);
-            cp_async_wait_all();
+            const int u = len - 1 - t;
+            const Package<T> K = package(u);
+            cp_async_wait_pending(D > 0 ? D - 1 : 0);   // this step's package has landed
             const T *nb = package_vectors<T>(K, v, t & 1, Wv, nrhs, nv);
             team_sync();
-            if (t > 0 && a.nbuf == 2) fetch(t - 1);   // overlaps with this stage
+            if (D > 0) fetch(u + D);   // into the slot read by the previous step
             const T *Ls = K.L, *Ds = K.D;
             const T *LQ = Ls + nu + nu * nux, *DQ = Ds + nu;
             if (first) {
@@ -500,9 +522,9 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
                     xn[i + r * nx] = acc;
                 }
                 T *tmp = xv; xv = xn; xn = tmp;
-                if (a.nbuf == 1) {
+                if (D == 0) {
                     team_sync();   // the single package is free again
-                    fetch(t - 1);
+                    fetch(u + 1);
                 }
             }
         }
