@@ -90,6 +90,32 @@ struct Walk {
 
 __host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 
+constexpr int kPairMaxNx = 16;
+
+// Two dot products with one accumulator, one FMA per step: the n1 terms
+// a1[q*sa1] b1[q] starting from init1, then the n2 terms a2[q*sa2] b2[q]
+// starting from init2 (n2 may be 0).  Each product sums its terms in the
+// same order as a loop of its own.  A thread that owns rows i and n-1-i of a
+// triangular product this way has n+1 terms, whatever i: the lanes of a warp
+// stay equally busy (one FP64 instruction costs a whole warp slot).
+template <typename T>
+__device__ __forceinline__ void dot2(const T *a1, int sa1, const T *b1, int n1, T init1, const T *a2, int sa2,
+                                     const T *b2, int n2, T init2, T &o1, T &o2) {
+    T acc = init1, first = init1;
+    const int n = n1 + n2;
+    for (int m = 0; m < n; ++m) {
+        if (m == n1) {
+            first = acc;
+            acc = init2;
+        }
+        const bool sec = m >= n1;
+        const int q = sec ? m - n1 : m;
+        acc = fma(sec ? a2[q * sa2] : a1[q * sa1], sec ? b2[q] : b1[q], acc);
+    }
+    o1 = n2 > 0 ? first : acc;
+    o2 = acc;
+}
+
 // Wait until at most n of this thread's committed cp.async groups are pending.
 __device__ __forceinline__ void cp_async_wait_pending(int n) {
     if (n <= 0)
@@ -213,11 +239,17 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
         const int N = in.N, P = in.P, c = wi.seg, nrhs = a.nrhs;
         const int nux = nx + nu, nv = nux + nx, w = nu + 2 * nx;
         const int len = seg_len(c, N, P);
-        Walk Wu, Wx, Wux, Wv;
+        // Wp: pairs of rows (i, nx-1-i) of the triangular products, in float64 for small
+        // nx, where unequal row lengths leave most lanes of an FP64 instruction idle
+        // (the pairing costs ALU work per step, which float32 and large nx do not repay)
+        const bool pair = sizeof(T) == 8 && nx <= kPairMaxNx;
+        const int half = (nx + 1) / 2;
+        Walk Wu, Wx, Wux, Wv, Wp;
         Wu.init(nu, TEAM);
         Wx.init(nx, TEAM);
         Wux.init(nux, TEAM);
         Wv.init(nv, TEAM);
+        Wp.init(half, TEAM);
         // ring of nbuf packages: the package of processing step u sits in slot u % nbuf
         // and is fetched D = nbuf - 1 steps ahead (right after use when nbuf == 1)
         const size_t pbytes = package_bytes(sizeof(T) == 8, nx, nu, nrhs);
@@ -282,7 +314,17 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
                 for (int k = 0; k < i; ++k) acc = fma(Ls[k + i * nux], hu[k], acc);
                 v.rho[i + r * nu] = acc;
             }
-            if (!last) {
+            if (!last && pair) {
+                for (int jp = Wp.i0, r = Wp.r0; r < nrhs; Wp.next(jp, r)) {
+                    const int j1 = jp, j2 = nx - 1 - jp;
+                    const T *cr = nb + r * nv + nux;   // b_lambda = -c
+                    T w1, w2;
+                    dot2(LQ + j1 + j1 * nux, 1, cr + j1, nx - j1, T(0), LQ + j2 + j2 * nux, 1, cr + j2,
+                         j2 != j1 ? nx - j2 : 0, T(0), w1, w2);
+                    v.wv[j1 + r * nx] = -w1;
+                    if (j2 != j1) v.wv[j2 + r * nx] = -w2;
+                }
+            } else if (!last) {
                 for (int j = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(j, r)) {
                     const T *cr = nb + r * nv + nux;   // b_lambda = -c
                     T acc = T(0);
@@ -295,7 +337,48 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
             // phase 2: p = h_x - L^S rho (parked);  g -= L^B rho;  t = L^Q w + p;  g += A^cl c
             for (int i = Wu.i0, r = Wu.r0; r < nrhs; Wu.next(i, r))
                 z[r * a.kkt + (long long)s * w + i] = (double)v.rho[i + r * nu];
-            for (int i = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(i, r)) {
+            for (int ip = Wp.i0, r = Wp.r0; r < nrhs && pair; Wp.next(ip, r)) {
+                const int i1 = ip, i2 = nx - 1 - ip;
+                const bool two = i2 != i1;
+                const T *ro = v.rho + r * nu;
+                T p1 = v.hh[r * nux + nu + i1], p2 = v.hh[r * nux + nu + i2];
+#pragma unroll 4
+                for (int k = 0; k < nu; ++k) {
+                    p1 = fma(-Ls[(nu + i1) + k * nux], ro[k], p1);
+                    p2 = fma(-Ls[(nu + i2) + k * nux], ro[k], p2);
+                }
+                z[r * a.kkt + (long long)(xq - 1) * w + nu + i1] = (double)p1;
+                if (two) z[r * a.kkt + (long long)(xq - 1) * w + nu + i2] = (double)p2;
+                T g1 = v.gmu[i1 + r * nx], g2 = v.gmu[i2 + r * nx];
+                if (hasG) {
+#pragma unroll 4
+                    for (int k = 0; k < nu; ++k) {
+                        g1 = fma(-K.LB[i1 + k * nx], ro[k], g1);
+                        g2 = fma(-K.LB[i2 + k * nx], ro[k], g2);
+                    }
+                }
+                if (!last) {
+                    const T *wr = v.wv + r * nx;
+                    T t1, t2;
+                    dot2(LQ + i1, nux, wr, i1 + 1, p1, LQ + i2, nux, wr, two ? i2 + 1 : 0, p2, t1, t2);
+                    v.tv[i1 + r * nx] = t1;
+                    if (two) v.tv[i2 + r * nx] = t2;
+                    if (c >= 1) {
+                        const T *cr = nb + r * nv + nux;
+#pragma unroll 4
+                        for (int k = 0; k < nx; ++k) {
+                            g1 = fma(-K.F[i1 + k * nx], cr[k], g1);
+                            g2 = fma(-K.F[i2 + k * nx], cr[k], g2);
+                        }
+                    }
+                } else {
+                    v.pv[i1 + r * nx] = p1;
+                    if (two) v.pv[i2 + r * nx] = p2;
+                }
+                v.gmu[i1 + r * nx] = g1;
+                if (two) v.gmu[i2 + r * nx] = g2;
+            }
+            for (int i = Wx.i0, r = Wx.r0; r < nrhs && !pair; Wx.next(i, r)) {
                 const T *ro = v.rho + r * nu;
                 T pacc = v.hh[r * nux + nu + i];
 #pragma unroll 4
@@ -379,10 +462,16 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
         const int N = in.N, P = in.P, c = wi.seg, nrhs = a.nrhs;
         const int nux = nx + nu, nv = nux + nx, w = nu + 2 * nx;
         const int len = seg_len(c, N, P);
-        Walk Wu, Wx, Wv;
+        // Wp: pairs of rows (i, nx-1-i) of the triangular products, in float64 for small
+        // nx, where unequal row lengths leave most lanes of an FP64 instruction idle
+        // (the pairing costs ALU work per step, which float32 and large nx do not repay)
+        const bool pair = sizeof(T) == 8 && nx <= kPairMaxNx;
+        const int half = (nx + 1) / 2;
+        Walk Wu, Wx, Wv, Wp;
         Wu.init(nu, TEAM);
         Wx.init(nx, TEAM);
         Wv.init(nv, TEAM);
+        Wp.init(half, TEAM);
         // ring of nbuf packages: the package of processing step u sits in slot u % nbuf
         // and is fetched D = nbuf - 1 steps ahead (right after use when nbuf == 1)
         const size_t pbytes = package_bytes(sizeof(T) == 8, nx, nu, nrhs);
@@ -472,7 +561,27 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
                 }
                 v.hh[k + r * nux] = acc;
             }
-            for (int j = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(j, r)) {
+            for (int jp = Wp.i0, r = Wp.r0; r < nrhs && pair; Wp.next(jp, r)) {
+                const int j1 = jp, j2 = nx - 1 - jp;
+                const bool two = j2 != j1;
+                const T *x = xv + r * nx;
+                if (!first) {
+                    T w1, w2;
+                    dot2(LQ + j1 + j1 * nux, 1, x + j1, nx - j1, T(0), LQ + j2 + j2 * nux, 1, x + j2,
+                         two ? nx - j2 : 0, T(0), w1, w2);
+                    v.wv[j1 + r * nx] = w1;
+                    if (two) v.wv[j2 + r * nx] = w2;
+                }
+                const long long o = r * a.kkt + (long long)(xq - 1) * w + nu;
+                if (zacc) {
+                    atomicAdd(zacc + o + j1, (double)x[j1]);
+                    if (two) atomicAdd(zacc + o + j2, (double)x[j2]);
+                } else {
+                    z[o + j1] = (double)x[j1];
+                    if (two) z[o + j2] = (double)x[j2];
+                }
+            }
+            for (int j = Wx.i0, r = Wx.r0; r < nrhs && !pair; Wx.next(j, r)) {
                 const T *x = xv + r * nx;
                 if (!first) {
                     T acc = T(0);
@@ -496,7 +605,30 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
             }
             if (!first) {
                 const int sp = (s - 1 + N) % N;
-                for (int i = Wx.i0, r = Wx.r0; r < nrhs; Wx.next(i, r)) {
+                for (int ip = Wp.i0, r = Wp.r0; r < nrhs && pair; Wp.next(ip, r)) {
+                    const int i1 = ip, i2 = nx - 1 - ip;
+                    const bool two = i2 != i1;
+                    const T *wr = v.wv + r * nx, *mr = mu + r * nx;
+                    T l1, l2;
+                    dot2(LQ + i1, nux, wr, i1 + 1, nb[r * nv + nu + i1], LQ + i2, nux, wr, two ? i2 + 1 : 0,
+                         nb[r * nv + nu + i2], l1, l2);
+                    if (c >= 1) {
+#pragma unroll 4
+                        for (int k = 0; k < nx; ++k) {
+                            l1 = fma(K.F[k + i1 * nx], mr[k], l1);
+                            l2 = fma(K.F[k + i2 * nx], mr[k], l2);
+                        }
+                    }
+                    const long long o = r * a.kkt + (long long)sp * w + nu + nx;
+                    if (zacc) {
+                        atomicAdd(zacc + o + i1, (double)l1);
+                        if (two) atomicAdd(zacc + o + i2, (double)l2);
+                    } else {
+                        z[o + i1] = (double)l1;
+                        if (two) z[o + i2] = (double)l2;
+                    }
+                }
+                for (int i = Wx.i0, r = Wx.r0; r < nrhs && !pair; Wx.next(i, r)) {
                     const T *wr = v.wv + r * nx, *mr = mu + r * nx;
                     T acc = nb[r * nv + nu + i];
 #pragma unroll 4
