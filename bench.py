@@ -48,6 +48,11 @@ METHODS = {"fp64": ("fp64", 0), "fp64_refine": ("fp64", 3), "fp32_refine": ("fp3
 # refinement target: the metric's gate, as evaluated by the library's float64
 # residual kernel
 REFINE_TOL = 1e-10
+# DRAM bytes (read + write) per launch of the dominant kernel (the stage factor),
+# from one ncu capture of the current kernel (profiles/k_factor_segments_*.md);
+# absent where no capture of the current kernel exists
+NCU_TRAFFIC = {("batch1024_n64_nx12_nu4", "fp64"): 217.7e6 + 110.1e6,
+               ("batch1024_n64_nx12_nu4", "fp32_refine"): 217.0e6 + 88.5e6}
 # workload -> methods (first = headline), CUDA-graph replay, adjoint in the step
 # workload -> methods (first = headline), CUDA-graph replay, adjoint in the step,
 # segment counts tuned by timing (cyq_tune_segments); launch shapes are always
@@ -533,7 +538,10 @@ def main():
         "refine_steps": R["stats"]["refine_steps"],
         "roofline": {"kernel": "k_factor_segments<%s> (+ cyclic reduction when P > 1)" % ("double" if f64 else "float"),
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": NCU_TRAFFIC.get((args.workload, METHODS[head][0])),
+                     "traffic_hbm_gbs": (NCU_TRAFFIC[(args.workload, METHODS[head][0])] / (R["factor_ms"] / 1e3) / 1e9
+                                         if (args.workload, METHODS[head][0]) in NCU_TRAFFIC else None),
                      "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz" if f64 else
                                      "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz")},
         "variants": variants,
