@@ -77,7 +77,11 @@ typedef enum cyq_status {
 
 typedef enum cyq_precision {
     CYQ_FP64 = 0,          /* factor and solve in float64 (+ float64 refinement if it_max > 0) */
-    CYQ_FP32_REFINE = 1    /* float32 factor/solve, float64 residual + iterative refinement */
+    CYQ_FP32_REFINE = 1,   /* float32 factor/solve, float64 residual + iterative refinement */
+    CYQ_FP64_IR32 = 2      /* float64 factor and solve; refinement corrections by float32 sweeps with a
+                              float32 copy of the factor (written by the float64 factorization), float64
+                              residual; instances still above tol after it_max steps get up to esc_max
+                              float64 corrections with the same factor */
 } cyq_precision;
 
 /* Opaque handle (host object owning device workspace). */

@@ -86,6 +86,7 @@ struct cyq_handle_s {
     Chunk *d_chunks = nullptr;
     FactorSet fac;                // factor in the handle's precision
     FactorSet fac64;              // float64 factor for precision escalation (float32 mode only)
+    FactorSet fac32;              // float32 copy of the float64 factor (float64 mode with float32 corrections)
     double *Mf = nullptr, *Mb = nullptr, *Kc = nullptr, *U = nullptr, *Y = nullptr;
     double *dF = nullptr, *dB = nullptr, *lam = nullptr;
     int *status = nullptr;
@@ -249,6 +250,14 @@ FactorArgs factor_args(cyq_handle h, const FactorSet &fs, const int *skip) {
     a.F = fs.F;
     a.DI = fs.DI;
     a.BAf = fs.fp64 ? nullptr : fs.BA;
+    if (fs.fp64 && &fs == &h->fac && h->precision == CYQ_FP64_IR32) {
+        // the float64 factorization also writes the float32 copy used by the corrections
+        a.Lc = static_cast<float *>(h->fac32.L);
+        a.LBc = static_cast<float *>(h->fac32.LB);
+        a.Fc = static_cast<float *>(h->fac32.F);
+        a.DIc = static_cast<float *>(h->fac32.DI);
+        a.BAf = h->fac32.BA;
+    }
     a.Mf = h->Mf;
     a.Mb = h->Mb;
     a.Kc = h->Kc;
@@ -312,6 +321,8 @@ cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, int nrhs,
     CYQ_CUDA(cudaMemsetAsync(h->bb, 0, sizeof(double) * B * h->max_nrhs, st));
     cyq_status s = run_solve(h, h->fac, b, z, nrhs, nullptr, st);
     if (s != CYQ_OK) return s;
+    // corrections: with the handle's factor, or with its float32 copy (CYQ_FP64_IR32)
+    const FactorSet &corr = h->precision == CYQ_FP64_IR32 ? h->fac32 : h->fac;
     int step = 0;
     for (int it = 0; it <= h->it_max; ++it, ++step) {
         // ||b||^2 once (first residual); later steps reuse it
@@ -320,17 +331,21 @@ cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, int nrhs,
         h->launches += 2;
         if (it == h->it_max) break;
         // correction: z += K~^{-1} r for the instances still above tol
-        s = run_solve(h, h->fac, h->r, h->dz, nrhs, h->done, st, z);
+        s = run_solve(h, corr, h->r, h->dz, nrhs, h->done, st, z);
         if (s != CYQ_OK) return s;
     }
-    if (!h->fac.fp64 && h->esc_max > 0) {
-        // precision escalation: instances the float32 factor could not bring to
-        // tol get a float64 factor, and the refinement continues with it
-        s = run_factor(h, h->fac64, h->done, st);
-        if (s != CYQ_OK) return s;
+    if (!corr.fp64 && h->esc_max > 0) {
+        // precision escalation: instances the float32 corrections could not bring to
+        // tol continue with float64 corrections (float32 mode: after a float64 factorization)
+        const bool refactor = !h->fac.fp64;
+        if (refactor) {
+            s = run_factor(h, h->fac64, h->done, st);
+            if (s != CYQ_OK) return s;
+        }
+        const FactorSet &f64 = refactor ? h->fac64 : h->fac;
         for (int it = 0; it < h->esc_max; ++it) {
             ++step;
-            s = run_solve(h, h->fac64, h->r, h->dz, nrhs, h->done, st, z);
+            s = run_solve(h, f64, h->r, h->dz, nrhs, h->done, st, z);
             if (s != CYQ_OK) return s;
             CYQ_CUDA(launch_residual(resid_args(h, b, z, h->r, h->done, false), nrhs, st));
             CYQ_CUDA(launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, step, true, st));
@@ -368,7 +383,8 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     if (!desc || !out) return CYQ_ERR_INVALID_ARG;
     *out = nullptr;
     if (desc->batch < 1 || !desc->N || !desc->nx || !desc->nu) return CYQ_ERR_INVALID_ARG;
-    if (desc->precision != CYQ_FP64 && desc->precision != CYQ_FP32_REFINE) return CYQ_ERR_INVALID_ARG;
+    if (desc->precision != CYQ_FP64 && desc->precision != CYQ_FP32_REFINE && desc->precision != CYQ_FP64_IR32)
+        return CYQ_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         g_last_error = "no CUDA device";
@@ -389,7 +405,9 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     h->it_max = desc->it_max >= 0 ? desc->it_max : 10;
     h->esc_max = desc->esc_max >= 0 ? desc->esc_max : 3;
     h->tol = desc->tol > 0 ? desc->tol : 1e-10;
-    const bool fp64 = h->precision == CYQ_FP64;
+    // float64 factorization (CYQ_FP64, CYQ_FP64_IR32); float32 plans for the sweeps unless CYQ_FP64
+    const bool fp64 = h->precision != CYQ_FP32_REFINE;
+    const bool float_sweeps = h->precision != CYQ_FP64;
 
     long long oQ = 0, oR = 0, oS = 0, oA = 0, oB = 0, oSig = 0, oZ = 0, oL = 0, oLB = 0, oF = 0, oDI = 0, oBA = 0, oBlk = 0,
               oVec = 0, oq = 0, orv = 0, oc = 0, ox0 = 0;
@@ -457,7 +475,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         for (const Item &it : g.items) g.need_G2 |= it.seg >= 1;
         for (int pi = 0; pi < 2; ++pi) {
             const bool f64 = pi == 1;
-            if (!f64 && fp64) continue;   // float32 plans only in float32 mode
+            if (!f64 && !float_sweeps) continue;   // float32 plans only where float32 sweeps run
             // stage the raw blocks in shared memory while two CTAs still fit on an SM
             g.staged[pi] = factor_smem_bytes(f64, g.max_nx, g.max_nu, true, g.need_G2) <= (size_t)smem_optin / 2;
             g.smem_factor[pi] = factor_smem_bytes(f64, g.max_nx, g.max_nu, g.staged[pi], g.need_G2);
@@ -538,9 +556,11 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     }
     ALLOC(h->d_all_list, (size_t)h->batch);
     for (Group &g : h->groups) ALLOC(g.d_items, g.items.size());
-    for (int pass = 0; pass < (fp64 ? 1 : 2); ++pass) {
-        FactorSet &fs = pass == 0 ? h->fac : h->fac64;
-        fs.fp64 = pass == 1 || fp64;
+    // fac (the handle's factor) and, in float32 mode, fac64 (escalation), in float64
+    // mode with float32 corrections, fac32 (float32 copy)
+    for (int pass = 0; pass < (float_sweeps ? 2 : 1); ++pass) {
+        FactorSet &fs = pass == 0 ? h->fac : (fp64 ? h->fac32 : h->fac64);
+        fs.fp64 = pass == 0 ? fp64 : !fp64;
         const size_t el = fs.fp64 ? sizeof(double) : sizeof(float);
         char *p;
         ALLOC(p, (size_t)oL * el); fs.L = p;
@@ -666,7 +686,7 @@ cyq_status cyq_solve_adjoint(cyq_handle h, const double *x_init, const double *z
     DeviceGuard guard(h->device);
     cudaStream_t st = to_stream(stream);
     double *wbuf = w ? w : h->dz;
-    if (!w && h->precision != CYQ_FP64) return CYQ_ERR_INVALID_ARG;   // dz is the refinement workspace
+    if (!w && h->it_max > 0) return CYQ_ERR_INVALID_ARG;   // dz is the refinement workspace
     cyq_status s = cyq_solve(h, dL_dz, wbuf, 1, stream);
     if (s != CYQ_OK) return s;
     GradArgs g{};
@@ -768,6 +788,8 @@ cyq_status cyq_autotune(cyq_handle h, const double *Q, const double *R, const do
     const FactorArgs fa = factor_args(h, fs, nullptr);
     static const int cand_factor[] = {32, 64, 128};
     static const int cand_sweep[] = {32, 64, 128, 256};
+    // the float32 correction sweeps of CYQ_FP64_IR32 (their plans exist once the handle is factored)
+    const bool tune32 = h->precision == CYQ_FP64_IR32;
     for (Group &g : h->groups) {
         float best = 3.0e38f;
         int pick = 0;
@@ -793,6 +815,22 @@ cyq_status cyq_autotune(cyq_handle h, const double *Q, const double *R, const do
             if (ms < best) { best = ms; pick = t; }
         }
         g.team_solve[pi] = pick;
+        if (tune32) {
+            best = 3.0e38f;
+            pick = 0;
+            for (int t : cand_sweep) {
+                g.team_solve[0] = t;
+                float ms = 0.0f;
+                s = time_ms(st, reps, [&] {
+                    cudaError_t e = launch_group_sweep(h, h->fac32, g, true, b, z, nrhs, nullptr, nullptr, st);
+                    return e != cudaSuccess ? e
+                                            : launch_group_sweep(h, h->fac32, g, false, b, z, nrhs, nullptr, nullptr, st);
+                }, &ms);
+                if (s != CYQ_OK) { g.team_solve[0] = 0; return s; }
+                if (ms < best) { best = ms; pick = t; }
+            }
+            g.team_solve[0] = pick;
+        }
     }
     // the timed launches left the factor intact (same data); refresh it as a whole
     s = run_factor(h, fs, nullptr, st);

@@ -317,7 +317,10 @@ struct FactorArgs {
     Data data;
     void *L, *LB, *F;               // factor arrays (float or double)
     void *DI;                       // reciprocal diagonals of the stage factors
-    void *BAf;                      // optional float32 copy of every stage's [B A] (float32 factors only)
+    void *BAf;                      // optional float32 copy of every stage's [B A]
+    // optional float32 copies of the stored factor written by a float64 factorization
+    // (L, L^B, A^cl / L^A, reciprocal diagonals), for float32 correction sweeps
+    float *Lc, *LBc, *Fc, *DIc;
     double *Mf, *Mb, *Kc;           // Schur blocks (float64)
     double *U, *Y;                  // cyclic-reduction factor blocks (float64)
     int *status;

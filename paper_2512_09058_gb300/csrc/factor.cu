@@ -123,6 +123,15 @@ __device__ void store_block(T *dst, const T *src, int rows, int cols, int ld) {
     for (; c < cols; rect_advance(r, c, rows, TEAM)) dst[r + c * rows] = src[r + c * ld];
 }
 
+// Float32 copy of a block a float64 factorization stores (dst may be null).
+template <typename T, int TEAM>
+__device__ void store_block_f32(float *dst, const T *src, int rows, int cols, int ld) {
+    if (!dst) return;
+    int r, c;
+    rect_start(threadIdx.x, rows, r, c);
+    for (; c < cols; rect_advance(r, c, rows, TEAM)) dst[r + c * rows] = (float)src[r + c * ld];
+}
+
 template <typename T, int TEAM>
 __device__ void store_block_f64(double *dst, const T *src, int rows, int cols, int ld) {
     int r, c;
@@ -359,6 +368,8 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
         const int ldBA = ba_alias ? nx : ldG;
 
         T *Lg = reinterpret_cast<T *>(a.L) + in.oL;
+        // float64 factorization that also writes a float32 copy for float32 correction sweeps
+        const bool copy32 = sizeof(T) == 8 && a.Lc != nullptr;
         T *LBg = reinterpret_cast<T *>(a.LB) + in.oLB;
         T *Fg = reinterpret_cast<T *>(a.F) + in.oF;
         T *DIg = reinterpret_cast<T *>(a.DI) + in.oDI;
@@ -420,14 +431,22 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
             team_sync();
             store_block<T, TEAM>(Lg + (long long)s * nux * nux, H, nux, nux, ldH);
             for (int i = threadIdx.x; i < nux; i += TEAM) DIg[(long long)s * nux + i] = dinv[i];
+            if (copy32) {
+                store_block_f32<T, TEAM>(a.Lc + in.oL + (long long)s * nux * nux, H, nux, nux, ldH);
+                for (int i = threadIdx.x; i < nux; i += TEAM) a.DIc[in.oDI + (long long)s * nux + i] = (float)dinv[i];
+            }
             if (hasG) {
                 // L^B = B^ L^{R-T}
                 team_trsm_rlt<T, TEAM>(G, nx, nu, ldG, H, ldH, dinv);
                 // A^cl = A^ - L^B L^{S T}   (L^S = rows nu.. of columns 0..nu-1)
                 team_gemm_nt<T, TEAM>(G + ldG * nu, ldG, G, ldG, H + nu, ldH, nx, nx, nu, -1);
                 store_block<T, TEAM>(LBg + (long long)s * nx * nu, G, nx, nu, ldG);
+                if (copy32) store_block_f32<T, TEAM>(a.LBc + in.oLB + (long long)s * nx * nu, G, nx, nu, ldG);
                 team_syrk_lower<T, double, TEAM>(Mf, nx, G, ldG, nx, nu, +1);
-                if (propagate && !last) store_block<T, TEAM>(Fg + (long long)s * nx * nx, G + ldG * nu, nx, nx, ldG);
+                if (propagate && !last) {
+                    store_block<T, TEAM>(Fg + (long long)s * nx * nx, G + ldG * nu, nx, nx, ldG);
+                    if (copy32) store_block_f32<T, TEAM>(a.Fc + in.oF + (long long)s * nx * nx, G + ldG * nu, nx, nx, ldG);
+                }
             }
             if (!last) {
                 if (staged) {
@@ -441,14 +460,17 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 const T *BA;
                 if (ba_alias) {
                     BA = reinterpret_cast<const T *>(src.B);
+                    if (copy32)   // float32 [B A] of stage s2 for the float32 correction sweeps
+                        store_block_f32<T, TEAM>(reinterpret_cast<float *>(a.BAf) + in.oBA + (long long)s2 * nx * nux, BA,
+                                                 nx, nux, nx);
                 } else {
                     fill_BA<T, TEAM>(BAc, ldBA, src, nx, nu);
                     team_sync();
                     BA = BAc;
                     // float32 copy for the solve sweeps (no conversions there)
                     if (a.BAf)
-                        store_block<T, TEAM>(reinterpret_cast<T *>(a.BAf) + in.oBA + (long long)s2 * nx * nux, BAc,
-                                             nx, nux, ldBA);
+                        store_block_f32<T, TEAM>(reinterpret_cast<float *>(a.BAf) + in.oBA + (long long)s2 * nx * nux,
+                                                 BAc, nx, nux, ldBA);
                 }
                 // V = [B A]^T L^Q : V[a][j] = sum_{k >= j} BA[k][a] L^Q[k][j]
                 const T *LQ = H + nu + nu * ldH;
@@ -493,6 +515,7 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                     // L^A = A^cl L^{Q-T}, stored in place of A^cl of the first stage
                     team_trsm_rlt<T, TEAM>(LA, nx, nx, ldG, LQ, ldH, dq);
                     store_block<T, TEAM>(Fg + (long long)s * nx * nx, LA, nx, nx, ldG);
+                    if (copy32) store_block_f32<T, TEAM>(a.Fc + in.oF + (long long)s * nx * nx, LA, nx, nx, ldG);
                     team_syrk_lower<T, double, TEAM>(Mf, nx, LA, ldG, nx, nx, +1);
                 }
                 // Tinv = L^{Q -1}  (in V's tile; L^Q is not needed after this)
@@ -505,7 +528,11 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                     int i, cc;
                     rect_start(threadIdx.x, nx, i, cc);
                     for (; cc < nx; rect_advance(i, cc, nx, TEAM))
-                        if (i > cc) Lq[cc + i * nux] = Ti[i + cc * ldT];
+                        if (i > cc) {
+                            Lq[cc + i * nux] = Ti[i + cc * ldT];
+                            if (copy32)
+                                a.Lc[in.oL + (long long)s * nux * nux + nu + nu * nux + cc + i * nux] = (float)Ti[i + cc * ldT];
+                        }
                 }
                 // M_bwd = Tinv^T Tinv  (full symmetric, in the H tile, leading dimension ldT)
                 T *Mb = H;

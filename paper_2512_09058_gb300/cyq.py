@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libcyq.so")
 
 CYQ_FP64 = 0
 CYQ_FP32_REFINE = 1
+CYQ_FP64_IR32 = 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "not positive definite", 3: "not converged", 4: "CUDA error",
           5: "timeout", 6: "no factor", 7: "unimplemented", 8: "no device"}
 
@@ -124,7 +125,7 @@ class _Desc:
         self.N = np.ascontiguousarray(N, dtype=np.int32)
         self.nx = np.ascontiguousarray(nx, dtype=np.int32)
         self.nu = np.ascontiguousarray(nu, dtype=np.int32)
-        self.precision = {"fp64": CYQ_FP64, "fp32_refine": CYQ_FP32_REFINE}[precision]
+        self.precision = {"fp64": CYQ_FP64, "fp32_refine": CYQ_FP32_REFINE, "fp64_ir32": CYQ_FP64_IR32}[precision]
         pp = None
         if P_per_instance is not None:
             self.P = np.ascontiguousarray(P_per_instance, dtype=np.int32)

@@ -28,7 +28,7 @@ def _residuals(batch, z, b):
     return np.array(out)
 
 
-@pytest.mark.parametrize("precision", ["fp32_refine", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32_refine", "fp64", "fp64_ir32"])
 @pytest.mark.parametrize("P", [1, 4])
 def test_refinement_reaches_tolerance_on_ragged_batch(precision, P):
     dims = [(8, 3, 2), (17, 6, 3), (32, 12, 4), (5, 2, 1), (40, 20, 8)]
@@ -57,6 +57,24 @@ def test_fp32_refine_on_batch1024_workload_sampled():
     for j in range(4):
         zs, bs = split_instances(batch, z[j]), split_instances(batch, b[j])
         for i in sample:
+            inst = batch.instances[i]
+            assert (oracle.kkt_residual(inst, zs[i], bs[i]) <=
+                    TOL + 2.0 * oracle.residual_eval_bound(inst, zs[i], bs[i]))
+            assert rel_err(zs[i], oracle.riccati_solve(inst, bs[i])) <= 1e-8
+
+
+def test_fp64_float32_corrections_on_batch1024_workload_sampled():
+    """float64 factor + solve, float32 correction sweeps (float32 copy of the
+    float64 factor), float64 residual: one correction reaches 1e-10 here."""
+    batch = inputs.make_batch("batch1024_n64_nx12_nu4", range(256))
+    z, s, _, b = gpu_solve(batch, precision="fp64_ir32", nrhs=4, it_max=10)
+    st = s.stats()
+    print("fp64 + float32 corrections on batch1024[:256]:", st)
+    assert (s.instance_status() == 0).all()
+    assert st["max_rel_residual"] <= 1e-10 and st["refine_steps"] <= 2
+    for j in (0, 3):
+        zs, bs = split_instances(batch, z[j]), split_instances(batch, b[j])
+        for i in (0, 17, 255):
             inst = batch.instances[i]
             assert (oracle.kkt_residual(inst, zs[i], bs[i]) <=
                     TOL + 2.0 * oracle.residual_eval_bound(inst, zs[i], bs[i]))
