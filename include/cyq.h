@@ -203,10 +203,12 @@ int64_t cyq_last_launch_count(cyq_handle h);
 /*
  * Launch-shape autotuner (the paper tunes its SIMD width and segment count
  * per problem size, Sec. 5; here the GPU analogue).  For every size class of
- * the handle, times the stage factorization with 32, 64 and 128 threads per
+ * the handle, times the stage factorization with 16, 32, 64 and 128 threads per
  * work item and the two solve sweeps with 32 to 256 threads per work item
  * (nrhs right-hand sides b), `reps` launches each (default 3 if < 1), with
- * CUDA events on `stream`, and keeps the fastest shapes in the handle: the
+ * CUDA events on `stream` (the stage factorization also with 16 threads, two
+ * items per warp, where their shared memory fits in one CTA), and keeps the
+ * fastest shapes in the handle: the
  * stage factor's for every later cyq_factor, the sweeps' for every later
  * cyq_solve with this nrhs.  Binds and factors the data like cyq_factor and
  * leaves the handle factored; z (nrhs * kkt_size) is scratch.  Synchronises
@@ -227,7 +229,8 @@ cyq_status cyq_get_launch_shapes(cyq_handle h, int32_t *n_groups, int32_t *facto
  * entry per size class (cyq_get_launch_shapes gives the count); 0 restores
  * the default of that class; the sweep shapes apply to cyq_solve calls with
  * nrhs right-hand sides.  Either array may be NULL (left unchanged).
- * Allowed values: factor 32, 64, 128; sweeps 32, 64, 128, 256.
+ * Allowed values: factor 16 (two items per warp, where their shared memory fits
+ * in one CTA), 32, 64, 128; sweeps 32, 64, 128, 256.
  * Errors: INVALID_ARG. */
 cyq_status cyq_set_launch_shapes(cyq_handle h, const int32_t *factor_team, const int32_t *sweep_team,
                                  int32_t nrhs);

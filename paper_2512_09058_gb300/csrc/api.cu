@@ -79,6 +79,7 @@ struct cyq_handle_s {
     long long kkt = 0, nL = 0, nLB = 0, nF = 0, nDI = 0, nblk = 0, nvec = 0;
     size_t crs_smem1 = 0;
     int max_nx = 0;
+    int smem_optin = 0;
     // device
     DevicePtrs mem;
     Inst *d_inst = nullptr;
@@ -405,6 +406,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     h->it_max = desc->it_max >= 0 ? desc->it_max : 10;
     h->esc_max = desc->esc_max >= 0 ? desc->esc_max : 3;
     h->tol = desc->tol > 0 ? desc->tol : 1e-10;
+    h->smem_optin = smem_optin;
     // float64 factorization (CYQ_FP64, CYQ_FP64_IR32); float32 plans for the sweeps unless CYQ_FP64
     const bool fp64 = h->precision != CYQ_FP32_REFINE;
     const bool float_sweeps = h->precision != CYQ_FP64;
@@ -786,7 +788,7 @@ cyq_status cyq_autotune(cyq_handle h, const double *Q, const double *R, const do
     s = run_solve(h, fs, b, z, nrhs, nullptr, st);
     if (s != CYQ_OK) return s;
     const FactorArgs fa = factor_args(h, fs, nullptr);
-    static const int cand_factor[] = {32, 64, 128};
+    static const int cand_factor[] = {16, 32, 64, 128};   // 16: two items per warp
     static const int cand_sweep[] = {32, 64, 128, 256};
     // the float32 correction sweeps of CYQ_FP64_IR32 (their plans exist once the handle is factored)
     const bool tune32 = h->precision == CYQ_FP64_IR32;
@@ -794,6 +796,7 @@ cyq_status cyq_autotune(cyq_handle h, const double *Q, const double *R, const do
         float best = 3.0e38f;
         int pick = 0;
         for (int t : cand_factor) {
+            if (t < 32 && (size_t)(32 / t) * ((g.smem_factor[pi] + 15) / 16 * 16) > (size_t)h->smem_optin) continue;
             g.team_factor[pi] = t;
             float ms = 0.0f;
             s = time_ms(st, reps, [&] { return launch_group_factor(fs, g, fa, st); }, &ms);
@@ -856,7 +859,9 @@ cyq_status cyq_set_launch_shapes(cyq_handle h, const int32_t *factor_team, const
     const int pi = h->fac.fp64 ? 1 : 0;
     for (size_t i = 0; i < h->groups.size(); ++i) {
         const int f = factor_team ? factor_team[i] : 0, w = sweep_team ? sweep_team[i] : 0;
-        if (!(f == 0 || f == 32 || f == 64 || f == 128)) return CYQ_ERR_INVALID_ARG;
+        if (!(f == 0 || f == 16 || f == 32 || f == 64 || f == 128)) return CYQ_ERR_INVALID_ARG;
+        if (f == 16 && 2 * ((h->groups[i].smem_factor[pi] + 15) / 16 * 16) > (size_t)h->smem_optin)
+            return CYQ_ERR_INVALID_ARG;
         if (!(w == 0 || w == 32 || w == 64 || w == 128 || w == 256)) return CYQ_ERR_INVALID_ARG;
     }
     if (sweep_team && nrhs < 1) return CYQ_ERR_INVALID_ARG;

@@ -79,6 +79,22 @@ __host__ __device__ inline int xstate(int s, int N) { return s == 0 ? N : s; }
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void team_sync() { __syncthreads(); }
 
+// A team is the group of threads that works on one item: the whole CTA when
+// TEAM >= 32, else TEAM consecutive lanes of a warp (several teams per warp,
+// whose instructions then serve several items at once).  Thread index within
+// the team, and a barrier over the team only.
+template <int TEAM>
+__device__ __forceinline__ int team_tid() {
+    return TEAM >= 32 ? (int)threadIdx.x : (int)(threadIdx.x & (TEAM - 1));
+}
+template <int TEAM>
+__device__ __forceinline__ void team_sync() {
+    if constexpr (TEAM >= 32)
+        __syncthreads();
+    else
+        __syncwarp(((1u << TEAM) - 1u) << (threadIdx.x & 31 & ~(TEAM - 1)));
+}
+
 template <typename T> __device__ __forceinline__ T ld_cvt(const double *p) { return (T)(*p); }
 
 // Element e of the lower triangle (diagonal included) of an n x n matrix in
@@ -169,7 +185,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 template <int TEAM>
 __device__ __forceinline__ void async_copy_f64(double *dst, const double *src, int count) {
-    for (int e = threadIdx.x; e < count; e += TEAM) cp_async8(dst + e, src + e);
+    for (int e = team_tid<TEAM>(); e < count; e += TEAM) cp_async8(dst + e, src + e);
 }
 
 // In-place lower Cholesky factor of the n x n matrix A (lower triangle read;
@@ -181,7 +197,7 @@ __device__ __forceinline__ void async_copy_f64(double *dst, const double *src, i
 // arithmetic stays finite).
 template <typename T, int TEAM>
 __device__ bool team_chol(T *A, int n, int ld, T *dinv = nullptr) {
-    const int tid = threadIdx.x;
+    const int tid = team_tid<TEAM>();
     int r0, c0;
     tri_index(tid, r0, c0);
     bool ok = true;
@@ -190,20 +206,20 @@ __device__ bool team_chol(T *A, int n, int ld, T *dinv = nullptr) {
         if (!finite_pos(d)) { ok = false; d = T(1); }
         T l, il;
         pivot(d, l, il);
-        team_sync();   // everyone has read A[k,k]
+        team_sync<TEAM>();   // everyone has read A[k,k]
         if (tid == 0) {
             A[k + k * ld] = l;
             if (dinv) dinv[k] = il;
         }
         for (int i = k + 1 + tid; i < n; i += TEAM) A[i + k * ld] *= il;
         for (int i = tid; i < k; i += TEAM) A[i + k * ld] = T(0);   // upper part of column k
-        team_sync();
+        team_sync<TEAM>();
         const int m = n - k - 1;                 // trailing size
         for (int r = r0, c = c0; r < m; tri_advance(r, c, TEAM)) {
             const int rr = r + k + 1, cc = c + k + 1;
             A[rr + cc * ld] = fma(-A[rr + k * ld], A[cc + k * ld], A[rr + cc * ld]);
         }
-        team_sync();
+        team_sync<TEAM>();
     }
     return ok;
 }
@@ -212,20 +228,20 @@ __device__ bool team_chol(T *A, int n, int ld, T *dinv = nullptr) {
 // (X L^T = Y).  One thread per row.  dinv (optional) holds 1/L_jj.
 template <typename T, int TEAM>
 __device__ void team_trsm_rlt(T *X, int m, int n, int ldx, const T *L, int ldl, const T *dinv = nullptr) {
-    for (int r = threadIdx.x; r < m; r += TEAM) {
+    for (int r = team_tid<TEAM>(); r < m; r += TEAM) {
         for (int j = 0; j < n; ++j) {
             T s = X[r + j * ldx];
             for (int t = 0; t < j; ++t) s = fma(-X[r + t * ldx], L[j + t * ldl], s);
             X[r + j * ldx] = dinv ? s * dinv[j] : s / L[j + j * ldl];
         }
     }
-    team_sync();
+    team_sync<TEAM>();
 }
 
 // Tinv (n x n, ldt) := L^{-1} for lower L (n x n, ldl); one thread per column.
 template <typename T, int TEAM>
 __device__ void team_trtri_lower(T *Tinv, int ldt, const T *L, int ldl, int n, const T *dinv = nullptr) {
-    for (int c = threadIdx.x; c < n; c += TEAM) {
+    for (int c = team_tid<TEAM>(); c < n; c += TEAM) {
         for (int i = 0; i < c; ++i) Tinv[i + c * ldt] = T(0);
         for (int i = c; i < n; ++i) {
             T s = (i == c) ? T(1) : T(0);
@@ -233,7 +249,7 @@ __device__ void team_trtri_lower(T *Tinv, int ldt, const T *L, int ldl, int n, c
             Tinv[i + c * ldt] = dinv ? s * dinv[i] : s / L[i + i * ldl];
         }
     }
-    team_sync();
+    team_sync<TEAM>();
 }
 
 // C (m x n, ldc) (op)= A (m x k, lda) * B (k x n, ldb).  Mode: 0 assign, 1 add, -1 subtract.
@@ -241,7 +257,7 @@ template <typename T, int TEAM>
 __device__ void team_gemm_nn(T *C, int ldc, const T *A, int lda, const T *B, int ldb, int m, int n, int k,
                              int mode) {
     int r, c;
-    rect_start(threadIdx.x, m, r, c);
+    rect_start(team_tid<TEAM>(), m, r, c);
     for (; c < n; rect_advance(r, c, m, TEAM)) {
         T s = mode == 0 ? T(0) : C[r + c * ldc];
         const T *a = A + r, *b = B + c * ldb;
@@ -254,7 +270,7 @@ __device__ void team_gemm_nn(T *C, int ldc, const T *A, int lda, const T *B, int
         }
         C[r + c * ldc] = s;
     }
-    team_sync();
+    team_sync<TEAM>();
 }
 
 // C (m x n) (op)= A (m x k) * B^T (B is n x k, ldb).
@@ -262,7 +278,7 @@ template <typename T, int TEAM>
 __device__ void team_gemm_nt(T *C, int ldc, const T *A, int lda, const T *B, int ldb, int m, int n, int k,
                              int mode) {
     int r, c;
-    rect_start(threadIdx.x, m, r, c);
+    rect_start(team_tid<TEAM>(), m, r, c);
     for (; c < n; rect_advance(r, c, m, TEAM)) {
         T s = mode == 0 ? T(0) : C[r + c * ldc];
         const T *a = A + r, *b = B + c;
@@ -275,14 +291,14 @@ __device__ void team_gemm_nt(T *C, int ldc, const T *A, int lda, const T *B, int
         }
         C[r + c * ldc] = s;
     }
-    team_sync();
+    team_sync<TEAM>();
 }
 
 // Lower triangle of C (n x n) (op)= A A^T, A is n x k.
 template <typename T, typename TC, int TEAM>
 __device__ void team_syrk_lower(TC *C, int ldc, const T *A, int lda, int n, int k, int mode) {
     int r, c;
-    tri_index(threadIdx.x, r, c);
+    tri_index(team_tid<TEAM>(), r, c);
     for (; r < n; tri_advance(r, c, TEAM)) {
         T s = T(0);
         const T *a = A + r, *b = A + c;
@@ -291,18 +307,18 @@ __device__ void team_syrk_lower(TC *C, int ldc, const T *A, int lda, int n, int 
         TC *o = C + r + c * ldc;
         *o = mode == 0 ? (TC)s : (mode > 0 ? *o + (TC)s : *o - (TC)s);
     }
-    team_sync();
+    team_sync<TEAM>();
 }
 
 // Mirror the lower triangle of an n x n matrix into its upper triangle.
 template <typename T, int TEAM>
 __device__ void team_symmetrize(T *C, int ldc, int n) {
     const int cnt = n * n;
-    for (int e = threadIdx.x; e < cnt; e += TEAM) {
+    for (int e = team_tid<TEAM>(); e < cnt; e += TEAM) {
         const int r = e % n, c = e / n;
         if (c > r) C[r + c * ldc] = C[c + r * ldc];
     }
-    team_sync();
+    team_sync<TEAM>();
 }
 
 // ---------------------------------------------------------------------------
@@ -327,6 +343,7 @@ struct FactorArgs {
     bool stage_in_smem;             // copy each stage's raw blocks to shared memory (cp.async)
     bool need_G2;                   // some item propagates A^cl (P > 1): second [B^ A^] buffer
     const int *skip;                // optional per-instance flag: nonzero = do not factor this instance
+    unsigned smem_team;             // shared-memory bytes per team (set by the launcher)
 };
 
 struct SolveArgs {

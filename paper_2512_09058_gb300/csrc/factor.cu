@@ -67,11 +67,11 @@ template <int TEAM>
 __device__ void stage_zero_fill(double *buf, const StageLayout &L, const Data &d, const Inst &in, int s) {
     const int nx = in.nx, nu = in.nu;
     if (s == 0 || !d.S)
-        for (int e = threadIdx.x; e < nu * nx; e += TEAM) buf[L.oS + e] = 0.0;
+        for (int e = team_tid<TEAM>(); e < nu * nx; e += TEAM) buf[L.oS + e] = 0.0;
     if (!d.Sig)
-        for (int e = threadIdx.x; e < nu + nx; e += TEAM) buf[L.oSu + e] = 0.0;
+        for (int e = team_tid<TEAM>(); e < nu + nx; e += TEAM) buf[L.oSu + e] = 0.0;
     if (s == 0)
-        for (int e = threadIdx.x; e < nx * nx; e += TEAM) buf[L.oA + e] = 0.0;
+        for (int e = team_tid<TEAM>(); e < nx * nx; e += TEAM) buf[L.oA + e] = 0.0;
 }
 
 // Where the blocks of one stage are read from: the shared-memory copy, or
@@ -110,16 +110,16 @@ __device__ __forceinline__ double stage_H(const StageSrc &src, int nu, int nx, i
 template <typename T, int TEAM>
 __device__ void fill_BA(T *BA, int ld, const StageSrc &src, int nx, int nu) {
     int r, c;
-    rect_start(threadIdx.x, nx, r, c);
+    rect_start(team_tid<TEAM>(), nx, r, c);
     for (; c < nu; rect_advance(r, c, nx, TEAM)) BA[r + c * ld] = (T)src.B[r + c * nx];
-    rect_start(threadIdx.x, nx, r, c);
+    rect_start(team_tid<TEAM>(), nx, r, c);
     for (; c < nx; rect_advance(r, c, nx, TEAM)) BA[r + (nu + c) * ld] = src.A ? (T)src.A[r + c * nx] : T(0);
 }
 
 template <typename T, int TEAM>
 __device__ void store_block(T *dst, const T *src, int rows, int cols, int ld) {
     int r, c;
-    rect_start(threadIdx.x, rows, r, c);
+    rect_start(team_tid<TEAM>(), rows, r, c);
     for (; c < cols; rect_advance(r, c, rows, TEAM)) dst[r + c * rows] = src[r + c * ld];
 }
 
@@ -128,14 +128,14 @@ template <typename T, int TEAM>
 __device__ void store_block_f32(float *dst, const T *src, int rows, int cols, int ld) {
     if (!dst) return;
     int r, c;
-    rect_start(threadIdx.x, rows, r, c);
+    rect_start(team_tid<TEAM>(), rows, r, c);
     for (; c < cols; rect_advance(r, c, rows, TEAM)) dst[r + c * rows] = (float)src[r + c * ld];
 }
 
 template <typename T, int TEAM>
 __device__ void store_block_f64(double *dst, const T *src, int rows, int cols, int ld) {
     int r, c;
-    rect_start(threadIdx.x, rows, r, c);
+    rect_start(team_tid<TEAM>(), rows, r, c);
     for (; c < cols; rect_advance(r, c, rows, TEAM)) dst[r + c * rows] = (double)src[r + c * ld];
 }
 
@@ -336,9 +336,15 @@ __device__ __forceinline__ bool stages_in_registers(float *H, int ldH, float *Vs
 }
 
 template <typename T, int TEAM, int NXC, int NUC>
-__global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+__global__ void __launch_bounds__(TEAM < 32 ? 32 : TEAM) k_factor_segments(FactorArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_all[];
+    // TEAM < 32: 32 / TEAM teams per CTA (one warp), each with its own item and
+    // its own a.smem_team bytes of shared memory
+    constexpr int TPC = TEAM < 32 ? 32 / TEAM : 1;
+    const int team = TEAM < 32 ? (int)threadIdx.x / TEAM : 0;
+    const int tid = team_tid<TEAM>();
+    unsigned char *smem_raw = smem_all + (size_t)team * a.smem_team;
+    for (int item = blockIdx.x * TPC + team; item < a.n_items; item += gridDim.x * TPC) {
         const Item wi = a.items[item];
         if (a.skip && a.skip[wi.inst]) continue;
         const Inst in = a.inst[wi.inst];
@@ -385,15 +391,15 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
         } else {
             src = stage_src_global(a.data, in, s);
         }
-        for (int e = threadIdx.x; e < nx * nx; e += TEAM) Mf[e] = 0.0;
-        team_sync();
+        for (int e = tid; e < nx * nx; e += TEAM) Mf[e] = 0.0;
+        team_sync<TEAM>();
         {
             int r, q;
-            tri_index(threadIdx.x, r, q);
+            tri_index(tid, r, q);
             for (; r < nux; tri_advance(r, q, TEAM)) H[r + q * ldH] = (T)stage_H(src, nu, nx, r, q);
             fill_BA<T, TEAM>(G, ldG, src, nx, nu);
         }
-        team_sync();
+        team_sync<TEAM>();
 
         bool ok = true;
         for (int t = 0; t < len; ++t) {
@@ -421,19 +427,19 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
             // L^{R-1} (strictly lower part) into the free upper triangle of the R block,
             // transposed: entry (k, i), k < i, holds (L^{R-1})_{ik}.  The solve sweeps
             // then apply L^{R-1} and L^{R-T} as parallel matrix-vector products.
-            for (int cc = threadIdx.x; cc < nu; cc += TEAM)
+            for (int cc = tid; cc < nu; cc += TEAM)
                 for (int i = cc + 1; i < nu; ++i) {
                     T acc = T(0);
                     for (int k = cc; k < i; ++k)
                         acc = fma(-H[i + k * ldH], k == cc ? dinv[cc] : H[cc + k * ldH], acc);
                     H[cc + i * ldH] = acc * dinv[i];
                 }
-            team_sync();
+            team_sync<TEAM>();
             store_block<T, TEAM>(Lg + (long long)s * nux * nux, H, nux, nux, ldH);
-            for (int i = threadIdx.x; i < nux; i += TEAM) DIg[(long long)s * nux + i] = dinv[i];
+            for (int i = tid; i < nux; i += TEAM) DIg[(long long)s * nux + i] = dinv[i];
             if (copy32) {
                 store_block_f32<T, TEAM>(a.Lc + in.oL + (long long)s * nux * nux, H, nux, nux, ldH);
-                for (int i = threadIdx.x; i < nux; i += TEAM) a.DIc[in.oDI + (long long)s * nux + i] = (float)dinv[i];
+                for (int i = tid; i < nux; i += TEAM) a.DIc[in.oDI + (long long)s * nux + i] = (float)dinv[i];
             }
             if (hasG) {
                 // L^B = B^ L^{R-T}
@@ -452,7 +458,7 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 if (staged) {
                     stage_zero_fill<TEAM>(buf, SL, a.data, in, s2);
                     cp_async_wait_all();
-                    team_sync();   // every thread's copies have landed
+                    team_sync<TEAM>();   // every thread's copies have landed
                     src = stage_src_smem(buf, SL);
                 } else {
                     src = stage_src_global(a.data, in, s2);
@@ -465,7 +471,7 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                                                  nx, nux, nx);
                 } else {
                     fill_BA<T, TEAM>(BAc, ldBA, src, nx, nu);
-                    team_sync();
+                    team_sync<TEAM>();
                     BA = BAc;
                     // float32 copy for the solve sweeps (no conversions there)
                     if (a.BAf)
@@ -476,7 +482,7 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 const T *LQ = H + nu + nu * ldH;
                 {
                     int aa, j;
-                    rect_start(threadIdx.x, nux, aa, j);
+                    rect_start(tid, nux, aa, j);
                     for (; j < nx; rect_advance(aa, j, nux, TEAM)) {
                         const T *ba = BA + aa * ldBA, *lq = LQ + j * ldH;
                         T acc = T(0);
@@ -489,12 +495,12 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                     // [B^ A^]_{s2} = A^cl [B A]_{s2}
                     team_gemm_nn<T, TEAM>(G2, ldG, G + ldG * nu, ldG, BA, ldBA, nx, nux, nx, 0);
                 } else {
-                    team_sync();
+                    team_sync<TEAM>();
                 }
                 // H^_{s2} = H_{s2} + V V^T  (lower triangle, straight from the raw record)
                 {
                     int r, q;
-                    tri_index(threadIdx.x, r, q);
+                    tri_index(tid, r, q);
                     for (; r < nux; tri_advance(r, q, TEAM)) {
                         T acc = (T)stage_H(src, nu, nx, r, q);
                         const T *vr = V + r, *vq = V + q;
@@ -503,7 +509,7 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                         H[r + q * ldH] = acc;
                     }
                 }
-                team_sync();
+                team_sync<TEAM>();
                 if (a.need_G2) {
                     T *tmp = G; G = G2; G2 = tmp;
                 }
@@ -526,7 +532,7 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 {
                     T *Lq = Lg + (long long)s * nux * nux + nu + nu * nux;
                     int i, cc;
-                    rect_start(threadIdx.x, nx, i, cc);
+                    rect_start(tid, nx, i, cc);
                     for (; cc < nx; rect_advance(i, cc, nx, TEAM))
                         if (i > cc) {
                             Lq[cc + i * nux] = Ti[i + cc * ldT];
@@ -538,7 +544,7 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                 T *Mb = H;
                 {
                     int i, j;
-                    rect_start(threadIdx.x, nx, i, j);
+                    rect_start(tid, nx, i, j);
                     for (; j < nx; rect_advance(i, j, nx, TEAM)) {
                         const int k0 = i > j ? i : j;
                         T acc = T(0);
@@ -546,38 +552,38 @@ __global__ void __launch_bounds__(TEAM) k_factor_segments(FactorArgs a) {
                         Mb[i + j * ldT] = acc;
                     }
                 }
-                team_sync();
+                team_sync<TEAM>();
                 const int cb = (c - 1 + P) % P;
                 store_block_f64<T, TEAM>(a.Mb + in.oBlk + (long long)cb * nx * nx, Mb, nx, nx, ldT);
                 team_symmetrize<double, TEAM>(Mf, nx, nx);
                 if (P == 1) {
                     // single coupling block: M = M_fwd + M_bwd, factor it (float64)
                     int i, j;
-                    rect_start(threadIdx.x, nx, i, j);
+                    rect_start(tid, nx, i, j);
                     for (; j < nx; rect_advance(i, j, nx, TEAM)) Mf[i + j * nx] += (double)Mb[i + j * ldT];
-                    team_sync();
+                    team_sync<TEAM>();
                     ok &= team_chol<double, TEAM>(Mf, nx, nx);
                 }
                 double *dst = a.Mf + in.oBlk + (long long)c * nx * nx;
-                for (int e = threadIdx.x; e < nx * nx; e += TEAM) dst[e] = Mf[e];
+                for (int e = tid; e < nx * nx; e += TEAM) dst[e] = Mf[e];
                 if (propagate) {
                     // K = -L^A Tinv (row lambda^{b_c}, column lambda^{b_{c-1}}), reusing the H tile
-                    team_sync();   // M_bwd has been read
+                    team_sync<TEAM>();   // M_bwd has been read
                     T *Kb = H;
                     int i, j;
-                    rect_start(threadIdx.x, nx, i, j);
+                    rect_start(tid, nx, i, j);
                     for (; j < nx; rect_advance(i, j, nx, TEAM)) {
                         T acc = T(0);
                         for (int k = j; k < nx; ++k) acc = fma(LA[i + k * ldG], Ti[k + j * ldT], acc);
                         Kb[i + j * ldT] = -acc;
                     }
-                    team_sync();
+                    team_sync<TEAM>();
                     store_block_f64<T, TEAM>(a.Kc + in.oBlk + (long long)c * nx * nx, Kb, nx, nx, ldT);
                 }
             }
         }
-        if (!ok && threadIdx.x == 0) atomicCAS(a.status + wi.inst, 0, ST_NOT_PD);
-        team_sync();
+        if (!ok && tid == 0) atomicCAS(a.status + wi.inst, 0, ST_NOT_PD);
+        team_sync<TEAM>();
     }
 }
 
@@ -598,16 +604,21 @@ size_t factor_smem_bytes(bool fp64, int nx, int nu, bool staged, bool need_G2) {
 }
 
 template <typename T, int TEAM, int NXC = 0, int NUC = 0>
-static cudaError_t launch_factor_t(size_t smem, const FactorArgs &a, cudaStream_t st) {
+static cudaError_t launch_factor_t(size_t smem, const FactorArgs &a0, cudaStream_t st) {
+    constexpr int TPC = TEAM < 32 ? 32 / TEAM : 1;
+    FactorArgs a = a0;
+    a.smem_team = (unsigned)((smem + 15) / 16 * 16);
+    const size_t total = (size_t)a.smem_team * TPC;
     auto k = k_factor_segments<T, TEAM, NXC, NUC>;
-    cudaError_t e = ensure_smem((const void *)k, smem);
+    cudaError_t e = ensure_smem((const void *)k, total);
     if (e != cudaSuccess) return e;
-    k<<<a.n_items, TEAM, smem, st>>>(a);
+    k<<<(a.n_items + TPC - 1) / TPC, TEAM < 32 ? 32 : TEAM, total, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_factor_segments(bool fp64, int team, int shape, size_t smem, const FactorArgs &a, cudaStream_t st) {
     if (a.n_items == 0) return cudaSuccess;
+    if (team == 16) return fp64 ? launch_factor_t<double, 16>(smem, a, st) : launch_factor_t<float, 16>(smem, a, st);
     if (fp64) {
         if (team == 32) return launch_factor_t<double, 32>(smem, a, st);
         if (team == 64) return launch_factor_t<double, 64>(smem, a, st);
