@@ -62,13 +62,13 @@ NCU_TRAFFIC = {("batch1024_n64_nx12_nu4", "fp64"): 217.7e6 + 110.1e6,
 # tuned by timing (cyq_autotune) before the timed region
 WORKLOADS = {
     "batch1024_n64_nx12_nu4": dict(methods=["fp64_ir32", "fp64_refine", "fp64", "fp32_refine"], graph=False,
-                                   adjoint=False, tune_segments=False),
+                                   adjoint=False, tune_segments=True),
     "single_n32_nx8_nu4": dict(methods=["fp64", "fp64_refine"], graph=True, adjoint=False, tune_segments=True),
     "long_n4096_nx32_nu16": dict(methods=["fp32_refine", "fp64", "fp64_refine"], graph=False, adjoint=False,
                                  tune_segments=True),
     "uneven4096": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=True, adjoint=False,
                        tune_segments=True),
-    "adjoint512_n128_nx24_nu8": dict(methods=["fp64_refine"], graph=False, adjoint=True, tune_segments=False),
+    "adjoint512_n128_nx24_nu8": dict(methods=["fp64_refine"], graph=False, adjoint=True, tune_segments=True),
 }
 
 
