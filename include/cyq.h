@@ -197,6 +197,18 @@ cyq_status cyq_get_stats(cyq_handle h, cyq_stats *out, cyq_stream stream);
 int64_t cyq_kkt_size(cyq_handle h);
 /* Segments chosen for each instance (host array [batch]). */
 cyq_status cyq_get_segments(cyq_handle h, int32_t *P_out);
+/*
+ * Diagnostics: the stored factor of one stage (instance, stage s in 0..N-1),
+ * copied to the host as (nu+nx) x (nu+nx) float64, column-major.  Its lower
+ * triangle is the Cholesky factor [L^R 0; L^S L^Q] of the stage matrix H^_s of
+ * Alg. fact-mod-riccati (stage 0 pairs u^0 with x^N); its strict upper triangle
+ * holds L^{R-1} (and, at the first stage of a segment, L^{Q-1}), transposed.
+ * Within segment 0, L^Q_s L^Q_s^T is the Riccati cost-to-go matrix P_s of
+ * x^s (P_N for stage 0).  Synchronises the device.  Errors: INVALID_ARG,
+ * NO_FACTOR, CUDA.
+ */
+cyq_status cyq_get_stage_factor(cyq_handle h, int32_t instance, int32_t stage, double *L_out);
+
 /* Number of kernels launched by the last cyq_factor and cyq_solve calls. */
 int64_t cyq_last_launch_count(cyq_handle h);
 

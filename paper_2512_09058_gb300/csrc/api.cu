@@ -623,6 +623,27 @@ void cyq_destroy(cyq_handle h) {
 
 int64_t cyq_kkt_size(cyq_handle h) { return h ? h->kkt : -1; }
 
+cyq_status cyq_get_stage_factor(cyq_handle h, int32_t instance, int32_t stage, double *L_out) {
+    if (!h || !L_out || instance < 0 || instance >= h->batch) return CYQ_ERR_INVALID_ARG;
+    if (!h->factored) return CYQ_ERR_NO_FACTOR;
+    const Inst &in = h->inst[instance];
+    if (stage < 0 || stage >= in.N) return CYQ_ERR_INVALID_ARG;
+    DeviceGuard guard(h->device);
+    const size_t nux = (size_t)in.nx + in.nu, n = nux * nux;
+    const long long off = in.oL + (long long)stage * (long long)n;
+    CYQ_CUDA(cudaDeviceSynchronize());
+    if (h->fac.fp64) {
+        CYQ_CUDA(cudaMemcpy(L_out, static_cast<const double *>(h->fac.L) + off, n * sizeof(double),
+                            cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> tmp(n);
+        CYQ_CUDA(cudaMemcpy(tmp.data(), static_cast<const float *>(h->fac.L) + off, n * sizeof(float),
+                            cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) L_out[i] = tmp[i];
+    }
+    return CYQ_OK;
+}
+
 cyq_status cyq_get_segments(cyq_handle h, int32_t *P_out) {
     if (!h || !P_out) return CYQ_ERR_INVALID_ARG;
     for (int i = 0; i < h->batch; ++i) P_out[i] = h->inst[i].P;

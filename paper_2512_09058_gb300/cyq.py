@@ -27,7 +27,7 @@ EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rh
            "cyq_solve_adjoint", "cyq_get_instance_status", "cyq_get_stats", "cyq_kkt_size",
            "cyq_get_segments", "cyq_last_launch_count", "cyq_status_string", "cyq_last_error",
            "cyq_factor_solve_noalloc", "cyq_autotune", "cyq_get_launch_shapes", "cyq_tune_segments",
-           "cyq_set_launch_shapes"]
+           "cyq_set_launch_shapes", "cyq_get_stage_factor"]
 
 
 class CyqError(RuntimeError):
@@ -87,9 +87,11 @@ def load(path: str = LIB_PATH):
     L.cyq_get_launch_shapes.argtypes = [vp, pi32, pi32, pi32, i32]
     L.cyq_tune_segments.argtypes = [ctypes.POINTER(cyq_desc)] + [vp] * 6 + [vp, vp, i32, i32, vp, pi32]
     L.cyq_set_launch_shapes.argtypes = [vp, pi32, pi32, i32]
+    L.cyq_get_stage_factor.argtypes = [vp, i32, i32, ctypes.POINTER(d)]
     for name in ["cyq_create", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual", "cyq_solve_adjoint",
                  "cyq_get_instance_status", "cyq_get_stats", "cyq_get_segments", "cyq_autotune",
-                 "cyq_get_launch_shapes", "cyq_tune_segments", "cyq_set_launch_shapes"]:
+                 "cyq_get_launch_shapes", "cyq_tune_segments", "cyq_set_launch_shapes",
+                 "cyq_get_stage_factor"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -199,6 +201,15 @@ class Solver:
         _check(_lib.cyq_autotune(self._h, _ptr(Q), _ptr(R), _ptr(S), _ptr(A), _ptr(B), _ptr(Sigma), _ptr(b),
                                  _ptr(z), nrhs, reps, _stream(stream)))
         self.factor_version += 1
+
+    def stage_factor(self, instance: int, stage: int) -> np.ndarray:
+        """Stored (nu+nx)^2 factor of one stage as a float64 matrix (lower: the Cholesky
+        factor of H^_s; strict upper: the stored triangular inverses, transposed)."""
+        n = int(self.nx[instance] + self.nu[instance])
+        out = np.zeros(n * n)
+        _check(_lib.cyq_get_stage_factor(self._h, instance, stage,
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out.reshape(n, n).T.copy()
 
     def launch_shapes(self, nrhs: int = 1) -> dict:
         i32p = ctypes.POINTER(ctypes.c_int32)

@@ -87,3 +87,18 @@ def test_adjoint_matches_finite_differences_of_gpu_solve():
             arr[i] = old
             fd = (lp - lm) / (2 * h)
             assert abs(fd - G[key][i]) <= 1e-6 * max(1.0, abs(fd)), (name, i, fd, G[key][i])
+
+
+def test_adjoint_vector_is_the_solve_of_the_loss_gradient():
+    """K is symmetric, so w = K^{-1} dL/dz is exactly a solve with dL/dz as the
+    right-hand side (the same kernels on the same factor)."""
+    torch, cyq = require_gpu()
+    batch = ragged_batch(53, [(9, 3, 2), (14, 5, 2)], sigma=(1e-2, 1e2))
+    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision="fp64", P=2, it_max=0)
+    data, rhs = cyq.to_device(batch)
+    s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
+    g = torch.from_numpy(np.random.default_rng(5).standard_normal(s.kkt_size)).cuda()
+    z = s.solve(g.clone())
+    w = s.solve_adjoint(rhs[0][3], z, g, want=("w", "dA"))["w"]
+    torch.cuda.synchronize()
+    assert torch.equal(w, s.solve(g))

@@ -149,3 +149,18 @@ def test_empty_right_hand_side_gives_zero():
     for prec in ("fp64", "fp32_refine"):
         z, _, _, _ = gpu_solve(batch, precision=prec, P=2, b_host=np.zeros((1, batch.kkt_size)))
         assert np.array_equal(z, np.zeros_like(z))
+
+
+@pytest.mark.parametrize("P", [2, 4])
+def test_padded_and_uneven_segments_agree(P):
+    """Equal segments by padding the horizon to a multiple of P (Sec. 4.6) and
+    uneven segments of the unpadded horizon give the same solution."""
+    from test_oracle_pins import pad_instance
+    base = ragged_batch(52, [(10, 4, 2), (13, 3, 3)], sigma=(1e-2, 1e2))
+    padded = inputs.make_batch(None, instances=[pad_instance(x, (-x.N) % P) for x in base.instances])
+    z0, _, _, _ = gpu_solve(base, P=P)
+    z1, _, _, _ = gpu_solve(padded, P=P)
+    for x, xp, a, b in zip(base.instances, padded.instances, split_instances(base, z0[0]),
+                           split_instances(padded, z1[0])):
+        assert rel_err(b[:x.kkt_size], a) <= 1e-11
+        assert np.linalg.norm(b[x.kkt_size:]) <= 1e-11 * np.linalg.norm(a)

@@ -261,3 +261,42 @@ def test_adjoint_matches_central_finite_differences():
             checks.append((name, fd(arr, a, bb), expect))
     for name, f, gr in checks:
         assert abs(f - gr) <= 1e-6 * max(1.0, abs(gr)), (name, f, gr)
+
+
+def pad_instance(inst, extra):
+    """The OCP with `extra` stages appended after the terminal stage: R = I,
+    Q = I, S = A = B = 0, no Sigma, zero right-hand side (paper Sec. 4.6).  The
+    dynamics after x^N are x^{k+1} = 0, so the original unknowns keep their
+    values and every padded unknown is zero."""
+    N, nx, nu = inst.N, inst.nx, inst.nu
+    M = N + extra
+    eye = lambda n: np.eye(n).T.reshape(-1)
+    Q = np.concatenate([inst.Q] + [eye(nx)] * extra)
+    R = np.concatenate([inst.R] + [eye(nu)] * extra)
+    S = np.concatenate([inst.S] + [np.zeros(nu * nx)] * extra)
+    A = np.concatenate([inst.A] + [np.zeros(nx * nx)] * extra)
+    B = np.concatenate([inst.B] + [np.zeros(nx * nu)] * extra)
+    Sigma = None
+    if inst.Sigma is not None:
+        Sigma = np.concatenate([inst.Sigma] + [np.zeros(nu + nx)] * extra)
+    rhs = []
+    for (q, r, c, x0) in inst.rhs:
+        rhs.append((np.concatenate([q, np.zeros(extra * nx)]), np.concatenate([r, np.zeros(extra * nu)]),
+                    np.concatenate([c, np.zeros(extra * nx)]), x0))
+    return inputs.OCPInstance(N=M, nx=nx, nu=nu, Q=Q, R=R, S=S, A=A, B=B, Sigma=Sigma, rhs=rhs)
+
+
+def test_padding_stages_leave_the_solution_unchanged():
+    """Padding reading (Sec. 4.6): stages appended after the terminal stage with
+    identity costs, zero dynamics and zero right-hand side do not change the
+    solution, and their own unknowns are zero."""
+    for seed, (N, nx, nu, extra) in enumerate([(5, 3, 2, 3), (7, 2, 1, 1), (4, 4, 3, 4)]):
+        inst = _small(400 + seed, N, nx, nu, sigma=(1e-2, 1e2))
+        pad = pad_instance(inst, extra)
+        q, r, c, x0 = inst.rhs[0]
+        z = oracle.riccati_solve(inst, oracle.build_rhs(inst, q, r, c, x0))
+        qp, rp, cp, x0p = pad.rhs[0]
+        zp = oracle.riccati_solve(pad, oracle.build_rhs(pad, qp, rp, cp, x0p))
+        n = inst.kkt_size
+        assert np.linalg.norm(zp[:n] - z) <= 1e-12 * np.linalg.norm(z)
+        assert np.linalg.norm(zp[n:]) <= 1e-12 * np.linalg.norm(z)
