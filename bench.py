@@ -240,6 +240,41 @@ def time_oracle(batch, nrhs, budget_s=2.0, max_instances=None):
     return done / el, done, el
 
 
+def _oracle_worker(job):
+    """One host core: regenerate instances `indices` of workload `name` from the
+    seeded generator (untimed) and solve them with the oracle until `budget_s`
+    seconds of solving; returns (count, seconds)."""
+    name, indices, nrhs, budget_s = job
+    import oracle   # CPU-baseline / reference leg only
+    done, el = 0, 0.0
+    for i in indices:
+        x = inputs.make_batch(name, [i]).instances[0]
+        b = np.stack([oracle.build_rhs(x, *x.rhs[j]) for j in range(nrhs)])
+        t = time.perf_counter()
+        oracle.riccati_solve(x, b)
+        el += time.perf_counter() - t
+        done += 1
+        if el >= budget_s:
+            break
+    return done, el
+
+
+def time_oracle_all_cores(name, n_instances, nrhs, budget_s=2.0, workers=None):
+    """The oracle on every host core at once (a spawn process pool, one process
+    per core, each on its own instances of the workload, round-robin); returns
+    (OCP/s summed over the concurrent processes, instances solved, cores)."""
+    import concurrent.futures
+    import multiprocessing
+    workers = workers or os.cpu_count() or 1
+    jobs = [(name, list(range(w, n_instances, workers)), nrhs, budget_s) for w in range(workers)]
+    jobs = [j for j in jobs if j[1]]
+    ctx = multiprocessing.get_context("spawn")
+    with concurrent.futures.ProcessPoolExecutor(max_workers=len(jobs), mp_context=ctx) as ex:
+        res = list(ex.map(_oracle_worker, jobs))
+    rate = sum(d / e for d, e in res if e > 0)
+    return rate, sum(d for d, _ in res), len(jobs)
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -419,29 +454,32 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        batch = inputs.make_batch(args.workload)
-        nrhs = len(batch.rhs)
+        n = cfg["batch"]
+        nrhs = int(cfg["nrhs"])
+        dims = inputs.config_dims(cfg, batch=n)
         for _ in range(args.warmup):
-            time_oracle(batch, nrhs, budget_s=0.05)
+            time_oracle_all_cores(args.workload, n, nrhs, budget_s=0.05)
         rates, samples = [], []
+        cores = 1
         for _ in range(args.steps):
-            r, d, e = time_oracle(batch, nrhs, budget_s=1.0)
+            r, d, cores = time_oracle_all_cores(args.workload, n, nrhs, budget_s=1.0)
             rates.append(r)
             samples.append(d)
         value = float(np.mean(rates))
-        per_stage = float(np.mean(batch.N))
-        ms = batch.size / value * 1e3
-        sample = ("per step the first OCPs of the workload in order for ~1 s of one host core "
-                  "(%d OCPs x %d rhs per step on average)" % (int(np.mean(samples)), nrhs))
+        per_stage = float(np.mean(dims[0]))
+        ms = n / value * 1e3
+        sample = ("per step, every host core solves its own OCPs of the workload (round-robin) for ~1 s "
+                  "of solving (%d OCPs x %d rhs per step on average over %d cores)"
+                  % (int(np.mean(samples)), nrhs, cores))
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "ns_per_stage": 1e9 / (value * per_stage),
-            "config": {"workload": args.workload, "global_batch": batch.size, "stages_per_ocp": nominal("N"),
+            "config": {"workload": args.workload, "global_batch": n, "stages_per_ocp": nominal("N"),
                        "nx": nominal("nx"), "nu": nominal("nu"), "nrhs": nrhs,
                        "method": "cpu oracle (textbook Riccati, FP64)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return 0
 
@@ -502,10 +540,14 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, done, el = time_oracle(batch, nrhs, budget_s=3.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first %d OCPs of the workload x %d rhs (%.1f s of one host core), scaled to OCP/s"
-                         % (done, nrhs, el)}
+        rate1, done1, el1 = time_oracle(batch, nrhs, budget_s=3.0)
+        rate, done, cores = time_oracle_all_cores(args.workload, batch.size, nrhs, budget_s=2.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "every host core (spawn process pool) solves its own OCPs of the workload, round-robin, "
+                         "for ~2 s of solving: %d OCPs x %d rhs in total; rates summed over the concurrent "
+                         "processes" % (done, nrhs),
+               "value_1core": rate1,
+               "sample_1core": "first %d OCPs of the workload x %d rhs (%.1f s of one host core)" % (done1, nrhs, el1)}
 
     variants = {}
     for m, r in results.items():
