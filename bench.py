@@ -69,6 +69,8 @@ WORKLOADS = {
     "uneven4096": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=True, adjoint=False,
                        tune_segments=True),
     "adjoint512_n128_nx24_nu8": dict(methods=["fp64_refine"], graph=False, adjoint=True, tune_segments=True),
+    "massspring150_M18_N96": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=True, adjoint=False,
+                                  tune_segments=True),
 }
 
 

@@ -154,7 +154,62 @@ CONFIGS = {
     # 512 OCPs, N=128, nx=24, nu=8, S=0, no Sigma (differentiation workload)
     "adjoint512_n128_nx24_nu8": dict(batch=512, N=128, nx=24, nu=8, S=False, sigma=None,
                                      nrhs=1, QN_equals_Q0=False, seed=4),
+    # the paper's mass-spring MPC (Sec. 8.1): M = 18 masses (nx = 36, nu = 9), N = 96,
+    # 150 initial states; Sigma (ALM penalties) on the boxed coordinates only
+    "massspring150_M18_N96": dict(kind="mass_spring", batch=150, M=18, N=96, nx=36, nu=9, S=False,
+                                  sigma=(1e-2, 1e4), nrhs=1, QN_equals_Q0=True, seed=5),
 }
+
+
+def mass_spring_dynamics(M: int, Ts: float):
+    """Zero-order-hold discretization (A, B) of the mass-spring chain of Sec. 8.1:
+    M unit masses joined by unit springs, the outer ones to walls at distance
+    zero, no friction; actuators between pairs of masses in the 6 x 3 pattern W,
+    repeated M/6 times.  The continuous model x' = A_c x + B_c u is integrated
+    over one sampling interval with u held constant, through the exponential of
+    the augmented matrix [[A_c, B_c], [0, 0]] Ts (scipy's scaling-and-squaring
+    Pade routine)."""
+    import scipy.linalg
+    if M % 6:
+        raise ValueError("M must be a multiple of 6")
+    nx, nu = 2 * M, M // 2
+    V = -2.0 * np.eye(M) + np.eye(M, k=1) + np.eye(M, k=-1)
+    W = np.zeros((6, 3))
+    W[0, 0], W[1, 0] = 1.0, -1.0
+    W[2, 1], W[4, 1] = 1.0, -1.0
+    W[3, 2], W[5, 2] = 1.0, -1.0
+    Ac = np.block([[np.zeros((M, M)), np.eye(M)], [V, np.zeros((M, M))]])
+    Bc = np.vstack([np.zeros((M, nu)), scipy.linalg.block_diag(*([W] * (M // 6)))])
+    aug = np.zeros((nx + nu, nx + nu))
+    aug[:nx, :nx] = Ac
+    aug[:nx, nx:] = Bc
+    E = scipy.linalg.expm(aug * Ts)
+    return E[:nx, :nx].copy(), E[:nx, nx:].copy(), Ac, Bc
+
+
+def _make_mass_spring(cfg, index: int, N: int, nrhs: int, g) -> "OCPInstance":
+    """Instance `index` of a mass-spring config: the paper's dynamics and costs
+    (Q = Q_N = R = I, S = 0, steady state at the origin, so q = r = c = 0),
+    Sigma log-uniform in cfg["sigma"] on the positions and the inputs (the
+    boxed coordinates; velocities have none), initial positions uniform in
+    [-3, 3] and zero velocities."""
+    M = int(cfg["M"])
+    nx, nu = 2 * M, M // 2
+    Ad, Bd, _, _ = mass_spring_dynamics(M, 15.0 / N)
+    A = np.broadcast_to(Ad, (N, nx, nx)).copy()
+    B = np.broadcast_to(Bd, (N, nx, nu)).copy()
+    Q = np.broadcast_to(np.eye(nx), (N + 1, nx, nx)).copy()
+    R = np.broadcast_to(np.eye(nu), (N, nu, nu)).copy()
+    S = np.zeros((N, nu, nx))
+    lo, hi = cfg["sigma"]
+    sig = 10.0 ** g.uniform(np.log10(lo), np.log10(hi), size=(N + 1, nu + nx))
+    sig[:, nu + M:] = 0.0   # velocities are not boxed
+    rhs = []
+    for _ in range(nrhs):
+        x0 = np.concatenate([g.uniform(-3.0, 3.0, size=M), np.zeros(M)])
+        rhs.append((np.zeros((N + 1) * nx), np.zeros(N * nu), np.zeros(N * nx), x0))
+    return OCPInstance(N=N, nx=nx, nu=nu, Q=blocks_to_flat(Q), R=blocks_to_flat(R), S=blocks_to_flat(S),
+                       A=blocks_to_flat(A), B=blocks_to_flat(B), Sigma=sig.reshape(-1), rhs=rhs)
 
 _DIMS_STREAM = 0x5EED_D135
 
@@ -201,6 +256,8 @@ def make_instance(cfg, index: int, *, N: Optional[int] = None, nx: Optional[int]
     nu = dnu if nu is None else int(nu)
     nrhs = cfg["nrhs"] if nrhs is None else nrhs
     g = np.random.Generator(np.random.PCG64([cfg["seed"], 1, index]))
+    if cfg.get("kind") == "mass_spring":
+        return _make_mass_spring(cfg, index, N, nrhs, g)
 
     # A_k: Gaussian scaled to spectral radius 0.95
     G = g.standard_normal((N, nx, nx))

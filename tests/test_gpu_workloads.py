@@ -127,3 +127,21 @@ def test_adjoint_workload_sampled():
                 assert rel_err(G[k][offs[k]:offs[k] + n], ref[k]) <= 1e-9, (i, k)
         for k, n in sizes.items():
             offs[k] += n
+
+
+@pytest.mark.parametrize("precision,it_max", [("fp64", 0), ("fp32_refine", 10)])
+def test_mass_spring_workload_sampled(precision, it_max):
+    """The paper's mass-spring MPC (Sec. 8.1) at M = 18, N = 96, 150 initial states."""
+    batch = inputs.make_batch("massspring150_M18_N96")
+    s, z, b, _, _ = _solve(batch, precision, it_max)
+    assert (s.instance_status() == 0).all()
+    st = s.stats()
+    if it_max:
+        assert st["max_rel_residual"] <= 1e-10
+    zs, bs = split_instances(batch, z[0]), split_instances(batch, b[0])
+    for i in (0, 74, 149):
+        inst = batch.instances[i]
+        zo = oracle.riccati_solve(inst, bs[i])
+        assert rel_err(zs[i], zo) <= 1e-8
+        if it_max:
+            assert oracle.kkt_residual(inst, zs[i], bs[i]) <= eval_gate(inst, zs[i], bs[i])
