@@ -84,6 +84,11 @@ struct cyq_handle_s {
     DevicePtrs mem;
     Inst *d_inst = nullptr;
     int *d_cr_list = nullptr, *d_all_list = nullptr;
+    // coupling solve: level-parallel over instances with P > 1 when they are few and have
+    // many segments (cr_levels), single-CTA per instance otherwise / for P = 1 (p1_list)
+    bool cr_levels = false;
+    std::vector<int> p1_list;
+    int *d_p1_list = nullptr;
     Chunk *d_chunks = nullptr;
     FactorSet fac;                // factor in the handle's precision
     FactorSet fac64;              // float64 factor for precision escalation (float32 mode only)
@@ -230,8 +235,16 @@ cyq_status run_solve(cyq_handle h, const FactorSet &fs, const double *b, double 
     {
         SolveArgs a = solve_args(h, fs, h->groups[0], b, z, nrhs, skip, zacc);
         size_t smem = ((size_t)h->crs_smem1) * (nrhs + 1);
-        CYQ_CUDA(launch_cr_solve(h->batch, h->d_all_list, 128, smem, a, st));
-        ++h->launches;
+        if (h->cr_levels) {
+            if (!h->p1_list.empty()) {
+                CYQ_CUDA(launch_cr_solve((int)h->p1_list.size(), h->d_p1_list, 128, smem, a, st));
+                ++h->launches;
+            }
+            CYQ_CUDA(launch_cr_solve_levels(h->cr_plan, h->max_nx, a, st, &h->launches));
+        } else {
+            CYQ_CUDA(launch_cr_solve(h->batch, h->d_all_list, 128, smem, a, st));
+            ++h->launches;
+        }
     }
     for (const Group &g : h->groups) {
         CYQ_CUDA(launch_group_sweep(h, fs, g, false, b, z, nrhs, skip, zacc, st));
@@ -294,6 +307,7 @@ ResidArgs resid_args(cyq_handle h, const double *b, const double *z, double *r, 
                      bool need_bb = true) {
     ResidArgs a{};
     a.need_bb = need_bb;
+    a.max_nx = h->max_nx;
     a.inst = h->d_inst;
     a.chunks = h->d_chunks;
     a.n_chunks = (int)h->chunks.size();
@@ -437,6 +451,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         oq += (long long)(N + 1) * nx; orv += (long long)N * nu; oc += (long long)N * nx; ox0 += nx;
         h->inst.push_back(in);
         if (P > 1) h->cr_list.push_back(i);
+        else h->p1_list.push_back(i);
         // work items and their team class
         const int team = choose_team(nx, nu);
         const int cls = size_class(nx, nu);
@@ -557,6 +572,12 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         h->cr_plan.jobs = pj;
     }
     ALLOC(h->d_all_list, (size_t)h->batch);
+    ALLOC(h->d_p1_list, h->p1_list.size());
+    {
+        int maxP = 0;
+        for (int i : h->cr_list) maxP = std::max(maxP, h->inst[i].P);
+        h->cr_levels = !h->cr_list.empty() && (int)h->cr_list.size() < 2 * kSMs && maxP >= 8;
+    }
     for (Group &g : h->groups) ALLOC(g.d_items, g.items.size());
     // fac (the handle's factor) and, in float32 mode, fac64 (escalation), in float64
     // mode with float32 corrections, fac32 (float32 copy)
@@ -594,6 +615,8 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     if ((e = cudaMemcpy(h->d_inst, h->inst.data(), sizeof(Inst) * h->inst.size(), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(h->d_chunks, h->chunks.data(), sizeof(Chunk) * h->chunks.size(), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(h->d_all_list, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice)) ||
+        (!h->p1_list.empty() && (e = cudaMemcpy(h->d_p1_list, h->p1_list.data(), sizeof(int) * h->p1_list.size(),
+                                                cudaMemcpyHostToDevice))) ||
         (e = cudaMemset(h->status, 0, sizeof(int) * h->batch)) ||
         (e = cudaMemset(h->rr, 0, sizeof(double) * h->batch * h->max_nrhs)) ||
         (e = cudaMemset(h->bb, 0, sizeof(double) * h->batch * h->max_nrhs)) ||

@@ -310,6 +310,234 @@ __global__ void __launch_bounds__(TEAM) k_cr_solve(SolveArgs a, const int *inst_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Level-parallel solve (instances with many segments in a small batch): the
+// single-CTA solve above runs a whole instance on one SM; here every level is
+// one launch with one warp per (block, right-hand side), so the O(P) blocks of
+// a level run on all SMs.  The coupling vector lam holds the right-hand side
+// and, in place, the solution; the arithmetic is that of k_cr_solve.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Block L (n x n, column-major) into shared memory and the reciprocals of its diagonal.
+__device__ void crs_load_factor(double *Ls, double *di, const double *L, int n) {
+    for (int e = threadIdx.x; e < n * n; e += 32) Ls[e] = L[e];
+    __syncwarp();
+    for (int i = threadIdx.x; i < n; i += 32) di[i] = 1.0 / Ls[i + i * n];
+    __syncwarp();
+}
+
+// v := L^{-1} v (column-oriented forward substitution; row i belongs to lane i % 32).
+__device__ void crs_forward(const double *Ls, const double *di, double *v, int n) {
+    for (int t = 0; t < n; ++t) {
+        if ((t & 31) == threadIdx.x) v[t] *= di[t];
+        __syncwarp();
+        const double xt = v[t];
+        for (int i = t + 1 + ((threadIdx.x - t - 1) & 31); i < n; i += 32) v[i] = fma(-Ls[i + t * n], xt, v[i]);
+    }
+    __syncwarp();
+}
+
+// v := L^{-T} v (column-oriented back substitution).
+__device__ void crs_backward(const double *Ls, const double *di, double *v, int n) {
+    for (int t = n - 1; t >= 0; --t) {
+        if ((t & 31) == threadIdx.x) v[t] *= di[t];
+        __syncwarp();
+        const double xt = v[t];
+        for (int i = threadIdx.x; i < t; i += 32) v[i] = fma(-Ls[t + i * n], xt, v[i]);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ double *crs_vec(const SolveArgs &a, const Inst &in, int r, int k) {
+    return a.lam + r * a.nvec + in.oVec + (long long)k * in.nx;
+}
+
+}  // namespace
+
+// Right-hand side of the coupling system: rhs_c = d_fwd,c + d_bwd,(c+1 mod P) - b_lambda^{b_c}.
+__global__ void k_crs_rhs(SolveArgs a, const int *inst_list) {
+    const int ii = inst_list[blockIdx.y];
+    if (a.skip && a.skip[ii]) return;
+    const Inst in = a.inst[ii];
+    const int P = in.P, n = in.nx, N = in.N, nu = in.nu, w = nu + 2 * n;
+    const long long total = (long long)P * n * a.nrhs;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / ((long long)P * n));
+        const int rem = (int)(e % ((long long)P * n));
+        const int c = rem / n, i = rem % n;
+        const int bc = seg_bound(c, N, P);
+        const double *dF = a.dF + r * a.nvec + in.oVec, *dB = a.dB + r * a.nvec + in.oVec;
+        const double bl = a.b[r * a.kkt + in.oZ + (long long)bc * w + nu + n + i];
+        a.lam[r * a.nvec + in.oVec + rem] = dF[c * n + i] + dB[((c + 1) % P) * n + i] - bl;
+    }
+}
+
+// Forward phase of level s, eliminated block k:  b~_k = L_k^{-1} b_k.
+__global__ void __launch_bounds__(32) k_crs_forward(SolveArgs a, const CrJob *jobs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CrJob job = jobs[blockIdx.x];
+    if (a.skip && a.skip[job.inst]) return;
+    const Inst in = a.inst[job.inst];
+    const int n = in.nx, r = blockIdx.y;
+    double *Ls = reinterpret_cast<double *>(smem_raw), *di = Ls + n * n, *v = di + n;
+    crs_load_factor(Ls, di, a.Mf + in.oBlk + (long long)job.k * n * n, n);
+    double *g = crs_vec(a, in, r, job.k);
+    for (int i = threadIdx.x; i < n; i += 32) v[i] = g[i];
+    __syncwarp();
+    crs_forward(Ls, di, v, n);
+    for (int i = threadIdx.x; i < n; i += 32) g[i] = v[i];
+}
+
+// Forward phase of level s, remaining block i:  b_i -= Y_{i-s} b~_{i-s} + U_{i+s} b~_{i+s}.
+__global__ void __launch_bounds__(32) k_crs_update(SolveArgs a, const CrJob *jobs, int s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CrJob job = jobs[blockIdx.x];
+    if (a.skip && a.skip[job.inst]) return;
+    const Inst in = a.inst[job.inst];
+    const int n = in.nx, P = in.P, i = job.k, r = blockIdx.y;
+    const long long nn = (long long)n * n;
+    double *xl = reinterpret_cast<double *>(smem_raw), *xh = xl + n;
+    const bool lo = i - s >= 0, hi = i + s < P;
+    if (lo) {
+        const double *g = crs_vec(a, in, r, i - s);
+        for (int t = threadIdx.x; t < n; t += 32) xl[t] = g[t];
+    }
+    if (hi) {
+        const double *g = crs_vec(a, in, r, i + s);
+        for (int t = threadIdx.x; t < n; t += 32) xh[t] = g[t];
+    }
+    __syncwarp();
+    const double *Y = a.Y + in.oBlk + (i - s) * nn, *U = a.U + in.oBlk + (i + s) * nn;
+    double *gi = crs_vec(a, in, r, i);
+    for (int row = threadIdx.x; row < n; row += 32) {
+        double acc = 0.0;
+        if (lo)
+            for (int t = 0; t < n; ++t) acc = fma(Y[row + t * n], xl[t], acc);
+        if (hi)
+            for (int t = 0; t < n; ++t) acc = fma(U[row + t * n], xh[t], acc);
+        gi[row] -= acc;
+    }
+}
+
+// Base block 0 of every listed instance:  x_0 = L_0^{-T} L_0^{-1} b_0.
+__global__ void __launch_bounds__(32) k_crs_base(SolveArgs a, const int *inst_list) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ii = inst_list[blockIdx.x];
+    if (a.skip && a.skip[ii]) return;
+    const Inst in = a.inst[ii];
+    const int n = in.nx, r = blockIdx.y;
+    double *Ls = reinterpret_cast<double *>(smem_raw), *di = Ls + n * n, *v = di + n;
+    crs_load_factor(Ls, di, a.Mf + in.oBlk, n);
+    double *g = crs_vec(a, in, r, 0);
+    for (int i = threadIdx.x; i < n; i += 32) v[i] = g[i];
+    __syncwarp();
+    crs_forward(Ls, di, v, n);
+    crs_backward(Ls, di, v, n);
+    for (int i = threadIdx.x; i < n; i += 32) g[i] = v[i];
+}
+
+// Back substitution of level s, eliminated block k:
+//   x_k = L_k^{-T} (b~_k - U_k^T x_{k-s} - Y_k^T x_{k+s}).
+__global__ void __launch_bounds__(32) k_crs_backward(SolveArgs a, const CrJob *jobs, int s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CrJob job = jobs[blockIdx.x];
+    if (a.skip && a.skip[job.inst]) return;
+    const Inst in = a.inst[job.inst];
+    const int n = in.nx, P = in.P, k = job.k, r = blockIdx.y;
+    const long long nn = (long long)n * n;
+    double *Ls = reinterpret_cast<double *>(smem_raw), *di = Ls + n * n, *v = di + n, *xp = v + n, *xn = xp + n;
+    crs_load_factor(Ls, di, a.Mf + in.oBlk + k * nn, n);
+    const bool hasn = k + s < P;
+    {
+        const double *gp = crs_vec(a, in, r, k - s);
+        for (int t = threadIdx.x; t < n; t += 32) xp[t] = gp[t];
+        if (hasn) {
+            const double *gn = crs_vec(a, in, r, k + s);
+            for (int t = threadIdx.x; t < n; t += 32) xn[t] = gn[t];
+        }
+    }
+    __syncwarp();
+    const double *Uk = a.U + in.oBlk + k * nn, *Yk = a.Y + in.oBlk + k * nn;
+    double *g = crs_vec(a, in, r, k);
+    for (int i = threadIdx.x; i < n; i += 32) {
+        double acc = g[i];
+        for (int t = 0; t < n; ++t) acc -= Uk[t + i * n] * xp[t];
+        if (hasn)
+            for (int t = 0; t < n; ++t) acc -= Yk[t + i * n] * xn[t];
+        v[i] = acc;
+    }
+    __syncwarp();
+    crs_backward(Ls, di, v, n);
+    for (int i = threadIdx.x; i < n; i += 32) g[i] = v[i];
+}
+
+// lambda^{b_c} of the solution into z (or added into zacc).
+__global__ void k_crs_scatter(SolveArgs a, const int *inst_list) {
+    const int ii = inst_list[blockIdx.y];
+    if (a.skip && a.skip[ii]) return;
+    const Inst in = a.inst[ii];
+    const int P = in.P, n = in.nx, N = in.N, nu = in.nu, w = nu + 2 * n;
+    const long long total = (long long)P * n * a.nrhs;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / ((long long)P * n));
+        const int rem = (int)(e % ((long long)P * n));
+        const int c = rem / n, i = rem % n;
+        const int bc = seg_bound(c, N, P);
+        const double x = a.lam[r * a.nvec + in.oVec + rem];
+        const long long o = r * a.kkt + in.oZ + (long long)bc * w + nu + n + i;
+        if (a.zacc) a.zacc[o] += x; else a.z[o] = x;
+    }
+}
+
+cudaError_t launch_cr_solve_levels(const CrPlan &plan, int nmax, const SolveArgs &a, cudaStream_t st,
+                                   long long *launches) {
+    if (plan.n_inst == 0) return cudaSuccess;
+    cudaError_t e;
+    const int nr = a.nrhs;
+    const size_t sm = ((size_t)nmax * nmax + 4 * (size_t)nmax) * sizeof(double);
+    if ((e = ensure_smem((const void *)k_crs_forward, sm)) != cudaSuccess) return e;
+    if ((e = ensure_smem((const void *)k_crs_base, sm)) != cudaSuccess) return e;
+    if ((e = ensure_smem((const void *)k_crs_backward, sm)) != cudaSuccess) return e;
+    k_crs_rhs<<<dim3(8, plan.n_inst), 256, 0, st>>>(a, plan.inst_list);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*launches;
+    for (int l = 0; l < plan.levels; ++l) {
+        const int s = 1 << l;
+        const int ne = plan.elim_off[l + 1] - plan.elim_off[l], nu_ = plan.upd_off[l + 1] - plan.upd_off[l];
+        if (ne > 0) {
+            k_crs_forward<<<dim3(ne, nr), 32, sm, st>>>(a, plan.jobs + plan.elim_off[l]);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            ++*launches;
+        }
+        if (nu_ > 0) {
+            k_crs_update<<<dim3(nu_, nr), 32, 2 * (size_t)nmax * sizeof(double), st>>>(
+                a, plan.jobs + plan.upd_off[l], s);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            ++*launches;
+        }
+    }
+    k_crs_base<<<dim3(plan.n_inst, nr), 32, sm, st>>>(a, plan.inst_list);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*launches;
+    for (int l = plan.levels - 1; l >= 0; --l) {
+        const int s = 1 << l;
+        const int ne = plan.elim_off[l + 1] - plan.elim_off[l];
+        if (ne > 0) {
+            k_crs_backward<<<dim3(ne, nr), 32, sm, st>>>(a, plan.jobs + plan.elim_off[l], s);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            ++*launches;
+        }
+    }
+    k_crs_scatter<<<dim3(8, plan.n_inst), 256, 0, st>>>(a, plan.inst_list);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cr_solve(int n_inst_cr, const int *inst_list, int team, size_t smem, const SolveArgs &a,
                             cudaStream_t st) {
     if (n_inst_cr == 0) return cudaSuccess;

@@ -387,6 +387,8 @@ cudaError_t launch_solve_backward(bool fp64, int team, int shape, size_t smem, c
 cudaError_t launch_cr_solve(int n_inst_cr, const int *inst_list, int team, size_t smem, const SolveArgs &a,
                             cudaStream_t st);
 cudaError_t launch_solve_forward(bool fp64, int team, int shape, size_t smem, const SolveArgs &a, cudaStream_t st);
+cudaError_t launch_cr_solve_levels(const CrPlan &plan, int nmax, const SolveArgs &a, cudaStream_t st,
+                                   long long *launches);
 
 struct Chunk {
     int inst, k0, k1;   // records [k0, k1) of one instance
@@ -404,6 +406,7 @@ struct ResidArgs {
     long long kkt;      // elements per right-hand side
     int batch;
     bool need_bb;       // accumulate ||b||^2 too (false: bb already holds it)
+    int max_nx;         // largest nx of the batch (launch choice)
 };
 
 struct GradArgs {

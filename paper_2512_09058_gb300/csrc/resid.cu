@@ -19,7 +19,9 @@ namespace cyq {
 // full warp slot per path.  Up to RG right-hand sides share every matrix load.
 constexpr int RG = 4;
 
-template <int TEAM>
+// UNROLL: unrolling of the inner products (several loads in flight for long rows,
+// fewer registers for short ones).
+template <int TEAM, int UNROLL>
 __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
     __shared__ double red[2 * RG][TEAM / 32];
     const Chunk ch = a.chunks[blockIdx.x];
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
             double acc[RG];
 #pragma unroll
             for (int r = 0; r < RG; ++r) acc[r] = 0.0;
+            #pragma unroll UNROLL
             for (int j = 0; j < nu; ++j) {
                 const double m = R[i + j * nu];
 #pragma unroll
@@ -75,6 +78,7 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
             }
             if (k > 0 && d.S) {
                 const double *S = d.S + in.oS + (long long)k * nu * nx;
+                #pragma unroll UNROLL
                 for (int j = 0; j < nx; ++j) {
                     const double m = S[i + j * nu];
 #pragma unroll
@@ -82,6 +86,7 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
                         if (r < nr) acc[r] = fma(m, zb[(r0 + r) * kk + (long long)(k - 1) * w + nu + j], acc[r]);
                 }
             }
+            #pragma unroll UNROLL
             for (int j = 0; j < nx; ++j) {
                 const double m = B[j + i * nx];
 #pragma unroll
@@ -102,6 +107,7 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
 #pragma unroll
             for (int r = 0; r < RG; ++r)
                 acc[r] = r < nr ? -zb[(r0 + r) * kk + (long long)k * w + nu + nx + i] : 0.0;
+            #pragma unroll UNROLL
             for (int m = 0; m < nx; ++m) {
                 const double v = Q[i + m * nx];
 #pragma unroll
@@ -116,6 +122,7 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
             }
             if (j1 < N) {
                 const double *A = d.A + in.oA + (long long)j1 * nx * nx;
+                #pragma unroll UNROLL
                 for (int m = 0; m < nx; ++m) {
                     const double v = A[m + i * nx];
 #pragma unroll
@@ -124,6 +131,7 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
                 }
                 if (d.S) {
                     const double *S = d.S + in.oS + (long long)j1 * nu * nx;
+                    #pragma unroll UNROLL
                     for (int m = 0; m < nu; ++m) {
                         const double v = S[m + i * nu];
 #pragma unroll
@@ -145,6 +153,7 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
             double acc[RG];
 #pragma unroll
             for (int r = 0; r < RG; ++r) acc[r] = r < nr ? -zb[(r0 + r) * kk + (long long)k * w + nu + i] : 0.0;
+            #pragma unroll UNROLL
             for (int m = 0; m < nu; ++m) {
                 const double v = B[i + m * nx];
 #pragma unroll
@@ -153,6 +162,7 @@ __global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
             }
             if (k > 0) {
                 const double *A = d.A + in.oA + (long long)k * nx * nx;
+                #pragma unroll UNROLL
                 for (int m = 0; m < nx; ++m) {
                     const double v = A[i + m * nx];
 #pragma unroll
@@ -362,7 +372,11 @@ __global__ void k_adjoint_dx0(const Inst *inst, int batch, Data d, const double 
 // ---------------------------------------------------------------------------
 cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st) {
     if (a.n_chunks == 0) return cudaSuccess;
-    k_residual<128><<<dim3(a.n_chunks, (nrhs + RG - 1) / RG), 128, 0, st>>>(a, nrhs);
+    const dim3 grid(a.n_chunks, (nrhs + RG - 1) / RG);
+    if (a.max_nx >= 24)
+        k_residual<128, 4><<<grid, 128, 0, st>>>(a, nrhs);
+    else
+        k_residual<128, 1><<<grid, 128, 0, st>>>(a, nrhs);
     return cudaGetLastError();
 }
 

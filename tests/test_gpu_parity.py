@@ -164,3 +164,17 @@ def test_padded_and_uneven_segments_agree(P):
                            split_instances(padded, z1[0])):
         assert rel_err(b[:x.kkt_size], a) <= 1e-11
         assert np.linalg.norm(b[x.kkt_size:]) <= 1e-11 * np.linalg.norm(a)
+
+
+def test_mixed_segment_counts_both_coupling_solves():
+    """Instances with one segment (coupling solved by one CTA each) next to
+    instances with 8 and 16 segments (level-parallel cyclic reduction), two
+    right-hand sides."""
+    dims = [(40, 4, 2), (64, 6, 3), (48, 5, 2), (30, 3, 1)]
+    batch = ragged_batch(54, dims, nrhs=2)
+    z, s, _, b = gpu_solve(batch, P_per_instance=[1, 8, 16, 1], nrhs=2)
+    assert list(s.segments) == [1, 8, 16, 1]
+    assert (s.instance_status() == 0).all()
+    for j in range(2):
+        for inst, zi, bi in zip(batch.instances, split_instances(batch, z[j]), split_instances(batch, b[j])):
+            assert rel_err(zi, oracle.riccati_solve(inst, bi)) <= 1e-10
