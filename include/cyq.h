@@ -104,7 +104,8 @@ typedef struct cyq_desc {
     int32_t device;         /* CUDA device ordinal (the caller's current device if < 0) */
     int32_t esc_max;        /* float32 mode: float64 corrections after re-factoring, in float64,
                                the instances still above tol after it_max steps; 0 = none,
-                               < 0: default 3 */
+                               < 0: default 3.  Not available (treated as 0) when the float64
+                               stage factor of some size class does not fit in shared memory */
 } cyq_desc;
 
 /*

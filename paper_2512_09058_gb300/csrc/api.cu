@@ -87,6 +87,7 @@ struct cyq_handle_s {
     // coupling solve: level-parallel over instances with P > 1 when they are few and have
     // many segments (cr_levels), single-CTA per instance otherwise / for P = 1 (p1_list)
     bool cr_levels = false;
+    bool esc_possible = true;     // every size class has a float64 plan (float32 mode escalation)
     std::vector<int> p1_list;
     int *d_p1_list = nullptr;
     Chunk *d_chunks = nullptr;
@@ -349,7 +350,7 @@ cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, int nrhs,
         s = run_solve(h, corr, h->r, h->dz, nrhs, h->done, st, z);
         if (s != CYQ_OK) return s;
     }
-    if (!corr.fp64 && h->esc_max > 0) {
+    if (!corr.fp64 && h->esc_max > 0 && h->esc_possible) {
         // precision escalation: instances the float32 corrections could not bring to
         // tol continue with float64 corrections (float32 mode: after a float64 factorization)
         const bool refactor = !h->fac.fp64;
@@ -511,8 +512,14 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
                 }
                 g.solve_nbuf[pi] = nb;
             }
-            if (g.smem_factor[pi] > (size_t)smem_optin ||
-                solve_smem_bytes(f64, g.max_nx, g.max_nu, h->max_nrhs, g.solve_nbuf[pi]) > (size_t)smem_optin) {
+            const bool fits = g.smem_factor[pi] <= (size_t)smem_optin &&
+                              solve_smem_bytes(f64, g.max_nx, g.max_nu, h->max_nrhs, g.solve_nbuf[pi]) <=
+                                  (size_t)smem_optin;
+            if (!fits && f64 && h->precision == CYQ_FP32_REFINE) {
+                h->esc_possible = false;   // float32 mode: only the float64 escalation needs this plan
+                continue;
+            }
+            if (!fits) {
                 delete h;
                 g_last_error = "stage blocks too large for shared memory";
                 return CYQ_ERR_INVALID_ARG;
