@@ -95,8 +95,6 @@ __device__ __forceinline__ void team_sync() {
         __syncwarp(((1u << TEAM) - 1u) << (threadIdx.x & 31 & ~(TEAM - 1)));
 }
 
-template <typename T> __device__ __forceinline__ T ld_cvt(const double *p) { return (T)(*p); }
-
 // Element e of the lower triangle (diagonal included) of an n x n matrix in
 // row order: row r holds r + 1 entries.  Returns (r, c) with c <= r.
 __device__ __forceinline__ void tri_index(int e, int &r, int &c) {
@@ -419,8 +417,6 @@ struct GradArgs {
 cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st);
 cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
                                   int *steps, int step, bool keep_bb, cudaStream_t st);
-cudaError_t launch_ir_update(const Inst *inst, int batch, double *z, const double *dz, const int *done, long long kkt,
-                             int nrhs, cudaStream_t st);
 cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, cudaStream_t st);
 cudaError_t launch_build_rhs(const Inst *inst, int batch, const Data &d, const double *q, const double *r,
                              const double *c, const double *x0, double *b, long long kkt, cudaStream_t st);

@@ -223,22 +223,7 @@ __global__ void k_resid_finalize(int batch, int nrhs, double *rr, double *bb, do
     if (steps) steps[i] = step;
 }
 
-// z += dz for instances not yet converged (grid-stride over all elements of all right-hand sides).
-__global__ void k_ir_update(const Inst *inst, int batch, double *z, const double *dz, const int *done,
-                            long long kkt, int nrhs) {
-    const long long total = kkt * nrhs;
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
-         g += (long long)gridDim.x * blockDim.x) {
-        const long long e = g % kkt;
-        int lo = 0, hi = batch - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (inst[mid].oZ <= e) lo = mid; else hi = mid - 1;
-        }
-        if (!done[lo]) z[g] += dz[g];
-    }
-}
-
+// Instances still above tol after the last refinement step: status NOT_CONVERGED.
 __global__ void k_mark_not_converged(int batch, const int *done, int *status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < batch && !done[i]) atomicCAS(status + i, 0, ST_NOT_CONVERGED);
@@ -386,14 +371,6 @@ cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, d
     return cudaGetLastError();
 }
 
-cudaError_t launch_ir_update(const Inst *inst, int batch, double *z, const double *dz, const int *done, long long kkt,
-                             int nrhs, cudaStream_t st) {
-    long long blocks = (kkt * nrhs + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks < 1) blocks = 1;
-    k_ir_update<<<(int)blocks, 256, 0, st>>>(inst, batch, z, dz, done, kkt, nrhs);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, cudaStream_t st) {
     k_mark_not_converged<<<(batch + 127) / 128, 128, 0, st>>>(batch, done, status);
