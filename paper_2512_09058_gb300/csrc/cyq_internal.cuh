@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <type_traits>
 #include <stdint.h>
 
 #include <string>
@@ -78,6 +79,16 @@ __host__ __device__ inline int xstate(int s, int N) { return s == 0 ? N : s; }
 // Team primitives
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void team_sync() { __syncthreads(); }
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1, so
+// that register arrays are only ever indexed by constants.
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
 
 // A team is the group of threads that works on one item: the whole CTA when
 // TEAM >= 32, else TEAM consecutive lanes of a warp (several teams per warp,

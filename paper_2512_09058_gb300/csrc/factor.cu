@@ -20,8 +20,6 @@
 // the current stage's copy is consumed by the end of the previous step, so
 // one buffer suffices.  H^ = H + V V^T is assembled directly from that copy,
 // or from global memory for blocks too large to stage.
-#include <type_traits>
-
 #include "cyq_internal.cuh"
 
 namespace cyq {
@@ -173,16 +171,6 @@ struct FactorTiles {
 // Largest nu + nx of the register path (a 32-row matrix and V no longer fit in
 // the registers of one thread without spilling).
 constexpr int kRegisterRows = 24;
-
-// Compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1, so
-// that register arrays are only ever indexed by constants.
-template <int B, int E, typename F>
-__device__ __forceinline__ void static_for(F &&f) {
-    if constexpr (B < E) {
-        f(std::integral_constant<int, B>{});
-        static_for<B + 1, E>(f);
-    }
-}
 
 // Interior stages t0 <= t < t1 of a segment that carries no A^cl (segment 0):
 // float32, one warp, a stage shape fixed at compile time with NU + NX <= 32.

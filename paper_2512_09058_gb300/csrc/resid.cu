@@ -19,185 +19,16 @@ namespace cyq {
 // full warp slot per path.  Up to RG right-hand sides share every matrix load.
 constexpr int RG = 4;
 
-// UNROLL: unrolling of the inner products (several loads in flight for long rows,
-// fewer registers for short ones).
-template <int TEAM, int UNROLL>
-__global__ void __launch_bounds__(TEAM) k_residual(ResidArgs a, int nrhs) {
-    __shared__ double red[2 * RG][TEAM / 32];
-    const Chunk ch = a.chunks[blockIdx.x];
-    if (a.skip && a.skip[ch.inst]) return;
-    const int r0 = blockIdx.y * RG;
-    const int nr = min(RG, nrhs - r0);
-    const Inst in = a.inst[ch.inst];
-    const int N = in.N, nx = in.nx, nu = in.nu, w = nu + 2 * nx;
-    const Data &d = a.data;
-    const double *zb = a.z + in.oZ, *bb = a.b + in.oZ;
-    const long long kk = a.kkt;
-    const int nrec = ch.k1 - ch.k0;
-    double sr[RG], sb[RG];
-#pragma unroll
-    for (int r = 0; r < RG; ++r) sr[r] = sb[r] = 0.0;
-
-    auto finish_row = [&](int k, int row, const double *acc) {
-#pragma unroll
-        for (int r = 0; r < RG; ++r) {
-            if (r < nr) {
-                const long long o = (long long)(r0 + r) * kk + (long long)k * w + row;
-                const double bv = bb[o];
-                const double rv = bv - acc[r];
-                if (a.r) a.r[in.oZ + o] = rv;
-                sr[r] = fma(rv, rv, sr[r]);
-                if (a.need_bb) sb[r] = fma(bv, bv, sb[r]);
-            }
-        }
-    };
-
-    // u^k rows: R_k u^k + Sigma_u u^k + S_k x^k + B_k^T lambda^k
-    {
-        int i, q;
-        rect_start(threadIdx.x, nu, i, q);
-        for (; q < nrec; rect_advance(i, q, nu, TEAM)) {
-            const int k = ch.k0 + q;
-            const double *R = d.R + in.oR + (long long)k * nu * nu;
-            const double *B = d.B + in.oB + (long long)k * nx * nu;
-            double acc[RG];
-#pragma unroll
-            for (int r = 0; r < RG; ++r) acc[r] = 0.0;
-            #pragma unroll UNROLL
-            for (int j = 0; j < nu; ++j) {
-                const double m = R[i + j * nu];
-#pragma unroll
-                for (int r = 0; r < RG; ++r)
-                    if (r < nr) acc[r] = fma(m, zb[(r0 + r) * kk + (long long)k * w + j], acc[r]);
-            }
-            if (d.Sig) {
-                const double sg = d.Sig[in.oSig + (long long)k * (nu + nx) + i];
-#pragma unroll
-                for (int r = 0; r < RG; ++r)
-                    if (r < nr) acc[r] = fma(sg, zb[(r0 + r) * kk + (long long)k * w + i], acc[r]);
-            }
-            if (k > 0 && d.S) {
-                const double *S = d.S + in.oS + (long long)k * nu * nx;
-                #pragma unroll UNROLL
-                for (int j = 0; j < nx; ++j) {
-                    const double m = S[i + j * nu];
-#pragma unroll
-                    for (int r = 0; r < RG; ++r)
-                        if (r < nr) acc[r] = fma(m, zb[(r0 + r) * kk + (long long)(k - 1) * w + nu + j], acc[r]);
-                }
-            }
-            #pragma unroll UNROLL
-            for (int j = 0; j < nx; ++j) {
-                const double m = B[j + i * nx];
-#pragma unroll
-                for (int r = 0; r < RG; ++r)
-                    if (r < nr) acc[r] = fma(m, zb[(r0 + r) * kk + (long long)k * w + nu + nx + j], acc[r]);
-            }
-            finish_row(k, i, acc);
-        }
-    }
-    // x^{k+1} rows: Q x - lambda^k (+ S_{k+1}^T u^{k+1} + A_{k+1}^T lambda^{k+1} when k+1 < N)
-    {
-        int i, q;
-        rect_start(threadIdx.x, nx, i, q);
-        for (; q < nrec; rect_advance(i, q, nx, TEAM)) {
-            const int k = ch.k0 + q, j1 = k + 1;
-            const double *Q = d.Q + in.oQ + (long long)j1 * nx * nx;
-            double acc[RG];
-#pragma unroll
-            for (int r = 0; r < RG; ++r)
-                acc[r] = r < nr ? -zb[(r0 + r) * kk + (long long)k * w + nu + nx + i] : 0.0;
-            #pragma unroll UNROLL
-            for (int m = 0; m < nx; ++m) {
-                const double v = Q[i + m * nx];
-#pragma unroll
-                for (int r = 0; r < RG; ++r)
-                    if (r < nr) acc[r] = fma(v, zb[(r0 + r) * kk + (long long)k * w + nu + m], acc[r]);
-            }
-            if (d.Sig) {
-                const double sg = d.Sig[in.oSig + (long long)j1 * (nu + nx) + nu + i];
-#pragma unroll
-                for (int r = 0; r < RG; ++r)
-                    if (r < nr) acc[r] = fma(sg, zb[(r0 + r) * kk + (long long)k * w + nu + i], acc[r]);
-            }
-            if (j1 < N) {
-                const double *A = d.A + in.oA + (long long)j1 * nx * nx;
-                #pragma unroll UNROLL
-                for (int m = 0; m < nx; ++m) {
-                    const double v = A[m + i * nx];
-#pragma unroll
-                    for (int r = 0; r < RG; ++r)
-                        if (r < nr) acc[r] = fma(v, zb[(r0 + r) * kk + (long long)j1 * w + nu + nx + m], acc[r]);
-                }
-                if (d.S) {
-                    const double *S = d.S + in.oS + (long long)j1 * nu * nx;
-                    #pragma unroll UNROLL
-                    for (int m = 0; m < nu; ++m) {
-                        const double v = S[m + i * nu];
-#pragma unroll
-                        for (int r = 0; r < RG; ++r)
-                            if (r < nr) acc[r] = fma(v, zb[(r0 + r) * kk + (long long)j1 * w + m], acc[r]);
-                    }
-                }
-            }
-            finish_row(k, nu + i, acc);
-        }
-    }
-    // lambda^k rows: B_k u^k + A_k x^k - x^{k+1}  (no A_0 x^0 term)
-    {
-        int i, q;
-        rect_start(threadIdx.x, nx, i, q);
-        for (; q < nrec; rect_advance(i, q, nx, TEAM)) {
-            const int k = ch.k0 + q;
-            const double *B = d.B + in.oB + (long long)k * nx * nu;
-            double acc[RG];
-#pragma unroll
-            for (int r = 0; r < RG; ++r) acc[r] = r < nr ? -zb[(r0 + r) * kk + (long long)k * w + nu + i] : 0.0;
-            #pragma unroll UNROLL
-            for (int m = 0; m < nu; ++m) {
-                const double v = B[i + m * nx];
-#pragma unroll
-                for (int r = 0; r < RG; ++r)
-                    if (r < nr) acc[r] = fma(v, zb[(r0 + r) * kk + (long long)k * w + m], acc[r]);
-            }
-            if (k > 0) {
-                const double *A = d.A + in.oA + (long long)k * nx * nx;
-                #pragma unroll UNROLL
-                for (int m = 0; m < nx; ++m) {
-                    const double v = A[i + m * nx];
-#pragma unroll
-                    for (int r = 0; r < RG; ++r)
-                        if (r < nr) acc[r] = fma(v, zb[(r0 + r) * kk + (long long)(k - 1) * w + nu + m], acc[r]);
-                }
-            }
-            finish_row(k, nu + nx + i, acc);
-        }
-    }
-    // per right-hand side block reduction of ||r||^2 and ||b||^2
-#pragma unroll
-    for (int r = 0; r < RG; ++r) {
-        double x = sr[r], y = sb[r];
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (a.need_bb) y += __shfl_xor_sync(0xffffffffu, y, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            red[2 * r][threadIdx.x >> 5] = x;
-            red[2 * r + 1][threadIdx.x >> 5] = y;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < nr) {
-        const int r = threadIdx.x;
-        double tr = 0.0, tb = 0.0;
-        for (int i = 0; i < TEAM / 32; ++i) {
-            tr += red[2 * r][i];
-            tb += red[2 * r + 1][i];
-        }
-        atomicAdd(a.rr + (long long)(r0 + r) * a.batch + ch.inst, tr);
-        if (a.need_bb) atomicAdd(a.bb + (long long)(r0 + r) * a.batch + ch.inst, tb);
-    }
-}
+#define CYQ_ROW_UNROLL _Pragma("unroll 4")
+#define CYQ_RESID_KERNEL k_residual_long_rows
+#include "resid_rows.inc"
+#undef CYQ_ROW_UNROLL
+#undef CYQ_RESID_KERNEL
+#define CYQ_ROW_UNROLL
+#define CYQ_RESID_KERNEL k_residual_short_rows
+#include "resid_rows.inc"
+#undef CYQ_ROW_UNROLL
+#undef CYQ_RESID_KERNEL
 
 // Per instance: rel[r] = ||res_r|| / ||b_r|| for each right-hand side r; the
 // instance is done once every right-hand side is at or below tol (refinement
@@ -359,9 +190,9 @@ cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st) {
     if (a.n_chunks == 0) return cudaSuccess;
     const dim3 grid(a.n_chunks, (nrhs + RG - 1) / RG);
     if (a.max_nx >= 24)
-        k_residual<128, 4><<<grid, 128, 0, st>>>(a, nrhs);
+        k_residual_long_rows<128><<<grid, 128, 0, st>>>(a, nrhs);
     else
-        k_residual<128, 1><<<grid, 128, 0, st>>>(a, nrhs);
+        k_residual_short_rows<128><<<grid, 128, 0, st>>>(a, nrhs);
     return cudaGetLastError();
 }
 

@@ -90,3 +90,4 @@ def test_launch_shapes_agree_on_a_fixed_shape_batch(precision):
         tol = 1e-3 if precision == "fp32_refine" else 1e-9
         for inst, zi, bi in zip(batch.instances, split_instances(batch, zs[0]), split_instances(batch, b_host)):
             assert rel_err(zi, oracle.riccati_solve(inst, bi)) <= tol
+
