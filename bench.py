@@ -55,6 +55,7 @@ REFINE_TOL = 1e-10
 # from one ncu capture of the current kernel (profiles/k_factor_segments_*.md);
 # absent where no capture of the current kernel exists
 NCU_TRAFFIC = {("batch1024_n64_nx12_nu4", "fp64"): 217.7e6 + 110.1e6,
+               ("batch1024_n64_nx12_nu4", "fp64_ir32"): 217.6e6 + 218.8e6,
                ("batch1024_n64_nx12_nu4", "fp32_refine"): 217.0e6 + 88.5e6}
 # workload -> methods (first = headline), CUDA-graph replay, adjoint in the step
 # workload -> methods (first = headline), CUDA-graph replay, adjoint in the step,
