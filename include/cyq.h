@@ -253,8 +253,10 @@ cyq_status cyq_set_launch_shapes(cyq_handle h, const int32_t *factor_team, const
  * desc->P = 0 and no P_per_instance), tries the counts scaled by 1/4, 1/2, 1,
  * 2 and 4 (clamped to [1, N_i]), each in a temporary handle: one untimed
  * factor + solve, then `reps` (default 2 if < 1) timed factor + solve with
- * nrhs right-hand sides b (refinement as set in desc).  Writes the fastest
- * counts to P_out (host array [batch]) for use as desc->P_per_instance.
+ * nrhs right-hand sides b (refinement as set in desc).  Writes to P_out (host
+ * array [batch], for use as desc->P_per_instance) the fastest counts among the
+ * candidates that leave the fewest instances with a non-OK status (not solved
+ * to desc->tol, or not positive definite).
  * Allocates and frees a handle per candidate (a candidate whose workspace
  * cannot be allocated is skipped); z is scratch; synchronises the stream.
  * Errors: INVALID_ARG, CUDA and the errors of cyq_create / cyq_solve.

@@ -945,6 +945,8 @@ cyq_status cyq_tune_segments(const cyq_desc *desc, const double *Q, const double
     std::vector<std::vector<int>> tried;
     std::vector<int> best_P = base;
     float best = 3.0e38f;
+    int best_fail = batch + 1;      // instances not solved to the tolerance (or not factored)
+    std::vector<int32_t> status(batch);
     for (int shift = -2; shift <= 2; ++shift) {
         std::vector<int> P(batch);
         for (int i = 0; i < batch; ++i) {
@@ -972,10 +974,19 @@ cyq_status cyq_tune_segments(const cyq_desc *desc, const double *Q, const double
                 if (q == CYQ_OK) q = cyq_solve(h, b, z, nrhs, stream);
                 return q == CYQ_OK ? cudaSuccess : cudaErrorUnknown;
             }, &ms);
+        // a candidate that leaves more instances uncertified (e.g. one whose float64
+        // escalation plan does not fit) loses to any that certifies more of them
+        int fail = 0;
+        if (s == CYQ_OK) {
+            const cyq_status g = cyq_get_instance_status(h, status.data(), stream);
+            if (g != CYQ_OK && g != CYQ_ERR_NOT_CONVERGED && g != CYQ_ERR_NOT_PD) s = g;
+            for (int i = 0; i < batch; ++i) fail += status[i] != CYQ_OK;
+        }
         cyq_destroy(h);
         if (s != CYQ_OK) return s;
-        if (ms < best) {
+        if (fail < best_fail || (fail == best_fail && ms < best)) {
             best = ms;
+            best_fail = fail;
             best_P = P;
         }
     }
