@@ -575,6 +575,289 @@ __global__ void __launch_bounds__(TEAM < 32 ? 32 : TEAM) k_factor_segments(Facto
     }
 }
 
+// ---------------------------------------------------------------------------
+// Float64 stage factor, two items per warp, for small stage shapes fixed at
+// compile time (NU + NX <= 16) and segments without A^cl (one segment per
+// instance).
+//
+// Each FP64 unit serves one SM sub-partition and takes ~64 cycles per warp
+// instruction whether 1 or 32 lanes are active, while a dependent FP64 chain
+// waits ~70 cycles: the float64 factor is bound by the number of FP64 warp
+// instructions per sub-partition, not by latency.  Here a team of 16 threads
+// owns an item, so every FP64 instruction serves two items, and the entries of
+// each triangular update are dealt out evenly over the team (a table of
+// (row, column) pairs) instead of one row per thread, so that few lanes sit
+// idle.  Four warps per CTA put one warp on each sub-partition.
+//
+// The arithmetic of every entry is that of the shared-memory path above
+// (team_chol, L^{R-1}, trsm, syrk, V, H^ = H + V V^T, trtri, M_bwd, the
+// coupling Cholesky) in the same order, so the stored factor is bit for bit
+// the same.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kPairTeam = 16;          // threads per item
+constexpr int kPairItemsPerCta = 8;    // four warps
+
+// Positive and finite (the test of finite_pos on the bits, without FP64 instructions).
+__device__ __forceinline__ bool pos_finite_bits(double d) {
+    const int hi = __double2hiint(d), lo = __double2loint(d);
+    return hi >= 0 && (hi | lo) != 0 && ((hi >> 20) & 0x7ff) != 0x7ff;
+}
+
+// Per-item shared memory (doubles): raw stage record | H | V | L^B | M_fwd | 1/diag.
+template <int NX, int NU>
+struct PairLayout {
+    static constexpr int NUX = NX + NU;
+    static constexpr int ldH = NUX | 1, ldV = NUX | 1, ldG = NX | 1, ldT = NX | 1;
+    static constexpr int raw = (NU * NU + NU * NX + NX * NX + NUX + NX * NU + NX * NX + 1) & ~1;
+    static constexpr int oH = raw;
+    static constexpr int oV = oH + ldH * NUX;
+    static constexpr int oG = oV + ldV * NX;
+    static constexpr int oMf = oG + ldG * NU;
+    static constexpr int oD = oMf + NX * NX;
+    static constexpr int size = (oD + NUX + 1) & ~1;
+    static constexpr int ntri = NUX * (NUX + 1) / 2;   // entries of the table of (row, column) pairs
+    static constexpr size_t bytes = (size_t)kPairItemsPerCta * size * 8 + ((size_t)ntri * 2 + 15) / 16 * 16;
+    static_assert(NUX <= kPairTeam, "one row of V per thread");
+    static_assert(ldT * NX <= ldV * NX && ldT * NX <= ldH * NUX, "L^{Q-1} and M_bwd reuse the V and H tiles");
+};
+
+template <int NX, int NU>
+__global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(FactorArgs a) {
+    using LY = PairLayout<NX, NU>;
+    constexpr int NUX = LY::NUX, ldH = LY::ldH, ldV = LY::ldV, ldG = LY::ldG, ldT = LY::ldT, NT = LY::ntri;
+    extern __shared__ __align__(16) unsigned char smem_all[];
+    // (row, column) of entry e of a lower triangle in row order, for e < NT
+    unsigned short *tab = reinterpret_cast<unsigned short *>(smem_all + (size_t)kPairItemsPerCta * LY::size * 8);
+    for (int e = threadIdx.x; e < NT; e += blockDim.x) {
+        int r, c;
+        tri_index(e, r, c);
+        tab[e] = (unsigned short)(r | (c << 8));
+    }
+    __syncthreads();
+    const int team = threadIdx.x / kPairTeam, q = threadIdx.x % kPairTeam;
+    const int item = blockIdx.x * kPairItemsPerCta + team;
+    if (item >= a.n_items) return;   // the team leaves as a whole; only team barriers follow
+    const Item wi = a.items[item];
+    if (a.skip && a.skip[wi.inst]) return;
+    const Inst in = a.inst[wi.inst];
+    const int N = in.N, P = in.P, c = wi.seg;
+    const int len = seg_len(c, N, P);
+    const StageLayout SL(NX, NU);
+    double *buf = reinterpret_cast<double *>(smem_all) + (size_t)team * LY::size;
+    double *H = buf + LY::oH, *V = buf + LY::oV, *G = buf + LY::oG, *Mf = buf + LY::oMf, *dinv = buf + LY::oD;
+    double *Lg = reinterpret_cast<double *>(a.L) + in.oL;
+    double *LBg = reinterpret_cast<double *>(a.LB) + in.oLB;
+    double *DIg = reinterpret_cast<double *>(a.DI) + in.oDI;
+    const bool copy32 = a.Lc != nullptr;
+
+    // first stage: H^ = H, B^ = B
+    int s = seg_stage(c, 0, N, P);
+    prefetch_stage<kPairTeam>(buf, SL, a.data, in, s);
+    stage_zero_fill<kPairTeam>(buf, SL, a.data, in, s);
+    cp_async_wait_all();
+    for (int e = q; e < NX * NX; e += kPairTeam) Mf[e] = 0.0;
+    team_sync<kPairTeam>();
+    {
+        const StageSrc src = stage_src_smem(buf, SL);
+        for (int e = q; e < NT; e += kPairTeam) {
+            const int r = tab[e] & 0xff, cc = tab[e] >> 8;
+            H[r + cc * ldH] = stage_H(src, NU, NX, r, cc);
+        }
+        for (int e = q; e < NX * NU; e += kPairTeam) G[e % NX + (e / NX) * ldG] = src.B[e];
+    }
+    team_sync<kPairTeam>();
+
+    bool ok = true;
+    for (int t = 0; t < len; ++t) {
+        s = seg_stage(c, t, N, P);
+        const bool last = (t == len - 1);
+        int s2 = 0;
+        if (!last) {
+            s2 = seg_stage(c, t + 1, N, P);
+            prefetch_stage<kPairTeam>(buf, SL, a.data, in, s2);   // lands while this stage is factored
+        }
+        // Cholesky (team_chol's arithmetic): pivot, scaled column, rank-1 update of the
+        // trailing triangle dealt out over the team; the diagonal is written at the end
+        double myl = 0.0, myil = 0.0;
+        static_for<0, NUX>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int m = NUX - 1 - k;
+            constexpr int T = m * (m + 1) / 2;
+            double d = H[k + k * ldH];
+            if (!pos_finite_bits(d)) {
+                ok = false;
+                d = 1.0;
+            }
+            double l, il;
+            pivot(d, l, il);
+            if (q == k) {
+                myl = l;
+                myil = il;
+            }
+            if (k + 1 + q < NUX) H[k + 1 + q + k * ldH] *= il;
+            team_sync<kPairTeam>();
+#pragma unroll
+            for (int it = 0; it < (T + kPairTeam - 1) / kPairTeam; ++it) {
+                const int e = q + kPairTeam * it;
+                if (e < T) {
+                    const int rr = (tab[e] & 0xff) + k + 1, cc = (tab[e] >> 8) + k + 1;
+                    H[rr + cc * ldH] = fma(-H[rr + k * ldH], H[cc + k * ldH], H[rr + cc * ldH]);
+                }
+            }
+            team_sync<kPairTeam>();
+        });
+        if (q < NUX) {
+            H[q + q * ldH] = myl;
+            dinv[q] = myil;
+        }
+        team_sync<kPairTeam>();
+        // L^{R-1}, transposed into the upper triangle of the R block (column q of it)
+        if (q < NU) {
+            for (int i = q + 1; i < NU; ++i) {
+                double acc = 0.0;
+                for (int k = q; k < i; ++k) acc = fma(-H[i + k * ldH], k == q ? dinv[q] : H[q + k * ldH], acc);
+                H[q + i * ldH] = acc * dinv[i];
+            }
+        }
+        team_sync<kPairTeam>();
+        {
+            double *Ls = Lg + (long long)s * NUX * NUX;
+            float *Lcs = copy32 ? a.Lc + in.oL + (long long)s * NUX * NUX : nullptr;
+            for (int e = q; e < NUX * NUX; e += kPairTeam) {
+                const int r = e % NUX, cc = e / NUX;
+                const bool keep = r >= cc || cc < NU;   // lower triangle, or L^{R-1} above the R diagonal
+                const double v = keep ? H[r + cc * ldH] : 0.0;
+                Ls[e] = v;
+                if (Lcs) Lcs[e] = keep ? (float)v : 0.0f;
+            }
+            for (int i = q; i < NUX; i += kPairTeam) {
+                DIg[(long long)s * NUX + i] = dinv[i];
+                if (copy32) a.DIc[in.oDI + (long long)s * NUX + i] = (float)dinv[i];
+            }
+        }
+        if (t == 0) {
+            // L^B = B^ L^{R-T} (one row per thread), then M_fwd = L^B L^B^T (lower)
+            if (q < NX) {
+                for (int j = 0; j < NU; ++j) {
+                    double v = G[q + j * ldG];
+                    for (int k = 0; k < j; ++k) v = fma(-G[q + k * ldG], H[j + k * ldH], v);
+                    G[q + j * ldG] = v * dinv[j];
+                }
+            }
+            team_sync<kPairTeam>();
+            for (int e = q; e < NX * NU; e += kPairTeam) {
+                const double v = G[e % NX + (e / NX) * ldG];
+                LBg[(long long)s * NX * NU + e] = v;
+                if (copy32) a.LBc[in.oLB + (long long)s * NX * NU + e] = (float)v;
+            }
+            for (int e = q; e < NX * (NX + 1) / 2; e += kPairTeam) {
+                const int r = tab[e] & 0xff, cc = tab[e] >> 8;
+                double v = 0.0;
+#pragma unroll
+                for (int k = 0; k < NU; ++k) v = fma(G[r + k * ldG], G[cc + k * ldG], v);
+                Mf[r + cc * NX] = Mf[r + cc * NX] + v;
+            }
+            team_sync<kPairTeam>();
+        }
+        if (!last) {
+            stage_zero_fill<kPairTeam>(buf, SL, a.data, in, s2);
+            cp_async_wait_all();
+            team_sync<kPairTeam>();   // every thread's copies have landed
+            const StageSrc src = stage_src_smem(buf, SL);
+            const double *BA = src.B;   // [B A] of stage s2, column-major, leading dimension NX
+            if (copy32 && a.BAf) {
+                float *dst = reinterpret_cast<float *>(a.BAf) + in.oBA + (long long)s2 * NX * NUX;
+                for (int e = q; e < NX * NUX; e += kPairTeam) dst[e] = (float)BA[e];
+            }
+            // V = [B A]^T L^Q, row q: V[q][j] = sum_{k >= j} BA[k][q] L^Q[k][j]
+            if (q < NUX) {
+                const double *LQ = H + NU + NU * ldH;
+                double ba[NX];
+                static_for<0, NX>([&](auto kc) { ba[decltype(kc)::value] = BA[decltype(kc)::value + q * NX]; });
+                static_for<0, NX>([&](auto jc) {
+                    constexpr int j = decltype(jc)::value;
+                    double acc = 0.0;
+                    static_for<j, NX>([&](auto kc) {
+                        constexpr int k = decltype(kc)::value;
+                        acc = fma(ba[k], LQ[k + j * ldH], acc);
+                    });
+                    V[q + j * ldV] = acc;
+                });
+            }
+            team_sync<kPairTeam>();
+            // H^_{s2} = H_{s2} + V V^T (lower triangle)
+            for (int e = q; e < NT; e += kPairTeam) {
+                const int r = tab[e] & 0xff, cc = tab[e] >> 8;
+                double acc = stage_H(src, NU, NX, r, cc);
+#pragma unroll
+                for (int k = 0; k < NX; ++k) acc = fma(V[r + k * ldV], V[cc + k * ldV], acc);
+                H[r + cc * ldH] = acc;
+            }
+            team_sync<kPairTeam>();
+        } else {
+            // close the segment: L^{Q-1} (one column per thread), M_bwd, coupling block
+            const double *LQ = H + NU + NU * ldH;
+            const double *dq = dinv + NU;
+            double *Ti = V;
+            if (q < NX) {
+                for (int i = 0; i < q; ++i) Ti[i + q * ldT] = 0.0;
+                for (int i = q; i < NX; ++i) {
+                    double v = (i == q) ? 1.0 : 0.0;
+                    for (int k = q; k < i; ++k) v = fma(-LQ[i + k * ldH], Ti[k + q * ldT], v);
+                    Ti[i + q * ldT] = v * dq[i];
+                }
+            }
+            team_sync<kPairTeam>();
+            {
+                double *Lq = Lg + (long long)s * NUX * NUX + NU + NU * NUX;
+                float *Lqc = copy32 ? a.Lc + in.oL + (long long)s * NUX * NUX + NU + NU * NUX : nullptr;
+                for (int e = q; e < NX * NX; e += kPairTeam) {
+                    const int i = e % NX, cc = e / NX;
+                    if (i > cc) {
+                        Lq[cc + i * NUX] = Ti[i + cc * ldT];
+                        if (Lqc) Lqc[cc + i * NUX] = (float)Ti[i + cc * ldT];
+                    }
+                }
+            }
+            double *Mb = H;   // M_bwd = L^{Q-T} L^{Q-1}, leading dimension ldT
+            for (int e = q; e < NX * NX; e += kPairTeam) {
+                const int i = e % NX, j = e / NX;
+                const int k0 = i > j ? i : j;
+                double v = 0.0;
+                for (int k = k0; k < NX; ++k) v = fma(Ti[k + i * ldT], Ti[k + j * ldT], v);
+                Mb[i + j * ldT] = v;
+            }
+            team_sync<kPairTeam>();
+            const int cb = (c - 1 + P) % P;
+            for (int e = q; e < NX * NX; e += kPairTeam)
+                a.Mb[in.oBlk + (long long)cb * NX * NX + e] = Mb[e % NX + (e / NX) * ldT];
+            team_symmetrize<double, kPairTeam>(Mf, NX, NX);
+            if (P == 1) {
+                for (int e = q; e < NX * NX; e += kPairTeam) Mf[e] += Mb[e % NX + (e / NX) * ldT];
+                team_sync<kPairTeam>();
+                ok &= team_chol<double, kPairTeam>(Mf, NX, NX);
+            }
+            double *dst = a.Mf + in.oBlk + (long long)c * NX * NX;
+            for (int e = q; e < NX * NX; e += kPairTeam) dst[e] = Mf[e];
+        }
+    }
+    if (!ok && q == 0) atomicCAS(a.status + wi.inst, 0, ST_NOT_PD);
+}
+
+template <int NX, int NU>
+cudaError_t launch_factor_pairs(const FactorArgs &a, cudaStream_t st) {
+    using LY = PairLayout<NX, NU>;
+    auto k = k_factor_pairs<NX, NU>;
+    cudaError_t e = ensure_smem((const void *)k, LY::bytes);
+    if (e != cudaSuccess) return e;
+    k<<<(a.n_items + kPairItemsPerCta - 1) / kPairItemsPerCta, kPairTeam * kPairItemsPerCta, LY::bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 size_t factor_stage_bytes(int nx, int nu) {
     const size_t nux = (size_t)nx + nu;
     size_t stage = (size_t)nu * nu + (size_t)nu * nx + (size_t)nx * nx + nux + (size_t)nx * nu + (size_t)nx * nx;
@@ -606,6 +889,11 @@ static cudaError_t launch_factor_t(size_t smem, const FactorArgs &a0, cudaStream
 
 cudaError_t launch_factor_segments(bool fp64, int team, int shape, size_t smem, const FactorArgs &a, cudaStream_t st) {
     if (a.n_items == 0) return cudaSuccess;
+    if (team == 16 && fp64 && !a.need_G2 && a.stage_in_smem) {
+        // every item is a whole horizon (no A^cl): two items per warp, compiled stage shapes
+        if (shape == 1) return launch_factor_pairs<kStageShapes[1].nx, kStageShapes[1].nu>(a, st);
+        if (shape == 2) return launch_factor_pairs<kStageShapes[2].nx, kStageShapes[2].nu>(a, st);
+    }
     if (team == 16) return fp64 ? launch_factor_t<double, 16>(smem, a, st) : launch_factor_t<float, 16>(smem, a, st);
     if (fp64) {
         if (team == 32) return launch_factor_t<double, 32>(smem, a, st);
