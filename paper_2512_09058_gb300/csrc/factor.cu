@@ -582,12 +582,15 @@ __global__ void __launch_bounds__(TEAM < 32 ? 32 : TEAM) k_factor_segments(Facto
 //
 // Each FP64 unit serves one SM sub-partition and takes ~64 cycles per warp
 // instruction whether 1 or 32 lanes are active, while a dependent FP64 chain
-// waits ~70 cycles: the float64 factor is bound by the number of FP64 warp
-// instructions per sub-partition, not by latency.  Here a team of 16 threads
-// owns an item, so every FP64 instruction serves two items, and the entries of
-// each triangular update are dealt out evenly over the team (a table of
-// (row, column) pairs) instead of one row per thread, so that few lanes sit
-// idle.  Four warps per CTA put one warp on each sub-partition.
+// waits ~70 cycles: with one warp per sub-partition the float64 factor is
+// bound by the FP64 warp instructions and by the other instructions between
+// them.  Here a team of 16 threads owns an item, so every FP64 instruction
+// serves two items, and four warps per CTA put one warp on each
+// sub-partition.  The lower triangle of the stage matrix lives in registers,
+// its entries dealt out column-major over the team (entry f to thread f % 16,
+// slot f / 16): the entries a pivot still updates are a suffix of that order,
+// so few lanes idle, and each column reaches the team through shared memory
+// once per pivot.
 //
 // The arithmetic of every entry is that of the shared-memory path above
 // (team_chol, L^{R-1}, trsm, syrk, V, H^ = H + V V^T, trtri, M_bwd, the
@@ -605,37 +608,49 @@ __device__ __forceinline__ bool pos_finite_bits(double d) {
     return hi >= 0 && (hi | lo) != 0 && ((hi >> 20) & 0x7ff) != 0x7ff;
 }
 
-// Per-item shared memory (doubles): raw stage record | H | V | L^B | M_fwd | 1/diag.
+// x + 0.0 without an FP64 instruction (-0 becomes +0, everything else is unchanged).
+__device__ __forceinline__ double plus_zero(double x) {
+    return __double_as_longlong(x) == (long long)0x8000000000000000ULL ? 0.0 : x;
+}
+
+// Per-item shared memory (doubles): raw stage record | H tile | V (row-major) |
+// L^B | M_fwd | 1/diag | two column buffers.
 template <int NX, int NU>
 struct PairLayout {
     static constexpr int NUX = NX + NU;
-    static constexpr int ldH = NUX | 1, ldV = NUX | 1, ldG = NX | 1, ldT = NX | 1;
+    static constexpr int ldH = NUX | 1, ldVr = (NX + 3) & ~1, ldG = NX | 1, ldT = NX | 1;
     static constexpr int raw = (NU * NU + NU * NX + NX * NX + NUX + NX * NU + NX * NX + 1) & ~1;
     static constexpr int oH = raw;
-    static constexpr int oV = oH + ldH * NUX;
-    static constexpr int oG = oV + ldV * NX;
+    static constexpr int oV = (oH + ldH * NUX + 1) & ~1;
+    static constexpr int oG = oV + NUX * ldVr;
     static constexpr int oMf = oG + ldG * NU;
     static constexpr int oD = oMf + NX * NX;
-    static constexpr int size = (oD + NUX + 1) & ~1;
-    static constexpr int ntri = NUX * (NUX + 1) / 2;   // entries of the table of (row, column) pairs
-    static constexpr size_t bytes = (size_t)kPairItemsPerCta * size * 8 + ((size_t)ntri * 2 + 15) / 16 * 16;
+    static constexpr int oC = oD + NUX;
+    static constexpr int size = (oC + 2 * NUX + 1) & ~1;
+    static constexpr int ntri = NUX * (NUX + 1) / 2;
+    static constexpr int slots = (ntri + kPairTeam - 1) / kPairTeam;
+    static constexpr size_t bytes = (size_t)kPairItemsPerCta * size * 8;
     static_assert(NUX <= kPairTeam, "one row of V per thread");
-    static_assert(ldT * NX <= ldV * NX && ldT * NX <= ldH * NUX, "L^{Q-1} and M_bwd reuse the V and H tiles");
+    static_assert(NX % 2 == 0, "rows of V as 16-byte pairs");
+    static_assert(ldT * NX <= NUX * ldVr && ldT * NX <= ldH * NUX, "L^{Q-1} and M_bwd reuse the V and H tiles");
 };
+
+// Column-major position f of a lower-triangle entry of an n x n matrix: (row, column).
+__device__ __forceinline__ void colmajor_entry(int f, int n, int &r, int &c) {
+    c = 0;
+    while (f >= n - c) {
+        f -= n - c;
+        ++c;
+    }
+    r = c + f;
+}
 
 template <int NX, int NU>
 __global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(FactorArgs a) {
     using LY = PairLayout<NX, NU>;
-    constexpr int NUX = LY::NUX, ldH = LY::ldH, ldV = LY::ldV, ldG = LY::ldG, ldT = LY::ldT, NT = LY::ntri;
+    constexpr int NUX = LY::NUX, ldH = LY::ldH, ldVr = LY::ldVr, ldG = LY::ldG, ldT = LY::ldT;
+    constexpr int NT = LY::ntri, NS = LY::slots;
     extern __shared__ __align__(16) unsigned char smem_all[];
-    // (row, column) of entry e of a lower triangle in row order, for e < NT
-    unsigned short *tab = reinterpret_cast<unsigned short *>(smem_all + (size_t)kPairItemsPerCta * LY::size * 8);
-    for (int e = threadIdx.x; e < NT; e += blockDim.x) {
-        int r, c;
-        tri_index(e, r, c);
-        tab[e] = (unsigned short)(r | (c << 8));
-    }
-    __syncthreads();
     const int team = threadIdx.x / kPairTeam, q = threadIdx.x % kPairTeam;
     const int item = blockIdx.x * kPairItemsPerCta + team;
     if (item >= a.n_items) return;   // the team leaves as a whole; only team barriers follow
@@ -645,12 +660,44 @@ __global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(F
     const int N = in.N, P = in.P, c = wi.seg;
     const int len = seg_len(c, N, P);
     const StageLayout SL(NX, NU);
+    const unsigned tmask = 0xffffu << (threadIdx.x & 16);
+    const int tbase = threadIdx.x & 16;
     double *buf = reinterpret_cast<double *>(smem_all) + (size_t)team * LY::size;
     double *H = buf + LY::oH, *V = buf + LY::oV, *G = buf + LY::oG, *Mf = buf + LY::oMf, *dinv = buf + LY::oD;
+    double *colbuf = buf + LY::oC;
     double *Lg = reinterpret_cast<double *>(a.L) + in.oL;
     double *LBg = reinterpret_cast<double *>(a.LB) + in.oLB;
     double *DIg = reinterpret_cast<double *>(a.DI) + in.oDI;
     const bool copy32 = a.Lc != nullptr;
+
+    // this thread's entries of the stage matrix: (row, column) and the raw-record
+    // offsets of R / S^T / Q and of Sigma (diagonal entries)
+    int er[NS], ec[NS], eraw[NS], esig[NS];
+    static_for<0, NS>([&](auto mc) {
+        constexpr int m = decltype(mc)::value;
+        const int f = q + kPairTeam * m;
+        int r = 0, cc = 0;
+        if (f < NT) colmajor_entry(f, NUX, r, cc);
+        er[m] = r;
+        ec[m] = cc;
+        if (r < NU) {
+            eraw[m] = SL.oR + r + cc * NU;
+            esig[m] = SL.oSu + r;
+        } else if (cc < NU) {
+            eraw[m] = SL.oS + cc + (r - NU) * NU;
+            esig[m] = -1;
+        } else {
+            eraw[m] = SL.oQ + (r - NU) + (cc - NU) * NX;
+            esig[m] = SL.oSx + r - NU;
+        }
+    });
+    // raw entry of the stage Hessian (stage_H's arithmetic: R and Q entries get
+    // Sigma on the diagonal and + 0.0 elsewhere, S entries nothing)
+    auto raw_entry = [&](int m) -> double {
+        const double v = buf[eraw[m]];
+        if (esig[m] < 0) return v;
+        return er[m] == ec[m] ? v + buf[esig[m]] : plus_zero(v);
+    };
 
     // first stage: H^ = H, B^ = B
     int s = seg_stage(c, 0, N, P);
@@ -659,14 +706,12 @@ __global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(F
     cp_async_wait_all();
     for (int e = q; e < NX * NX; e += kPairTeam) Mf[e] = 0.0;
     team_sync<kPairTeam>();
-    {
-        const StageSrc src = stage_src_smem(buf, SL);
-        for (int e = q; e < NT; e += kPairTeam) {
-            const int r = tab[e] & 0xff, cc = tab[e] >> 8;
-            H[r + cc * ldH] = stage_H(src, NU, NX, r, cc);
-        }
-        for (int e = q; e < NX * NU; e += kPairTeam) G[e % NX + (e / NX) * ldG] = src.B[e];
-    }
+    double h[NS];
+    static_for<0, NS>([&](auto mc) {
+        constexpr int m = decltype(mc)::value;
+        h[m] = (q + kPairTeam * m < NT) ? raw_entry(m) : 0.0;
+    });
+    for (int e = q; e < NX * NU; e += kPairTeam) G[e % NX + (e / NX) * ldG] = buf[SL.oB + e];
     team_sync<kPairTeam>();
 
     bool ok = true;
@@ -678,40 +723,47 @@ __global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(F
             s2 = seg_stage(c, t + 1, N, P);
             prefetch_stage<kPairTeam>(buf, SL, a.data, in, s2);   // lands while this stage is factored
         }
-        // Cholesky (team_chol's arithmetic): pivot, scaled column, rank-1 update of the
-        // trailing triangle dealt out over the team; the diagonal is written at the end
-        double myl = 0.0, myil = 0.0;
+        // Cholesky in registers (team_chol's arithmetic)
+        double myil = 0.0;
         static_for<0, NUX>([&](auto kc) {
             constexpr int k = decltype(kc)::value;
-            constexpr int m = NUX - 1 - k;
-            constexpr int T = m * (m + 1) / 2;
-            double d = H[k + k * ldH];
+            constexpr int Fk = k * NUX - k * (k - 1) / 2;               // entry (k, k)
+            constexpr int Fk1 = (k + 1) * NUX - (k + 1) * k / 2;        // first entry of column k + 1
+            double *col = colbuf + (k & 1) * NUX;
+            double d = __shfl_sync(tmask, h[Fk / kPairTeam], tbase + Fk % kPairTeam);
             if (!pos_finite_bits(d)) {
                 ok = false;
                 d = 1.0;
             }
             double l, il;
             pivot(d, l, il);
-            if (q == k) {
-                myl = l;
-                myil = il;
-            }
-            if (k + 1 + q < NUX) H[k + 1 + q + k * ldH] *= il;
-            team_sync<kPairTeam>();
-#pragma unroll
-            for (int it = 0; it < (T + kPairTeam - 1) / kPairTeam; ++it) {
-                const int e = q + kPairTeam * it;
-                if (e < T) {
-                    const int rr = (tab[e] & 0xff) + k + 1, cc = (tab[e] >> 8) + k + 1;
-                    H[rr + cc * ldH] = fma(-H[rr + k * ldH], H[cc + k * ldH], H[rr + cc * ldH]);
+            if (q == k) myil = il;
+            if (q == Fk % kPairTeam) h[Fk / kPairTeam] = l;
+            // column k below the diagonal: scale, then publish
+            static_for<(Fk + 1) / kPairTeam, (Fk1 - 1) / kPairTeam + 1>([&](auto mc) {
+                constexpr int m = decltype(mc)::value;
+                const int f = q + kPairTeam * m;
+                if (f > Fk && f < Fk1) {
+                    h[m] *= il;
+                    col[er[m]] = h[m];
                 }
-            }
+            });
             team_sync<kPairTeam>();
+            // trailing update: the entries of columns k+1.. (a suffix of the slots)
+            if constexpr (Fk1 < NT) {
+                static_for<Fk1 / kPairTeam, NS>([&](auto mc) {
+                    constexpr int m = decltype(mc)::value;
+                    const int f = q + kPairTeam * m;
+                    if (f >= Fk1 && f < NT) h[m] = fma(-col[er[m]], col[ec[m]], h[m]);
+                });
+            }
         });
-        if (q < NUX) {
-            H[q + q * ldH] = myl;
-            dinv[q] = myil;
-        }
+        // the factor into the H tile (lower triangle) and 1/diag
+        static_for<0, NS>([&](auto mc) {
+            constexpr int m = decltype(mc)::value;
+            if (q + kPairTeam * m < NT) H[er[m] + ec[m] * ldH] = h[m];
+        });
+        if (q < NUX) dinv[q] = myil;
         team_sync<kPairTeam>();
         // L^{R-1}, transposed into the upper triangle of the R block (column q of it)
         if (q < NU) {
@@ -753,7 +805,8 @@ __global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(F
                 if (copy32) a.LBc[in.oLB + (long long)s * NX * NU + e] = (float)v;
             }
             for (int e = q; e < NX * (NX + 1) / 2; e += kPairTeam) {
-                const int r = tab[e] & 0xff, cc = tab[e] >> 8;
+                int r, cc;
+                tri_index(e, r, cc);
                 double v = 0.0;
 #pragma unroll
                 for (int k = 0; k < NU; ++k) v = fma(G[r + k * ldG], G[cc + k * ldG], v);
@@ -765,8 +818,7 @@ __global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(F
             stage_zero_fill<kPairTeam>(buf, SL, a.data, in, s2);
             cp_async_wait_all();
             team_sync<kPairTeam>();   // every thread's copies have landed
-            const StageSrc src = stage_src_smem(buf, SL);
-            const double *BA = src.B;   // [B A] of stage s2, column-major, leading dimension NX
+            const double *BA = buf + SL.oB;   // [B A] of stage s2, column-major, leading dimension NX
             if (copy32 && a.BAf) {
                 float *dst = reinterpret_cast<float *>(a.BAf) + in.oBA + (long long)s2 * NX * NUX;
                 for (int e = q; e < NX * NUX; e += kPairTeam) dst[e] = (float)BA[e];
@@ -774,7 +826,7 @@ __global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(F
             // V = [B A]^T L^Q, row q: V[q][j] = sum_{k >= j} BA[k][q] L^Q[k][j]
             if (q < NUX) {
                 const double *LQ = H + NU + NU * ldH;
-                double ba[NX];
+                double ba[NX], v[NX];
                 static_for<0, NX>([&](auto kc) { ba[decltype(kc)::value] = BA[decltype(kc)::value + q * NX]; });
                 static_for<0, NX>([&](auto jc) {
                     constexpr int j = decltype(jc)::value;
@@ -783,19 +835,31 @@ __global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(F
                         constexpr int k = decltype(kc)::value;
                         acc = fma(ba[k], LQ[k + j * ldH], acc);
                     });
-                    V[q + j * ldV] = acc;
+                    v[j] = acc;
+                });
+                static_for<0, NX / 2>([&](auto jc) {
+                    constexpr int j = 2 * decltype(jc)::value;
+                    *reinterpret_cast<double2 *>(V + q * ldVr + j) = make_double2(v[j], v[j + 1]);
                 });
             }
             team_sync<kPairTeam>();
-            // H^_{s2} = H_{s2} + V V^T (lower triangle)
-            for (int e = q; e < NT; e += kPairTeam) {
-                const int r = tab[e] & 0xff, cc = tab[e] >> 8;
-                double acc = stage_H(src, NU, NX, r, cc);
-#pragma unroll
-                for (int k = 0; k < NX; ++k) acc = fma(V[r + k * ldV], V[cc + k * ldV], acc);
-                H[r + cc * ldH] = acc;
-            }
-            team_sync<kPairTeam>();
+            // H^_{s2} = H_{s2} + V V^T, this thread's entries, into registers
+            static_for<0, NS>([&](auto mc) {
+                constexpr int m = decltype(mc)::value;
+                if (q + kPairTeam * m < NT) {
+                    double acc = raw_entry(m);
+                    const double *vr = V + er[m] * ldVr, *vc = V + ec[m] * ldVr;
+                    static_for<0, NX / 2>([&](auto kc) {
+                        constexpr int k = 2 * decltype(kc)::value;
+                        const double2 x = *reinterpret_cast<const double2 *>(vr + k);
+                        const double2 y = *reinterpret_cast<const double2 *>(vc + k);
+                        acc = fma(x.x, y.x, acc);
+                        acc = fma(x.y, y.y, acc);
+                    });
+                    h[m] = acc;
+                }
+            });
+            team_sync<kPairTeam>();   // the raw record and V have been read
         } else {
             // close the segment: L^{Q-1} (one column per thread), M_bwd, coupling block
             const double *LQ = H + NU + NU * ldH;
