@@ -197,6 +197,17 @@ __device__ __forceinline__ void async_copy_f64(double *dst, const double *src, i
     for (int e = team_tid<TEAM>(); e < count; e += TEAM) cp_async8(dst + e, src + e);
 }
 
+// 16-byte asynchronous copies (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// count doubles (even), dst and src 16-byte aligned, as pairs.
+template <int TEAM>
+__device__ __forceinline__ void async_copy_f64x2(double *dst, const double *src, int count) {
+    for (int e = 2 * team_tid<TEAM>(); e < count; e += 2 * TEAM) cp_async16(dst + e, src + e);
+}
+
 // In-place lower Cholesky factor of the n x n matrix A (lower triangle read;
 // upper triangle set to zero).  Right-looking: per column a pivot, a scaled
 // column and a rank-1 update of the trailing lower triangle.  Every thread

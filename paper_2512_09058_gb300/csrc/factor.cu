@@ -608,6 +608,29 @@ __device__ __forceinline__ bool pos_finite_bits(double d) {
     return hi >= 0 && (hi | lo) != 0 && ((hi >> 20) & 0x7ff) != 0x7ff;
 }
 
+// The raw blocks of stage s as 16-byte copies: every block of the compiled
+// shapes has an even number of doubles; `pairs` says that the instance's
+// blocks start on 16-byte boundaries (else 8-byte copies).
+template <int NX, int NU>
+__device__ void prefetch_stage_pairs(double *buf, const StageLayout &L, const Data &d, const Inst &in, int s,
+                                     bool pairs) {
+    if (!pairs) {
+        prefetch_stage<kPairTeam>(buf, L, d, in, s);
+        return;
+    }
+    const int N = in.N, xq = xstate(s, N);
+    async_copy_f64x2<kPairTeam>(buf + L.oR, d.R + in.oR + (long long)s * NU * NU, NU * NU);
+    if (s != 0 && d.S) async_copy_f64x2<kPairTeam>(buf + L.oS, d.S + in.oS + (long long)s * NU * NX, NU * NX);
+    async_copy_f64x2<kPairTeam>(buf + L.oQ, d.Q + in.oQ + (long long)xq * NX * NX, NX * NX);
+    if (d.Sig) {
+        async_copy_f64x2<kPairTeam>(buf + L.oSu, d.Sig + in.oSig + (long long)s * (NU + NX), NU);
+        async_copy_f64x2<kPairTeam>(buf + L.oSx, d.Sig + in.oSig + (long long)xq * (NU + NX) + NU, NX);
+    }
+    async_copy_f64x2<kPairTeam>(buf + L.oB, d.B + in.oB + (long long)s * NX * NU, NX * NU);
+    if (s != 0) async_copy_f64x2<kPairTeam>(buf + L.oA, d.A + in.oA + (long long)s * NX * NX, NX * NX);
+    cp_async_commit();
+}
+
 // x + 0.0 without an FP64 instruction (-0 becomes +0, everything else is unchanged).
 __device__ __forceinline__ double plus_zero(double x) {
     return __double_as_longlong(x) == (long long)0x8000000000000000ULL ? 0.0 : x;
@@ -631,7 +654,7 @@ struct PairLayout {
     static constexpr int slots = (ntri + kPairTeam - 1) / kPairTeam;
     static constexpr size_t bytes = (size_t)kPairItemsPerCta * size * 8;
     static_assert(NUX <= kPairTeam, "one row of V per thread");
-    static_assert(NX % 2 == 0, "rows of V as 16-byte pairs");
+    static_assert(NX % 2 == 0 && NU % 2 == 0, "rows of V and the raw blocks as 16-byte pairs");
     static_assert(ldT * NX <= NUX * ldVr && ldT * NX <= ldH * NUX, "L^{Q-1} and M_bwd reuse the V and H tiles");
 };
 
@@ -669,6 +692,11 @@ __global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(F
     double *LBg = reinterpret_cast<double *>(a.LB) + in.oLB;
     double *DIg = reinterpret_cast<double *>(a.DI) + in.oDI;
     const bool copy32 = a.Lc != nullptr;
+    const Data &dd = a.data;
+    const bool pairs = ((reinterpret_cast<size_t>(dd.R) | reinterpret_cast<size_t>(dd.S) |
+                         reinterpret_cast<size_t>(dd.Q) | reinterpret_cast<size_t>(dd.Sig) |
+                         reinterpret_cast<size_t>(dd.B) | reinterpret_cast<size_t>(dd.A)) & 15) == 0 &&
+                       ((in.oR | in.oS | in.oQ | in.oSig | in.oB | in.oA) & 1) == 0;
 
     // this thread's entries of the stage matrix: (row, column) and the raw-record
     // offsets of R / S^T / Q and of Sigma (diagonal entries)
@@ -701,7 +729,7 @@ __global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(F
 
     // first stage: H^ = H, B^ = B
     int s = seg_stage(c, 0, N, P);
-    prefetch_stage<kPairTeam>(buf, SL, a.data, in, s);
+    prefetch_stage_pairs<NX, NU>(buf, SL, a.data, in, s, pairs);
     stage_zero_fill<kPairTeam>(buf, SL, a.data, in, s);
     cp_async_wait_all();
     for (int e = q; e < NX * NX; e += kPairTeam) Mf[e] = 0.0;
@@ -721,7 +749,7 @@ __global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(F
         int s2 = 0;
         if (!last) {
             s2 = seg_stage(c, t + 1, N, P);
-            prefetch_stage<kPairTeam>(buf, SL, a.data, in, s2);   // lands while this stage is factored
+            prefetch_stage_pairs<NX, NU>(buf, SL, a.data, in, s2, pairs);   // lands while this stage is factored
         }
         // Cholesky in registers (team_chol's arithmetic)
         double myil = 0.0;
@@ -774,20 +802,19 @@ __global__ void __launch_bounds__(kPairTeam * kPairItemsPerCta) k_factor_pairs(F
             }
         }
         team_sync<kPairTeam>();
-        {
-            double *Ls = Lg + (long long)s * NUX * NUX;
-            float *Lcs = copy32 ? a.Lc + in.oL + (long long)s * NUX * NUX : nullptr;
-            for (int e = q; e < NUX * NUX; e += kPairTeam) {
-                const int r = e % NUX, cc = e / NUX;
-                const bool keep = r >= cc || cc < NU;   // lower triangle, or L^{R-1} above the R diagonal
-                const double v = keep ? H[r + cc * ldH] : 0.0;
-                Ls[e] = v;
-                if (Lcs) Lcs[e] = keep ? (float)v : 0.0f;
-            }
-            for (int i = q; i < NUX; i += kPairTeam) {
-                DIg[(long long)s * NUX + i] = dinv[i];
-                if (copy32) a.DIc[in.oDI + (long long)s * NUX + i] = (float)dinv[i];
-            }
+        if (q < NUX) {
+            // row q of the stored factor: lower triangle, L^{R-1} above the R diagonal, zeros
+            double *Ls = Lg + (long long)s * NUX * NUX + q;
+            float *Lcs = copy32 ? a.Lc + in.oL + (long long)s * NUX * NUX + q : nullptr;
+            static_for<0, NUX>([&](auto cc_) {
+                constexpr int cc = decltype(cc_)::value;
+                const bool keep = q >= cc || cc < NU;
+                const double v = keep ? H[q + cc * ldH] : 0.0;
+                Ls[cc * NUX] = v;
+                if (Lcs) Lcs[cc * NUX] = keep ? (float)v : 0.0f;
+            });
+            DIg[(long long)s * NUX + q] = dinv[q];
+            if (copy32) a.DIc[in.oDI + (long long)s * NUX + q] = (float)dinv[q];
         }
         if (t == 0) {
             // L^B = B^ L^{R-T} (one row per thread), then M_fwd = L^B L^B^T (lower)

@@ -100,10 +100,12 @@ def test_two_items_per_warp_float64_factor_is_bitwise_the_one_warp_factor(precis
     instance) against the one-warp and multi-warp factors: the same stored
     factor bit for bit, hence the same solutions, with S, Sigma over [1e-6, 1e6],
     horizons of different lengths (1 and 2 included) side by side in one warp,
-    4 right-hand sides and float32 corrections from the factor's float32 copy."""
+    4 right-hand sides and float32 corrections from the factor's float32 copy;
+    an instance of another shape in front puts the blocks of the others at odd
+    offsets (8-byte copies instead of 16-byte ones)."""
     torch, cyq = require_gpu()
-    for nx, nu in [(12, 4), (8, 4)]:
-        dims = [(64, nx, nu)] * 9 + [(17, nx, nu), (1, nx, nu), (2, nx, nu), (40, nx, nu)]
+    for nx, nu, front in [(12, 4, []), (8, 4, []), (12, 4, [(3, 5, 3)])]:
+        dims = front + [(64, nx, nu)] * 9 + [(17, nx, nu), (1, nx, nu), (2, nx, nu), (40, nx, nu)]
         batch = ragged_batch(44 + nx, dims, sigma=(1e-6, 1e6), nrhs=4)
         data, _ = cyq.to_device(batch)
         b = torch.from_numpy(np.stack([oracle_rhs(batch, j) for j in range(4)])).cuda()
@@ -113,11 +115,12 @@ def test_two_items_per_warp_float64_factor_is_bitwise_the_one_warp_factor(precis
             s.set_launch_shapes(factor=[team] * len(s.launch_shapes()["factor"]))
             s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
             zs.append(s.solve(b, nrhs=4).cpu().numpy())
-            facs.append([s.stage_factor(i, st) for i in (0, 9, 10, 11) for st in range(batch.instances[i].N)])
+            o = len(front)
+            facs.append([s.stage_factor(i, st) for i in (o, o + 9, o + 10, o + 11) for st in range(batch.instances[i].N)])
             sts.append(s.instance_status())
             s.close()
         assert (sts[0] != 2).all()   # every factorization succeeded
         for k in (1, 2):
             assert np.array_equal(sts[0], sts[k])
-            assert np.array_equal(zs[0], zs[k]), (nx, nu, k, rel_err(zs[0], zs[k]))
-            assert all(np.array_equal(x, y) for x, y in zip(facs[0], facs[k])), (nx, nu, k)
+            assert np.array_equal(zs[0], zs[k]), (nx, nu, front, k, rel_err(zs[0], zs[k]))
+            assert all(np.array_equal(x, y) for x, y in zip(facs[0], facs[k])), (nx, nu, front, k)
