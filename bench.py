@@ -53,11 +53,10 @@ METHODS = {"fp64": ("fp64", 0), "fp64_refine": ("fp64", 3), "fp32_refine": ("fp3
 # residual kernel
 REFINE_TOL = 1e-10
 # DRAM bytes (read + write) per launch of the dominant kernel (the stage factor),
-# from one ncu capture of the current kernel (profiles/k_factor_segments_*.md);
-# absent where no capture of the current kernel exists
-NCU_TRAFFIC = {("batch1024_n64_nx12_nu4", "fp64"): 217.7e6 + 110.1e6,
-               ("batch1024_n64_nx12_nu4", "fp64_ir32"): 217.6e6 + 218.8e6,
-               ("batch1024_n64_nx12_nu4", "fp32_refine"): 217.0e6 + 88.5e6}
+# from one ncu capture of the current kernel (profiles/k_factor_*.md), keyed by
+# workload, factor precision and kernel; absent where no capture exists
+NCU_TRAFFIC = {("batch1024_n64_nx12_nu4", "fp64_ir32", "k_factor_pairs<12, 4>"): 217.1e6 + 219.5e6,
+               ("batch1024_n64_nx12_nu4", "fp32_refine", "k_factor_segments<float>"): 217.0e6 + 88.5e6}
 # workload -> methods (headline: the first one that certifies every instance),
 # CUDA-graph replay, adjoint in the step, segment counts tuned by timing
 # (cyq_tune_segments); launch shapes are always tuned by timing (cyq_autotune)
@@ -76,17 +75,29 @@ WORKLOADS = {
 }
 
 
+# Fixed segment count / launch shapes (--segments, --launch-shapes) in place of
+# the timing tuners, e.g. to reproduce a tuned configuration under a profiler,
+# whose serialised launches distort the tuners' timings.
+FIXED = {"P": 0, "shapes": None}
+
+
 def tuned_solver(torch, cyq, batch, data, b, method, tune_segments, P=None):
     """A solver for `method` with timed-autotuned segment counts (when asked, or
     the given P) and launch shapes; returns (solver, P).  Untimed setup."""
     precision, it_max = METHODS[method]
     nrhs = len(batch.rhs)
+    if P is None and FIXED["P"] > 0:
+        P = np.minimum(np.asarray(batch.N), FIXED["P"]).astype(np.int32)
     if P is None and tune_segments:
         P = cyq.tune_segments(batch.N, batch.nx, batch.nu, data, b, nrhs=nrhs, reps=2, precision=precision,
                               it_max=it_max, tol=REFINE_TOL)
     s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, max_nrhs=nrhs, it_max=it_max,
                    tol=REFINE_TOL, P_per_instance=P)
-    s.autotune(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"], b, nrhs=nrhs, reps=3)
+    if FIXED["shapes"] is not None:
+        n = len(s.launch_shapes(nrhs=nrhs)["factor"])
+        s.set_launch_shapes(factor=[FIXED["shapes"][0]] * n, sweep=[FIXED["shapes"][1]] * n, nrhs=nrhs)
+    else:
+        s.autotune(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"], b, nrhs=nrhs, reps=3)
     return s, P
 
 
@@ -102,7 +113,20 @@ def parse():
                    help="use only the first K instances of the workload (small profiling cases)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--segments", type=int, default=0, help="segments per OCP instead of the segment tuner")
+    p.add_argument("--launch-shapes", default="",
+                   help="F,S: threads per item of the factor and of the sweeps instead of the launch tuner")
     return p.parse_args()
+
+
+def factor_kernel_name(batch, r, f64):
+    """The stage-factor kernel the timed factorization launched (the roofline's kernel)."""
+    nx, nu = set(np.asarray(batch.nx).tolist()), set(np.asarray(batch.nu).tolist())
+    one_seg = int(r["segments"].max()) == 1
+    if f64 and one_seg and set(r["shapes"]["factor"]) == {16} and len(nx) == 1 and len(nu) == 1 \
+            and (nx.pop(), nu.pop()) in ((12, 4), (8, 4)):
+        return "k_factor_pairs<%d, %d>" % (int(batch.nx[0]), int(batch.nu[0]))
+    return "k_factor_segments<%s>%s" % ("double" if f64 else "float", "" if one_seg else " (+ cyclic reduction)")
 
 
 def riccati_fma_per_stage(nx, nu):
@@ -448,6 +472,9 @@ def run_e2e(torch, cyq, batch, method, steps, warmup, data, b, P=None, adjoint=F
 
 def main():
     args = parse()
+    FIXED["P"] = args.segments
+    if args.launch_shapes:
+        FIXED["shapes"] = tuple(int(v) for v in args.launch_shapes.split(","))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -573,6 +600,8 @@ def main():
     fl = 2.0 * batch_factor_fma(batch, R["segments"])
     f64 = METHODS[head][0] in ("fp64", "fp64_ir32")
     peak = FP64_PEAK_GFLOPS if f64 else FP32_PEAK_GFLOPS
+    kname = factor_kernel_name(batch, R, f64)
+    tkey = (args.workload, METHODS[head][0], kname)
     achieved = fl / (R["factor_ms"] / 1e3) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -588,12 +617,12 @@ def main():
         "max_rel_residual": R["stats"]["max_rel_residual"],
         "refine_steps": R["stats"]["refine_steps"],
         "status_ok": R["status_ok"],
-        "roofline": {"kernel": "k_factor_segments<%s> (+ cyclic reduction when P > 1)" % ("double" if f64 else "float"),
+        "roofline": {"kernel": kname,
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": NCU_TRAFFIC.get((args.workload, METHODS[head][0])),
-                     "traffic_hbm_gbs": (NCU_TRAFFIC[(args.workload, METHODS[head][0])] / (R["factor_ms"] / 1e3) / 1e9
-                                         if (args.workload, METHODS[head][0]) in NCU_TRAFFIC else None),
+                     "traffic": NCU_TRAFFIC.get(tkey),
+                     "traffic_hbm_gbs": (NCU_TRAFFIC[tkey] / (R["factor_ms"] / 1e3) / 1e9
+                                         if tkey in NCU_TRAFFIC else None),
                      "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz" if f64 else
                                      "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz")},
         "variants": variants,
