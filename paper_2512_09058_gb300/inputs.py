@@ -39,6 +39,7 @@ import numpy as np
 __all__ = [
     "OCPInstance", "Batch", "CONFIGS", "make_instance", "make_batch",
     "config_dims", "instance_dims", "blocks_to_flat", "flat_to_blocks",
+    "ALMData", "make_alm", "concat_alm",
 ]
 
 
@@ -365,3 +366,82 @@ def make_batch(cfg, indices: Optional[Sequence[int]] = None, *, instances=None, 
     return Batch(N=np.array([x.N for x in insts], np.int32), nx=np.array([x.nx for x in insts], np.int32),
                  nu=np.array([x.nu for x in insts], np.int32), Q=cat("Q"), R=cat("R"), S=cat("S"),
                  A=cat("A"), B=cat("B"), Sigma=sig, rhs=rhs, instances=insts)
+
+
+# ---------------------------------------------------------------------------
+# Augmented Lagrangian inner problem (paper Sec. 5): inequality constraints
+# b_l <= C_k x^k + D_k u^k <= b_u (k < N) and b_l <= C_N x^N <= b_u, multiplier
+# estimates y, diagonal penalties Sigma, proximal weights Gamma and centres, and
+# the current iterate (u, x).  Draws only.
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class ALMData:
+    """Flat layout per instance (float64, blocks column-major):
+        C     (N+1) blocks ny*nx    D  N blocks ny*nu
+        bl, bu, y, sig   (N+1)*ny   (box, multiplier estimate, Sigma_k diagonal)
+        gx  nx, gu  nu              (diagonals of Gamma_x^{-1}, Gamma_u^{-1})
+        xbar (N+1)*nx, ubar N*nu    (proximal centres)
+        u  N*nu, x  (N+1)*nx        (current iterate; x^0 is the fixed x_init)
+    A batch concatenates the arrays of each kind in instance order (ny may
+    differ between instances)."""
+    ny: object
+    C: np.ndarray
+    D: np.ndarray
+    bl: np.ndarray
+    bu: np.ndarray
+    y: np.ndarray
+    sig: np.ndarray
+    gx: np.ndarray
+    gu: np.ndarray
+    xbar: np.ndarray
+    ubar: np.ndarray
+    u: np.ndarray
+    x: np.ndarray
+
+
+def make_alm(inst: OCPInstance, ny: int, seed: int, index: int = 0, bounds: str = "mixed",
+             sigma=(1e-2, 1e4)) -> ALMData:
+    """Constraint data and an iterate for one instance.  C ~ N(0, 1/nx) and
+    D ~ N(0, 1/nu) entries, iterate u, x ~ N(0, 1), y ~ 0.1 N(0, 1), Sigma
+    log-uniform in `sigma`, Gamma^{-1} diagonals log-uniform in [1e-3, 1e-1],
+    centres = iterate + 0.1 N(0, 1).  Bounds: "mixed" draws a box around
+    [-1, 1] (each row's interval jittered), so that some rows are active and
+    some not; "inactive" uses [-1e6, 1e6]; "fixed" alternates rows that stay
+    inactive ([-1e6, 1e6]) and rows that are active on either side of a box
+    far from the origin ([1e3, 2e3] or [-2e3, -1e3]); with penalties small
+    against the cost's curvature a Newton step keeps that active set."""
+    N, nx, nu = inst.N, inst.nx, inst.nu
+    g = np.random.Generator(np.random.PCG64([seed, 7, index]))
+    C = g.standard_normal((N + 1, ny, nx)) / np.sqrt(nx)
+    D = g.standard_normal((N, ny, nu)) / np.sqrt(nu)
+    u = g.standard_normal(N * nu)
+    x = g.standard_normal((N + 1) * nx)
+    y = 0.1 * g.standard_normal((N + 1) * ny)
+    lo, hi = sigma
+    sig = 10.0 ** g.uniform(np.log10(lo), np.log10(hi), size=(N + 1) * ny)
+    gx = 10.0 ** g.uniform(-3.0, -1.0, size=nx)
+    gu = 10.0 ** g.uniform(-3.0, -1.0, size=nu)
+    xbar = x + 0.1 * g.standard_normal(x.shape)
+    ubar = u + 0.1 * g.standard_normal(u.shape)
+    m = (N + 1) * ny
+    if bounds == "mixed":
+        bl = -1.0 + 0.5 * g.standard_normal(m)
+        bu = bl + 2.0 * g.uniform(0.5, 1.5, size=m)
+    elif bounds == "inactive":
+        bl, bu = np.full(m, -1e6), np.full(m, 1e6)
+    elif bounds == "fixed":
+        row = np.arange(m) % ny
+        side = g.choice([-1.0, 1.0], size=m)
+        bl = np.where(row % 2 == 0, -1e6, np.where(side > 0, 1e3, -2e3))
+        bu = np.where(row % 2 == 0, 1e6, np.where(side > 0, 2e3, -1e3))
+    else:
+        raise ValueError(bounds)
+    return ALMData(ny=ny, C=blocks_to_flat(C), D=blocks_to_flat(D), bl=bl, bu=bu, y=y, sig=sig, gx=gx, gu=gu,
+                   xbar=xbar, ubar=ubar, u=u, x=x)
+
+
+def concat_alm(items: Sequence[ALMData]) -> ALMData:
+    """Batch layout: each kind concatenated in instance order; ny becomes an int32 array."""
+    cat = lambda k: np.concatenate([getattr(a, k) for a in items])
+    return ALMData(ny=np.array([a.ny for a in items], np.int32), **{k: cat(k) for k in (
+        "C", "D", "bl", "bu", "y", "sig", "gx", "gu", "xbar", "ubar", "u", "x")})
