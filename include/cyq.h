@@ -292,6 +292,59 @@ cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu, const dou
                                     const double *S, const double *A, const double *B, const double *Sigma,
                                     const double *b, double *z, int32_t *status, cyq_stream stream);
 
+/*
+ * Newton system of the augmented Lagrangian inner problem (Sec. 5, eqs.
+ * ocp-al, ocp-al-funcs, qpalm-ocp-hessians, newton-sys-with-x0, elim-x0).
+ *
+ * The QP adds to the OCP the constraints bl <= C_k x^k + D_k u^k <= bu
+ * (0 <= k < N) and bl <= C_N x^N <= bu, relaxed with multiplier estimates y,
+ * diagonal penalties Sigma_k and proximal terms (1/2)|x - xbar|^2 in the
+ * Gamma_x^{-1} norm and (1/2)|u - ubar|^2 in the Gamma_u^{-1} norm.  At the
+ * iterate (u, x), x^0 = x_init, stage k's rows w = C_k x^k + D_k u^k are active
+ * where w + Sigma_k^{-1} y^k lies outside [bl, bu]; Sigma^J is Sigma on the
+ * active rows and 0 elsewhere, y^ = y + Sigma (w - Pi(w + Sigma^{-1} y; [bl, bu])),
+ * and the call writes
+ *   Q~_k = Q_k + C_k^T Sigma^J C_k + Gamma_x^{-1}      (k = 0..N)
+ *   R~_k = R_k + D_k^T Sigma^J D_k + Gamma_u^{-1},  S~_k = S_k + D_k^T Sigma^J C_k
+ *   r~_k = R_k u^k + S_k x^k + r_k + D_k^T y^_k + Gamma_u^{-1}(u^k - ubar^k)
+ *   q~_k = Q_k x^k + S_k^T u^k + q_k + C_k^T y^_k + Gamma_x^{-1}(x^k - xbar^k)
+ *          (no S term at k = N)
+ *   c~_k = B_k u^k + A_k x^k + f_k - x^{k+1}
+ * in the data layout of the OCP, so that the Newton step (du, dx, lambda) is
+ * cyq_factor(Q~, R~, S~, A, B, Sigma = NULL) and cyq_solve of
+ * cyq_build_rhs(q~, r~, c~, x_init = 0) (dx^0 = 0).
+ *
+ * Layout (device float64 unless noted; per instance, instances concatenated
+ * kind by kind; blocks column-major): C (N+1) blocks ny x nx, D N blocks
+ * ny x nu, bl / bu / y / sigma (N+1) ny, gx nx and gu nu (diagonals of
+ * Gamma_x^{-1} and Gamma_u^{-1}; NULL: no proximal term, then xbar / ubar are
+ * not read), xbar (N+1) nx, ubar N nu; u N nu, x (N+1) nx (x^0 not read);
+ * q, r, c (= f), x_init as for cyq_build_rhs.  ny is a HOST array [batch]
+ * (rows per stage, >= 1).  Outputs: Q, R, S as the data, q (N+1) nx, r N nu,
+ * c N nx, active (int32, 1 = active; may be NULL) and yhat (may be NULL)
+ * (N+1) ny.  Every input pointer other than S, gx, gu, xbar, ubar must be
+ * non-NULL, as must the six block and vector outputs; the outputs must not
+ * overlap the inputs.  The handle supplies the dimensions (no factorization
+ * needed); asynchronous on `stream`.
+ * Errors: INVALID_ARG (null pointer, ny < 1, N + 1 > 65535, a stage's
+ * [D C] rows too large for shared memory), CUDA.
+ */
+typedef struct cyq_newton_in {
+    const double *Q, *R, *S, *A, *B;
+    const double *q, *r, *c, *x_init;
+    const double *u, *x;
+    const int32_t *ny;
+    const double *C, *D, *bl, *bu, *y, *sigma;
+    const double *gx, *gu, *xbar, *ubar;
+} cyq_newton_in;
+typedef struct cyq_newton_out {
+    double *Q, *R, *S, *q, *r, *c;
+    int32_t *active;
+    double *yhat;
+} cyq_newton_out;
+cyq_status cyq_assemble_newton(cyq_handle h, const cyq_newton_in *in, const cyq_newton_out *out,
+                               cyq_stream stream);
+
 const char *cyq_status_string(cyq_status s);
 /* Text of the last CUDA error seen by this thread's calls ("" if none). */
 const char *cyq_last_error(void);

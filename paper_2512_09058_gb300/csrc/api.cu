@@ -103,6 +103,11 @@ struct cyq_handle_s {
     bool factored = false;
     long long launches = 0;
     int last_nrhs = 0;
+    // Newton-system assembly: constraint rows per instance and the offsets they imply
+    std::vector<int> alm_ny;
+    std::vector<AlmOff> alm_off;
+    AlmOff *d_alm_off = nullptr;
+    size_t alm_smem = 0;
 };
 
 namespace {
@@ -715,6 +720,63 @@ cyq_status cyq_build_rhs(cyq_handle h, const double *q, const double *r, const d
     if (!h->factored) return CYQ_ERR_NO_FACTOR;
     DeviceGuard guard(h->device);
     CYQ_CUDA(launch_build_rhs(h->d_inst, h->batch, h->data, q, r, c, x_init, b, h->kkt, to_stream(stream)));
+    return CYQ_OK;
+}
+
+cyq_status cyq_assemble_newton(cyq_handle h, const cyq_newton_in *in, const cyq_newton_out *out,
+                               cyq_stream stream) {
+    if (!h || !in || !out || !in->ny) return CYQ_ERR_INVALID_ARG;
+    if (!in->Q || !in->R || !in->A || !in->B || !in->q || !in->r || !in->c || !in->x_init || !in->u || !in->x ||
+        !in->C || !in->D || !in->bl || !in->bu || !in->y || !in->sigma)
+        return CYQ_ERR_INVALID_ARG;
+    if ((in->gx && !in->xbar) || (in->gu && !in->ubar)) return CYQ_ERR_INVALID_ARG;
+    if (!out->Q || !out->R || !out->S || !out->q || !out->r || !out->c) return CYQ_ERR_INVALID_ARG;
+    DeviceGuard guard(h->device);
+    cudaStream_t st = to_stream(stream);
+    const std::vector<int> ny(in->ny, in->ny + h->batch);
+    int max_stages = 0;
+    for (int i = 0; i < h->batch; ++i) {
+        if (ny[i] < 1) return CYQ_ERR_INVALID_ARG;
+        max_stages = std::max(max_stages, h->inst[i].N + 1);
+    }
+    if (max_stages > 65535) return CYQ_ERR_INVALID_ARG;
+    if (ny != h->alm_ny) {
+        // offsets of the constraint arrays, uploaded once per distinct ny
+        std::vector<AlmOff> off(h->batch);
+        long long oC = 0, oD = 0, oY = 0, ogx = 0, ogu = 0;
+        size_t smem = 0;
+        for (int i = 0; i < h->batch; ++i) {
+            const Inst &n = h->inst[i];
+            off[i] = AlmOff{oC, oD, oY, ogx, ogu, ny[i], 0};
+            oC += (long long)(n.N + 1) * ny[i] * n.nx;
+            oD += (long long)n.N * ny[i] * n.nu;
+            oY += (long long)(n.N + 1) * ny[i];
+            ogx += n.nx;
+            ogu += n.nu;
+            smem = std::max(smem, newton_smem_bytes(ny[i], n.nx, n.nu));
+        }
+        if (smem > (size_t)h->smem_optin) {
+            g_last_error = "constraint rows of a stage too large for shared memory";
+            return CYQ_ERR_INVALID_ARG;
+        }
+        if (!h->d_alm_off) CYQ_CUDA(h->mem.alloc(&h->d_alm_off, (size_t)h->batch));
+        CYQ_CUDA(cudaStreamSynchronize(st));   // the previous table may still be read
+        h->alm_off = off;
+        CYQ_CUDA(cudaMemcpy(h->d_alm_off, h->alm_off.data(), sizeof(AlmOff) * h->batch, cudaMemcpyHostToDevice));
+        h->alm_ny = ny;
+        h->alm_smem = smem;
+    }
+    NewtonArgs a{};
+    a.inst = h->d_inst;
+    a.off = h->d_alm_off;
+    a.Q = in->Q; a.R = in->R; a.S = in->S; a.A = in->A; a.B = in->B;
+    a.q = in->q; a.r = in->r; a.f = in->c; a.x0 = in->x_init; a.u = in->u; a.x = in->x;
+    a.C = in->C; a.D = in->D; a.bl = in->bl; a.bu = in->bu; a.y = in->y; a.sig = in->sigma;
+    a.gx = in->gx; a.gu = in->gu; a.xbar = in->xbar; a.ubar = in->ubar;
+    a.Qo = out->Q; a.Ro = out->R; a.So = out->S; a.qo = out->q; a.ro = out->r; a.co = out->c;
+    a.active = out->active; a.yhat = out->yhat;
+    CYQ_CUDA(launch_newton_assemble(a, h->batch, max_stages, h->alm_smem, st));
+    ++h->launches;
     return CYQ_OK;
 }
 

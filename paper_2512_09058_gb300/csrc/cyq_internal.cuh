@@ -440,6 +440,23 @@ cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st);
 cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
                                   int *steps, int step, bool keep_bb, cudaStream_t st);
 cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, cudaStream_t st);
+// Newton-system assembly of the augmented Lagrangian inner problem (newton.cu).
+struct AlmOff {
+    long long oC, oD, oY;   // offsets of C, D and the per-row vectors (bl, bu, y, sigma, active, y^)
+    long long ogx, ogu;     // offsets of the Gamma^{-1} diagonals
+    int ny, pad;
+};
+struct NewtonArgs {
+    const Inst *inst;
+    const AlmOff *off;
+    const double *Q, *R, *S, *A, *B, *q, *r, *f, *x0, *u, *x;
+    const double *C, *D, *bl, *bu, *y, *sig, *gx, *gu, *xbar, *ubar;
+    double *Qo, *Ro, *So, *qo, *ro, *co, *yhat;
+    int *active;
+};
+size_t newton_smem_bytes(int ny, int nx, int nu);
+cudaError_t launch_newton_assemble(const NewtonArgs &a, int batch, int max_stages, size_t smem, cudaStream_t st);
+
 cudaError_t launch_build_rhs(const Inst *inst, int batch, const Data &d, const double *q, const double *r,
                              const double *c, const double *x0, double *b, long long kkt, cudaStream_t st);
 cudaError_t launch_adjoint(const GradArgs &g, int n_chunks, int batch, const Data &d, double *dx0, cudaStream_t st);

@@ -27,7 +27,7 @@ EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rh
            "cyq_solve_adjoint", "cyq_get_instance_status", "cyq_get_stats", "cyq_kkt_size",
            "cyq_get_segments", "cyq_last_launch_count", "cyq_status_string", "cyq_last_error",
            "cyq_factor_solve_noalloc", "cyq_autotune", "cyq_get_launch_shapes", "cyq_tune_segments",
-           "cyq_set_launch_shapes", "cyq_get_stage_factor"]
+           "cyq_set_launch_shapes", "cyq_get_stage_factor", "cyq_assemble_newton"]
 
 
 class CyqError(RuntimeError):
@@ -48,6 +48,16 @@ class cyq_desc(ctypes.Structure):
 class cyq_stats(ctypes.Structure):
     _fields_ = [("refine_steps", ctypes.c_int32), ("max_rel_residual", ctypes.c_double),
                 ("P_min", ctypes.c_int32), ("P_max", ctypes.c_int32), ("work_items", ctypes.c_int64)]
+
+
+class cyq_newton_in(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("Q", "R", "S", "A", "B", "q", "r", "c", "x_init", "u", "x")] + \
+               [("ny", ctypes.POINTER(ctypes.c_int32))] + \
+               [(n, ctypes.c_void_p) for n in ("C", "D", "bl", "bu", "y", "sigma", "gx", "gu", "xbar", "ubar")]
+
+
+class cyq_newton_out(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("Q", "R", "S", "q", "r", "c", "active", "yhat")]
 
 
 _lib = None
@@ -88,6 +98,7 @@ def load(path: str = LIB_PATH):
     L.cyq_tune_segments.argtypes = [ctypes.POINTER(cyq_desc)] + [vp] * 6 + [vp, vp, i32, i32, vp, pi32]
     L.cyq_set_launch_shapes.argtypes = [vp, pi32, pi32, i32]
     L.cyq_get_stage_factor.argtypes = [vp, i32, i32, ctypes.POINTER(d)]
+    L.cyq_assemble_newton.argtypes = [vp, ctypes.POINTER(cyq_newton_in), ctypes.POINTER(cyq_newton_out), vp]
     for name in ["cyq_create", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual", "cyq_solve_adjoint",
                  "cyq_get_instance_status", "cyq_get_stats", "cyq_get_segments", "cyq_autotune",
                  "cyq_get_launch_shapes", "cyq_tune_segments", "cyq_set_launch_shapes",
@@ -248,6 +259,32 @@ class Solver:
             b = torch.empty(self.kkt_size, dtype=torch.float64, device=q.device)
         _check(_lib.cyq_build_rhs(self._h, _ptr(q), _ptr(r), _ptr(c), _ptr(x0), _ptr(b), _stream(stream)))
         return b
+
+    def assemble_newton(self, data, q, r, c, x_init, u, x, alm, out=None, stream=None):
+        """Newton system of the augmented Lagrangian inner problem at (u, x):
+        returns dict(Q, R, S, q, r, c, active, yhat) of device tensors in the data
+        layout (see cyq_assemble_newton).  `data`: dict of device Q, R, S, A, B;
+        `alm`: dict of device C, D, bl, bu, y, sigma and optional gx, gu, xbar,
+        ubar, plus `ny` (host int32 array [batch])."""
+        import torch
+        dev = q.device
+        ny = np.ascontiguousarray(alm["ny"], dtype=np.int32)
+        N, nx, nu = self.N.astype(np.int64), self.nx.astype(np.int64), self.nu.astype(np.int64)
+        if out is None:
+            f64 = lambda n: torch.empty(int(n), dtype=torch.float64, device=dev)
+            out = dict(Q=f64(((N + 1) * nx * nx).sum()), R=f64((N * nu * nu).sum()), S=f64((N * nu * nx).sum()),
+                       q=f64(((N + 1) * nx).sum()), r=f64((N * nu).sum()), c=f64((N * nx).sum()),
+                       active=torch.empty(int(((N + 1) * ny).sum()), dtype=torch.int32, device=dev),
+                       yhat=f64(((N + 1) * ny).sum()))
+        g = lambda k: _ptr(alm.get(k))
+        a = cyq_newton_in(Q=_ptr(data["Q"]), R=_ptr(data["R"]), S=_ptr(data.get("S")), A=_ptr(data["A"]),
+                          B=_ptr(data["B"]), q=_ptr(q), r=_ptr(r), c=_ptr(c), x_init=_ptr(x_init), u=_ptr(u),
+                          x=_ptr(x), ny=ny.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), C=g("C"), D=g("D"),
+                          bl=g("bl"), bu=g("bu"), y=g("y"), sigma=g("sigma"), gx=g("gx"), gu=g("gu"),
+                          xbar=g("xbar"), ubar=g("ubar"))
+        o = cyq_newton_out(**{k: _ptr(out.get(k)) for k in ("Q", "R", "S", "q", "r", "c", "active", "yhat")})
+        _check(_lib.cyq_assemble_newton(self._h, ctypes.byref(a), ctypes.byref(o), _stream(stream)))
+        return out
 
     def residual(self, b, z, res=None, stream=None):
         import torch
