@@ -72,6 +72,9 @@ WORKLOADS = {
     "adjoint512_n128_nx24_nu8": dict(methods=["fp64_refine"], graph=False, adjoint=True, tune_segments=True),
     "massspring150_M18_N96": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=True, adjoint=False,
                                   tune_segments=True),
+    # step = Newton-system assembly + factor + solve of the augmented Lagrangian inner problem
+    "newton1024_n64_nx12_nu4_ny16": dict(methods=["fp64_ir32", "fp64_refine", "fp32_refine"], graph=False,
+                                         adjoint=False, tune_segments=True, newton=True),
 }
 
 
@@ -320,11 +323,34 @@ def _loss_grad(torch, batch, z):
 L2_BYTES = 129e6
 
 
+def newton_setup(torch, cyq, batch, data, rhs_dev, indices, cfg):
+    """Newton workload: the constraint data and iterate on the device, the assembled
+    blocks (which the timing tuners factor) and the Newton system's right-hand side."""
+    alms = inputs.config_alm(cfg, batch.instances, indices)
+    cat = inputs.concat_alm(alms)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    alm = {k: t(getattr(cat, k)) for k in ("C", "D", "bl", "bu", "y", "gx", "gu", "xbar", "ubar")}
+    alm["sigma"], alm["ny"] = t(cat.sig), cat.ny
+    q, r, c, x0 = rhs_dev[0]
+    ctx = dict(data=data, q=q, r=r, c=c, x0=x0, u=t(cat.u), x=t(cat.x), alm=alm, zero=torch.zeros_like(x0))
+    s0 = cyq.Solver(batch.N, batch.nx, batch.nu, it_max=0)
+    ctx["out"] = s0.assemble_newton(data, q, r, c, x0, ctx["u"], ctx["x"], alm)
+    out = ctx["out"]
+    ndata = dict(Q=out["Q"], R=out["R"], S=out["S"], A=data["A"], B=data["B"], Sigma=None)
+    s0.factor(ndata["Q"], ndata["R"], ndata["S"], ndata["A"], ndata["B"], None)
+    b = s0.build_rhs(out["q"], out["r"], out["c"], ctx["zero"])
+    torch.cuda.synchronize()
+    s0.close()
+    return ctx, ndata, b
+
+
 def run_method(torch, cyq, batch, data, b, x0, method, steps, warmup, dist, graph=False, adjoint=False,
-               flush=None, tune_segments=False):
+               flush=None, tune_segments=False, newton=None):
     """Time `steps` factor+solve steps.  With `flush` (a device buffer larger than
     L2), the buffer is rewritten between steps, outside the per-step events, and
-    the step time is the sum of the per-step event intervals."""
+    the step time is the sum of the per-step event intervals.  With `newton`
+    (newton_setup's context) the factor part starts with the Newton-system
+    assembly and the solve part with building its right-hand side."""
     precision, it_max = METHODS[method]
     nrhs = len(batch.rhs)
     s, P = tuned_solver(torch, cyq, batch, data, b, method, tune_segments)
@@ -333,18 +359,25 @@ def run_method(torch, cyq, batch, data, b, x0, method, steps, warmup, dist, grap
     mask = _loss_grad(torch, batch, torch.ones_like(b[:s.kkt_size])) / 2.0 if adjoint else None
 
     def factor():
+        if newton is not None:
+            n = newton
+            s.assemble_newton(n["data"], n["q"], n["r"], n["c"], n["x0"], n["u"], n["x"], n["alm"], out=n["out"])
         s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
 
     def solve():
+        if newton is not None:
+            o = newton["out"]
+            s.build_rhs(o["q"], o["r"], o["c"], newton["zero"], b=b)
         s.solve(b, z, nrhs=nrhs)
         if adjoint:
             g = 2.0 * z[:s.kkt_size] * mask
             s.solve_adjoint(x0, z[:s.kkt_size], g)
 
     factor()
-    launches_factor = s.launch_count()
-    s.solve(b, z, nrhs=nrhs)
-    launches_solve = s.launch_count() + (1 + 2 * 3 + 1 if adjoint else 0)   # adjoint: solve + grads
+    launches_factor = s.launch_count() + (1 if newton is not None else 0)   # + the assembly
+    solve()
+    launches_solve = s.launch_count() + (1 if newton is not None else 0)     # + building b
+    launches_solve += (1 + 2 * 3 + 1 if adjoint else 0)   # adjoint: solve + grads
     for _ in range(warmup):
         factor()
         solve()
@@ -485,6 +518,10 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
+        if "alm" in cfg:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the LQ KKT workloads; "
+                              "the Newton-step workload has no oracle timing"}))
+            return 0
         n = cfg["batch"]
         nrhs = int(cfg["nrhs"])
         dims = inputs.config_dims(cfg, batch=n)
@@ -545,6 +582,10 @@ def main():
     torch.cuda.synchronize()
     s0.close()
     x0 = rhs_dev[0][3]
+    newton = None
+    if prof.get("newton"):
+        # the Newton system's blocks replace the OCP data in the timing tuners and the residual
+        newton, data, b = newton_setup(torch, cyq, batch, data, rhs_dev, shard.shard_indices(n, rank), cfg)
 
     methods = [m for m in (args.methods.split(",") if args.methods else prof["methods"]) if m]
     sbytes = (batch.Q.nbytes + batch.R.nbytes + batch.S.nbytes + batch.A.nbytes + batch.B.nbytes
@@ -554,7 +595,7 @@ def main():
     clocks.start()
     results = {m: run_method(torch, cyq, batch, data, b, x0, m, args.steps, args.warmup, dist,
                              graph=prof["graph"], adjoint=prof["adjoint"], flush=flush,
-                             tune_segments=prof["tune_segments"]) for m in methods}
+                             tune_segments=prof["tune_segments"], newton=newton) for m in methods}
     clk = clocks.stop()
     # headline: the first listed method that solved every instance to the tolerance
     head = next((m for m in methods if results[m]["status_ok"]), methods[0])
@@ -563,7 +604,7 @@ def main():
     value = shard.job_throughput(batch.size, world, ms)
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and newton is None:
         e2e_ms, h2d, d2h = run_e2e(torch, cyq, batch, head, max(3, args.steps // 4), args.warmup, data, b,
                                    P=R["P"], adjoint=prof["adjoint"])
         e2e_ms = shard.reduce_time_ms(e2e_ms, dist, device="cuda")
@@ -571,7 +612,7 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and newton is None:
         rate1, done1, el1 = time_oracle(batch, nrhs, budget_s=3.0)
         rate, done, cores = time_oracle_all_cores(args.workload, batch.size, nrhs, budget_s=2.0)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -15,9 +15,11 @@
 // initial state.
 //
 // One warp per (instance, stage): the stage's [D C] rows and the iterate are
-// staged in shared memory, each lane owns rows of the constraint block, then
-// entries of the Hessian blocks (sums over the active rows only, a loop that
-// is uniform across the warp), then entries of the gradient vectors.
+// staged in shared memory; each lane owns rows of the constraint block (active
+// flag, y^, and the row scaled by Sigma^J), then entries of the lower triangle
+// of the Hessian blocks (sums over the compacted list of active rows, a loop
+// that is uniform across the warp), then one gradient or residual row each, all
+// rows written as one dot product over (u; x; y^) so that the lanes share a loop.
 #include "cyq_internal.cuh"
 
 namespace cyq {
@@ -33,8 +35,9 @@ __global__ void __launch_bounds__(32) k_newton_assemble(NewtonArgs a) {
     if (k > N) return;
     const bool hasu = k < N;
     const int nux = nx + nu;
-    // shared: V = [D C] (ny x nux, column-major), z = (u; x), y^, Sigma^J
-    double *V = sm, *z = V + (size_t)ny * nux, *yh = z + nux, *sJ = yh + ny;
+    // shared: V = [D C] (ny x nux, column-major), W = Sigma^J V, z = (u; x), y^, zeros
+    double *V = sm, *W = V + (size_t)ny * nux, *z = W + (size_t)ny * nux, *yh = z + nux, *zr = yh + ny;
+    int *act = reinterpret_cast<int *>(zr + ny);   // active rows, compacted
     const double *Ck = a.C + ao.oC + (long long)k * ny * nx;
     const double *Dk = hasu ? a.D + ao.oD + (long long)k * ny * nu : nullptr;
     for (int e = lane; e < ny * nux; e += 32) {
@@ -44,106 +47,125 @@ __global__ void __launch_bounds__(32) k_newton_assemble(NewtonArgs a) {
     const double *xk = k == 0 ? a.x0 + in.ox0 : a.x + in.oq + (long long)k * nx;
     for (int j = lane; j < nu; j += 32) z[j] = hasu ? a.u[in.orv + (long long)k * nu + j] : 0.0;
     for (int j = lane; j < nx; j += 32) z[nu + j] = xk[j];
+    for (int i = lane; i < ny; i += 32) zr[i] = 0.0;
     __syncwarp();
-    // constraint rows: active set and multiplier estimate
+    // constraint rows: w = C x + D u; the row is active where w + y / Sigma leaves
+    // [bl, bu], i.e. (Sigma > 0) where Sigma w + y leaves [Sigma bl, Sigma bu]; then
+    // y^ = y + Sigma (w - bound), and y^ = 0 on inactive rows (Pi is the identity there)
     const long long oy = ao.oY + (long long)k * ny;
-    for (int i = lane; i < ny; i += 32) {
-        double cx = 0.0, du = 0.0;
-        for (int j = 0; j < nx; ++j) cx = fma(V[i + (nu + j) * ny], z[nu + j], cx);
-        for (int j = 0; j < nu; ++j) du = fma(V[i + j * ny], z[j], du);
-        const double w = cx + du;
-        const double y = a.y[oy + i], sg = a.sig[oy + i], bl = a.bl[oy + i], bu = a.bu[oy + i];
-        const double zz = w + y / sg;
-        const bool act = zz < bl || zz > bu;
-        const double pr = fmin(fmax(zz, bl), bu);
-        const double yhat = y + sg * (w - pr);
-        yh[i] = yhat;
-        sJ[i] = act ? sg : 0.0;
-        if (a.active) a.active[oy + i] = act ? 1 : 0;
-        if (a.yhat) a.yhat[oy + i] = yhat;
+    int n_act = 0;
+    for (int i0 = 0; i0 < ny; i0 += 32) {
+        const int i = i0 + lane;
+        bool on = false;
+        if (i < ny) {
+            double cx = 0.0, du = 0.0;
+            for (int j = 0; j < nx; ++j) cx = fma(V[i + (nu + j) * ny], z[nu + j], cx);
+            for (int j = 0; j < nu; ++j) du = fma(V[i + j * ny], z[j], du);
+            const double w = cx + du;
+            const double y = a.y[oy + i], sg = a.sig[oy + i], bl = a.bl[oy + i], bu = a.bu[oy + i];
+            const double t = fma(sg, w, y);
+            const bool lo = t < sg * bl, hi = t > sg * bu;
+            on = lo || hi;
+            const double yhat = lo ? fma(sg, w - bl, y) : (hi ? fma(sg, w - bu, y) : 0.0);
+            yh[i] = yhat;
+            for (int c = 0; c < nux; ++c) W[i + c * ny] = on ? sg * V[i + c * ny] : 0.0;
+            if (a.active) a.active[oy + i] = on ? 1 : 0;
+            if (a.yhat) a.yhat[oy + i] = yhat;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, on);
+        if (on) act[n_act + __popc(m & ((1u << lane) - 1u))] = i;
+        n_act += __popc(m);
     }
     __syncwarp();
     const double *gx = a.gx ? a.gx + ao.ogx : nullptr, *gu = a.gu ? a.gu + ao.ogu : nullptr;
-    // Hessian blocks: entry (p, q) of [R S; S^T Q] in the (u; x) numbering
+    // Hessian blocks: lower triangle of [R S; S^T Q] in the (u; x) numbering, R and Q mirrored
     const double *Qk = a.Q + in.oQ + (long long)k * nx * nx;
     double *Qo = a.Qo + in.oQ + (long long)k * nx * nx;
-    const int nR = hasu ? nu * nu : 0, nS = hasu ? nu * nx : 0, total = nR + nS + nx * nx;
-    for (int e = lane; e < total; e += 32) {
+    const double *Rk = hasu ? a.R + in.oR + (long long)k * nu * nu : nullptr;
+    double *Ro = hasu ? a.Ro + in.oR + (long long)k * nu * nu : nullptr;
+    const double *Sk = (hasu && a.S) ? a.S + in.oS + (long long)k * nu * nx : nullptr;
+    double *So = hasu ? a.So + in.oS + (long long)k * nu * nx : nullptr;
+    // (the last stage has no u rows: only the Q block)
+    const int ntri = hasu ? nux * (nux + 1) / 2 : nx * (nx + 1) / 2, shift = hasu ? 0 : nu;
+    for (int e = lane; e < ntri; e += 32) {
         int p, q;
-        double base;
-        double *dst;
-        if (e < nR) {
-            p = e % nu;
-            q = e / nu;
-            base = a.R[in.oR + (long long)k * nu * nu + e] + ((p == q && gu) ? gu[p] : 0.0);
-            dst = a.Ro + in.oR + (long long)k * nu * nu + e;
-        } else if (e < nR + nS) {
-            const int f = e - nR;
-            p = f % nu;
-            q = nu + f / nu;
-            base = a.S ? a.S[in.oS + (long long)k * nu * nx + f] : 0.0;
-            dst = a.So + in.oS + (long long)k * nu * nx + f;
-        } else {
-            const int f = e - nR - nS;
-            p = nu + f % nx;
-            q = nu + f / nx;
-            base = Qk[f] + ((p == q && gx) ? gx[p - nu] : 0.0);
-            dst = Qo + f;
-        }
+        tri_index(e, p, q);
+        p += shift;
+        q += shift;
         double acc = 0.0;
-        for (int i = 0; i < ny; ++i) {
-            const double s = sJ[i];
-            if (s != 0.0) acc = fma(s * V[i + p * ny], V[i + q * ny], acc);
+        for (int j = 0; j < n_act; ++j) {
+            const int i = act[j];
+            acc = fma(W[i + p * ny], V[i + q * ny], acc);
         }
-        *dst = base + acc;
-    }
-    // gradient rows
-    if (hasu) {
-        const double *Rk = a.R + in.oR + (long long)k * nu * nu;
-        const double *Sk = a.S ? a.S + in.oS + (long long)k * nu * nx : nullptr;
-        for (int p = lane; p < nu; p += 32) {
-            double g = 0.0;
-            for (int j = 0; j < nu; ++j) g = fma(Rk[p + j * nu], z[j], g);
-            if (Sk)
-                for (int j = 0; j < nx; ++j) g = fma(Sk[p + j * nu], z[nu + j], g);
-            double cy = 0.0;
-            for (int i = 0; i < ny; ++i) cy = fma(V[i + p * ny], yh[i], cy);
-            g = g + a.r[in.orv + (long long)k * nu + p] + cy;
-            if (gu) g = fma(gu[p], z[p] - a.ubar[in.orv + (long long)k * nu + p], g);
-            a.ro[in.orv + (long long)k * nu + p] = g;
+        if (p < nu) {
+            const double v = Rk[p + q * nu] + ((p == q && gu) ? gu[p] : 0.0) + acc;
+            Ro[p + q * nu] = v;
+            Ro[q + p * nu] = v;
+        } else if (q < nu) {
+            So[q + (p - nu) * nu] = (Sk ? Sk[q + (p - nu) * nu] : 0.0) + acc;
+        } else {
+            const int pp = p - nu, qq = q - nu;
+            const double v = Qk[pp + qq * nx] + ((pp == qq && gx) ? gx[pp] : 0.0) + acc;
+            Qo[pp + qq * nx] = v;
+            Qo[qq + pp * nx] = v;
         }
     }
-    {
-        const double *Sk = (hasu && a.S) ? a.S + in.oS + (long long)k * nu * nx : nullptr;
-        for (int p = lane; p < nx; p += 32) {
-            double g = 0.0;
-            for (int j = 0; j < nx; ++j) g = fma(Qk[p + j * nx], z[nu + j], g);
-            if (Sk)
-                for (int j = 0; j < nu; ++j) g = fma(Sk[j + p * nu], z[j], g);
-            double cy = 0.0;
-            for (int i = 0; i < ny; ++i) cy = fma(V[i + (nu + p) * ny], yh[i], cy);
-            g = g + a.q[in.oq + (long long)k * nx + p] + cy;
-            if (gx) g = fma(gx[p], z[nu + p] - a.xbar[in.oq + (long long)k * nx + p], g);
-            a.qo[in.oq + (long long)k * nx + p] = g;
+    // gradient and residual rows as one product [coefficients] . (u; x; y^) per row:
+    //   r~_p: (R row p, S row p, D column p),  q~_p: (S column p, Q row p, C column p),
+    //   c~_p: (B row p, A row p, 0)
+    const int nr = hasu ? nu : 0, nc = hasu ? nx : 0, nout = nr + nx + nc;
+    for (int o = lane; o < nout; o += 32) {
+        const double *cu, *cx, *cy;
+        int su, sx, sy;
+        double add;
+        double *dst;
+        if (o < nr) {
+            const int p = o;
+            cu = Rk + p;
+            su = nu;
+            cx = Sk ? Sk + p : zr;
+            sx = Sk ? nu : 0;
+            cy = V + p * ny;
+            sy = 1;
+            add = a.r[in.orv + (long long)k * nu + p];
+            if (gu) add = fma(gu[p], z[p] - a.ubar[in.orv + (long long)k * nu + p], add);
+            dst = a.ro + in.orv + (long long)k * nu + p;
+        } else if (o < nr + nx) {
+            const int p = o - nr;
+            cu = Sk ? Sk + p * nu : zr;
+            su = Sk ? 1 : 0;
+            cx = Qk + p;
+            sx = nx;
+            cy = V + (nu + p) * ny;
+            sy = 1;
+            add = a.q[in.oq + (long long)k * nx + p];
+            if (gx) add = fma(gx[p], z[nu + p] - a.xbar[in.oq + (long long)k * nx + p], add);
+            dst = a.qo + in.oq + (long long)k * nx + p;
+        } else {
+            const int p = o - nr - nx;
+            cu = a.B + in.oB + (long long)k * nx * nu + p;
+            su = nx;
+            cx = a.A + in.oA + (long long)k * nx * nx + p;
+            sx = nx;
+            cy = zr;
+            sy = 1;
+            add = a.f[in.oc + (long long)k * nx + p] - a.x[in.oq + (long long)(k + 1) * nx + p];
+            dst = a.co + in.oc + (long long)k * nx + p;
         }
-    }
-    // dynamics residual c~ = B u + A x + f - x^{k+1}
-    if (hasu) {
-        const double *Ak = a.A + in.oA + (long long)k * nx * nx, *Bk = a.B + in.oB + (long long)k * nx * nu;
-        const double *xn = a.x + in.oq + (long long)(k + 1) * nx;
-        for (int p = lane; p < nx; p += 32) {
-            double g = 0.0;
-            for (int j = 0; j < nu; ++j) g = fma(Bk[p + j * nx], z[j], g);
-            for (int j = 0; j < nx; ++j) g = fma(Ak[p + j * nx], z[nu + j], g);
-            a.co[in.oc + (long long)k * nx + p] = g + a.f[in.oc + (long long)k * nx + p] - xn[p];
-        }
+        double g = 0.0;
+        if (hasu)
+            for (int j = 0; j < nu; ++j) g = fma(cu[j * su], z[j], g);
+        for (int j = 0; j < nx; ++j) g = fma(cx[j * sx], z[nu + j], g);
+        for (int i = 0; i < ny; ++i) g = fma(cy[i * sy], yh[i], g);
+        *dst = g + add;
     }
 }
 
 }  // namespace
 
 size_t newton_smem_bytes(int ny, int nx, int nu) {
-    return ((size_t)ny * (nx + nu) + (size_t)(nx + nu) + 2 * (size_t)ny) * sizeof(double);
+    return (2 * (size_t)ny * (nx + nu) + (size_t)(nx + nu) + 2 * (size_t)ny) * sizeof(double) +
+           (size_t)ny * sizeof(int);
 }
 
 cudaError_t launch_newton_assemble(const NewtonArgs &a, int batch, int max_stages, size_t smem, cudaStream_t st) {

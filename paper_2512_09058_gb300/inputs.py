@@ -39,7 +39,7 @@ import numpy as np
 __all__ = [
     "OCPInstance", "Batch", "CONFIGS", "make_instance", "make_batch",
     "config_dims", "instance_dims", "blocks_to_flat", "flat_to_blocks",
-    "ALMData", "make_alm", "concat_alm",
+    "ALMData", "make_alm", "concat_alm", "config_alm",
 ]
 
 
@@ -159,6 +159,12 @@ CONFIGS = {
     # 150 initial states; Sigma (ALM penalties) on the boxed coordinates only
     "massspring150_M18_N96": dict(kind="mass_spring", batch=150, M=18, N=96, nx=36, nu=9, S=False,
                                   sigma=(1e-2, 1e4), nrhs=1, QN_equals_Q0=True, seed=5),
+    # Newton step of the augmented Lagrangian inner problem (Sec. 5) on the batch1024
+    # shapes: 16 general constraint rows per stage (C, D dense), boxes around [-1, 1]
+    # (a mix of active and inactive rows), penalties log-uniform in [1e-2, 1e4]
+    "newton1024_n64_nx12_nu4_ny16": dict(batch=1024, N=64, nx=12, nu=4, S=True, sigma=None, nrhs=1,
+                                         QN_equals_Q0=False, seed=6,
+                                         alm=dict(ny=16, bounds="mixed", sigma=(1e-2, 1e4))),
 }
 
 
@@ -438,6 +444,15 @@ def make_alm(inst: OCPInstance, ny: int, seed: int, index: int = 0, bounds: str 
         raise ValueError(bounds)
     return ALMData(ny=ny, C=blocks_to_flat(C), D=blocks_to_flat(D), bl=bl, bu=bu, y=y, sig=sig, gx=gx, gu=gu,
                    xbar=xbar, ubar=ubar, u=u, x=x)
+
+
+def config_alm(cfg, instances: Sequence[OCPInstance], indices: Sequence[int]) -> List[ALMData]:
+    """The constraint data and iterate of a config with an ``alm`` entry, per instance."""
+    if isinstance(cfg, str):
+        cfg = CONFIGS[cfg]
+    a = cfg["alm"]
+    return [make_alm(inst, a["ny"], seed=cfg["seed"], index=int(i), bounds=a["bounds"], sigma=a["sigma"])
+            for inst, i in zip(instances, indices)]
 
 
 def concat_alm(items: Sequence[ALMData]) -> ALMData:
