@@ -293,6 +293,23 @@ cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu, const dou
                                     const double *b, double *z, int32_t *status, cyq_stream stream);
 
 /*
+ * Parallel cyclic reduction for the last levels of the coupling solve (App. A,
+ * Alg. pcr; Sec. 7.5.2).  With levels = T > 0 the cyclic reduction of the
+ * segment couplings stops T levels early; the blocks left (every 2^(L-T)-th of
+ * an instance's P blocks, L = ceil(log2 max P)) are then all eliminated into
+ * both of their neighbours at each of the T remaining levels, which leaves
+ * them decoupled: the solve runs those levels forward only, without back
+ * substitution.  T is clamped to L; T = 0 restores plain cyclic reduction.
+ * Instances with one segment are unaffected.  Re-plans the handle (device
+ * allocations; the previous plan's buffers are released by cyq_destroy); the
+ * next cyq_solve needs a new cyq_factor (NO_FACTOR until then).  The solution
+ * is the same up to rounding.  Errors: INVALID_ARG, CUDA.
+ */
+cyq_status cyq_set_pcr_tail(cyq_handle h, int32_t levels);
+/* Tail levels in use (after clamping). */
+cyq_status cyq_get_pcr_tail(cyq_handle h, int32_t *levels);
+
+/*
  * Newton system of the augmented Lagrangian inner problem (Sec. 5, eqs.
  * ocp-al, ocp-al-funcs, qpalm-ocp-hessians, newton-sys-with-x0, elim-x0).
  *

@@ -723,6 +723,92 @@ cyq_status cyq_build_rhs(cyq_handle h, const double *q, const double *r, const d
     return CYQ_OK;
 }
 
+cyq_status cyq_set_pcr_tail(cyq_handle h, int32_t levels) {
+    if (!h || levels < 0) return CYQ_ERR_INVALID_ARG;
+    if (h->cr_list.empty()) return CYQ_OK;   // no instance has more than one segment
+    DeviceGuard guard(h->device);
+    CYQ_CUDA(cudaDeviceSynchronize());   // the old plan may still be in use
+    int maxP = 1;
+    for (int i : h->cr_list) maxP = std::max(maxP, h->inst[i].P);
+    int total = 0;
+    while ((1 << total) < maxP) ++total;
+    const int T = std::min<int>(levels, total), L0 = total - T, s0 = 1 << L0;
+    std::vector<CrJob> jobs;
+    CrPlan cp = h->cr_plan;
+    cp.levels = L0;
+    for (int l = 0; l < L0; ++l) {
+        const int st = 1 << l;
+        cp.elim_off[l] = (int)jobs.size();
+        for (int i : h->cr_list)
+            for (int k = st; k < h->inst[i].P; k += 2 * st) jobs.push_back(CrJob{i, k});
+    }
+    cp.elim_off[L0] = (int)jobs.size();
+    for (int l = 0; l < L0; ++l) {
+        const int st = 1 << l;
+        cp.upd_off[l] = (int)jobs.size();
+        for (int i : h->cr_list)
+            for (int k = 0; k < h->inst[i].P; k += 2 * st) jobs.push_back(CrJob{i, k});
+    }
+    cp.upd_off[L0] = (int)jobs.size();
+    cp.tail = T;
+    cp.s0 = s0;
+    std::vector<long long> oT(h->batch, 0), oV(h->batch, 0);
+    long long nT = 0, nV = 0;
+    for (int i : h->cr_list) {
+        const int v = (h->inst[i].P + s0 - 1) / s0, nx = h->inst[i].nx;
+        oT[i] = nT;
+        oV[i] = nV;
+        nT += (long long)v * T * nx * nx;
+        nV += (long long)v * nx;
+    }
+    for (int t = 0; t < T; ++t) {
+        cp.pcr_off[t] = (int)jobs.size();
+        for (int i : h->cr_list) {
+            const int v = (h->inst[i].P + s0 - 1) / s0;
+            if (v > (1 << t))
+                for (int j = 0; j < v; ++j) jobs.push_back(CrJob{i, j});
+        }
+    }
+    cp.pcr_off[T] = (int)jobs.size();
+    if (T > 0)
+        for (int i : h->cr_list) {
+            const int v = (h->inst[i].P + s0 - 1) / s0;
+            for (int j = 0; j < v; ++j) jobs.push_back(CrJob{i, j});
+        }
+    cp.pcr_base_end = (int)jobs.size();
+    // new device buffers (the previous plan's stay allocated until cyq_destroy)
+    CrJob *dj = nullptr;
+    CYQ_CUDA(h->mem.alloc(&dj, jobs.size()));
+    CYQ_CUDA(cudaMemcpy(dj, jobs.data(), sizeof(CrJob) * jobs.size(), cudaMemcpyHostToDevice));
+    cp.jobs = dj;
+    if (T > 0) {
+        long long *doT = nullptr, *doV = nullptr;
+        CYQ_CUDA(h->mem.alloc(&doT, (size_t)h->batch));
+        CYQ_CUDA(h->mem.alloc(&doV, (size_t)h->batch));
+        CYQ_CUDA(cudaMemcpy(doT, oT.data(), sizeof(long long) * h->batch, cudaMemcpyHostToDevice));
+        CYQ_CUDA(cudaMemcpy(doV, oV.data(), sizeof(long long) * h->batch, cudaMemcpyHostToDevice));
+        cp.oT_dev = doT;
+        cp.oV_dev = doV;
+        CYQ_CUDA(h->mem.alloc(&cp.Lt, (size_t)nT));
+        CYQ_CUDA(h->mem.alloc(&cp.At, (size_t)nT));
+        CYQ_CUDA(h->mem.alloc(&cp.Bt, (size_t)nT));
+        CYQ_CUDA(h->mem.alloc(&cp.bt, (size_t)nV * h->max_nrhs));
+        cp.nvt = nV;
+    }
+    h->cr_jobs = jobs;
+    h->cr_plan = cp;
+    // the parallel tail runs on the level-parallel coupling solve
+    h->cr_levels = T > 0 || ((int)h->cr_list.size() < 2 * kSMs && maxP >= 8);
+    h->factored = false;
+    return CYQ_OK;
+}
+
+cyq_status cyq_get_pcr_tail(cyq_handle h, int32_t *levels) {
+    if (!h || !levels) return CYQ_ERR_INVALID_ARG;
+    *levels = h->cr_plan.tail;
+    return CYQ_OK;
+}
+
 cyq_status cyq_assemble_newton(cyq_handle h, const cyq_newton_in *in, const cyq_newton_out *out,
                                cyq_stream stream) {
     if (!h || !in || !out || !in->ny) return CYQ_ERR_INVALID_ARG;

@@ -52,6 +52,77 @@ __global__ void k_cr_assemble(FactorArgs a, const int *inst_list, int n_inst) {
         M[e] += Mb[e];
 }
 
+// Elimination of one block (shared by cyclic reduction and its parallel tail):
+//   L = chol(M),  U = Klo^T L^{-T} (Klo: the block's coupling to its lower
+//   neighbour, row = this block),  Y = Khi L^{-T} (Khi: the upper neighbour's
+//   coupling to this block).  Klo / Khi null: that product is skipped.  L goes
+//   to Lout, which may be M itself.  Returns false on a non-positive pivot.
+template <int TEAM>
+__device__ bool cr_eliminate_block(double *W0, const double *M, const double *Klo, const double *Khi, double *Lout,
+                                   double *Uout, double *Yout, int n) {
+    const long long nn = (long long)n * n;
+    double *W1 = W0 + nn, *W2 = W1 + nn, *dinv = W2 + nn;
+    load_blk<TEAM>(W0, M, n, false);
+    if (Klo) load_blk<TEAM>(W1, Klo, n, true);
+    if (Khi) load_blk<TEAM>(W2, Khi, n, false);
+    team_sync();
+    const bool ok = team_chol<double, TEAM>(W0, n, n, dinv);
+    store_blk<TEAM>(Lout, W0, n);
+    // both triangular solves in one pass: rows of U then rows of Y
+    const int r0 = Klo ? 0 : n, rows = Khi ? 2 * n : n;
+    for (int r = r0 + threadIdx.x; r < rows; r += TEAM) {
+        double *X = r < n ? W1 : W2;
+        const int rr = r < n ? r : r - n;
+        for (int j = 0; j < n; ++j) {
+            double acc = X[rr + j * n];
+            for (int t = 0; t < j; ++t) acc = fma(-X[rr + t * n], W0[j + t * n], acc);
+            X[rr + j * n] = acc * dinv[j];
+        }
+    }
+    team_sync();
+    if (Klo) store_blk<TEAM>(Uout, W1, n);
+    if (Khi) store_blk<TEAM>(Yout, W2, n);
+    return ok;
+}
+
+// Update of one remaining block: M -= Ylo Ylo^T + Uhi Uhi^T, and where Ufill is
+// given, Kout = -Ylo Ufill^T (the fill coupling to the neighbour two strides down).
+template <int TEAM>
+__device__ void cr_update_block(double *W0, double *M, const double *Ylo, const double *Uhi, const double *Ufill,
+                                double *Kout, int n) {
+    const long long nn = (long long)n * n;
+    double *W1 = W0 + nn, *W2 = W1 + nn, *W3 = W2 + nn;
+    if (Ylo) load_blk<TEAM>(W1, Ylo, n, false);
+    if (Uhi) load_blk<TEAM>(W2, Uhi, n, false);
+    if (Ufill) load_blk<TEAM>(W3, Ufill, n, false);
+    team_sync();
+    // lower triangle of M minus the two symmetric products, straight from global
+    const int cnt = n * (n + 1) / 2;
+    for (int e = threadIdx.x; e < cnt; e += TEAM) {
+        int r, c;
+        tri_index(e, r, c);
+        double acc = M[r + c * n];
+        if (Ylo)
+            for (int t = 0; t < n; ++t) acc = fma(-W1[r + t * n], W1[c + t * n], acc);
+        if (Uhi)
+            for (int t = 0; t < n; ++t) acc = fma(-W2[r + t * n], W2[c + t * n], acc);
+        W0[r + c * n] = acc;
+    }
+    if (Ufill) {
+        for (int e = threadIdx.x; e < n * n; e += TEAM) {
+            const int r = e % n, c = e / n;
+            double acc = 0.0;
+            for (int t = 0; t < n; ++t) acc = fma(W1[r + t * n], W3[c + t * n], acc);
+            Kout[e] = -acc;
+        }
+    }
+    team_sync();
+    for (int e = threadIdx.x; e < n * n; e += TEAM) {
+        const int r = e % n, c = e / n;
+        M[e] = r >= c ? W0[r + c * n] : W0[c + r * n];
+    }
+}
+
 // Eliminate block k at stride s:  L_k = chol(M_k),  U_k = K_k^T L_k^{-T},  Y_k = K_{k+s} L_k^{-T}.
 template <int TEAM>
 __global__ void __launch_bounds__(TEAM) k_cr_eliminate(FactorArgs a, const CrJob *jobs, int s) {
@@ -62,28 +133,10 @@ __global__ void __launch_bounds__(TEAM) k_cr_eliminate(FactorArgs a, const CrJob
     const int P = in.P, n = in.nx, k = job.k;
     const long long nn = (long long)n * n;
     double *M = a.Mf + in.oBlk, *K = a.Kc + in.oBlk, *U = a.U + in.oBlk, *Y = a.Y + in.oBlk;
-    double *W0 = reinterpret_cast<double *>(smem_raw), *W1 = W0 + nn, *W2 = W1 + nn, *dinv = W2 + nn;
-    load_blk<TEAM>(W0, M + k * nn, n, false);
-    load_blk<TEAM>(W1, K + k * nn, n, true);
     const bool hasY = k + s < P;
-    if (hasY) load_blk<TEAM>(W2, K + (k + s) * nn, n, false);
-    team_sync();
-    const bool ok = team_chol<double, TEAM>(W0, n, n, dinv);
-    store_blk<TEAM>(M + k * nn, W0, n);
-    // both triangular solves in one pass: rows of U then rows of Y
-    const int rows = hasY ? 2 * n : n;
-    for (int r = threadIdx.x; r < rows; r += TEAM) {
-        double *X = r < n ? W1 : W2;
-        const int rr = r < n ? r : r - n;
-        for (int j = 0; j < n; ++j) {
-            double acc = X[rr + j * n];
-            for (int t = 0; t < j; ++t) acc = fma(-X[rr + t * n], W0[j + t * n], acc);
-            X[rr + j * n] = acc * dinv[j];
-        }
-    }
-    team_sync();
-    store_blk<TEAM>(U + k * nn, W1, n);
-    if (hasY) store_blk<TEAM>(Y + k * nn, W2, n);
+    const bool ok = cr_eliminate_block<TEAM>(reinterpret_cast<double *>(smem_raw), M + k * nn, K + k * nn,
+                                             hasY ? K + (k + s) * nn : nullptr, M + k * nn, U + k * nn,
+                                             Y + k * nn, n);
     if (!ok && threadIdx.x == 0) atomicCAS(a.status + job.inst, 0, ST_NOT_PD);
 }
 
@@ -99,39 +152,78 @@ __global__ void __launch_bounds__(TEAM) k_cr_update(FactorArgs a, const CrJob *j
     const long long nn = (long long)n * n;
     double *M = a.Mf + in.oBlk, *K = a.Kc + in.oBlk;
     const double *U = a.U + in.oBlk, *Y = a.Y + in.oBlk;
-    double *W0 = reinterpret_cast<double *>(smem_raw), *W1 = W0 + nn, *W2 = W1 + nn, *W3 = W2 + nn;
     const bool lo = i - s >= 0, hi = i + s < P, fill = i - 2 * s >= 0;
-    if (lo) load_blk<TEAM>(W1, Y + (i - s) * nn, n, false);
-    if (hi) load_blk<TEAM>(W2, U + (i + s) * nn, n, false);
-    if (fill) load_blk<TEAM>(W3, U + (i - s) * nn, n, false);
+    cr_update_block<TEAM>(reinterpret_cast<double *>(smem_raw), M + i * nn, lo ? Y + (i - s) * nn : nullptr,
+                          hi ? U + (i + s) * nn : nullptr, fill ? U + (i - s) * nn : nullptr, K + i * nn, n);
+}
+
+// ---------------------------------------------------------------------------
+// Parallel cyclic reduction of the last levels (paper App. A, Alg. pcr): the
+// blocks left after the cyclic-reduction levels (every s0-th block, v of them
+// per instance, tail index j = block / s0) are all eliminated into both of
+// their neighbours at each tail level t (stride 2^t in tail indices), until
+// no coupling is left; the right-hand side then needs no back substitution
+// over these levels.  Per block and level:
+//   L_j = chol(M_j),  A_j = E_{j+2^t} L_j^{-T},  B_j = E_j^T L_j^{-T}
+//   M_j -= A_{j-2^t} A_{j-2^t}^T + B_{j+2^t} B_{j+2^t}^T,
+//   E_j <- -A_{j-2^t} B_{j-2^t}^T   (E_j: coupling of j to j - stride),
+// with L, A, B of every level kept for the solve (tail storage, per instance
+// v x levels x 3 blocks).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pcr_count(int P, int s0) { return (P + s0 - 1) / s0; }
+
+__device__ __forceinline__ double *pcr_blk(const CrPlan &p, double *base, const CrJob &job, int n, int v, int t, int j) {
+    return base + p.oT_dev[job.inst] + ((long long)t * v + j) * n * n;
+}
+
+template <int TEAM>
+__global__ void __launch_bounds__(TEAM) k_pcr_eliminate(FactorArgs a, CrPlan p, const CrJob *jobs, int t) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CrJob job = jobs[blockIdx.x];
+    if (a.skip && a.skip[job.inst]) return;
+    const Inst in = a.inst[job.inst];
+    const int n = in.nx, v = pcr_count(in.P, p.s0), j = job.k, sg = 1 << t;
+    const long long nn = (long long)n * n;
+    double *M = a.Mf + in.oBlk, *K = a.Kc + in.oBlk;
+    const double *Klo = j - sg >= 0 ? K + (long long)j * p.s0 * nn : nullptr;
+    const double *Khi = j + sg < v ? K + (long long)(j + sg) * p.s0 * nn : nullptr;
+    const bool ok = cr_eliminate_block<TEAM>(reinterpret_cast<double *>(smem_raw), M + (long long)j * p.s0 * nn, Klo,
+                                             Khi, pcr_blk(p, p.Lt, job, n, v, t, j), pcr_blk(p, p.Bt, job, n, v, t, j),
+                                             pcr_blk(p, p.At, job, n, v, t, j), n);
+    if (!ok && threadIdx.x == 0) atomicCAS(a.status + job.inst, 0, ST_NOT_PD);
+}
+
+template <int TEAM>
+__global__ void __launch_bounds__(TEAM) k_pcr_update(FactorArgs a, CrPlan p, const CrJob *jobs, int t) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CrJob job = jobs[blockIdx.x];
+    if (a.skip && a.skip[job.inst]) return;
+    const Inst in = a.inst[job.inst];
+    const int n = in.nx, v = pcr_count(in.P, p.s0), j = job.k, sg = 1 << t;
+    const long long nn = (long long)n * n;
+    double *M = a.Mf + in.oBlk, *K = a.Kc + in.oBlk;
+    const bool lo = j - sg >= 0, hi = j + sg < v, fill = j - 2 * sg >= 0;
+    cr_update_block<TEAM>(reinterpret_cast<double *>(smem_raw), M + (long long)j * p.s0 * nn,
+                          lo ? pcr_blk(p, p.At, job, n, v, t, j - sg) : nullptr,
+                          hi ? pcr_blk(p, p.Bt, job, n, v, t, j + sg) : nullptr,
+                          fill ? pcr_blk(p, p.Bt, job, n, v, t, j - sg) : nullptr, K + (long long)j * p.s0 * nn, n);
+}
+
+// Last factor of every tail block: L_j = chol(M_j) (in place).
+template <int TEAM>
+__global__ void __launch_bounds__(TEAM) k_pcr_base(FactorArgs a, CrPlan p, const CrJob *jobs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CrJob job = jobs[blockIdx.x];
+    if (a.skip && a.skip[job.inst]) return;
+    const Inst in = a.inst[job.inst];
+    const int n = in.nx;
+    double *M = a.Mf + in.oBlk + (long long)job.k * p.s0 * n * n;
+    double *W0 = reinterpret_cast<double *>(smem_raw);
+    load_blk<TEAM>(W0, M, n, false);
     team_sync();
-    // lower triangle of M_i minus the two symmetric products, straight from global
-    const int cnt = n * (n + 1) / 2;
-    double *Mi = M + i * nn;
-    for (int e = threadIdx.x; e < cnt; e += TEAM) {
-        int r, c;
-        tri_index(e, r, c);
-        double acc = Mi[r + c * n];
-        if (lo)
-            for (int t = 0; t < n; ++t) acc = fma(-W1[r + t * n], W1[c + t * n], acc);
-        if (hi)
-            for (int t = 0; t < n; ++t) acc = fma(-W2[r + t * n], W2[c + t * n], acc);
-        W0[r + c * n] = acc;
-    }
-    if (fill) {
-        double *Ki = K + i * nn;
-        for (int e = threadIdx.x; e < n * n; e += TEAM) {
-            const int r = e % n, c = e / n;
-            double acc = 0.0;
-            for (int t = 0; t < n; ++t) acc = fma(W1[r + t * n], W3[c + t * n], acc);
-            Ki[e] = -acc;
-        }
-    }
-    team_sync();
-    for (int e = threadIdx.x; e < n * n; e += TEAM) {
-        const int r = e % n, c = e / n;
-        Mi[e] = r >= c ? W0[r + c * n] : W0[c + r * n];
-    }
+    const bool ok = team_chol<double, TEAM>(W0, n, n);
+    store_blk<TEAM>(M, W0, n);
+    if (!ok && threadIdx.x == 0) atomicCAS(a.status + job.inst, 0, ST_NOT_PD);
 }
 
 // Last block of every instance: L_0 = chol(M_0).
@@ -183,10 +275,34 @@ cudaError_t launch_cr_factor_levels(const CrPlan &plan, int team, int nmax, cons
             ++*launches;
         }
     }
-    base<<<plan.n_inst, team, nn, st>>>(a, plan.inst_list);
+    if (plan.tail == 0) {
+        base<<<plan.n_inst, team, nn, st>>>(a, plan.inst_list);
+        ++*launches;
+        return cudaGetLastError();
+    }
+    // parallel tail: every remaining block at every tail level, then each block's last factor
+    auto pel = team == 32 ? k_pcr_eliminate<32> : k_pcr_eliminate<128>;
+    auto pup = team == 32 ? k_pcr_update<32> : k_pcr_update<128>;
+    auto pba = team == 32 ? k_pcr_base<32> : k_pcr_base<128>;
+    if ((e = ensure_smem((const void *)pel, se)) != cudaSuccess) return e;
+    if ((e = ensure_smem((const void *)pup, su)) != cudaSuccess) return e;
+    if ((e = ensure_smem((const void *)pba, nn)) != cudaSuccess) return e;
+    for (int t = 0; t < plan.tail; ++t) {
+        const int nj = plan.pcr_off[t + 1] - plan.pcr_off[t];
+        if (nj == 0) continue;
+        pel<<<nj, team, se, st>>>(a, plan, plan.jobs + plan.pcr_off[t], t);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        pup<<<nj, team, su, st>>>(a, plan, plan.jobs + plan.pcr_off[t], t);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *launches += 2;
+    }
+    const int nb = plan.pcr_base_end - plan.pcr_off[plan.tail];
+    pba<<<nb, team, nn, st>>>(a, plan, plan.jobs + plan.pcr_off[plan.tail]);
     ++*launches;
     return cudaGetLastError();
 }
+
+size_t cr_tail_smem_bytes(int nmax) { return 4 * (size_t)nmax * nmax * sizeof(double); }
 
 // Coupling right-hand side and cyclic-reduction solve, one CTA per instance:
 //   rhs_c = d_fwd,c + d_bwd,(c+1 mod P) - b_lambda^{b_c},
@@ -318,8 +434,6 @@ __global__ void __launch_bounds__(TEAM) k_cr_solve(SolveArgs a, const int *inst_
 // and, in place, the solution; the arithmetic is that of k_cr_solve.
 // ---------------------------------------------------------------------------
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
 
 // Block L (n x n, column-major) into shared memory and the reciprocals of its diagonal.
 __device__ void crs_load_factor(double *Ls, double *di, const double *L, int n) {
@@ -475,6 +589,69 @@ __global__ void __launch_bounds__(32) k_crs_backward(SolveArgs a, const CrJob *j
     for (int i = threadIdx.x; i < n; i += 32) g[i] = v[i];
 }
 
+// Parallel tail of the solve, level t, every tail block j:  b~_j = L_j^{(t)-1} b_j
+// (kept beside b_j: the neighbours' updates read it).
+__global__ void __launch_bounds__(32) k_pcrs_forward(SolveArgs a, CrPlan p, const CrJob *jobs, int t) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CrJob job = jobs[blockIdx.x];
+    if (a.skip && a.skip[job.inst]) return;
+    const Inst in = a.inst[job.inst];
+    const int n = in.nx, r = blockIdx.y, v = pcr_count(in.P, p.s0), j = job.k;
+    double *Ls = reinterpret_cast<double *>(smem_raw), *di = Ls + n * n, *w = di + n;
+    crs_load_factor(Ls, di, pcr_blk(p, p.Lt, job, n, v, t, j), n);
+    const double *g = crs_vec(a, in, r, j * p.s0);
+    for (int i = threadIdx.x; i < n; i += 32) w[i] = g[i];
+    __syncwarp();
+    crs_forward(Ls, di, w, n);
+    double *o = p.bt + r * p.nvt + p.oV_dev[job.inst] + (long long)j * n;
+    for (int i = threadIdx.x; i < n; i += 32) o[i] = w[i];
+}
+
+// Parallel tail of the solve, level t:  b_j -= A_{j-2^t} b~_{j-2^t} + B_{j+2^t} b~_{j+2^t}.
+__global__ void __launch_bounds__(32) k_pcrs_update(SolveArgs a, CrPlan p, const CrJob *jobs, int t) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CrJob job = jobs[blockIdx.x];
+    if (a.skip && a.skip[job.inst]) return;
+    const Inst in = a.inst[job.inst];
+    const int n = in.nx, r = blockIdx.y, v = pcr_count(in.P, p.s0), j = job.k, sg = 1 << t;
+    double *xl = reinterpret_cast<double *>(smem_raw), *xh = xl + n;
+    const bool lo = j - sg >= 0, hi = j + sg < v;
+    const double *bt = p.bt + r * p.nvt + p.oV_dev[job.inst];
+    if (lo)
+        for (int i = threadIdx.x; i < n; i += 32) xl[i] = bt[(long long)(j - sg) * n + i];
+    if (hi)
+        for (int i = threadIdx.x; i < n; i += 32) xh[i] = bt[(long long)(j + sg) * n + i];
+    __syncwarp();
+    const double *A = lo ? pcr_blk(p, p.At, job, n, v, t, j - sg) : nullptr;
+    const double *B = hi ? pcr_blk(p, p.Bt, job, n, v, t, j + sg) : nullptr;
+    double *g = crs_vec(a, in, r, j * p.s0);
+    for (int row = threadIdx.x; row < n; row += 32) {
+        double acc = 0.0;
+        if (lo)
+            for (int c = 0; c < n; ++c) acc = fma(A[row + c * n], xl[c], acc);
+        if (hi)
+            for (int c = 0; c < n; ++c) acc = fma(B[row + c * n], xh[c], acc);
+        g[row] -= acc;
+    }
+}
+
+// Every tail block, decoupled after the last tail level:  x_j = L_j^{-T} L_j^{-1} b_j.
+__global__ void __launch_bounds__(32) k_pcrs_base(SolveArgs a, CrPlan p, const CrJob *jobs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CrJob job = jobs[blockIdx.x];
+    if (a.skip && a.skip[job.inst]) return;
+    const Inst in = a.inst[job.inst];
+    const int n = in.nx, r = blockIdx.y;
+    double *Ls = reinterpret_cast<double *>(smem_raw), *di = Ls + n * n, *w = di + n;
+    crs_load_factor(Ls, di, a.Mf + in.oBlk + (long long)job.k * p.s0 * n * n, n);
+    double *g = crs_vec(a, in, r, job.k * p.s0);
+    for (int i = threadIdx.x; i < n; i += 32) w[i] = g[i];
+    __syncwarp();
+    crs_forward(Ls, di, w, n);
+    crs_backward(Ls, di, w, n);
+    for (int i = threadIdx.x; i < n; i += 32) g[i] = w[i];
+}
+
 // lambda^{b_c} of the solution into z (or added into zacc).
 __global__ void k_crs_scatter(SolveArgs a, const int *inst_list) {
     const int ii = inst_list[blockIdx.y];
@@ -521,9 +698,28 @@ cudaError_t launch_cr_solve_levels(const CrPlan &plan, int nmax, const SolveArgs
             ++*launches;
         }
     }
-    k_crs_base<<<dim3(plan.n_inst, nr), 32, sm, st>>>(a, plan.inst_list);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ++*launches;
+    if (plan.tail == 0) {
+        k_crs_base<<<dim3(plan.n_inst, nr), 32, sm, st>>>(a, plan.inst_list);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++*launches;
+    } else {
+        if ((e = ensure_smem((const void *)k_pcrs_forward, sm)) != cudaSuccess) return e;
+        if ((e = ensure_smem((const void *)k_pcrs_base, sm)) != cudaSuccess) return e;
+        for (int t = 0; t < plan.tail; ++t) {
+            const int nj = plan.pcr_off[t + 1] - plan.pcr_off[t];
+            if (nj == 0) continue;
+            k_pcrs_forward<<<dim3(nj, nr), 32, sm, st>>>(a, plan, plan.jobs + plan.pcr_off[t], t);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            k_pcrs_update<<<dim3(nj, nr), 32, 2 * (size_t)nmax * sizeof(double), st>>>(
+                a, plan, plan.jobs + plan.pcr_off[t], t);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            *launches += 2;
+        }
+        const int nb = plan.pcr_base_end - plan.pcr_off[plan.tail];
+        k_pcrs_base<<<dim3(nb, nr), 32, sm, st>>>(a, plan, plan.jobs + plan.pcr_off[plan.tail]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++*launches;
+    }
     for (int l = plan.levels - 1; l >= 0; --l) {
         const int s = 1 << l;
         const int ne = plan.elim_off[l + 1] - plan.elim_off[l];

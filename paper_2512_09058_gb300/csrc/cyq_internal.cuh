@@ -396,13 +396,25 @@ struct CrPlan {
     int n_inst = 0;                 // instances with P > 1
     const int *inst_list = nullptr; // device
     const CrJob *jobs = nullptr;    // device
-    int levels = 0;
+    int levels = 0;                 // cyclic-reduction levels (before the parallel tail)
     int elim_off[33] = {0}, upd_off[33] = {0};
+    // parallel cyclic reduction of the last levels (tail = 0: none, block 0 is the base):
+    // the blocks left are every s0-th one; jobs (instance, tail index) of tail level t are
+    // jobs[pcr_off[t] .. pcr_off[t+1]), every tail block is in jobs[pcr_off[tail] .. pcr_base_end)
+    int tail = 0, s0 = 1;
+    int pcr_off[33] = {0};
+    int pcr_base_end = 0;
+    const long long *oT_dev = nullptr;    // per instance: offset of its tail factor blocks (doubles)
+    const long long *oV_dev = nullptr;    // per instance: offset of its tail vectors (doubles, per rhs)
+    double *Lt = nullptr, *At = nullptr, *Bt = nullptr;   // tail L, A, B per (level, tail block)
+    double *bt = nullptr;                 // tail vectors L^{-1} b, [rhs][nvt]
+    long long nvt = 0;
 };
 
 cudaError_t launch_factor_segments(bool fp64, int team, int shape, size_t smem, const FactorArgs &a, cudaStream_t st);
 cudaError_t launch_cr_factor_levels(const CrPlan &plan, int team, int nmax, const FactorArgs &a, cudaStream_t st,
                                     long long *launches);
+size_t cr_tail_smem_bytes(int nmax);
 cudaError_t launch_solve_backward(bool fp64, int team, int shape, size_t smem, const SolveArgs &a, cudaStream_t st);
 cudaError_t launch_cr_solve(int n_inst_cr, const int *inst_list, int team, size_t smem, const SolveArgs &a,
                             cudaStream_t st);

@@ -27,7 +27,8 @@ EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rh
            "cyq_solve_adjoint", "cyq_get_instance_status", "cyq_get_stats", "cyq_kkt_size",
            "cyq_get_segments", "cyq_last_launch_count", "cyq_status_string", "cyq_last_error",
            "cyq_factor_solve_noalloc", "cyq_autotune", "cyq_get_launch_shapes", "cyq_tune_segments",
-           "cyq_set_launch_shapes", "cyq_get_stage_factor", "cyq_assemble_newton"]
+           "cyq_set_launch_shapes", "cyq_get_stage_factor", "cyq_assemble_newton", "cyq_set_pcr_tail",
+           "cyq_get_pcr_tail"]
 
 
 class CyqError(RuntimeError):
@@ -99,6 +100,8 @@ def load(path: str = LIB_PATH):
     L.cyq_set_launch_shapes.argtypes = [vp, pi32, pi32, i32]
     L.cyq_get_stage_factor.argtypes = [vp, i32, i32, ctypes.POINTER(d)]
     L.cyq_assemble_newton.argtypes = [vp, ctypes.POINTER(cyq_newton_in), ctypes.POINTER(cyq_newton_out), vp]
+    L.cyq_set_pcr_tail.argtypes = [vp, i32]
+    L.cyq_get_pcr_tail.argtypes = [vp, pi32]
     for name in ["cyq_create", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual", "cyq_solve_adjoint",
                  "cyq_get_instance_status", "cyq_get_stats", "cyq_get_segments", "cyq_autotune",
                  "cyq_get_launch_shapes", "cyq_tune_segments", "cyq_set_launch_shapes",
@@ -259,6 +262,16 @@ class Solver:
             b = torch.empty(self.kkt_size, dtype=torch.float64, device=q.device)
         _check(_lib.cyq_build_rhs(self._h, _ptr(q), _ptr(r), _ptr(c), _ptr(x0), _ptr(b), _stream(stream)))
         return b
+
+    def set_pcr_tail(self, levels: int):
+        """Solve the last `levels` levels of the coupling system by parallel cyclic
+        reduction (0: plain cyclic reduction); factor again afterwards."""
+        _check(_lib.cyq_set_pcr_tail(self._h, int(levels)))
+
+    def pcr_tail(self) -> int:
+        v = ctypes.c_int32(0)
+        _check(_lib.cyq_get_pcr_tail(self._h, ctypes.byref(v)))
+        return v.value
 
     def assemble_newton(self, data, q, r, c, x_init, u, x, alm, out=None, stream=None):
         """Newton system of the augmented Lagrangian inner problem at (u, x):
