@@ -81,7 +81,7 @@ WORKLOADS = {
 # Fixed segment count / launch shapes (--segments, --launch-shapes) in place of
 # the timing tuners, e.g. to reproduce a tuned configuration under a profiler,
 # whose serialised launches distort the tuners' timings.
-FIXED = {"P": 0, "shapes": None}
+FIXED = {"P": 0, "shapes": None, "pcr_tail": 0}
 
 
 def tuned_solver(torch, cyq, batch, data, b, method, tune_segments, P=None):
@@ -96,6 +96,8 @@ def tuned_solver(torch, cyq, batch, data, b, method, tune_segments, P=None):
                               it_max=it_max, tol=REFINE_TOL)
     s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, max_nrhs=nrhs, it_max=it_max,
                    tol=REFINE_TOL, P_per_instance=P)
+    if FIXED["pcr_tail"] > 0:
+        s.set_pcr_tail(FIXED["pcr_tail"])
     if FIXED["shapes"] is not None:
         n = len(s.launch_shapes(nrhs=nrhs)["factor"])
         s.set_launch_shapes(factor=[FIXED["shapes"][0]] * n, sweep=[FIXED["shapes"][1]] * n, nrhs=nrhs)
@@ -117,6 +119,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--segments", type=int, default=0, help="segments per OCP instead of the segment tuner")
+    p.add_argument("--pcr-tail", type=int, default=0,
+                   help="levels of the coupling solve done by parallel cyclic reduction (0: plain)")
     p.add_argument("--launch-shapes", default="",
                    help="F,S: threads per item of the factor and of the sweeps instead of the launch tuner")
     return p.parse_args()
@@ -506,6 +510,7 @@ def run_e2e(torch, cyq, batch, method, steps, warmup, data, b, P=None, adjoint=F
 def main():
     args = parse()
     FIXED["P"] = args.segments
+    FIXED["pcr_tail"] = args.pcr_tail
     if args.launch_shapes:
         FIXED["shapes"] = tuple(int(v) for v in args.launch_shapes.split(","))
     rank = int(os.environ.get("RANK", "0"))
@@ -652,6 +657,7 @@ def main():
         "config": {"workload": args.workload, "global_batch": world * batch.size,
                    "stages_per_ocp": nominal("N"), "nx": nominal("nx"), "nu": nominal("nu"), "nrhs": nrhs,
                    "method": head, "cuda_graph": prof["graph"], "adjoint": prof["adjoint"],
+                   "pcr_tail_levels": args.pcr_tail,
                    "parallelism": "dp%d" % world,
                    "l2": ("inputs larger than L2 (%.0f MB float64 data per GPU)" % (sbytes / 1e6))
                    if flush is None else "L2 flushed between steps (%.1f MB float64 data per GPU < L2)" % (sbytes / 1e6)},
