@@ -73,7 +73,7 @@ WORKLOADS = {
     "massspring150_M18_N96": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=True, adjoint=False,
                                   tune_segments=True),
     # step = Newton-system assembly + factor + solve of the augmented Lagrangian inner problem
-    "newton1024_n64_nx12_nu4_ny16": dict(methods=["fp64_ir32", "fp64_refine", "fp32_refine"], graph=False,
+    "newton1024_n64_nx12_nu4_ny16": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=False,
                                          adjoint=False, tune_segments=True, newton=True),
 }
 
