@@ -62,18 +62,18 @@ NCU_TRAFFIC = {("batch1024_n64_nx12_nu4", "fp64_ir32", "k_factor_pairs<12, 4>"):
 # (cyq_tune_segments); launch shapes are always tuned by timing (cyq_autotune)
 # before the timed region
 WORKLOADS = {
-    "batch1024_n64_nx12_nu4": dict(methods=["fp64_ir32", "fp64_refine", "fp64", "fp32_refine"], graph=False,
+    "batch1024_n64_nx12_nu4": dict(methods=["fp64_ir32", "fp64_refine", "fp64", "fp32_refine"], graph=True,
                                    adjoint=False, tune_segments=True),
     "single_n32_nx8_nu4": dict(methods=["fp64", "fp64_refine"], graph=True, adjoint=False, tune_segments=True),
-    "long_n4096_nx32_nu16": dict(methods=["fp32_refine", "fp64", "fp64_refine"], graph=False, adjoint=False,
+    "long_n4096_nx32_nu16": dict(methods=["fp32_refine", "fp64", "fp64_refine"], graph=True, adjoint=False,
                                  tune_segments=True),
     "uneven4096": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=True, adjoint=False,
                        tune_segments=True),
-    "adjoint512_n128_nx24_nu8": dict(methods=["fp64_refine"], graph=False, adjoint=True, tune_segments=True),
+    "adjoint512_n128_nx24_nu8": dict(methods=["fp64_refine"], graph=True, adjoint=True, tune_segments=True),
     "massspring150_M18_N96": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=True, adjoint=False,
                                   tune_segments=True),
     # step = Newton-system assembly + factor + solve of the augmented Lagrangian inner problem
-    "newton1024_n64_nx12_nu4_ny16": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=False,
+    "newton1024_n64_nx12_nu4_ny16": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=True,
                                          adjoint=False, tune_segments=True, newton=True),
 }
 
@@ -119,6 +119,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--segments", type=int, default=0, help="segments per OCP instead of the segment tuner")
+    p.add_argument("--graph", type=int, default=-1, help="1 / 0: force CUDA-graph replay on / off")
     p.add_argument("--pcr-tail", type=int, default=0,
                    help="levels of the coupling solve done by parallel cyclic reduction (0: plain)")
     p.add_argument("--launch-shapes", default="",
@@ -517,7 +518,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     cfg = inputs.CONFIGS[args.workload]
-    prof = WORKLOADS[args.workload]
+    prof = dict(WORKLOADS[args.workload])
+    if args.graph >= 0:
+        prof["graph"] = bool(args.graph)
     nominal = lambda key: cfg[key] if not isinstance(cfg[key], tuple) else "U%s" % (cfg[key],)
 
     if args.impl == "reference":
