@@ -69,12 +69,15 @@ __device__ void async_copy(T *dst, const T *src, int count) {
 
 // Column-major walk over the (row, right-hand side) pairs of an n x nrhs
 // grid: the thread's first pair and the step, computed once per work item.
+// Pair 0 goes to thread `first` (the assignment wraps around the team), so
+// that two products of one phase can start on different warps.
 struct Walk {
     int i0, r0, di, dr, n;
-    __device__ __forceinline__ void init(int n_, int team) {
+    __device__ __forceinline__ void init(int n_, int team, int first = 0) {
         n = n_;
-        r0 = threadIdx.x / n;
-        i0 = threadIdx.x - r0 * n;
+        const int vt = ((int)threadIdx.x - first + team) % team;
+        r0 = vt / n;
+        i0 = vt - r0 * n;
         dr = team / n;
         di = team - dr * n;
     }
@@ -249,7 +252,9 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
         Wx.init(nx, TEAM);
         Wux.init(nux, TEAM);
         Wv.init(nv, TEAM);
-        Wp.init(half, TEAM);
+        // the paired triangular products start on the second warp: the first one has the
+        // u rows of the same phase
+        Wp.init(half, TEAM, TEAM >= 64 ? 32 : 0);
         // ring of nbuf packages: the package of processing step u sits in slot u % nbuf
         // and is fetched D = nbuf - 1 steps ahead (right after use when nbuf == 1)
         const size_t pbytes = package_bytes(sizeof(T) == 8, nx, nu, nrhs);
@@ -471,7 +476,9 @@ __global__ void __launch_bounds__(TEAM) k_solve_forward(SolveArgs a) {
         Wu.init(nu, TEAM);
         Wx.init(nx, TEAM);
         Wv.init(nv, TEAM);
-        Wp.init(half, TEAM);
+        // the paired triangular products start on the second warp: the first one has the
+        // u rows of the same phase
+        Wp.init(half, TEAM, TEAM >= 64 ? 32 : 0);
         // ring of nbuf packages: the package of processing step u sits in slot u % nbuf
         // and is fetched D = nbuf - 1 steps ahead (right after use when nbuf == 1)
         const size_t pbytes = package_bytes(sizeof(T) == 8, nx, nu, nrhs);
