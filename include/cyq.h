@@ -342,7 +342,9 @@ cyq_status cyq_get_pcr_tail(cyq_handle h, int32_t *levels);
  * (N+1) ny.  Every input pointer other than S, gx, gu, xbar, ubar must be
  * non-NULL, as must the six block and vector outputs; the outputs must not
  * overlap the inputs.  The handle supplies the dimensions (no factorization
- * needed); asynchronous on `stream`.
+ * needed).  Asynchronous on `stream`, except that the first call with a given
+ * ny array synchronises the stream and uploads the per-instance offsets it
+ * implies: make that call before capturing later ones in a CUDA graph.
  * Errors: INVALID_ARG (null pointer, ny < 1, N + 1 > 65535, a stage's
  * [D C] rows too large for shared memory), CUDA.
  */
