@@ -255,6 +255,12 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
         // the paired triangular products start on the second warp: the first one has the
         // u rows of the same phase
         Wp.init(half, TEAM, TEAM >= 64 ? 32 : 0);
+        // when the u rows and the pairs each fit one warp, the first warp also forms the
+        // pairs' p = h_x - L^S rho right after rho (its own rows: a warp barrier suffices),
+        // which leaves the second warp only the products that need w
+        const bool early_p = pair && TEAM >= 64 && nu * nrhs <= 32 && half * nrhs <= 32;
+        Walk Wq;
+        Wq.init(half, TEAM);
         // ring of nbuf packages: the package of processing step u sits in slot u % nbuf
         // and is fetched D = nbuf - 1 steps ahead (right after use when nbuf == 1)
         const size_t pbytes = package_bytes(sizeof(T) == 8, nx, nu, nrhs);
@@ -319,6 +325,21 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
                 for (int k = 0; k < i; ++k) acc = fma(Ls[k + i * nux], hu[k], acc);
                 v.rho[i + r * nu] = acc;
             }
+            if (early_p && threadIdx.x < 32) {
+                __syncwarp();   // rho of every right-hand side (all on this warp)
+                for (int ip = Wq.i0, r = Wq.r0; r < nrhs; Wq.next(ip, r)) {
+                    const int i1 = ip, i2 = nx - 1 - ip;
+                    const T *ro = v.rho + r * nu;
+                    T p1 = v.hh[r * nux + nu + i1], p2 = v.hh[r * nux + nu + i2];
+#pragma unroll 4
+                    for (int k = 0; k < nu; ++k) {
+                        p1 = fma(-Ls[(nu + i1) + k * nux], ro[k], p1);
+                        p2 = fma(-Ls[(nu + i2) + k * nux], ro[k], p2);
+                    }
+                    v.pv[i1 + r * nx] = p1;
+                    v.pv[i2 + r * nx] = p2;
+                }
+            }
             if (!last && pair) {
                 for (int jp = Wp.i0, r = Wp.r0; r < nrhs; Wp.next(jp, r)) {
                     const int j1 = jp, j2 = nx - 1 - jp;
@@ -346,11 +367,18 @@ __global__ void __launch_bounds__(TEAM) k_solve_backward(SolveArgs a) {
                 const int i1 = ip, i2 = nx - 1 - ip;
                 const bool two = i2 != i1;
                 const T *ro = v.rho + r * nu;
-                T p1 = v.hh[r * nux + nu + i1], p2 = v.hh[r * nux + nu + i2];
+                T p1, p2;
+                if (early_p) {
+                    p1 = v.pv[i1 + r * nx];
+                    p2 = v.pv[i2 + r * nx];
+                } else {
+                    p1 = v.hh[r * nux + nu + i1];
+                    p2 = v.hh[r * nux + nu + i2];
 #pragma unroll 4
-                for (int k = 0; k < nu; ++k) {
-                    p1 = fma(-Ls[(nu + i1) + k * nux], ro[k], p1);
-                    p2 = fma(-Ls[(nu + i2) + k * nux], ro[k], p2);
+                    for (int k = 0; k < nu; ++k) {
+                        p1 = fma(-Ls[(nu + i1) + k * nux], ro[k], p1);
+                        p2 = fma(-Ls[(nu + i2) + k * nux], ro[k], p2);
+                    }
                 }
                 z[r * a.kkt + (long long)(xq - 1) * w + nu + i1] = (double)p1;
                 if (two) z[r * a.kkt + (long long)(xq - 1) * w + nu + i2] = (double)p2;
