@@ -45,3 +45,20 @@ def test_host_logic_without_device():
     assert L.cyq_create(ctypes.byref(d), ctypes.byref(h)) == 8     # CYQ_ERR_NO_DEVICE
     bad = cyq.cyq_desc(0, N, N, N, 0, 0, None, 1, 0, 0.0, -1, -1)
     assert L.cyq_create(ctypes.byref(bad), ctypes.byref(h)) == 1   # CYQ_ERR_INVALID_ARG
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_device():
+    """Host-side argument checks of the coupling-tail and Newton-assembly entry
+    points (no device work: a null handle is refused before anything runs)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("host-only check")
+    from paper_2512_09058_gb300 import build, cyq
+    build.build()
+    L = cyq.load()
+    INVALID = 1
+    assert L.cyq_set_pcr_tail(None, 2) == INVALID
+    v = ctypes.c_int32(-1)
+    assert L.cyq_get_pcr_tail(None, ctypes.byref(v)) == INVALID
+    a, o = cyq.cyq_newton_in(), cyq.cyq_newton_out()
+    assert L.cyq_assemble_newton(None, ctypes.byref(a), ctypes.byref(o), None) == INVALID
