@@ -1,14 +1,16 @@
 #!/usr/bin/env python3
 """KKT factor+solve benchmark on one node.
 
-Workload (default): 1024 independent linear-quadratic OCPs, N = 64 stages,
-nx = 12, nu = 4, stage cross terms S and diagonal regularisation Sigma
-log-uniform in [1e-6, 1e6]; one factorization + 4 right-hand sides per OCP.
-One step = factor all OCPs + solve the 4 right-hand sides, with the inputs
-resident in device memory (218 MB of float64 data, larger than the 129 MB L2).
-``--workload`` selects the other workloads (single OCP, long horizon, uneven
-batch, adjoint); each has its own list of methods, and the headline is the
-first of them that solves every instance to the tolerance.
+Workload (default): the uneven batch, 4096 independent linear-quadratic OCPs
+with N uniform in [16, 256], nx in {4..64}, nu in {2..32} (565,757 stages,
+20 GB of float64 data), stage cross terms S and diagonal regularisation Sigma
+log-uniform in [1e-6, 1e6]; one factorization + one right-hand side per OCP.
+One step = factor all OCPs + solve, with the inputs resident in device
+memory (far larger than the 129 MB L2).  ``--workload`` selects the other
+workloads (single OCP, 1024 OCPs of N = 64 with 4 right-hand sides, long
+horizon, adjoint, mass-spring MPC, Newton step); each has its own list of
+methods, and the headline is the first of them that solves every instance
+to the tolerance.
 
 Methods (each timed over the same K steps):
   fp64_refine  float64 factor + solve, float64 residual and refinement until
@@ -42,9 +44,12 @@ from paper_2512_09058_gb300 import inputs, shard  # noqa: E402
 
 METRIC = "KKT factor+solve/sec and ns/stage at rel. residual ≤1e-10; % of roofline"
 UNIT = "OCP factor+solve/s"
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07    # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1258.6
-FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz = 80549
-WORKLOAD = "batch1024_n64_nx12_nu4"
+# pipe peaks per SM and clock: 2 FP64 FMA (measured on this GPU: one warp instruction per
+# 64 cycles on each of the four sub-partitions' FP64 units) and 128 FP32 lanes
+FP64_FMA_PER_CLK_SM = 2
+FP32_FMA_PER_CLK_SM = 128
+HBM_FALLBACK_GBS = 6800.0
+WORKLOAD = "uneven4096"
 # method -> (factor precision, refinement step budget).  Float64 refinement
 # converges in one step here; float32 needs ~5 at cond(K) ~ 1e11.
 METHODS = {"fp64": ("fp64", 0), "fp64_refine": ("fp64", 3), "fp32_refine": ("fp32_refine", 8),
@@ -52,8 +57,8 @@ METHODS = {"fp64": ("fp64", 0), "fp64_refine": ("fp64", 3), "fp32_refine": ("fp3
 # refinement target: the metric's gate, as evaluated by the library's float64
 # residual kernel
 REFINE_TOL = 1e-10
-# DRAM bytes (read + write) per launch of the dominant kernel (the stage factor),
-# from one ncu capture of the current kernel (profiles/k_factor_*.md), keyed by
+# DRAM bytes (read + write) per step of the factor phase, from one ncu capture of
+# its current kernels (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # workload, factor precision and kernel; absent where no capture exists
 NCU_TRAFFIC = {("batch1024_n64_nx12_nu4", "fp64_ir32", "k_factor_pairs<12, 4>"): 217.1e6 + 219.5e6,
                ("batch1024_n64_nx12_nu4", "fp32_refine", "k_factor_segments<float>"): 217.0e6 + 88.5e6}
@@ -67,8 +72,7 @@ WORKLOADS = {
     "single_n32_nx8_nu4": dict(methods=["fp64", "fp64_refine"], graph=True, adjoint=False, tune_segments=True),
     "long_n4096_nx32_nu16": dict(methods=["fp32_refine", "fp64", "fp64_refine"], graph=True, adjoint=False,
                                  tune_segments=True),
-    "uneven4096": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=True, adjoint=False,
-                       tune_segments=True),
+    "uneven4096": dict(methods=["fp32_refine", "fp64_refine"], graph=True, adjoint=False, tune_segments=True),
     "adjoint512_n128_nx24_nu8": dict(methods=["fp64_refine"], graph=True, adjoint=True, tune_segments=True),
     "massspring150_M18_N96": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=True, adjoint=False,
                                   tune_segments=True),
@@ -128,12 +132,16 @@ def parse():
 
 
 def factor_kernel_name(batch, r, f64):
-    """The stage-factor kernel the timed factorization launched (the roofline's kernel)."""
+    """The stage-factor kernels the timed factorization launched (the roofline's kernel)."""
     nx, nu = set(np.asarray(batch.nx).tolist()), set(np.asarray(batch.nu).tolist())
     one_seg = int(r["segments"].max()) == 1
     if f64 and one_seg and set(r["shapes"]["factor"]) == {16} and len(nx) == 1 and len(nu) == 1 \
             and (nx.pop(), nu.pop()) in ((12, 4), (8, 4)):
         return "k_factor_pairs<%d, %d>" % (int(batch.nx[0]), int(batch.nu[0]))
+    path = r.get("path") or {}
+    if not f64 and path.get("one_warp_per_item") and path.get("warp_items", 0) > 0:
+        return "k_ingest_f32 + k_factor_team + k_inv_R_f32%s" % (
+            "" if one_seg else " (+ k_factor_segments<float> for segments >= 1, cyclic reduction)")
     return "k_factor_segments<%s>%s" % ("double" if f64 else "float", "" if one_seg else " (+ cyclic reduction)")
 
 
@@ -183,6 +191,67 @@ def factor_fma(N, nx, nu, P):
             s *= 2
         total += n3 / 6.0
     return total
+
+
+def device_peaks(torch, clk):
+    """Pipe peaks (GFLOP/s) from the device's SM count and the SM clock sampled
+    under load (its maximum), and the HBM peak: the measured copy bandwidth in
+    MEASURED_PEAKS.json when the file is there, else the fallback figure."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    measured = {}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            measured = json.load(f)
+    mhz = (clk or {}).get("sm_max_mhz") or measured.get("sm_max_mhz") or 2070.0
+    ghz = float(mhz) / 1e3
+    hbm = measured.get("hbm_gbs")
+    return dict(sms=sms, ghz=ghz, fp64=sms * FP64_FMA_PER_CLK_SM * 2 * ghz, fp32=sms * FP32_FMA_PER_CLK_SM * 2 * ghz,
+                hbm=float(hbm) if hbm else HBM_FALLBACK_GBS,
+                hbm_source="of measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "of fallback",
+                pipe_source="derived: %d SMs x %%d FMA/clk x 2 x %.3f GHz" % (sms, ghz))
+
+
+def data_bytes(batch):
+    """Float64 bytes of the stage data (Q, R, S, A, B, Sigma) that a pass over the batch reads."""
+    b = batch.Q.nbytes + batch.R.nbytes + batch.S.nbytes + batch.A.nbytes + batch.B.nbytes
+    return b + (batch.Sigma.nbytes if batch.Sigma is not None else 0)
+
+
+def factor_store_elems(batch):
+    """Elements of the stored stage factor per batch: L ((nu+nx)^2), 1/diag (nu+nx),
+    [B A] (nx (nu+nx)) per stage."""
+    N, nx, nu = (np.asarray(v, np.int64) for v in (batch.N, batch.nx, batch.nu))
+    nux = nx + nu
+    return int((N * (nux * nux + nux + nx * nux)).sum())
+
+
+def residual_fma(batch):
+    """FMAs of one float64 residual (rows of eq. opt-cond-ocp-eq) per right-hand side."""
+    N, nx, nu = (np.asarray(v, np.int64) for v in (batch.N, batch.nx, batch.nu))
+    return int((N * (nu * nu + 4 * nx * nu + 3 * nx * nx + nu + nx)).sum())
+
+
+def roofline_of(name, flops, bytes_alg, ms, pipe_peak, hbm_peak, pipe_name, peaks, traffic=None):
+    """The roofline entry of one kernel (or phase): its bound is the larger of the
+    time at the pipe peak and the time at the HBM peak for its algorithmic work."""
+    t_alu = flops / (pipe_peak * 1e9)
+    t_hbm = bytes_alg / (hbm_peak * 1e9)
+    sec = ms / 1e3
+    if t_hbm >= t_alu:
+        ach = bytes_alg / sec / 1e9
+        out = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+               "frac": ach / hbm_peak, "peak_source": peaks["hbm_source"]}
+    else:
+        ach = flops / sec / 1e9
+        out = {"kernel": name, "bound": "alu", "achieved": ach, "peak": pipe_peak, "unit": "GFLOP/s",
+               "frac": ach / pipe_peak,
+               "peak_source": peaks["pipe_source"] % (FP64_FMA_PER_CLK_SM if pipe_name == "fp64" else
+                                                     FP32_FMA_PER_CLK_SM) + " (%s pipe)" % pipe_name}
+    out.update({"traffic": traffic, "algorithmic_bytes": bytes_alg, "algorithmic_flops": flops, "ms": ms,
+                "t_at_hbm_peak_ms": t_hbm * 1e3, "t_at_pipe_peak_ms": t_alu * 1e3})
+    return out
 
 
 def batch_factor_fma(batch, segments):
@@ -360,6 +429,7 @@ def run_method(torch, cyq, batch, data, b, x0, method, steps, warmup, dist, grap
     nrhs = len(batch.rhs)
     s, P = tuned_solver(torch, cyq, batch, data, b, method, tune_segments)
     shapes = s.launch_shapes(nrhs=nrhs)
+    path = s.factor_path()
     z = torch.empty_like(b)
     mask = _loss_grad(torch, batch, torch.ones_like(b[:s.kkt_size])) / 2.0 if adjoint else None
 
@@ -439,6 +509,34 @@ def run_method(torch, cyq, batch, data, b, x0, method, steps, warmup, dist, grap
         dist.barrier()
     factor_ms = [e[0].elapsed_time(e[1]) for e in ev]
     solve_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    # the residual and the correction (one substitution with the stored factor, both sweeps
+    # and the coupling solve) timed on their own with CUDA events, for their rooflines
+    kk = s.kkt_size
+    dz = torch.empty_like(b)
+    reps = max(3, min(steps, 10))
+    phase = {}
+    for name, fn in (("residual", lambda: s.residual(b[:kk], z[:kk])),
+                     ("correction", lambda: s.apply_factor(b, dz, nrhs=nrhs))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            if flush is not None:
+                flush.zero_()
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        phase[name] = e0.elapsed_time(e1) / reps
+    if flush is not None:   # the flushes inside the loop above are not the phases' time
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(reps):
+            flush.zero_()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        for k in phase:
+            phase[k] = max(0.0, phase[k] - f0.elapsed_time(f1) / reps)
     status = s.instance_status()
     st = s.stats()
     if it_max == 0:   # plain solve: measure the residual it reached (outside the timed region)
@@ -452,7 +550,8 @@ def run_method(torch, cyq, batch, data, b, x0, method, steps, warmup, dist, grap
     s.close()
     return dict(total_ms=total_ms, factor_ms=float(np.mean(factor_ms)), solve_ms=float(np.mean(solve_ms)),
                 status_ok=bool((status == 0).all()), stats=st, segments=segments,
-                launches_per_step=launches_factor + launches_solve, P=P, shapes=shapes)
+                launches_per_step=launches_factor + launches_solve, P=P, shapes=shapes, phase=phase,
+                path=path)
 
 
 def run_e2e(torch, cyq, batch, method, steps, warmup, data, b, P=None, adjoint=False):
@@ -630,28 +729,55 @@ def main():
                "value_1core": rate1,
                "sample_1core": "first %d OCPs of the workload x %d rhs (%.1f s of one host core)" % (done1, nrhs, el1)}
 
+    peaks = device_peaks(torch, clk)
+    dbytes = data_bytes(batch)
+    felems = factor_store_elems(batch)
+
+    def phase_rooflines(m, r):
+        """Rooflines of the factor phase, the residual and the correction of method m."""
+        prec = METHODS[m][0]
+        f64 = prec in ("fp64", "fp64_ir32")   # the stage factor runs in float64
+        el = 8 if prec == "fp64" else (12 if prec == "fp64_ir32" else 4)   # bytes of the stored factor per element
+        fl = 2.0 * batch_factor_fma(batch, r["segments"])
+        kname = factor_kernel_name(batch, r, f64)
+        tkey = (args.workload, prec, kname)
+        fac = roofline_of(kname, fl, dbytes + el * felems, r["factor_ms"], peaks["fp64" if f64 else "fp32"],
+                          peaks["hbm"], "fp64" if f64 else "fp32", peaks, NCU_TRAFFIC.get(tkey))
+        kk8 = 8.0 * batch.kkt_size
+        res = roofline_of("k_residual (1 rhs) + k_resid_finalize", 2.0 * residual_fma(batch), dbytes + 3 * kk8,
+                          r["phase"]["residual"], peaks["fp64"], peaks["hbm"], "fp64", peaks)
+        cel = 8 if prec == "fp64" else 4   # the correction's factor
+        nux = np.asarray(batch.nx, np.int64) + np.asarray(batch.nu, np.int64)
+        cfl = 2.0 * nrhs * float((np.asarray(batch.N, np.int64) * (2 * nux * nux + 2 * np.asarray(batch.nx) * nux)).sum())
+        cor = roofline_of("k_solve_backward + k_cr_solve + k_solve_forward (%d rhs)" % nrhs, cfl,
+                          2.0 * cel * felems + nrhs * 4 * kk8, r["phase"]["correction"],
+                          peaks["fp64" if cel == 8 else "fp32"], peaks["hbm"], "fp64" if cel == 8 else "fp32", peaks)
+        return {"factor": fac, "residual": res, "correction": cor}
+
     variants = {}
     for m, r in results.items():
         msm = r["total_ms"] / args.steps
-        fl = 2.0 * batch_factor_fma(batch, r["segments"])
-        f64 = METHODS[m][0] in ("fp64", "fp64_ir32")   # the stage factor runs in float64
-        peak = FP64_PEAK_GFLOPS if f64 else FP32_PEAK_GFLOPS
+        rl = phase_rooflines(m, r)
         variants[m] = {"value": world * batch.size / (msm / 1e3), "ms_per_step": msm,
                        "factor_ms": r["factor_ms"], "solve_ms": r["solve_ms"],
+                       "residual_ms": r["phase"]["residual"], "correction_ms": r["phase"]["correction"],
                        "ns_per_stage": msm * 1e6 / stages,
                        "max_rel_residual": r["stats"]["max_rel_residual"],
                        "refine_steps": r["stats"]["refine_steps"], "status_ok": r["status_ok"],
                        "segments_per_ocp": [int(r["segments"].min()), int(r["segments"].max())],
                        "segments_tuned": r["P"] is not None,
-                       "threads_per_item": r["shapes"],
-                       "factor_gflops": fl / (r["factor_ms"] / 1e3) / 1e9,
-                       "factor_frac_of_pipe_peak": fl / (r["factor_ms"] / 1e3) / 1e9 / peak}
-    fl = 2.0 * batch_factor_fma(batch, R["segments"])
-    f64 = METHODS[head][0] in ("fp64", "fp64_ir32")
-    peak = FP64_PEAK_GFLOPS if f64 else FP32_PEAK_GFLOPS
-    kname = factor_kernel_name(batch, R, f64)
-    tkey = (args.workload, METHODS[head][0], kname)
-    achieved = fl / (R["factor_ms"] / 1e3) / 1e9
+                       "threads_per_item": r["shapes"], "factor_path": r["path"],
+                       "factor_gflops": rl["factor"]["algorithmic_flops"] / (r["factor_ms"] / 1e3) / 1e9,
+                       "rooflines": {k: {kk: v[kk] for kk in ("bound", "achieved", "unit", "frac", "ms")}
+                                     for k, v in rl.items()}}
+    rl = phase_rooflines(head, R)
+    # the dominant part of the step: the factor phase against the residual and the correction
+    # times the number of refinement steps (an upper bound of their share: later steps skip the
+    # instances already at the tolerance)
+    nsteps = max(1, R["stats"]["refine_steps"] + 1)
+    share = {"factor": R["factor_ms"], "residual": R["phase"]["residual"] * nsteps,
+             "correction": R["phase"]["correction"] * nsteps}
+    dominant = max(share, key=share.get)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -667,14 +793,9 @@ def main():
         "max_rel_residual": R["stats"]["max_rel_residual"],
         "refine_steps": R["stats"]["refine_steps"],
         "status_ok": R["status_ok"],
-        "roofline": {"kernel": kname,
-                     "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": NCU_TRAFFIC.get(tkey),
-                     "traffic_hbm_gbs": (NCU_TRAFFIC[tkey] / (R["factor_ms"] / 1e3) / 1e9
-                                         if tkey in NCU_TRAFFIC else None),
-                     "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz" if f64 else
-                                     "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz")},
+        "roofline": dict(rl[dominant], part=dominant),
+        "rooflines": rl,
+        "peaks": {k: peaks[k] for k in ("sms", "ghz", "fp64", "fp32", "hbm", "hbm_source")},
         "variants": variants,
         "gpu_launches": R["launches_per_step"] * args.steps,
         "clocks": clk,

@@ -72,7 +72,9 @@ typedef enum cyq_status {
     CYQ_ERR_TIMEOUT = 5,       /* a bounded device wait expired */
     CYQ_ERR_NO_FACTOR = 6,     /* solve called before a successful factor */
     CYQ_ERR_UNIMPLEMENTED = 7,
-    CYQ_ERR_NO_DEVICE = 8      /* no CUDA device visible */
+    CYQ_ERR_NO_DEVICE = 8,     /* no CUDA device visible */
+    CYQ_ERR_UPDATE_RANK = 9    /* (instance status) a factorization update carried more columns than its
+                                  workspace holds: factor this instance again */
 } cyq_status;
 
 typedef enum cyq_precision {
@@ -145,6 +147,46 @@ cyq_status cyq_factor(cyq_handle h, const double *Q, const double *R, const doub
 cyq_status cyq_solve(cyq_handle h, const double *b, double *z, int32_t nrhs, cyq_stream stream);
 
 /*
+ * One forward/backward substitution with the stored factor, without residual
+ * or refinement: dz = K~^{-1} r for nrhs right-hand sides, where K~ is the
+ * factor a refinement correction uses (the handle's factor; in CYQ_FP64_IR32
+ * mode its float32 copy).  This is the correction step of the refinement loop
+ * of cyq_solve on its own (e.g. to apply the factor as a preconditioner).
+ * r and dz as b and z of cyq_solve (must not overlap).  Asynchronous.
+ * Errors returned: INVALID_ARG, NO_FACTOR, CUDA.
+ */
+cyq_status cyq_apply_factor(cyq_handle h, const double *r, double *dz, int32_t nrhs, cyq_stream stream);
+
+/*
+ * Factorization update (Sec. 6, Alg. fact-mod-riccati-update): turns the
+ * stored factor into the factor of the KKT matrix whose stage matrices are
+ *   H~_s = H_s + sum_r delta_{s,r} w_{s,r} w_{s,r}^T      (s = 0 .. N-1)
+ * without factoring the data again (e.g. the constraint rows whose activity
+ * changed between two augmented-Lagrangian Newton iterations, eq.
+ * low-rank-update-Hj).  Stage s's matrix couples (u^s, x^s) for s >= 1 and
+ * (u^0, x^N) for s = 0, so w_{s,r} has nu + nx entries [u part | x part]; at
+ * s = 0 every row must be zero in its u part or in its x part (a row of D_0
+ * or of C_N).  Each row is applied by sigma-orthogonal rotations (Givens for
+ * delta > 0, hyperbolic for delta < 0) and carried to the earlier stages
+ * through the dynamics, so the rank per stage grows with the rows added on the
+ * way; the single coupling block is factored again.  One-segment handles only.
+ *   Q, R, S: device float64 data of the updated problem (same layout as for
+ *   cyq_factor; S may be NULL): the residual and refinement of later solves
+ *   read them (A, B, Sigma of the last cyq_factor stay bound).
+ *   w: device float64, per instance (in instance order) N * m_max rows of
+ *   nu + nx entries, stage-major; delta: device float64, N * m_max per
+ *   instance; a row with delta = 0 is skipped.
+ * Instance status: CYQ_ERR_NOT_PD if a downdate leaves a stage matrix
+ * indefinite, CYQ_ERR_UPDATE_RANK if a stage carries more than max(32, nx)
+ * update columns (refactor that instance).  Asynchronous.  The factor of the
+ * handle's precision is updated (and the float32 copy of CYQ_FP64_IR32).
+ * Errors returned: INVALID_ARG, NO_FACTOR, UNIMPLEMENTED (more than one
+ * segment), CUDA.
+ */
+cyq_status cyq_update_factor(cyq_handle h, const double *Q, const double *R, const double *S, const double *w,
+                             const double *delta, int32_t m_max, cyq_stream stream);
+
+/*
  * b = -(r~, q, f~) for one right-hand side of the original problem
  * (eq. opt-cond-ocp-eq: r~^0 = r^0 + S_0 x_init, f~^0 = f^0 + A_0 x_init),
  * using the data passed to the last cyq_factor.  q, r, c, x_init are device
@@ -210,6 +252,18 @@ cyq_status cyq_get_segments(cyq_handle h, int32_t *P_out);
  */
 cyq_status cyq_get_stage_factor(cyq_handle h, int32_t instance, int32_t stage, double *L_out);
 
+/*
+ * Diagnostics: the Cholesky pivot routine of the stage factorizations applied
+ * element-wise: l[i] = sqrt(d[i]), il[i] = 1 / sqrt(d[i]) for positive finite
+ * d (float64: a float32 estimate refined by a float64 series, with the library
+ * routines outside [2^-120, 2^120]; float32: rsqrtf and one Newton step).
+ * d, l, il (float64) and df, lf, ilf (float32) are device arrays of n
+ * elements; either triple may be NULL.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (n < 0, missing outputs), CUDA.
+ */
+cyq_status cyq_pivot_eval(const double *d, double *l, double *il, const float *df, float *lf, float *ilf,
+                          int64_t n, cyq_stream stream);
+
 /* Number of kernels launched by the last cyq_factor and cyq_solve calls. */
 int64_t cyq_last_launch_count(cyq_handle h);
 
@@ -268,12 +322,11 @@ cyq_status cyq_tune_segments(const cyq_desc *desc, const double *Q, const double
 /*
  * Allocation-free factor + solve of ONE OCP in float64 (one segment, one
  * right-hand side).  The paper has no counterpart: this entry point exists
- * for callers that must not allocate device memory at call time (a CUDA
- * graph captured into a fixed memory plan, a real-time control loop that
- * allocates only at start-up, a host whose device allocator belongs to
- * another runtime).  Its workspace is one fixed array of 2^20 doubles
- * (8 MiB) in the library's device image, held on every GPU that loads the
- * library until the process exits; it calls no allocator.
+ * for callers that must not allocate device memory while they run (a
+ * real-time control loop that allocates only at start-up, a host whose device
+ * memory belongs to another runtime or allocator).  Its workspace is one fixed
+ * array of 2^20 doubles (8 MiB) in the library's device image, held on every
+ * GPU that loads the library until the process exits; it calls no allocator.
  *   Inputs: N, nx, nu and device float64 data Q, R, S (or NULL), A, B, Sigma
  *   (or NULL) of one instance in the layout above, and the right-hand side b
  *   (N (nu + 2 nx) elements).  Outputs: the solution z (same size, must not
@@ -282,11 +335,14 @@ cyq_status cyq_tune_segments(const cyq_desc *desc, const double *Q, const double
  *   Size limit: N (nu+nx)^2 + N nx (nu+nx) + N (nu+nx) + 5 nx^2 + 3 nx (+ padding) must
  *   not exceed 2^20 doubles; larger problems return CYQ_ERR_INVALID_ARG with
  *   the needed size in cyq_last_error().
- *   The workspace is shared by every call on a device: calls that overlap on
- *   the GPU (different streams or host threads) race and must be serialised.
- *   The first call on a device looks up the workspace address with that
- *   device current; make it before any stream capture.  Asynchronous on
- *   `stream` (the data pointers must stay valid until it completes).
+ *   The workspace is shared by every call on a device and keeps the last
+ *   call's contents: calls that overlap on the GPU (different streams or host
+ *   threads) race and must be serialised.  The first call on a device looks up
+ *   the workspace address with that device current and keeps it for the life
+ *   of the process (a device reset after it is not supported); make that first
+ *   call before any stream capture.  The plan records are written on the
+ *   device by a small kernel.  Asynchronous on `stream` (the data pointers must
+ *   stay valid until it completes).
  */
 cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu, const double *Q, const double *R,
                                     const double *S, const double *A, const double *B, const double *Sigma,
@@ -308,6 +364,23 @@ cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu, const dou
 cyq_status cyq_set_pcr_tail(cyq_handle h, int32_t levels);
 /* Tail levels in use (after clamping). */
 cyq_status cyq_get_pcr_tail(cyq_handle h, int32_t *levels);
+
+/*
+ * Float32 factor path (CYQ_FP32_REFINE handles).  With one_warp_per_item = 1
+ * (the default) every segment that carries no A^cl (segment 0 of every
+ * instance, i.e. whole horizons when P = 1) whose padded blocks satisfy
+ * nu <= 32, nx <= 64 is factored by one warp in one persistent launch for the
+ * whole batch (the modified Riccati recursion of Alg. fact-mod-riccati and the
+ * segment's compute-schur blocks, same stored factor layout); the other
+ * segments, and every segment when one_warp_per_item = 0, run the
+ * per-size-class kernels.  Both
+ * paths compute the same factor up to float32 rounding (different summation
+ * order).  The next cyq_solve needs a new cyq_factor.  Errors: INVALID_ARG.
+ */
+cyq_status cyq_set_factor_path(cyq_handle h, int32_t one_warp_per_item);
+/* The float32 factor path in use and the number of work items the one-warp
+ * launch covers (0 for float64 handles); either pointer may be NULL. */
+cyq_status cyq_get_factor_path(cyq_handle h, int32_t *one_warp_per_item, int64_t *warp_items);
 
 /*
  * Newton system of the augmented Lagrangian inner problem (Sec. 5, eqs.

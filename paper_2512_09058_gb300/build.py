@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcyq.so")
-SOURCES = ["api.cu", "factor.cu", "cr.cu", "solve.cu", "resid.cu", "noalloc.cu", "newton.cu"]
+SOURCES = ["api.cu", "factor.cu", "factor_warp.cu", "cr.cu", "solve.cu", "resid.cu", "noalloc.cu", "newton.cu", "update.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "-I", CSRC]

@@ -22,7 +22,18 @@ namespace {
 
 thread_local std::string g_last_error;
 
-constexpr int kSMs = 152;
+// Streaming multiprocessors of a device (queried once per device).
+int sm_count(int dev) {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    cache[dev] = n;
+    return n;
+}
 
 struct Group {
     int cls = 0;
@@ -38,11 +49,17 @@ struct Group {
     int max_nx = 0, max_nu = 0;
     std::vector<Item> items;
     Item *d_items = nullptr;
+    // float32 factor: the items not covered by the one-warp-per-item launch
+    std::vector<Item> items_rest;
+    Item *d_items_rest = nullptr;
+    bool rest_set = false;                     // items_rest replaces items in float32 factor launches
+    bool warp_on = true;                       // (mirrors the handle's factor path)
 };
 
 struct FactorSet {
     void *L = nullptr, *LB = nullptr, *F = nullptr, *DI = nullptr;
     void *BA = nullptr;   // float32 [B A] copies (float32 sets only)
+    float *Hf = nullptr;  // float32 stage matrices of the one-warp factor (float32 sets only)
     bool fp64 = true;
 };
 
@@ -80,6 +97,7 @@ struct cyq_handle_s {
     size_t crs_smem1 = 0;
     int max_nx = 0;
     int smem_optin = 0;
+    int sms = 1;                  // streaming multiprocessors of the device
     // device
     DevicePtrs mem;
     Inst *d_inst = nullptr;
@@ -103,6 +121,17 @@ struct cyq_handle_s {
     bool factored = false;
     long long launches = 0;
     int last_nrhs = 0;
+    // float32 factor, one team per item: items by class (longest first), the plan, the queue heads
+    std::vector<Item> warp_items;
+    TeamPlanDev team_plan;
+    Item *d_warp_items = nullptr;
+    int *d_warp_counter = nullptr;
+    std::vector<IngestChunk> ingest_chunks;
+    IngestChunk *d_ingest_chunks = nullptr;
+    long long nHf = 0;            // floats of the ingested stage matrices
+    size_t warp_arena = 0;
+    int warp_grid = 0;
+    bool warp_on = true;          // float32 factor path: one team per item in one launch (else per-class kernels)
     // Newton-system assembly: constraint rows per instance and the offsets they imply
     std::vector<int> alm_ny;
     std::vector<AlmOff> alm_off;
@@ -133,6 +162,9 @@ struct DeviceGuard {
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
+
+// Update columns a stage of cyq_update_factor can carry (at least nx).
+constexpr int kUpdateColumns = 32;
 
 // Records per residual work item: small enough that the last refinement steps,
 // with few instances left, still spread over many SMs.
@@ -177,8 +209,8 @@ int size_class(int nx, int nu) {
 
 // Segments per instance: enough (instance, segment) work items to occupy the
 // GPU when the batch is small, at least 8 stages per segment, a power of two.
-int auto_segments(int batch, int N) {
-    const int target = 2 * kSMs;
+int auto_segments(int batch, int N, int sms) {
+    const int target = 2 * sms;
     if (batch >= target) return 1;
     const int want = (target + batch - 1) / batch;
     int P = 1;
@@ -285,14 +317,17 @@ FactorArgs factor_args(cyq_handle h, const FactorSet &fs, const int *skip) {
     a.Y = h->Y;
     a.status = h->status;
     a.skip = skip;
+    a.Hf = fs.Hf;
     return a;
 }
 
 // The stage factor over the work items of one size class.
 cudaError_t launch_group_factor(const FactorSet &fs, const Group &g, FactorArgs a, cudaStream_t st) {
     const int pi = fs.fp64 ? 1 : 0;
-    a.items = g.d_items;
-    a.n_items = (int)g.items.size();
+    const bool rest = !fs.fp64 && g.rest_set && g.warp_on;
+    a.items = rest ? g.d_items_rest : g.d_items;
+    a.n_items = (int)(rest ? g.items_rest.size() : g.items.size());
+    if (a.n_items == 0) return cudaSuccess;
     a.stage_in_smem = g.staged[pi];
     a.need_G2 = g.need_G2;
     return launch_factor_segments(fs.fp64, factor_team_of(g, fs.fp64), g.shape > 0 ? g.shape : 0, g.smem_factor[pi], a,
@@ -301,7 +336,26 @@ cudaError_t launch_group_factor(const FactorSet &fs, const Group &g, FactorArgs 
 
 cyq_status run_factor(cyq_handle h, const FactorSet &fs, const int *skip, cudaStream_t st) {
     FactorArgs a = factor_args(h, fs, skip);
+    if (!fs.fp64 && !h->warp_items.empty() && h->warp_on) {
+        // every segment without A^cl of the batch in one persistent launch
+        IngestArgs g{};
+        g.inst = h->d_inst;
+        g.chunks = h->d_ingest_chunks;
+        g.n_chunks = (int)h->ingest_chunks.size();
+        g.data = h->data;
+        g.Hf = fs.Hf;
+        g.BAf = static_cast<float *>(fs.BA);
+        CYQ_CUDA(launch_ingest_f32(g, st));
+        ++h->launches;
+        TeamPlanDev plan = h->team_plan;
+        plan.items = h->d_warp_items;
+        plan.counter = h->d_warp_counter;
+        CYQ_CUDA(launch_factor_team(a, plan, h->warp_grid, st));
+        CYQ_CUDA(launch_inv_R_f32(g, static_cast<float *>(fs.L), static_cast<const float *>(fs.DI), st));
+        h->launches += 2;
+    }
     for (const Group &g : h->groups) {
+        if (!fs.fp64 && g.rest_set && g.warp_on && g.items_rest.empty()) continue;
         CYQ_CUDA(launch_group_factor(fs, g, a, st));
         ++h->launches;
     }
@@ -394,6 +448,7 @@ const char *cyq_status_string(cyq_status s) {
         case CYQ_ERR_NO_FACTOR: return "no factorization";
         case CYQ_ERR_UNIMPLEMENTED: return "unimplemented";
         case CYQ_ERR_NO_DEVICE: return "no CUDA device";
+        case CYQ_ERR_UPDATE_RANK: return "update rank above the workspace";
     }
     return "unknown status";
 }
@@ -417,8 +472,10 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     DeviceGuard guard(dev);
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int sms = sm_count(dev);
 
     cyq_handle h = new cyq_handle_s();
+    h->sms = sms;
     h->device = dev;
     h->batch = desc->batch;
     h->precision = desc->precision;
@@ -432,20 +489,21 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     const bool float_sweeps = h->precision != CYQ_FP64;
 
     long long oQ = 0, oR = 0, oS = 0, oA = 0, oB = 0, oSig = 0, oZ = 0, oL = 0, oLB = 0, oF = 0, oDI = 0, oBA = 0, oBlk = 0,
-              oVec = 0, oq = 0, orv = 0, oc = 0, ox0 = 0;
+              oVec = 0, oq = 0, orv = 0, oc = 0, ox0 = 0, oNs = 0, oNn = 0;
     std::vector<Item> all_items;
     int item = 0;
     for (int i = 0; i < desc->batch; ++i) {
         const int N = desc->N[i], nx = desc->nx[i], nu = desc->nu[i];
         if (N < 1 || nx < 1 || nu < 1) { delete h; return CYQ_ERR_INVALID_ARG; }
         int P = desc->P_per_instance ? desc->P_per_instance[i] : desc->P;
-        if (P <= 0) P = auto_segments(desc->batch, N);
+        if (P <= 0) P = auto_segments(desc->batch, N, sms);
         if (P > N) P = N;
         Inst in{};
         in.N = N; in.nx = nx; in.nu = nu; in.P = P; in.item0 = item;
         in.oQ = oQ; in.oR = oR; in.oS = oS; in.oA = oA; in.oB = oB; in.oSig = oSig; in.oZ = oZ;
         in.oL = oL; in.oLB = oLB; in.oF = oF; in.oDI = oDI; in.oBA = oBA; in.oBlk = oBlk; in.oVec = oVec;
         in.oq = oq; in.orv = orv; in.oc = oc; in.ox0 = ox0;
+        in.oN = oNs; in.oNn = oNn;
         const long long nux = nx + nu;
         oQ += (long long)(N + 1) * nx * nx; oR += (long long)N * nu * nu; oS += (long long)N * nu * nx;
         oA += (long long)N * nx * nx; oB += (long long)N * nx * nu; oSig += (long long)(N + 1) * (nu + nx);
@@ -455,6 +513,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         oBA += (long long)N * nx * nux;
         oBlk += (long long)P * nx * nx; oVec += (long long)P * nx;
         oq += (long long)(N + 1) * nx; orv += (long long)N * nu; oc += (long long)N * nx; ox0 += nx;
+        oNs += N; oNn += (long long)N * nux;
         h->inst.push_back(in);
         if (P > 1) h->cr_list.push_back(i);
         else h->p1_list.push_back(i);
@@ -505,7 +564,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
             // solve: a ring of up to 4 stage packages (prefetch depth 3) within the shared
             // memory one CTA may take while all of the class's items stay resident
             {
-                const long long per_sm = std::max<long long>(1, ((long long)g.items.size() + kSMs - 1) / kSMs);
+                const long long per_sm = std::max<long long>(1, ((long long)g.items.size() + sms - 1) / sms);
                 const size_t budget = std::max<size_t>(48 * 1024, (size_t)228 * 1024 / per_sm);
                 int nb = 1;
                 for (int cand = 4; cand >= 2; --cand) {
@@ -532,6 +591,81 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         }
     }
     if (h->crs_smem1 * (h->max_nrhs + 1) > (size_t)smem_optin) { delete h; return CYQ_ERR_INVALID_ARG; }
+    if (h->precision == CYQ_FP32_REFINE) {
+        // float32 factor: segments without A^cl (segment 0) whose padded blocks fit
+        // three rows per lane go to the one-warp-per-item launch, longest first,
+        // packed into CTA arenas (two CTAs per SM)
+        int smem_sm = 0;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        // two CTAs per SM: each takes its arena, its static shared memory and the 1 KB the
+        // system reserves per CTA
+        const size_t half = (size_t)smem_sm / 2;
+        const size_t arena = std::min<size_t>((size_t)smem_optin, half > 2048 ? half - 2048 : 0);
+        struct Cand { Item it; double cost; size_t bytes; };
+        std::vector<Cand> cand;
+        for (Group &g : h->groups) {
+            g.rest_set = true;
+            g.items_rest.clear();
+            for (const Item &it : g.items) {
+                const Inst &in = h->inst[it.inst];
+                const int nup = (in.nu + 3) & ~3, nxp = (in.nx + 3) & ~3;
+                const size_t bytes = warp_slot_bytes(in.nx, in.nu);
+                if (it.seg == 0 && nup + nxp <= kWarpMaxNp && nxp <= kWarpMaxNxp && nup <= 32 && bytes <= arena) {
+                    const double np = nup + nxp;
+                    const double per = np * np * np / 6.0 + 0.5 * np * np * nxp + 0.5 * np * nxp * nxp;
+                    cand.push_back(Cand{it, seg_len(it.seg, in.N, in.P) * per, bytes});
+                } else {
+                    g.items_rest.push_back(it);
+                }
+            }
+        }
+        std::stable_sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) { return x.cost > y.cost; });
+        // classes by the slot an item needs: four per CTA arena (teams of 32), two (64), one (128)
+        const int arena_floats = (int)(arena / 64 * 16);   // every team slot a multiple of 16 bytes
+        const size_t slot2 = (size_t)(arena_floats / 4) / 4 * 16, slot1 = (size_t)(arena_floats / 2) / 4 * 16;
+        std::vector<Item> cls[3];
+        double work[3] = {0.0, 0.0, 0.0};
+        for (const Cand &c : cand) {
+            const int k = c.bytes <= slot2 ? 2 : (c.bytes <= slot1 ? 1 : 0);
+            cls[k].push_back(c.it);
+            work[k] += c.cost;
+        }
+        TeamPlanDev &tp = h->team_plan;
+        int off = 0;
+        for (int k = 0; k < 3; ++k) {
+            tp.off[k] = off;
+            tp.n[k] = (int)cls[k].size();
+            off += tp.n[k];
+            for (const Item &it : cls[k]) h->warp_items.push_back(it);
+        }
+        tp.arena_floats = arena_floats;
+        // CTAs per configuration in proportion to the class's work (every CTA has four warps);
+        // teams that run out of items continue with the smaller classes
+        const int grid = 2 * sms;
+        const double wsum = work[0] + work[1] + work[2];
+        int g[3] = {0, 0, 0};
+        for (int k = 0; k < 2; ++k) {
+            if (tp.n[k] == 0) continue;
+            const int teams = k == 0 ? 1 : 2;
+            g[k] = std::max(1, (int)std::lround(grid * work[k] / std::max(wsum, 1.0)));
+            g[k] = std::min(g[k], (tp.n[k] + teams - 1) / teams);
+        }
+        g[2] = tp.n[2] > 0 ? std::max(1, grid - g[0] - g[1]) : 0;
+        tp.g0 = g[0];
+        tp.g1 = g[1];
+        // float32 stage matrices of the covered segments (stage s of instance i at oHf + s np^2)
+        long long oHf = 0;
+        for (const Item &it : h->warp_items) {
+            Inst &in = h->inst[it.inst];
+            in.oHf = oHf;
+            oHf += (long long)in.N * (long long)warp_stage_floats(in.nx, in.nu);
+            const int len = seg_len(it.seg, in.N, in.P);
+            for (int t0 = 0; t0 < len; t0 += 16) h->ingest_chunks.push_back(IngestChunk{it.inst, t0, std::min(len, t0 + 16)});
+        }
+        h->nHf = oHf;
+        h->warp_arena = arena;
+        h->warp_grid = g[0] + g[1] + g[2];
+    }
     // level-parallel cyclic-reduction jobs
     {
         int maxP = 1;
@@ -588,9 +722,17 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     {
         int maxP = 0;
         for (int i : h->cr_list) maxP = std::max(maxP, h->inst[i].P);
-        h->cr_levels = !h->cr_list.empty() && (int)h->cr_list.size() < 2 * kSMs && maxP >= 8;
+        h->cr_levels = !h->cr_list.empty() && (int)h->cr_list.size() < 2 * sms && maxP >= 8;
     }
     for (Group &g : h->groups) ALLOC(g.d_items, g.items.size());
+    for (Group &g : h->groups)
+        if (g.rest_set) ALLOC(g.d_items_rest, g.items_rest.size());
+    if (!h->warp_items.empty()) {
+        ALLOC(h->d_warp_items, h->warp_items.size());
+        ALLOC(h->d_warp_counter, 3);
+        ALLOC(h->d_ingest_chunks, h->ingest_chunks.size());
+        ALLOC(h->fac.Hf, (size_t)h->nHf);
+    }
     // fac (the handle's factor) and, in float32 mode, fac64 (escalation), in float64
     // mode with float32 corrections, fac32 (float32 copy)
     for (int pass = 0; pass < (float_sweeps ? 2 : 1); ++pass) {
@@ -644,6 +786,17 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     for (Group &g : h->groups)
         if ((e = cudaMemcpy(g.d_items, g.items.data(), sizeof(Item) * g.items.size(), cudaMemcpyHostToDevice)))
             return fail(e, "cudaMemcpy");
+    for (Group &g : h->groups)
+        if (g.rest_set && !g.items_rest.empty() &&
+            (e = cudaMemcpy(g.d_items_rest, g.items_rest.data(), sizeof(Item) * g.items_rest.size(),
+                            cudaMemcpyHostToDevice)))
+            return fail(e, "cudaMemcpy");
+    if (!h->warp_items.empty() &&
+        ((e = cudaMemcpy(h->d_warp_items, h->warp_items.data(), sizeof(Item) * h->warp_items.size(),
+                         cudaMemcpyHostToDevice)) ||
+         (e = cudaMemcpy(h->d_ingest_chunks, h->ingest_chunks.data(), sizeof(IngestChunk) * h->ingest_chunks.size(),
+                         cudaMemcpyHostToDevice))))
+        return fail(e, "cudaMemcpy");
     *out = h;
     return CYQ_OK;
 }
@@ -712,6 +865,65 @@ cyq_status cyq_solve(cyq_handle h, const double *b, double *z, int32_t nrhs, cyq
         return run_solve(h, h->fac, b, z, nrhs, nullptr, st);
     }
     return run_refined_solve(h, b, z, nrhs, st);
+}
+
+cyq_status cyq_apply_factor(cyq_handle h, const double *r, double *dz, int32_t nrhs, cyq_stream stream) {
+    if (!h || !r || !dz || nrhs < 1 || nrhs > h->max_nrhs) return CYQ_ERR_INVALID_ARG;
+    if (!h->factored) return CYQ_ERR_NO_FACTOR;
+    DeviceGuard guard(h->device);
+    h->launches = 0;
+    // the factor the refinement corrections use: the float32 copy in CYQ_FP64_IR32 mode
+    const FactorSet &fs = h->precision == CYQ_FP64_IR32 ? h->fac32 : h->fac;
+    return run_solve(h, fs, r, dz, nrhs, nullptr, to_stream(stream));
+}
+
+cyq_status cyq_update_factor(cyq_handle h, const double *Q, const double *R, const double *S, const double *w,
+                             const double *delta, int32_t m_max, cyq_stream stream) {
+    if (!h || !Q || !R || !w || !delta || m_max < 1) return CYQ_ERR_INVALID_ARG;
+    if (!h->factored) return CYQ_ERR_NO_FACTOR;
+    if (!h->cr_list.empty()) {
+        set_last_error_message("cyq_update_factor: instances with more than one segment are not supported");
+        return CYQ_ERR_UNIMPLEMENTED;
+    }
+    DeviceGuard guard(h->device);
+    cudaStream_t st = to_stream(stream);
+    int max_nu = 0;
+    for (const Inst &in : h->inst) max_nu = std::max(max_nu, in.nu);
+    UpdateArgs u{};
+    u.inst = h->d_inst;
+    u.inst_list = h->d_all_list;
+    u.n_inst = h->batch;
+    u.data = h->data;
+    u.L = h->fac.L;
+    u.LB = h->fac.LB;
+    u.DI = h->fac.DI;
+    if (h->precision == CYQ_FP64_IR32) {
+        u.Lc = static_cast<float *>(h->fac32.L);
+        u.LBc = static_cast<float *>(h->fac32.LB);
+        u.DIc = static_cast<float *>(h->fac32.DI);
+    }
+    u.Mf = h->Mf;
+    u.Mb = h->Mb;
+    u.w = w;
+    u.delta = delta;
+    u.m_max = m_max;
+    u.mcap = std::max(h->max_nx, kUpdateColumns);
+    u.max_nx = h->max_nx;
+    u.max_nu = max_nu;
+    u.status = h->status;
+    const size_t smem = h->fac.fp64 ? update_smem_bytes<double>(h->max_nx, max_nu, u.mcap)
+                                    : update_smem_bytes<float>(h->max_nx, max_nu, u.mcap);
+    if (smem > (size_t)h->smem_optin) {
+        set_last_error_message("cyq_update_factor: stage blocks too large for the update workspace");
+        return CYQ_ERR_INVALID_ARG;
+    }
+    CYQ_CUDA(launch_update_factor(h->fac.fp64, u, st));
+    h->launches = 1;
+    // the residual and the refinement read the updated matrices from now on
+    h->data.Q = Q;
+    h->data.R = R;
+    h->data.S = S;
+    return CYQ_OK;
 }
 
 cyq_status cyq_build_rhs(cyq_handle h, const double *q, const double *r, const double *c, const double *x_init,
@@ -798,8 +1010,23 @@ cyq_status cyq_set_pcr_tail(cyq_handle h, int32_t levels) {
     h->cr_jobs = jobs;
     h->cr_plan = cp;
     // the parallel tail runs on the level-parallel coupling solve
-    h->cr_levels = T > 0 || ((int)h->cr_list.size() < 2 * kSMs && maxP >= 8);
+    h->cr_levels = T > 0 || ((int)h->cr_list.size() < 2 * h->sms && maxP >= 8);
     h->factored = false;
+    return CYQ_OK;
+}
+
+cyq_status cyq_set_factor_path(cyq_handle h, int32_t one_warp_per_item) {
+    if (!h || one_warp_per_item < 0 || one_warp_per_item > 1) return CYQ_ERR_INVALID_ARG;
+    h->warp_on = one_warp_per_item == 1;
+    for (Group &g : h->groups) g.warp_on = h->warp_on;
+    h->factored = false;
+    return CYQ_OK;
+}
+
+cyq_status cyq_get_factor_path(cyq_handle h, int32_t *one_warp_per_item, int64_t *warp_items) {
+    if (!h) return CYQ_ERR_INVALID_ARG;
+    if (one_warp_per_item) *one_warp_per_item = h->warp_on ? 1 : 0;
+    if (warp_items) *warp_items = (int64_t)h->warp_items.size();
     return CYQ_OK;
 }
 
@@ -898,6 +1125,13 @@ cyq_status cyq_solve_adjoint(cyq_handle h, const double *x_init, const double *z
     g.w = wbuf;
     g.dQ = dQ; g.dq = dq; g.dR = dR; g.dr = dr; g.dS = dS; g.dA = dA; g.dB = dB; g.dc = dc; g.dSig = dSigma;
     CYQ_CUDA(launch_adjoint(g, (int)h->chunks.size(), h->batch, h->data, dx_init, st));
+    return CYQ_OK;
+}
+
+cyq_status cyq_pivot_eval(const double *d, double *l, double *il, const float *df, float *lf, float *ilf,
+                          int64_t n, cyq_stream stream) {
+    if (n < 0 || (d && (!l || !il)) || (df && (!lf || !ilf))) return CYQ_ERR_INVALID_ARG;
+    CYQ_CUDA(launch_pivot_eval(d, l, il, df, lf, ilf, (long long)n, to_stream(stream)));
     return CYQ_OK;
 }
 
@@ -1081,12 +1315,15 @@ cyq_status cyq_tune_segments(const cyq_desc *desc, const double *Q, const double
     if (!desc || !P_out || desc->batch < 1 || !desc->N || !b || !z || nrhs < 1) return CYQ_ERR_INVALID_ARG;
     if (reps < 1) reps = 2;
     const int batch = desc->batch;
+    int dev = desc->device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return CYQ_ERR_NO_DEVICE;
+    const int sms = sm_count(dev);
     std::vector<int> base(batch);
     for (int i = 0; i < batch; ++i) {
         const int N = desc->N[i];
         if (N < 1) return CYQ_ERR_INVALID_ARG;
         int P = desc->P_per_instance ? desc->P_per_instance[i] : desc->P;
-        if (P <= 0) P = auto_segments(batch, N);
+        if (P <= 0) P = auto_segments(batch, N, sms);
         base[i] = std::min(P, N);
     }
     cudaStream_t st = to_stream(stream);

@@ -29,6 +29,9 @@ struct Inst {
     long long oBlk;                      // offset of the P coupling blocks (nx*nx each)
     long long oVec;                      // offset of the P coupling vectors (nx each)
     long long oq, orv, oc, ox0;          // offsets of q ((N+1) nx), r (N nu), c (N nx), x_init (nx)
+    long long oHf;                       // offset of the float32 stage matrices of segment 0 (padded tiles)
+    long long oN;                        // stages of the instances before this one (sum of N)
+    long long oNn;                       // sum of N (nu + nx) of the instances before this one
 };
 
 // Stage shapes (nx, nu) for which float32 kernels are also compiled with fixed
@@ -55,7 +58,7 @@ struct Data {
 };
 
 // Device status codes (mirror cyq_status).
-enum : int { ST_OK = 0, ST_NOT_PD = 2, ST_NOT_CONVERGED = 3 };
+enum : int { ST_OK = 0, ST_NOT_PD = 2, ST_NOT_CONVERGED = 3, ST_RANK = 9 };
 
 // Segment c of an instance with horizon N split into P segments: boundaries
 // b(c) = floor(c N / P).  Segment c >= 1 holds stages b(c-1)+1 .. b(c);
@@ -364,6 +367,7 @@ struct FactorArgs {
     bool need_G2;                   // some item propagates A^cl (P > 1): second [B^ A^] buffer
     const int *skip;                // optional per-instance flag: nonzero = do not factor this instance
     unsigned smem_team;             // shared-memory bytes per team (set by the launcher)
+    const float *Hf;                // float32 stage matrices (one-warp factor; written by the ingest)
 };
 
 struct SolveArgs {
@@ -412,6 +416,41 @@ struct CrPlan {
 };
 
 cudaError_t launch_factor_segments(bool fp64, int team, int shape, size_t smem, const FactorArgs &a, cudaStream_t st);
+
+// Float32 factor with one team of threads per item (segments without A^cl,
+// padded blocks nu + nx <= 96, nx <= 64, nu <= 32) in one persistent launch: three item
+// classes by shared memory (one team of 128 threads per CTA, two of 64 or four
+// of 32); teams take items from their class's counter, then from the classes
+// of smaller items.
+constexpr int kTeamCtaThreads = 128;
+constexpr int kWarpMaxNp = 96;        // padded nu + nx
+constexpr int kWarpMaxNxp = 64;       // padded nx
+struct TeamPlanDev {
+    const Item *items = nullptr;      // class 0, 1, 2 items (each sorted longest first)
+    int off[3] = {0, 0, 0}, n[3] = {0, 0, 0};
+    int *counter = nullptr;           // three queue heads (zeroed before each launch)
+    int g0 = 0, g1 = 0;               // CTAs [0, g0) serve class 0, [g0, g0 + g1) class 1, the rest class 2
+    int arena_floats = 0;             // shared memory per CTA (floats)
+};
+size_t warp_slot_bytes(int nx, int nu);
+size_t warp_stage_floats(int nx, int nu);   // floats of one ingested stage matrix
+// Ingest of the one-warp factor's stages: float32 stage matrices in the padded
+// tile layout and float32 [B A]; one warp per chunk of stages of segment 0.
+struct IngestChunk {
+    int inst, t0, t1;
+};
+struct IngestArgs {
+    const Inst *inst;
+    const IngestChunk *chunks;
+    int n_chunks;
+    Data data;
+    float *Hf;                      // stage matrices
+    float *BAf;                     // [B A] copies (may be null)
+};
+cudaError_t launch_ingest_f32(const IngestArgs &g, cudaStream_t st);
+// L^{R-1} of every stage of the one-team factor's segments into the stored factor.
+cudaError_t launch_inv_R_f32(const IngestArgs &g, float *L, const float *DI, cudaStream_t st);
+cudaError_t launch_factor_team(const FactorArgs &a, const TeamPlanDev &plan, int grid, cudaStream_t st);
 cudaError_t launch_cr_factor_levels(const CrPlan &plan, int team, int nmax, const FactorArgs &a, cudaStream_t st,
                                     long long *launches);
 size_t cr_tail_smem_bytes(int nmax);
@@ -452,6 +491,26 @@ cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st);
 cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
                                   int *steps, int step, bool keep_bb, cudaStream_t st);
 cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, cudaStream_t st);
+// Factorization update (update.cu): low-rank modifications of the stage matrices
+// applied to the stored factor of one-segment instances.
+struct UpdateArgs {
+    const Inst *inst;
+    const int *inst_list;           // instances to update
+    int n_inst;
+    Data data;                      // float64 data (the [B A] that carries the update between stages)
+    void *L, *LB, *DI;              // stored factor (float or double)
+    float *Lc, *LBc, *DIc;          // float32 copy to refresh (float64 factor with float32 corrections), or null
+    double *Mf, *Mb;                // coupling block factor and M_bwd
+    const double *w, *delta;        // update rows: instance, stage, row (m_max per stage); w has nu + nx entries
+    int m_max;                      // rows per stage in w / delta
+    int mcap;                       // update columns a stage can carry (workspace)
+    int max_nx, max_nu;
+    int *status;
+};
+template <typename T>
+size_t update_smem_bytes(int nx, int nu, int mcap);
+cudaError_t launch_update_factor(bool fp64, const UpdateArgs &u, cudaStream_t st);
+
 // Newton-system assembly of the augmented Lagrangian inner problem (newton.cu).
 struct AlmOff {
     long long oC, oD, oY;   // offsets of C, D and the per-row vectors (bl, bu, y, sigma, active, y^)
@@ -474,6 +533,8 @@ cudaError_t launch_build_rhs(const Inst *inst, int batch, const Data &d, const d
 cudaError_t launch_adjoint(const GradArgs &g, int n_chunks, int batch, const Data &d, double *dx0, cudaStream_t st);
 
 size_t factor_smem_bytes(bool fp64, int nx, int nu, bool staged, bool need_G2);
+cudaError_t launch_pivot_eval(const double *d, double *l, double *il, const float *df, float *lf, float *ilf,
+                              long long n, cudaStream_t st);
 size_t factor_stage_bytes(int nx, int nu);
 
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` on the

@@ -20,6 +20,8 @@
 // the current stage's copy is consumed by the end of the previous step, so
 // one buffer suffices.  H^ = H + V V^T is assembled directly from that copy,
 // or from global memory for blocks too large to stage.
+#include <algorithm>
+
 #include "cyq_internal.cuh"
 
 namespace cyq {
@@ -948,6 +950,34 @@ cudaError_t launch_factor_pairs(const FactorArgs &a, cudaStream_t st) {
 }
 
 }  // namespace
+
+// Diagnostics: the stage factor's pivot routine (sqrt(d), 1/sqrt(d)) applied
+// element-wise, float64 and float32, so that its accuracy can be tested.
+__global__ void k_pivot_eval(const double *d, double *l, double *il, const float *df, float *lf, float *ilf,
+                             long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (d) {
+            double a, b;
+            pivot(d[i], a, b);
+            l[i] = a;
+            il[i] = b;
+        }
+        if (df) {
+            float a, b;
+            pivot(df[i], a, b);
+            lf[i] = a;
+            ilf[i] = b;
+        }
+    }
+}
+
+cudaError_t launch_pivot_eval(const double *d, double *l, double *il, const float *df, float *lf, float *ilf,
+                              long long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    k_pivot_eval<<<(int)blocks, 256, 0, st>>>(d, l, il, df, lf, ilf, n);
+    return cudaGetLastError();
+}
 
 size_t factor_stage_bytes(int nx, int nu) {
     const size_t nux = (size_t)nx + nu;

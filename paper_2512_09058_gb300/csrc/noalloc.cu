@@ -1,18 +1,20 @@
 // Allocation-free factor + solve of one OCP (float64, one segment).
 //
-// Some callers cannot allocate device memory: code that runs while a CUDA
-// graph is being captured into a fixed memory plan, real-time control loops
-// that forbid allocation after start-up, or hosts whose allocator is owned by
-// another runtime.  This entry point serves them: its workspace (factor,
-// coupling block, plan records) lives in one file-scope __device__ array of
-// fixed size that every GPU loading the library holds until the process exits.
-// The caller passes inputs and outputs only.
+// Some callers cannot allocate device memory while they run: real-time
+// control loops that allocate only at start-up, and hosts whose device memory
+// belongs to another runtime or allocator.  This entry point serves them: its
+// workspace (factor, coupling block, plan records) lives in one file-scope
+// __device__ array of fixed size that every GPU loading the library holds
+// until the process exits.  The caller passes inputs and outputs only.
 //
 // The array is shared by every call on a device and keeps the last call's
 // contents.  Calls that overlap on the GPU (other streams, other host threads)
 // race on it; serialise them.  The first call on a device looks up the
-// array's device address (cudaGetSymbolAddress, with that device current);
-// make that first call before any stream capture.
+// array's device address (cudaGetSymbolAddress, with that device current) and
+// keeps it for the life of the process, so a device reset after that first
+// call is not supported; make the first call before any stream capture.  The
+// plan records are written by a one-thread kernel from its arguments, so
+// nothing is copied from host memory.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -52,6 +54,21 @@ long long required_doubles(int N, int nx, int nu) {
     n += 5 * round32((long long)nx * nx);     // Mf, Mb, Kc, U, Y
     n += 3 * round32(nx);                     // dF, dB, lam
     return n;
+}
+
+// The plan of a single instance with one segment, written on the device from
+// kernel arguments (no host buffer is involved), and the status word cleared.
+__global__ void k_noalloc_setup(Inst *inst, Item *item, int *list, int *status, int N, int nx, int nu) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Inst in{};
+    in.N = N;
+    in.nx = nx;
+    in.nu = nu;
+    in.P = 1;
+    *inst = in;
+    *item = Item{0, 0};
+    *list = 0;
+    *status = 0;
 }
 
 int team_for(int nx, int nu) {
@@ -122,16 +139,10 @@ extern "C" cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu
     double *dB = p;  p += round32(nx);
     double *lam = p; p += round32(nx);
 
-    // plan records of a single instance with one segment (host stack -> workspace)
-    Inst in{};
-    in.N = N; in.nx = nx; in.nu = nu; in.P = 1;
-    Item it{0, 0};
-    const int zero = 0;
+    // plan records of a single instance with one segment, and a cleared status word
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(d_inst, &in, sizeof(Inst), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d_item, &it, sizeof(Item), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d_list, &zero, sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(d_status, 0, sizeof(int), st)) != cudaSuccess)
+    k_noalloc_setup<<<1, 32, 0, st>>>(d_inst, d_item, d_list, d_status, N, nx, nu);
+    if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(CYQ_ERR_CUDA, std::string("cyq_factor_solve_noalloc: ") + cudaGetErrorString(e));
 
     const int team = team_for(nx, nu);

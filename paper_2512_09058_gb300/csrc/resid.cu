@@ -186,13 +186,26 @@ __global__ void k_adjoint_dx0(const Inst *inst, int batch, Data d, const double 
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+template <int NR>
+static void launch_residual_nr(const ResidArgs &a, int r_first, int groups, cudaStream_t st) {
+    const dim3 grid(a.n_chunks, groups);
+    if (a.max_nx >= 24)
+        k_residual_long_rows<128, NR><<<grid, 128, 0, st>>>(a, r_first);
+    else
+        k_residual_short_rows<128, NR><<<grid, 128, 0, st>>>(a, r_first);
+}
+
 cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st) {
     if (a.n_chunks == 0) return cudaSuccess;
-    const dim3 grid(a.n_chunks, (nrhs + RG - 1) / RG);
-    if (a.max_nx >= 24)
-        k_residual_long_rows<128><<<grid, 128, 0, st>>>(a, nrhs);
-    else
-        k_residual_short_rows<128><<<grid, 128, 0, st>>>(a, nrhs);
+    // full groups of RG right-hand sides, then one launch for the remainder
+    const int full = nrhs / RG, rest = nrhs % RG;
+    if (full > 0) launch_residual_nr<RG>(a, 0, full, st);
+    switch (rest) {
+        case 1: launch_residual_nr<1>(a, full * RG, 1, st); break;
+        case 2: launch_residual_nr<2>(a, full * RG, 1, st); break;
+        case 3: launch_residual_nr<3>(a, full * RG, 1, st); break;
+        default: break;
+    }
     return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ CYQ_FP64 = 0
 CYQ_FP32_REFINE = 1
 CYQ_FP64_IR32 = 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "not positive definite", 3: "not converged", 4: "CUDA error",
-          5: "timeout", 6: "no factor", 7: "unimplemented", 8: "no device"}
+          5: "timeout", 6: "no factor", 7: "unimplemented", 8: "no device", 9: "update rank above the workspace"}
 
 # every entry point declared in include/cyq.h
 EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual",
@@ -28,7 +28,7 @@ EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rh
            "cyq_get_segments", "cyq_last_launch_count", "cyq_status_string", "cyq_last_error",
            "cyq_factor_solve_noalloc", "cyq_autotune", "cyq_get_launch_shapes", "cyq_tune_segments",
            "cyq_set_launch_shapes", "cyq_get_stage_factor", "cyq_assemble_newton", "cyq_set_pcr_tail",
-           "cyq_get_pcr_tail"]
+           "cyq_get_pcr_tail", "cyq_pivot_eval", "cyq_set_factor_path", "cyq_get_factor_path", "cyq_apply_factor", "cyq_update_factor"]
 
 
 class CyqError(RuntimeError):
@@ -102,10 +102,16 @@ def load(path: str = LIB_PATH):
     L.cyq_assemble_newton.argtypes = [vp, ctypes.POINTER(cyq_newton_in), ctypes.POINTER(cyq_newton_out), vp]
     L.cyq_set_pcr_tail.argtypes = [vp, i32]
     L.cyq_get_pcr_tail.argtypes = [vp, pi32]
+    L.cyq_pivot_eval.argtypes = [vp] * 6 + [i64, vp]
+    L.cyq_set_factor_path.argtypes = [vp, i32]
+    L.cyq_apply_factor.argtypes = [vp, vp, vp, i32, vp]
+    L.cyq_update_factor.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp]
+    L.cyq_get_factor_path.argtypes = [vp, pi32, ctypes.POINTER(i64)]
     for name in ["cyq_create", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual", "cyq_solve_adjoint",
                  "cyq_get_instance_status", "cyq_get_stats", "cyq_get_segments", "cyq_autotune",
                  "cyq_get_launch_shapes", "cyq_tune_segments", "cyq_set_launch_shapes",
-                 "cyq_get_stage_factor"]:
+                 "cyq_get_stage_factor", "cyq_pivot_eval", "cyq_set_factor_path", "cyq_get_factor_path",
+                 "cyq_apply_factor", "cyq_update_factor"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -256,6 +262,20 @@ class Solver:
         _check(_lib.cyq_solve(self._h, _ptr(b), _ptr(z), nrhs, _stream(stream)))
         return z
 
+    def update_factor(self, Q, R, S, w, delta, m_max: int, stream=None):
+        """Update the stored factor to that of the stage matrices H_s + sum delta w w^T
+        (see cyq_update_factor); Q, R, S are the updated data for later residuals."""
+        _check(_lib.cyq_update_factor(self._h, _ptr(Q), _ptr(R), _ptr(S), _ptr(w), _ptr(delta), int(m_max),
+                                      _stream(stream)))
+
+    def apply_factor(self, r, dz=None, nrhs: int = 1, stream=None):
+        """dz = K~^{-1} r with the stored factor (one substitution, no refinement)."""
+        import torch
+        if dz is None:
+            dz = torch.empty_like(r)
+        _check(_lib.cyq_apply_factor(self._h, _ptr(r), _ptr(dz), int(nrhs), _stream(stream)))
+        return dz
+
     def build_rhs(self, q, r, c, x0, b=None, stream=None):
         import torch
         if b is None:
@@ -267,6 +287,16 @@ class Solver:
         """Solve the last `levels` levels of the coupling system by parallel cyclic
         reduction (0: plain cyclic reduction); factor again afterwards."""
         _check(_lib.cyq_set_pcr_tail(self._h, int(levels)))
+
+    def set_factor_path(self, one_warp_per_item: bool):
+        """Float32 factor: one warp per item in one launch (True, the default) or
+        the per-size-class kernels (False); factor again afterwards."""
+        _check(_lib.cyq_set_factor_path(self._h, 1 if one_warp_per_item else 0))
+
+    def factor_path(self) -> dict:
+        on, n = ctypes.c_int32(0), ctypes.c_int64(0)
+        _check(_lib.cyq_get_factor_path(self._h, ctypes.byref(on), ctypes.byref(n)))
+        return {"one_warp_per_item": bool(on.value), "warp_items": int(n.value)}
 
     def pcr_tail(self) -> int:
         v = ctypes.c_int32(0)

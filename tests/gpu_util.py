@@ -51,6 +51,26 @@ def rel_err(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def block_rel_err(inst, z, zo):
+    """Worst blockwise relative error: the maximum over the stage blocks u^k,
+    x^{k+1}, lambda^k of ||z_blk - zo_blk|| / ||zo_blk|| (blocks whose reference
+    norm is below 1e-6 ||zo|| are skipped: a ratio there measures nothing).  A
+    wrong small block can hide under the normwise error of a long horizon; it
+    cannot hide here."""
+    nu, nx = inst.nu, inst.nx
+    w = nu + 2 * nx
+    Z, ZO = z.reshape(inst.N, w), zo.reshape(inst.N, w)
+    floor = 1e-6 * np.linalg.norm(zo)
+    worst = 0.0
+    for lo, hi in ((0, nu), (nu, nu + nx), (nu + nx, w)):
+        e = np.linalg.norm(Z[:, lo:hi] - ZO[:, lo:hi], axis=1)
+        n = np.linalg.norm(ZO[:, lo:hi], axis=1)
+        keep = n > floor
+        if keep.any():
+            worst = max(worst, float((e[keep] / n[keep]).max()))
+    return worst
+
+
 def small_cfg(seed, S=True, sigma=(1e-2, 1e2)):
     return dict(batch=1, N=8, nx=3, nu=2, S=S, sigma=sigma, nrhs=1, QN_equals_Q0=False, seed=seed)
 

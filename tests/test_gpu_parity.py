@@ -15,12 +15,15 @@ import pytest
 import oracle
 from paper_2512_09058_gb300 import inputs
 
-from gpu_util import gpu_solve, oracle_rhs, ragged_batch, rel_err, require_gpu, split_instances
+from gpu_util import block_rel_err, gpu_solve, oracle_rhs, ragged_batch, rel_err, require_gpu, split_instances
 
 pytestmark = pytest.mark.gpu
 
 
-def _check_against_oracle(batch, z, b, tol_fwd, tol_res=None):
+def _check_against_oracle(batch, z, b, tol_fwd, tol_res=None, blockwise=True):
+    """Normwise forward error per instance and right-hand side <= tol_fwd and,
+    on these well-conditioned inputs, every stage block (u^k, x^{k+1}, lambda^k)
+    within 100 tol_fwd of its own norm."""
     worst = 0.0
     for j in range(z.shape[0]):
         zs = split_instances(batch, z[j])
@@ -30,6 +33,9 @@ def _check_against_oracle(batch, z, b, tol_fwd, tol_res=None):
             e = rel_err(zi, zo)
             worst = max(worst, e)
             assert e <= tol_fwd, (inst.N, inst.nx, inst.nu, e)
+            if blockwise:
+                eb = block_rel_err(inst, zi, zo)
+                assert eb <= 100 * tol_fwd, (inst.N, inst.nx, inst.nu, eb)
             if tol_res is not None:
                 r = oracle.kkt_residual(inst, zi, bi)
                 assert r <= tol_res, (inst.N, inst.nx, inst.nu, r)

@@ -4,9 +4,11 @@ C ABI, must give the same solution as the regular entry points
 in a row with different problems (its fixed workspace keeps the previous
 call's contents, which must not leak into the next result).
 
-Callers that cannot allocate device memory at call time (graph capture into
-a fixed memory plan, real-time loops, foreign allocators) use that entry
-point.  This file is collected last on purpose."""
+Callers that cannot allocate device memory while they run (real-time loops
+that allocate only at start-up, hosts whose device memory belongs to another
+allocator) use that entry point.  The cases cover every team size of its
+kernels (nu + nx up to 24, 48 and beyond) and problems without S and Sigma.
+This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -18,8 +20,8 @@ from paper_2512_09058_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 
-def _instance(seed, N, nx, nu):
-    cfg = dict(batch=1, N=N, nx=nx, nu=nu, S=True, sigma=(1e-2, 1e2), nrhs=1, QN_equals_Q0=False, seed=seed)
+def _instance(seed, N, nx, nu, S=True, sigma=(1e-2, 1e2)):
+    cfg = dict(batch=1, N=N, nx=nx, nu=nu, S=S, sigma=sigma, nrhs=1, QN_equals_Q0=False, seed=seed)
     return inputs.make_instance(cfg, 0)
 
 
@@ -55,8 +57,15 @@ def test_noalloc_matches_regular_entry_points_twice():
     lib = cyq.load()
     lib.cyq_factor_solve_noalloc.argtypes = [ctypes.c_int32] * 3 + [ctypes.c_void_p] * 10
     lib.cyq_factor_solve_noalloc.restype = ctypes.c_int
-    for seed, (N, nx, nu) in [(41, (40, 10, 4)), (42, (17, 6, 3))]:
-        inst = _instance(seed, N, nx, nu)
+    cases = [(41, (40, 10, 4), True, (1e-2, 1e2)), (42, (17, 6, 3), True, (1e-2, 1e2)),
+             (43, (16, 32, 12), True, (1e-2, 1e2)), (44, (9, 40, 16), False, None),
+             (45, (12, 7, 5), False, None)]
+    for seed, (N, nx, nu), S, sigma in cases:
+        inst = _instance(seed, N, nx, nu, S=S, sigma=sigma)
+        assert (inst.Sigma is None) == (sigma is None)
+        if not S:   # S = 0: both paths get a NULL S pointer
+            assert not np.any(inst.S)
+            inst.S = None
         b = oracle.build_rhs(inst, *inst.rhs[0])
         z_reg = _regular(cyq, torch, inst, b)
         z_na, status = _noalloc(lib, torch, inst, b)
