@@ -35,6 +35,8 @@ def lib():
         L.oracle_kkt_abs_matvec.restype = None
         L.oracle_kkt_residual.argtypes = [i, i, i, d, d, d, d, d, d, d, d, d]
         L.oracle_kkt_residual.restype = ctypes.c_double
+        L.oracle_kkt_residual_fp64.argtypes = [i, i, i, d, d, d, d, d, d, d, d, d]
+        L.oracle_kkt_residual_fp64.restype = ctypes.c_double
         L.oracle_kkt_dense.argtypes = [i, i, i, d, d, d, d, d, d, d]
         L.oracle_kkt_dense.restype = i
         L.oracle_dense_solve.argtypes = [i, d, d, d]
@@ -105,11 +107,24 @@ def residual_eval_bound(inst, z, b) -> float:
 
 
 def kkt_residual(inst, z, b) -> float:
-    """Relative KKT residual ||b - K z||_2 / ||b||_2."""
+    """Relative KKT residual ||b - K z||_2 / ||b||_2 of the data as given, every
+    row accumulated by a compensated dot product (Ogita-Rump-Oishi Dot2) and
+    rounded once: accurate to about 1e-16 relative plus u^2-size terms, so it
+    measures the residual itself, not the rounding of a float64 evaluation."""
     N, nx, nu, Q, R, S, A, B, Sg = _data(inst)
     z, b = _f(z), _f(b)
     return float(lib().oracle_kkt_residual(N, nx, nu, _p(Q), _p(R), _p(S), _p(A), _p(B), _p(Sg),
                                            _p(z), _p(b), None))
+
+
+def kkt_residual_fp64(inst, z, b) -> float:
+    """The same residual evaluated in plain float64 (rounded products and sums,
+    Sigma added to the diagonals first): one float64 evaluation, within
+    residual_eval_bound of the exact value."""
+    N, nx, nu, Q, R, S, A, B, Sg = _data(inst)
+    z, b = _f(z), _f(b)
+    return float(lib().oracle_kkt_residual_fp64(N, nx, nu, _p(Q), _p(R), _p(S), _p(A), _p(B), _p(Sg),
+                                                _p(z), _p(b), None))
 
 
 def kkt_dense(inst) -> np.ndarray:

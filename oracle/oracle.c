@@ -283,9 +283,15 @@ void oracle_kkt_abs_matvec(int N, int nx, int nu, const double *Q, const double 
 }
 
 /* relative residual ||b - K z||_2 / ||b||_2 (returns ||b - Kz|| if b = 0) */
-double oracle_kkt_residual(int N, int nx, int nu, const double *Q, const double *R, const double *S,
-                           const double *A, const double *B, const double *Sigma,
-                           const double *z, const double *b, double *r_out) {
+/* Relative KKT residual ||b - K z||_2 / ||b||_2 with every row evaluated in
+ * plain float64 (products and sums rounded in the order of oracle_kkt_matvec,
+ * Sigma already added to the diagonals of R and Q).  Its rounding error can
+ * exceed the residual itself when the terms of a row cancel by many orders of
+ * magnitude; oracle_kkt_residual below evaluates the same definition
+ * accurately. */
+double oracle_kkt_residual_fp64(int N, int nx, int nu, const double *Q, const double *R, const double *S,
+                                const double *A, const double *B, const double *Sigma,
+                                const double *z, const double *b, double *r_out) {
     size_t n = (size_t)N * ((size_t)nu + 2 * (size_t)nx);
     double *y = r_out ? r_out : malloc(sizeof(double) * n);
     oracle_kkt_matvec(N, nx, nu, Q, R, S, A, B, Sigma, z, y);
@@ -296,6 +302,97 @@ double oracle_kkt_residual(int N, int nx, int nu, const double *Q, const double 
         bn += b[i] * b[i];
     }
     if (!r_out) free(y);
+    rn = sqrt(rn);
+    bn = sqrt(bn);
+    return bn > 0.0 ? rn / bn : rn;
+}
+
+/* Error-free transformations: a + b = s + t exactly (Knuth's TwoSum) and
+ * a b = p + e exactly (TwoProduct with a fused multiply-add; C99 fma is
+ * correctly rounded). */
+static void two_sum(double a, double b, double *s, double *t) {
+    double x = a + b, bv = x - a;
+    *s = x;
+    *t = (a - (x - bv)) + (b - bv);
+}
+
+/* A row sum b_i - sum_j c_j v_j carried as hi + lo (Ogita, Rump and Oishi,
+ * "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005), Dot2): the
+ * result is as accurate as if computed in twice the working precision and
+ * then rounded, |error| <= u |exact| + gamma_n^2 (|b_i| + sum |c_j v_j|). */
+typedef struct { double hi, lo; } acc2_t;
+
+static void acc2_sub_prod(acc2_t *a, double c, double v) {
+    const double q = c * v, e = fma(c, v, -q); /* c v = q + e exactly */
+    double s, t;
+    two_sum(a->hi, -q, &s, &t);
+    a->hi = s;
+    a->lo += t - e;
+}
+
+static void acc2_sub_mat_vec(acc2_t *y, int m, int n, const double *M, const double *x) {
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) acc2_sub_prod(&y[i], M[IX(i, j, m)], x[j]);
+}
+static void acc2_sub_mat_tvec(acc2_t *y, int m, int n, const double *M, const double *x) {
+    /* y (n) -= M^T x, M is m x n */
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < m; ++i) acc2_sub_prod(&y[j], M[IX(i, j, m)], x[i]);
+}
+
+/* Relative KKT residual ||b - K z||_2 / ||b||_2, the quantity the refinement
+ * drives below its tolerance (eq. opt-cond-ocp-eq rows as in oracle_kkt_matvec,
+ * Sigma_k as its own diagonal term, so K is the data exactly).  Every row is
+ * accumulated with the compensated dot product above and rounded once; the
+ * squared norms are then summed in plain float64 (relative error about
+ * n u / 2, far below the quantity measured). */
+double oracle_kkt_residual(int N, int nx, int nu, const double *Q, const double *R, const double *S,
+                           const double *A, const double *B, const double *Sigma,
+                           const double *z, const double *b, double *r_out) {
+    ocp_t p = {N, nx, nu, Q, R, S, A, B, Sigma};
+    size_t w = rec(&p), n = (size_t)N * w;
+    acc2_t *y = malloc(sizeof(acc2_t) * n);
+    for (size_t i = 0; i < n; ++i) {
+        y[i].hi = b[i];
+        y[i].lo = 0.0;
+    }
+    for (int k = 0; k < N; ++k) {
+        const double *u = z + k * w;
+        const double *xn = u + nu;
+        const double *lam = xn + nx;
+        const double *xk = k > 0 ? z + (k - 1) * w + nu : NULL;
+        acc2_t *yu = y + k * w, *yx = yu + nu, *yl = yx + nx;
+        /* row u^k: R_k u + Sigma_u u + S_k x^k + B_k^T lambda^k */
+        acc2_sub_mat_vec(yu, nu, nu, blkR(&p, k), u);
+        if (Sigma)
+            for (int i = 0; i < nu; ++i) acc2_sub_prod(&yu[i], Sigma[(size_t)k * (nu + nx) + i], u[i]);
+        if (xk && S) acc2_sub_mat_vec(yu, nu, nx, blkS(&p, k), xk);
+        acc2_sub_mat_tvec(yu, nx, nu, blkB(&p, k), lam);
+        /* row x^{k+1}: Q x - lambda^k (+ S^T u^{k+1} + A^T lambda^{k+1}) */
+        int j = k + 1;
+        acc2_sub_mat_vec(yx, nx, nx, blkQ(&p, j), xn);
+        if (Sigma)
+            for (int i = 0; i < nx; ++i) acc2_sub_prod(&yx[i], Sigma[(size_t)j * (nu + nx) + nu + i], xn[i]);
+        for (int i = 0; i < nx; ++i) acc2_sub_prod(&yx[i], -1.0, lam[i]);
+        if (j < N) {
+            const double *un = z + j * w;
+            const double *ln = un + nu + nx;
+            if (S) acc2_sub_mat_tvec(yx, nu, nx, blkS(&p, j), un);
+            acc2_sub_mat_tvec(yx, nx, nx, blkA(&p, j), ln);
+        }
+        /* row lambda^k: B u + A x^k - x^{k+1} */
+        acc2_sub_mat_vec(yl, nx, nu, blkB(&p, k), u);
+        if (xk) acc2_sub_mat_vec(yl, nx, nx, blkA(&p, k), xk);
+        for (int i = 0; i < nx; ++i) acc2_sub_prod(&yl[i], -1.0, xn[i]);
+    }
+    double rn = 0.0, bn = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        const double r = y[i].hi + y[i].lo;
+        if (r_out) r_out[i] = r;
+        rn += r * r;
+        bn += b[i] * b[i];
+    }
+    free(y);
     rn = sqrt(rn);
     bn = sqrt(bn);
     return bn > 0.0 ? rn / bn : rn;

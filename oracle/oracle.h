@@ -14,6 +14,9 @@ void oracle_kkt_abs_matvec(int N, int nx, int nu, const double *Q, const double 
 double oracle_kkt_residual(int N, int nx, int nu, const double *Q, const double *R, const double *S,
                            const double *A, const double *B, const double *Sigma,
                            const double *z, const double *b, double *r_out);
+double oracle_kkt_residual_fp64(int N, int nx, int nu, const double *Q, const double *R, const double *S,
+                                const double *A, const double *B, const double *Sigma,
+                                const double *z, const double *b, double *r_out);
 int oracle_kkt_dense(int N, int nx, int nu, const double *Q, const double *R, const double *S,
                      const double *A, const double *B, const double *Sigma, double *K);
 int oracle_dense_solve(int n, const double *K, const double *b, double *x);

@@ -86,22 +86,81 @@ def test_abs_matvec_equals_dense_abs_product(N, nx, nu):
     assert np.allclose(np.abs(K) @ np.abs(v), oracle.kkt_abs_matvec(inst, v), rtol=1e-13, atol=0.0)
 
 
+def _exact_residual(inst, z, b):
+    """||b - K z|| / ||b|| in exact rational arithmetic from the optimality
+    conditions of the OCP (gradient of the Lagrangian in u^k and x^{k+1}, the
+    dynamics), with Sigma on the diagonals of R and Q; only the final norm is
+    rounded (to float64, after an exact sum of squares)."""
+    from fractions import Fraction as F
+    N, nx, nu = inst.N, inst.nx, inst.nu
+    w = nu + 2 * nx
+    Z = [F(float(v)) for v in z]
+    res = []
+    for k in range(N):
+        u = Z[k * w:k * w + nu]
+        xn = Z[k * w + nu:k * w + nu + nx]
+        lam = Z[k * w + nu + nx:(k + 1) * w]
+        xk = Z[(k - 1) * w + nu:(k - 1) * w + nu + nx] if k > 0 else None
+        Rk, Bk = inst.Rk(k), inst.Bk(k)
+        su = inst.Sigma_u(k) if inst.Sigma is not None else np.zeros(nu)
+        for i in range(nu):
+            g = sum(F(float(Rk[i, j])) * u[j] for j in range(nu)) + F(float(su[i])) * u[i]
+            g += sum(F(float(Bk[j, i])) * lam[j] for j in range(nx))
+            if xk is not None and inst.S is not None:
+                g += sum(F(float(inst.Sk(k)[i, j])) * xk[j] for j in range(nx))
+            res.append(F(float(b[k * w + i])) - g)
+        j1 = k + 1
+        Qj = inst.Qk(j1)
+        sx = inst.Sigma_x(j1) if inst.Sigma is not None else np.zeros(nx)
+        for i in range(nx):
+            g = sum(F(float(Qj[i, m])) * xn[m] for m in range(nx)) + F(float(sx[i])) * xn[i] - lam[i]
+            if j1 < N:
+                un = Z[j1 * w:j1 * w + nu]
+                ln = Z[j1 * w + nu + nx:(j1 + 1) * w]
+                g += sum(F(float(inst.Ak(j1)[m, i])) * ln[m] for m in range(nx))
+                if inst.S is not None:
+                    g += sum(F(float(inst.Sk(j1)[m, i])) * un[m] for m in range(nu))
+            res.append(F(float(b[k * w + nu + i])) - g)
+        for i in range(nx):
+            g = sum(F(float(Bk[i, m])) * u[m] for m in range(nu)) - xn[i]
+            if xk is not None:
+                g += sum(F(float(inst.Ak(k)[i, m])) * xk[m] for m in range(nx))
+            res.append(F(float(b[k * w + nu + nx + i])) - g)
+    rr = sum(r * r for r in res)
+    bb = sum(F(float(v)) ** 2 for v in b)
+    return float(np.sqrt(float(rr / bb)))
+
+
+def _near_solutions(seed, N, nx, nu, sigma):
+    inst = _small(300 + seed, N, nx, nu, sigma=sigma)
+    q, r, c, x0 = inst.rhs[0]
+    b = oracle.build_rhs(inst, q, r, c, x0)
+    z0 = oracle.riccati_solve(inst, b)
+    rng = np.random.default_rng(seed)
+    # the solution itself (residual near the float64 floor) and a perturbed one
+    return inst, b, (z0, z0 * (1.0 + 1e-9 * rng.standard_normal(z0.size)))
+
+
+def test_accurate_residual_equals_exact_rational_arithmetic():
+    """kkt_residual (compensated rows) against the residual computed exactly with
+    fractions, on badly scaled instances (Sigma in [1e-6, 1e6]) where the terms
+    of a row cancel by many orders of magnitude."""
+    for seed, (N, nx, nu) in enumerate([(4, 3, 2), (5, 4, 1), (3, 5, 3)]):
+        inst, b, zs = _near_solutions(seed, N, nx, nu, (1e-6, 1e6))
+        for z in zs:
+            exact = _exact_residual(inst, z, b)
+            assert abs(oracle.kkt_residual(inst, z, b) - exact) <= 1e-14 * exact + 1e-24
+
+
 def test_residual_evaluation_bound_holds():
-    """The float64 residual of a near-solution differs from the residual computed
-    in extended precision (dense K, numpy longdouble) by at most the stated bound."""
-    for seed, (N, nx, nu) in enumerate([(6, 5, 2), (8, 4, 3), (5, 6, 4)]):
-        inst = _small(300 + seed, N, nx, nu, sigma=(1e-6, 1e6))
-        q, r, c, x0 = inst.rhs[0]
-        b = oracle.build_rhs(inst, q, r, c, x0)
-        z0 = oracle.riccati_solve(inst, b)
-        rng = np.random.default_rng(seed)
-        K = oracle.kkt_dense(inst).astype(np.longdouble)
-        # the solution itself (residual near the float64 floor) and a perturbed one
-        for z in (z0, z0 * (1.0 + 1e-9 * rng.standard_normal(z0.size))):
-            exact = np.linalg.norm((b.astype(np.longdouble) - K @ z.astype(np.longdouble)).astype(np.float64))
-            rel_exact = exact / np.linalg.norm(b)
+    """A plain float64 evaluation of the residual of a near-solution differs from
+    the exact residual (fractions) by at most the stated bound."""
+    for seed, (N, nx, nu) in enumerate([(4, 3, 2), (5, 4, 1), (3, 5, 3)]):
+        inst, b, zs = _near_solutions(seed, N, nx, nu, (1e-6, 1e6))
+        for z in zs:
+            exact = _exact_residual(inst, z, b)
             bound = oracle.residual_eval_bound(inst, z, b)
-            assert abs(oracle.kkt_residual(inst, z, b) - rel_exact) <= bound
+            assert abs(oracle.kkt_residual_fp64(inst, z, b) - exact) <= bound
             assert bound < 1e-10   # informative at the 1e-10 refinement target
 
 
