@@ -108,6 +108,29 @@ typedef struct cyq_desc {
                                the instances still above tol after it_max steps; 0 = none,
                                < 0: default 3.  Not available (treated as 0) when the float64
                                stage factor of some size class does not fit in shared memory */
+    int32_t recompute_factors; /* 0 (default): every stage factor is stored by cyq_factor and
+                               reused by every solve and adjoint (store_factors_for_adjoint).
+                               1: the batch is planned as recompute_chunks consecutive chunks of
+                               instances that share one stage-factor workspace of the largest
+                               chunk; cyq_factor keeps only the statuses and the coupling
+                               factors, and every cyq_solve / cyq_solve_adjoint factors each
+                               chunk again just before its sweeps (stage-factor memory / chunks,
+                               one more factorization per call) */
+    int32_t recompute_chunks;  /* chunks of the recompute mode (0: 4; at most batch) */
+    int32_t early_escalation;  /* float32 mode, 1: after two float32 corrections the instances
+                               whose residual contracts too slowly to reach tol in the remaining
+                               ones stop the float32 corrections and are factored in float64 on a
+                               second stream while the others continue.  0 (default): every
+                               instance takes the it_max float32 corrections first (on the uneven
+                               batch both take the same time) */
+    int32_t certify;           /* 0 (default): an instance stops once its float64 residual
+                               ||b - Kz|| / ||b|| <= tol.  1: it stops only once that residual plus
+                               2 gamma_m || |b| + |K||z| || / ||b|| (m = 2 nx + nu + 3; Higham,
+                               Accuracy and Stability of Numerical Algorithms, Sec. 3.1) is
+                               <= tol: then every float64 evaluation of the residual of the
+                               returned z, in any summation order, is <= tol.  For ill-conditioned
+                               instances that bound can lie far above 1e-10 (they then end
+                               NOT_CONVERGED) */
 } cyq_desc;
 
 /*
@@ -231,10 +254,20 @@ cyq_status cyq_get_instance_status(cyq_handle h, int32_t *host_status, cyq_strea
 typedef struct cyq_stats {
     int32_t refine_steps;    /* corrections applied (max over instances) */
     double max_rel_residual; /* max over instances and rhs of ||b - Kz|| / ||b|| (-1 if it_max = 0) */
+    double max_certified;    /* cyq_desc.certify = 1: max over instances and rhs of the certified
+                                stop value ||b - Kz|| / ||b|| + 2 gamma_m || |b| + |K||z| || / ||b||,
+                                m = 2 nx + nu + 3 (the largest value any float64 evaluation of the
+                                residual of the returned z can give), evaluated where the residual
+                                reached tol; -1 if it_max = 0 or certify = 0 */
     int32_t P_min, P_max;    /* segments per instance chosen by the plan */
     int64_t work_items;      /* (instance, segment) pairs */
 } cyq_stats;
 cyq_status cyq_get_stats(cyq_handle h, cyq_stats *out, cyq_stream stream);
+
+/* Device bytes the handle allocated (its workspace: stage factors, coupling
+ * blocks, refinement vectors, plans; the recompute mode's chunks included).
+ * -1 for NULL.  Host-only, no synchronisation. */
+int64_t cyq_workspace_bytes(cyq_handle h);
 
 /* Number of float64 elements of one right-hand side (sum_i N_i (nu_i + 2 nx_i)). */
 int64_t cyq_kkt_size(cyq_handle h);

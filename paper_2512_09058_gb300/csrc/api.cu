@@ -65,22 +65,32 @@ struct FactorSet {
 
 struct DevicePtrs {
     std::vector<void *> all;
+    long long bytes = 0;
     template <typename T> cudaError_t alloc(T **p, size_t count) {
         *p = nullptr;
         if (count == 0) count = 1;
         cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
-        if (e == cudaSuccess) all.push_back((void *)*p);
+        if (e == cudaSuccess) {
+            all.push_back((void *)*p);
+            bytes += (long long)(count * sizeof(T));
+        }
         return e;
     }
     void free_all() {
         for (void *p : all) cudaFree(p);
         all.clear();
+        bytes = 0;
     }
 };
 
 }  // namespace
 
 struct cyq_handle_s {
+    // recompute mode: the batch is planned as consecutive chunks of instances (sub-handles)
+    // that share one stage-factor window; every solve re-factors each chunk before its sweeps
+    std::vector<cyq_handle_s *> subs;
+    std::vector<int> sub_first;   // first instance of each chunk
+    long long z_lo = 0, z_n = 0;  // elements of the KKT vector this handle's instances cover
     int device = 0;
     int batch = 0;
     int precision = CYQ_FP64;
@@ -106,6 +116,8 @@ struct cyq_handle_s {
     // many segments (cr_levels), single-CTA per instance otherwise / for P = 1 (p1_list)
     bool cr_levels = false;
     bool esc_possible = true;     // every size class has a float64 plan (float32 mode escalation)
+    bool early_esc = false;       // float32 mode: predicted escalation after two corrections
+    bool certify = false;         // stop only when the worst-case evaluation bound allows (k_certify)
     std::vector<int> p1_list;
     int *d_p1_list = nullptr;
     Chunk *d_chunks = nullptr;
@@ -116,7 +128,16 @@ struct cyq_handle_s {
     double *dF = nullptr, *dB = nullptr, *lam = nullptr;
     int *status = nullptr;
     double *r = nullptr, *dz = nullptr, *rr = nullptr, *bb = nullptr, *rel = nullptr;
+    // certified stop: || |b| + |K||z| ||^2 accumulators and the certified value of the last stop
+    double *aa = nullptr, *cert = nullptr;
     int *done = nullptr, *steps = nullptr;
+    int *comp = nullptr;          // instances whose residual rows are evaluated compensated
+    // early float64 escalation: residuals after the first solve, the instances to factor
+    // now, and the side stream (with its fork / join events) that factors them
+    double *rel0 = nullptr;
+    int *esc = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     Data data{};
     bool factored = false;
     long long launches = 0;
@@ -126,12 +147,19 @@ struct cyq_handle_s {
     TeamPlanDev team_plan;
     Item *d_warp_items = nullptr;
     int *d_warp_counter = nullptr;
+    // float32 sweeps in one persistent launch each (all float32 items, by class)
+    std::vector<Item> sweep_items;
+    TeamPlanDev sweep_plan;
+    Item *d_sweep_items = nullptr;
+    int *d_sweep_counter = nullptr;
+    int sweep_grid = 0;
     std::vector<IngestChunk> ingest_chunks;
     IngestChunk *d_ingest_chunks = nullptr;
     long long nHf = 0;            // floats of the ingested stage matrices
     size_t warp_arena = 0;
     int warp_grid = 0;
     bool warp_on = true;          // float32 factor path: one team per item in one launch (else per-class kernels)
+    bool sweep_on = true;         // float32 sweeps: one persistent launch per sweep (else per-class kernels)
     // Newton-system assembly: constraint rows per instance and the offsets they imply
     std::vector<int> alm_ny;
     std::vector<AlmOff> alm_off;
@@ -266,9 +294,20 @@ cudaError_t launch_group_sweep(cyq_handle h, const FactorSet &fs, const Group &g
 // zacc, the solution is added into zacc and z only holds sweep intermediates.
 cyq_status run_solve(cyq_handle h, const FactorSet &fs, const double *b, double *z, int nrhs, const int *skip,
                      cudaStream_t st, double *zacc = nullptr) {
-    for (const Group &g : h->groups) {
-        CYQ_CUDA(launch_group_sweep(h, fs, g, true, b, z, nrhs, skip, zacc, st));
+    // float32 sweeps: one persistent launch per sweep for the whole batch
+    const bool team = !fs.fp64 && h->sweep_on && !h->sweep_items.empty();
+    TeamPlanDev plan = h->sweep_plan;
+    plan.items = h->d_sweep_items;
+    plan.counter = h->d_sweep_counter;
+    if (team) {
+        SolveArgs a = solve_args(h, fs, h->groups[0], b, z, nrhs, skip, zacc);
+        CYQ_CUDA(launch_sweep_team(true, a, plan, h->sweep_grid, st));
         ++h->launches;
+    } else {
+        for (const Group &g : h->groups) {
+            CYQ_CUDA(launch_group_sweep(h, fs, g, true, b, z, nrhs, skip, zacc, st));
+            ++h->launches;
+        }
     }
     {
         SolveArgs a = solve_args(h, fs, h->groups[0], b, z, nrhs, skip, zacc);
@@ -284,9 +323,15 @@ cyq_status run_solve(cyq_handle h, const FactorSet &fs, const double *b, double 
             ++h->launches;
         }
     }
-    for (const Group &g : h->groups) {
-        CYQ_CUDA(launch_group_sweep(h, fs, g, false, b, z, nrhs, skip, zacc, st));
+    if (team) {
+        SolveArgs a = solve_args(h, fs, h->groups[0], b, z, nrhs, skip, zacc);
+        CYQ_CUDA(launch_sweep_team(false, a, plan, h->sweep_grid, st));
         ++h->launches;
+    } else {
+        for (const Group &g : h->groups) {
+            CYQ_CUDA(launch_group_sweep(h, fs, g, false, b, z, nrhs, skip, zacc, st));
+            ++h->launches;
+        }
     }
     return CYQ_OK;
 }
@@ -385,46 +430,94 @@ ResidArgs resid_args(cyq_handle h, const double *b, const double *z, double *r, 
 
 // Solve + float64 iterative refinement on all right-hand sides at once:
 //   z = K~^{-1} b;  repeat: r = b - K z (float64), stop per instance once
-//   every ||r|| / ||b|| <= tol, else z += K~^{-1} r
+//   every ||r|| / ||b|| plus twice the rounding bound of its evaluation is
+//   <= tol (certified stop, k_certify), else z += K~^{-1} r
 // where K~ is the stored factor (float32 or float64).  All decisions are taken
 // on the device (per-instance flags), so the sequence can be graph-captured.
 cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, int nrhs, cudaStream_t st) {
     const int B = h->batch;
     CYQ_CUDA(cudaMemsetAsync(h->done, 0, sizeof(int) * B, st));
+    CYQ_CUDA(cudaMemsetAsync(h->comp, 0, sizeof(int) * B, st));
     CYQ_CUDA(cudaMemsetAsync(h->steps, 0, sizeof(int) * B, st));
     CYQ_CUDA(cudaMemsetAsync(h->rr, 0, sizeof(double) * B * h->max_nrhs, st));
     CYQ_CUDA(cudaMemsetAsync(h->bb, 0, sizeof(double) * B * h->max_nrhs, st));
+    CYQ_CUDA(cudaMemsetAsync(h->aa, 0, sizeof(double) * B * h->max_nrhs, st));
+    CYQ_CUDA(cudaMemsetAsync(h->cert, 0, sizeof(double) * B * h->max_nrhs, st));
     cyq_status s = run_solve(h, h->fac, b, z, nrhs, nullptr, st);
     if (s != CYQ_OK) return s;
     // corrections: with the handle's factor, or with its float32 copy (CYQ_FP64_IR32)
     const FactorSet &corr = h->precision == CYQ_FP64_IR32 ? h->fac32 : h->fac;
     int step = 0;
+    // residual of every instance still refining; with certify, the ones at or below tol
+    // (done = 3) evaluate || |b| + |K||z| || and stop only if the certified value is at or
+    // below tol too
+    auto evaluate = [&](bool first) -> cudaError_t {
+        cudaError_t e;
+        ResidArgs ra = resid_args(h, b, z, h->r, h->done, first);
+        ra.comp = h->comp;
+        if ((e = launch_residual(ra, nrhs, st)) ||
+            (e = launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, step, true,
+                                       h->certify ? 3 : 1, h->comp, st)))
+            return e;
+        h->launches += 3;
+        if (!h->certify) return cudaSuccess;
+        ResidArgs sa = resid_args(h, b, z, nullptr, h->done, false);
+        sa.rr = h->aa;
+        sa.run_if = 3;
+        if ((e = launch_residual_scale(sa, nrhs, st)) ||
+            (e = launch_certify(h->d_inst, B, nrhs, h->aa, h->bb, h->rel, h->cert, h->done, h->tol, st)))
+            return e;
+        h->launches += 2;
+        return cudaSuccess;
+    };
+    // float32 mode: after kPredict corrections, the instances whose residual contracts too
+    // slowly to reach tol in the remaining ones are parked, and their float64 factorization
+    // starts on the side stream while the float32 corrections of the others continue
+    constexpr int kPredict = 2;
+    const bool early = h->early_esc && !h->fac.fp64 && h->esc_max > 0 && h->esc_possible && h->side &&
+                       h->it_max > kPredict + 1;
+    bool forked = false;
     for (int it = 0; it <= h->it_max; ++it, ++step) {
         // ||b||^2 once (first residual); later steps reuse it
-        CYQ_CUDA(launch_residual(resid_args(h, b, z, h->r, h->done, it == 0), nrhs, st));
-        CYQ_CUDA(launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, step, true, st));
-        h->launches += 2;
+        CYQ_CUDA(evaluate(it == 0));
         if (it == h->it_max) break;
+        if (early && it == 0)
+            CYQ_CUDA(cudaMemcpyAsync(h->rel0, h->rel, sizeof(double) * B * nrhs, cudaMemcpyDeviceToDevice, st));
+        if (early && it == kPredict) {
+            CYQ_CUDA(launch_predict_escalation(B, nrhs, h->rel0, h->rel, h->done, h->esc, h->tol, kPredict,
+                                               h->it_max - kPredict, st));
+            CYQ_CUDA(cudaEventRecord(h->ev_fork, st));
+            CYQ_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+            s = run_factor(h, h->fac64, h->esc, h->side);
+            if (s != CYQ_OK) return s;
+            CYQ_CUDA(cudaEventRecord(h->ev_join, h->side));
+            h->launches += 1;
+            forked = true;
+        }
         // correction: z += K~^{-1} r for the instances still above tol
         s = run_solve(h, corr, h->r, h->dz, nrhs, h->done, st, z);
         if (s != CYQ_OK) return s;
     }
+    if (forked) CYQ_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
     if (!corr.fp64 && h->esc_max > 0 && h->esc_possible) {
         // precision escalation: instances the float32 corrections could not bring to
-        // tol continue with float64 corrections (float32 mode: after a float64 factorization)
+        // tol continue with float64 corrections (float32 mode: after a float64 factorization;
+        // the parked instances have theirs already, the others still above tol get it now)
         const bool refactor = !h->fac.fp64;
         if (refactor) {
             s = run_factor(h, h->fac64, h->done, st);
             if (s != CYQ_OK) return s;
+        }
+        if (forked) {
+            CYQ_CUDA(launch_unpark(B, h->done, st));
+            ++h->launches;
         }
         const FactorSet &f64 = refactor ? h->fac64 : h->fac;
         for (int it = 0; it < h->esc_max; ++it) {
             ++step;
             s = run_solve(h, f64, h->r, h->dz, nrhs, h->done, st, z);
             if (s != CYQ_OK) return s;
-            CYQ_CUDA(launch_residual(resid_args(h, b, z, h->r, h->done, false), nrhs, st));
-            CYQ_CUDA(launch_resid_finalize(B, nrhs, h->rr, h->bb, h->rel, h->done, h->tol, h->steps, step, true, st));
-            h->launches += 2;
+            CYQ_CUDA(evaluate(false));
         }
     }
     CYQ_CUDA(launch_mark_not_converged(B, h->done, h->status, st));
@@ -455,7 +548,21 @@ const char *cyq_status_string(cyq_status s) {
 
 const char *cyq_last_error(void) { return g_last_error.c_str(); }
 
-cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
+}  // extern "C"
+
+namespace {
+
+// Options of a chunk of a recompute-mode handle: the offsets of its first
+// instance in the whole batch's data and vectors, the whole batch's KKT size,
+// shared refinement vectors, and no stage-factor allocation of its own.
+struct CreateOpts {
+    bool chunk = false;
+    Inst base{};
+    long long kkt_full = 0;
+    double *r = nullptr, *dz = nullptr;
+};
+
+cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *out) {
     if (!desc || !out) return CYQ_ERR_INVALID_ARG;
     *out = nullptr;
     if (desc->batch < 1 || !desc->N || !desc->nx || !desc->nu) return CYQ_ERR_INVALID_ARG;
@@ -483,6 +590,8 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     h->it_max = desc->it_max >= 0 ? desc->it_max : 10;
     h->esc_max = desc->esc_max >= 0 ? desc->esc_max : 3;
     h->tol = desc->tol > 0 ? desc->tol : 1e-10;
+    h->early_esc = desc->early_escalation != 0;
+    h->certify = desc->certify != 0;
     h->smem_optin = smem_optin;
     // float64 factorization (CYQ_FP64, CYQ_FP64_IR32); float32 plans for the sweeps unless CYQ_FP64
     const bool fp64 = h->precision != CYQ_FP32_REFINE;
@@ -504,6 +613,11 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         in.oL = oL; in.oLB = oLB; in.oF = oF; in.oDI = oDI; in.oBA = oBA; in.oBlk = oBlk; in.oVec = oVec;
         in.oq = oq; in.orv = orv; in.oc = oc; in.ox0 = ox0;
         in.oN = oNs; in.oNn = oNn;
+        if (o.chunk) {   // data and vectors of the whole batch
+            in.oQ += o.base.oQ; in.oR += o.base.oR; in.oS += o.base.oS; in.oA += o.base.oA; in.oB += o.base.oB;
+            in.oSig += o.base.oSig; in.oZ += o.base.oZ;
+            in.oq += o.base.oq; in.orv += o.base.orv; in.oc += o.base.oc; in.ox0 += o.base.ox0;
+        }
         const long long nux = nx + nu;
         oQ += (long long)(N + 1) * nx * nx; oR += (long long)N * nu * nu; oS += (long long)N * nu * nx;
         oA += (long long)N * nx * nx; oB += (long long)N * nx * nu; oSig += (long long)(N + 1) * (nu + nx);
@@ -591,6 +705,60 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         }
     }
     if (h->crs_smem1 * (h->max_nrhs + 1) > (size_t)smem_optin) { delete h; return CYQ_ERR_INVALID_ARG; }
+    if (float_sweeps) {
+        // float32 sweeps: every item by the smallest shared memory its packages need
+        // (one package, no prefetch), longest first, in the arena classes of the one-team
+        // factor; used only when every item fits
+        int smem_sm = 0;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        const size_t half = (size_t)smem_sm / 2;
+        const size_t arena = std::min<size_t>((size_t)smem_optin, half > 2048 ? half - 2048 : 0);
+        const int arena_floats = (int)(arena / 64 * 16);
+        const size_t slot2 = (size_t)(arena_floats / 4) * 4, slot1 = (size_t)(arena_floats / 2) * 4,
+                     slot0 = (size_t)arena_floats * 4;
+        struct Cand { Item it; double cost; int cls; };
+        std::vector<Cand> cand;
+        bool all = true;
+        for (const Group &g : h->groups)
+            for (const Item &it : g.items) {
+                const Inst &in = h->inst[it.inst];
+                const size_t b = solve_smem_bytes(false, in.nx, in.nu, h->max_nrhs, 1);
+                if (b > slot0) all = false;
+                const double nux = in.nx + in.nu;
+                cand.push_back(Cand{it, seg_len(it.seg, in.N, in.P) * (nux * nux + in.nx * nux),
+                                    b <= slot2 ? 2 : (b <= slot1 ? 1 : 0)});
+            }
+        if (all) {
+            std::stable_sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) { return x.cost > y.cost; });
+            TeamPlanDev &tp = h->sweep_plan;
+            double work[3] = {0.0, 0.0, 0.0};
+            int off = 0;
+            for (int k = 0; k < 3; ++k) {
+                tp.off[k] = off;
+                for (const Cand &c : cand)
+                    if (c.cls == k) {
+                        h->sweep_items.push_back(c.it);
+                        work[k] += c.cost;
+                        ++off;
+                    }
+                tp.n[k] = off - tp.off[k];
+            }
+            tp.arena_floats = arena_floats;
+            const int grid = 2 * sms;
+            const double wsum = work[0] + work[1] + work[2];
+            int gg[3] = {0, 0, 0};
+            for (int k = 0; k < 2; ++k) {
+                if (tp.n[k] == 0) continue;
+                const int teams = k == 0 ? 1 : 2;
+                gg[k] = std::max(1, (int)std::lround(grid * work[k] / std::max(wsum, 1.0)));
+                gg[k] = std::min(gg[k], (tp.n[k] + teams - 1) / teams);
+            }
+            gg[2] = tp.n[2] > 0 ? std::max(1, grid - gg[0] - gg[1]) : 0;
+            tp.g0 = gg[0];
+            tp.g1 = gg[1];
+            h->sweep_grid = gg[0] + gg[1] + gg[2];
+        }
+    }
     if (h->precision == CYQ_FP32_REFINE) {
         // float32 factor: segments without A^cl (segment 0) whose padded blocks fit
         // three rows per lane go to the one-warp-per-item launch, longest first,
@@ -696,7 +864,9 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
             return CYQ_ERR_INVALID_ARG;
         }
     }
-    h->kkt = oZ; h->nL = oL; h->nLB = oLB; h->nF = oF; h->nDI = oDI; h->nblk = oBlk; h->nvec = oVec;
+    h->kkt = o.chunk ? o.kkt_full : oZ; h->nL = oL; h->nLB = oLB; h->nF = oF; h->nDI = oDI; h->nblk = oBlk; h->nvec = oVec;
+    h->z_lo = o.chunk ? o.base.oZ : 0;
+    h->z_n = oZ;
 
     auto fail = [&](cudaError_t e, const char *what) {
         cyq_status s = fail_cuda(e, what);
@@ -727,11 +897,15 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     for (Group &g : h->groups) ALLOC(g.d_items, g.items.size());
     for (Group &g : h->groups)
         if (g.rest_set) ALLOC(g.d_items_rest, g.items_rest.size());
+    if (!h->sweep_items.empty()) {
+        ALLOC(h->d_sweep_items, h->sweep_items.size());
+        ALLOC(h->d_sweep_counter, 3);
+    }
     if (!h->warp_items.empty()) {
         ALLOC(h->d_warp_items, h->warp_items.size());
         ALLOC(h->d_warp_counter, 3);
         ALLOC(h->d_ingest_chunks, h->ingest_chunks.size());
-        ALLOC(h->fac.Hf, (size_t)h->nHf);
+        if (!o.chunk) ALLOC(h->fac.Hf, (size_t)h->nHf);
     }
     // fac (the handle's factor) and, in float32 mode, fac64 (escalation), in float64
     // mode with float32 corrections, fac32 (float32 copy)
@@ -739,6 +913,7 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         FactorSet &fs = pass == 0 ? h->fac : (fp64 ? h->fac32 : h->fac64);
         fs.fp64 = pass == 0 ? fp64 : !fp64;
         const size_t el = fs.fp64 ? sizeof(double) : sizeof(float);
+        if (o.chunk) continue;   // the chunk's stage factors live in the shared window
         char *p;
         ALLOC(p, (size_t)oL * el); fs.L = p;
         ALLOC(p, (size_t)oLB * el); fs.LB = p;
@@ -755,14 +930,35 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     ALLOC(h->dB, (size_t)oVec * h->max_nrhs);
     ALLOC(h->lam, (size_t)oVec * h->max_nrhs);
     ALLOC(h->status, (size_t)h->batch);
-    ALLOC(h->r, (size_t)oZ * h->max_nrhs);
-    ALLOC(h->dz, (size_t)oZ * h->max_nrhs);
+    if (o.chunk) {
+        h->r = o.r;
+        h->dz = o.dz;
+    } else {
+        ALLOC(h->r, (size_t)oZ * h->max_nrhs);
+        ALLOC(h->dz, (size_t)oZ * h->max_nrhs);
+    }
     ALLOC(h->rr, (size_t)h->batch * h->max_nrhs);
     ALLOC(h->bb, (size_t)h->batch * h->max_nrhs);
     ALLOC(h->rel, (size_t)h->batch * h->max_nrhs);
+    ALLOC(h->aa, (size_t)h->batch * h->max_nrhs);
+    ALLOC(h->cert, (size_t)h->batch * h->max_nrhs);
     ALLOC(h->done, (size_t)h->batch);
+    ALLOC(h->comp, (size_t)h->batch);
     ALLOC(h->steps, (size_t)h->batch);
+    if (h->precision == CYQ_FP32_REFINE) {
+        ALLOC(h->rel0, (size_t)h->batch * h->max_nrhs);
+        ALLOC(h->esc, (size_t)h->batch);
+    }
 #undef ALLOC
+    {
+        // default paths (cyq_autotune times both): the persistent launches where the batch has
+        // several size classes or stage blocks wider than the compiled register kernels
+        int max_nux = 0;
+        for (const Inst &in : h->inst) max_nux = std::max(max_nux, in.nx + in.nu);
+        const bool persistent = h->groups.size() > 1 || max_nux > 24;
+        h->warp_on = h->sweep_on = persistent;
+        for (Group &g : h->groups) g.warp_on = persistent;
+    }
     std::vector<int> all(h->batch);
     for (int i = 0; i < h->batch; ++i) all[i] = i;
     cudaError_t e;
@@ -775,6 +971,8 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
         (e = cudaMemset(h->rr, 0, sizeof(double) * h->batch * h->max_nrhs)) ||
         (e = cudaMemset(h->bb, 0, sizeof(double) * h->batch * h->max_nrhs)) ||
         (e = cudaMemset(h->rel, 0, sizeof(double) * h->batch * h->max_nrhs)) ||
+        (e = cudaMemset(h->aa, 0, sizeof(double) * h->batch * h->max_nrhs)) ||
+        (e = cudaMemset(h->cert, 0, sizeof(double) * h->batch * h->max_nrhs)) ||
         (e = cudaMemset(h->steps, 0, sizeof(int) * h->batch)))
         return fail(e, "cudaMemcpy");
     if (!h->cr_list.empty() &&
@@ -786,11 +984,20 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     for (Group &g : h->groups)
         if ((e = cudaMemcpy(g.d_items, g.items.data(), sizeof(Item) * g.items.size(), cudaMemcpyHostToDevice)))
             return fail(e, "cudaMemcpy");
+    if (h->precision == CYQ_FP32_REFINE &&
+        ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) ||
+         (e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) ||
+         (e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming))))
+        return fail(e, "cudaStreamCreate");
     for (Group &g : h->groups)
         if (g.rest_set && !g.items_rest.empty() &&
             (e = cudaMemcpy(g.d_items_rest, g.items_rest.data(), sizeof(Item) * g.items_rest.size(),
                             cudaMemcpyHostToDevice)))
             return fail(e, "cudaMemcpy");
+    if (!h->sweep_items.empty() &&
+        (e = cudaMemcpy(h->d_sweep_items, h->sweep_items.data(), sizeof(Item) * h->sweep_items.size(),
+                        cudaMemcpyHostToDevice)))
+        return fail(e, "cudaMemcpy");
     if (!h->warp_items.empty() &&
         ((e = cudaMemcpy(h->d_warp_items, h->warp_items.data(), sizeof(Item) * h->warp_items.size(),
                          cudaMemcpyHostToDevice)) ||
@@ -801,10 +1008,145 @@ cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
     return CYQ_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+cyq_status cyq_create(const cyq_desc *desc, cyq_handle *out) {
+    if (!desc || !out) return CYQ_ERR_INVALID_ARG;
+    if (!desc->recompute_factors) return create_impl(desc, CreateOpts{}, out);
+    *out = nullptr;
+    if (desc->batch < 1 || !desc->N || !desc->nx || !desc->nu) return CYQ_ERR_INVALID_ARG;
+    const int B = desc->batch;
+    const int K = std::max(1, std::min(B, desc->recompute_chunks > 0 ? desc->recompute_chunks : 4));
+    // chunks of consecutive instances with about equal stage-factor storage
+    std::vector<long long> fsz(B);
+    long long tot = 0;
+    for (int i = 0; i < B; ++i) {
+        if (desc->N[i] < 1 || desc->nx[i] < 1 || desc->nu[i] < 1) return CYQ_ERR_INVALID_ARG;
+        const long long nux = desc->nx[i] + desc->nu[i];
+        fsz[i] = (long long)desc->N[i] * (nux * nux + nux + desc->nx[i] * nux);
+        tot += fsz[i];
+    }
+    std::vector<int> first;
+    long long acc = 0;
+    for (int i = 0; i < B; ++i) {
+        if (first.empty() || (acc * K >= tot * (long long)first.size() && (int)first.size() < K)) first.push_back(i);
+        acc += fsz[i];
+    }
+    cyq_handle h = new cyq_handle_s();
+    h->batch = B;
+    h->precision = desc->precision;
+    h->max_nrhs = desc->max_nrhs > 0 ? desc->max_nrhs : 1;
+    h->it_max = desc->it_max >= 0 ? desc->it_max : 10;
+    h->device = desc->device;
+    if (h->device < 0) cudaGetDevice(&h->device);
+    DeviceGuard guard(h->device);
+    // offsets of every instance in the whole batch (the layout of include/cyq.h)
+    std::vector<Inst> base(B);
+    {
+        Inst c{};
+        for (int i = 0; i < B; ++i) {
+            base[i] = c;
+            const long long N = desc->N[i], nx = desc->nx[i], nu = desc->nu[i];
+            c.oQ += (N + 1) * nx * nx; c.oR += N * nu * nu; c.oS += N * nu * nx; c.oA += N * nx * nx;
+            c.oB += N * nx * nu; c.oSig += (N + 1) * (nu + nx); c.oZ += N * (nu + 2 * nx);
+            c.oq += (N + 1) * nx; c.orv += N * nu; c.oc += N * nx; c.ox0 += nx;
+        }
+        h->kkt = c.oZ;
+    }
+    h->z_n = h->kkt;
+    auto fail = [&](cyq_status st) {
+        for (cyq_handle sh : h->subs) cyq_destroy(sh);
+        h->mem.free_all();
+        delete h;
+        return st;
+    };
+    if (h->mem.alloc(&h->r, (size_t)h->kkt * h->max_nrhs) != cudaSuccess ||
+        h->mem.alloc(&h->dz, (size_t)h->kkt * h->max_nrhs) != cudaSuccess)
+        return fail(fail_cuda(cudaGetLastError(), "cudaMalloc"));
+    for (size_t k = 0; k < first.size(); ++k) {
+        const int i0 = first[k], i1 = k + 1 < first.size() ? first[k + 1] : B;
+        cyq_desc d = *desc;
+        d.batch = i1 - i0;
+        d.N = desc->N + i0;
+        d.nx = desc->nx + i0;
+        d.nu = desc->nu + i0;
+        d.P_per_instance = desc->P_per_instance ? desc->P_per_instance + i0 : nullptr;
+        d.recompute_factors = 0;
+        CreateOpts o;
+        o.chunk = true;
+        o.base = base[i0];
+        o.kkt_full = h->kkt;
+        o.r = h->r;
+        o.dz = h->dz;
+        cyq_handle sh = nullptr;
+        const cyq_status st = create_impl(&d, o, &sh);
+        if (st != CYQ_OK) return fail(st);
+        h->subs.push_back(sh);
+        h->sub_first.push_back(i0);
+    }
+    // the shared window: the largest chunk's stage factors of each factor set
+    FactorSet *sets[3] = {&h->fac, &h->fac64, &h->fac32};
+    for (int si = 0; si < 3; ++si) {
+        long long nL = 0, nLB = 0, nF = 0, nDI = 0, nBA = 0, nHf = 0;
+        bool used = false, fp64 = true;
+        for (cyq_handle sh : h->subs) {
+            FactorSet *ss[3] = {&sh->fac, &sh->fac64, &sh->fac32};
+            const bool present = si == 0 || (si == 1 && sh->precision == CYQ_FP32_REFINE) ||
+                                 (si == 2 && sh->precision == CYQ_FP64_IR32);
+            if (!present) continue;
+            used = true;
+            fp64 = ss[si]->fp64;
+            nL = std::max(nL, sh->nL); nLB = std::max(nLB, sh->nLB); nF = std::max(nF, sh->nF);
+            nDI = std::max(nDI, sh->nDI);
+            long long ba = 0;
+            for (const Inst &in : sh->inst) ba += (long long)in.N * in.nx * (in.nx + in.nu);
+            nBA = std::max(nBA, ba);
+            if (si == 0) nHf = std::max(nHf, sh->nHf);
+        }
+        if (!used) continue;
+        FactorSet &fs = *sets[si];
+        fs.fp64 = fp64;
+        const size_t el = fp64 ? 8 : 4;
+        char *p;
+        if (h->mem.alloc(&p, (size_t)nL * el) != cudaSuccess) return fail(fail_cuda(cudaGetLastError(), "cudaMalloc"));
+        fs.L = p;
+        if (h->mem.alloc(&p, (size_t)nLB * el) != cudaSuccess) return fail(fail_cuda(cudaGetLastError(), "cudaMalloc"));
+        fs.LB = p;
+        if (h->mem.alloc(&p, (size_t)nF * el) != cudaSuccess) return fail(fail_cuda(cudaGetLastError(), "cudaMalloc"));
+        fs.F = p;
+        if (h->mem.alloc(&p, (size_t)nDI * el) != cudaSuccess) return fail(fail_cuda(cudaGetLastError(), "cudaMalloc"));
+        fs.DI = p;
+        if (!fp64) {
+            if (h->mem.alloc(&p, (size_t)nBA * el) != cudaSuccess)
+                return fail(fail_cuda(cudaGetLastError(), "cudaMalloc"));
+            fs.BA = p;
+        }
+        if (si == 0 && nHf > 0) {
+            if (h->mem.alloc(&fs.Hf, (size_t)nHf) != cudaSuccess) return fail(fail_cuda(cudaGetLastError(), "cudaMalloc"));
+        }
+        for (cyq_handle sh : h->subs) {
+            FactorSet *ss[3] = {&sh->fac, &sh->fac64, &sh->fac32};
+            const bool present = si == 0 || (si == 1 && sh->precision == CYQ_FP32_REFINE) ||
+                                 (si == 2 && sh->precision == CYQ_FP64_IR32);
+            if (!present) continue;
+            ss[si]->L = fs.L; ss[si]->LB = fs.LB; ss[si]->F = fs.F; ss[si]->DI = fs.DI; ss[si]->BA = fs.BA;
+            if (si == 0) ss[si]->Hf = fs.Hf;
+        }
+    }
+    *out = h;
+    return CYQ_OK;
+}
+
 void cyq_destroy(cyq_handle h) {
     if (!h) return;
     DeviceGuard guard(h->device);
     cudaDeviceSynchronize();
+    for (cyq_handle sh : h->subs) cyq_destroy(sh);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     h->mem.free_all();
     delete h;
 }
@@ -813,6 +1155,7 @@ int64_t cyq_kkt_size(cyq_handle h) { return h ? h->kkt : -1; }
 
 cyq_status cyq_get_stage_factor(cyq_handle h, int32_t instance, int32_t stage, double *L_out) {
     if (!h || !L_out || instance < 0 || instance >= h->batch) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) return CYQ_ERR_UNIMPLEMENTED;   // not offered for recompute-mode handles
     if (!h->factored) return CYQ_ERR_NO_FACTOR;
     const Inst &in = h->inst[instance];
     if (stage < 0 || stage >= in.N) return CYQ_ERR_INVALID_ARG;
@@ -834,6 +1177,10 @@ cyq_status cyq_get_stage_factor(cyq_handle h, int32_t instance, int32_t stage, d
 
 cyq_status cyq_get_segments(cyq_handle h, int32_t *P_out) {
     if (!h || !P_out) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) {
+        for (size_t k = 0; k < h->subs.size(); ++k) cyq_get_segments(h->subs[k], P_out + h->sub_first[k]);
+        return CYQ_OK;
+    }
     for (int i = 0; i < h->batch; ++i) P_out[i] = h->inst[i].P;
     return CYQ_OK;
 }
@@ -843,6 +1190,18 @@ int64_t cyq_last_launch_count(cyq_handle h) { return h ? h->launches : -1; }
 cyq_status cyq_factor(cyq_handle h, const double *Q, const double *R, const double *S, const double *A,
                       const double *B, const double *Sigma, cyq_stream stream) {
     if (!h || !Q || !R || !A || !B) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) {
+        // every chunk in turn through the shared window: statuses and coupling factors remain
+        h->launches = 0;
+        for (cyq_handle sh : h->subs) {
+            const cyq_status st = cyq_factor(sh, Q, R, S, A, B, Sigma, stream);
+            if (st != CYQ_OK) return st;
+            h->launches += sh->launches;
+        }
+        h->data = Data{Q, R, S, A, B, Sigma};
+        h->factored = true;
+        return CYQ_OK;
+    }
     DeviceGuard guard(h->device);
     cudaStream_t st = to_stream(stream);
     h->launches = 0;
@@ -857,6 +1216,20 @@ cyq_status cyq_factor(cyq_handle h, const double *Q, const double *R, const doub
 cyq_status cyq_solve(cyq_handle h, const double *b, double *z, int32_t nrhs, cyq_stream stream) {
     if (!h || !b || !z || nrhs < 1 || nrhs > h->max_nrhs) return CYQ_ERR_INVALID_ARG;
     if (!h->factored) return CYQ_ERR_NO_FACTOR;
+    if (!h->subs.empty()) {
+        // recompute mode: each chunk's stage factors again, then its solve
+        h->launches = 0;
+        for (cyq_handle sh : h->subs) {
+            DeviceGuard guard(sh->device);
+            cyq_status st = run_factor(sh, sh->fac, nullptr, to_stream(stream));
+            if (st != CYQ_OK) return st;
+            h->launches += sh->launches;
+            st = cyq_solve(sh, b, z, nrhs, stream);
+            if (st != CYQ_OK) return st;
+            h->launches += sh->launches;
+        }
+        return CYQ_OK;
+    }
     DeviceGuard guard(h->device);
     cudaStream_t st = to_stream(stream);
     h->launches = 0;
@@ -869,6 +1242,7 @@ cyq_status cyq_solve(cyq_handle h, const double *b, double *z, int32_t nrhs, cyq
 
 cyq_status cyq_apply_factor(cyq_handle h, const double *r, double *dz, int32_t nrhs, cyq_stream stream) {
     if (!h || !r || !dz || nrhs < 1 || nrhs > h->max_nrhs) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) return CYQ_ERR_UNIMPLEMENTED;   // not offered for recompute-mode handles
     if (!h->factored) return CYQ_ERR_NO_FACTOR;
     DeviceGuard guard(h->device);
     h->launches = 0;
@@ -880,6 +1254,7 @@ cyq_status cyq_apply_factor(cyq_handle h, const double *r, double *dz, int32_t n
 cyq_status cyq_update_factor(cyq_handle h, const double *Q, const double *R, const double *S, const double *w,
                              const double *delta, int32_t m_max, cyq_stream stream) {
     if (!h || !Q || !R || !w || !delta || m_max < 1) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) return CYQ_ERR_UNIMPLEMENTED;   // not offered for recompute-mode handles
     if (!h->factored) return CYQ_ERR_NO_FACTOR;
     if (!h->cr_list.empty()) {
         set_last_error_message("cyq_update_factor: instances with more than one segment are not supported");
@@ -931,12 +1306,20 @@ cyq_status cyq_build_rhs(cyq_handle h, const double *q, const double *r, const d
     if (!h || !q || !r || !c || !x_init || !b) return CYQ_ERR_INVALID_ARG;
     if (!h->factored) return CYQ_ERR_NO_FACTOR;
     DeviceGuard guard(h->device);
-    CYQ_CUDA(launch_build_rhs(h->d_inst, h->batch, h->data, q, r, c, x_init, b, h->kkt, to_stream(stream)));
+    if (!h->subs.empty()) {
+        for (cyq_handle sh : h->subs) {
+            const cyq_status st = cyq_build_rhs(sh, q, r, c, x_init, b, stream);
+            if (st != CYQ_OK) return st;
+        }
+        return CYQ_OK;
+    }
+    CYQ_CUDA(launch_build_rhs(h->d_inst, h->batch, h->data, q, r, c, x_init, b, h->z_lo, h->z_n, to_stream(stream)));
     return CYQ_OK;
 }
 
 cyq_status cyq_set_pcr_tail(cyq_handle h, int32_t levels) {
     if (!h || levels < 0) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) return CYQ_ERR_UNIMPLEMENTED;   // not offered for recompute-mode handles
     if (h->cr_list.empty()) return CYQ_OK;   // no instance has more than one segment
     DeviceGuard guard(h->device);
     CYQ_CUDA(cudaDeviceSynchronize());   // the old plan may still be in use
@@ -1017,7 +1400,9 @@ cyq_status cyq_set_pcr_tail(cyq_handle h, int32_t levels) {
 
 cyq_status cyq_set_factor_path(cyq_handle h, int32_t one_warp_per_item) {
     if (!h || one_warp_per_item < 0 || one_warp_per_item > 1) return CYQ_ERR_INVALID_ARG;
+    for (cyq_handle sh : h->subs) cyq_set_factor_path(sh, one_warp_per_item);
     h->warp_on = one_warp_per_item == 1;
+    h->sweep_on = h->warp_on;
     for (Group &g : h->groups) g.warp_on = h->warp_on;
     h->factored = false;
     return CYQ_OK;
@@ -1025,6 +1410,13 @@ cyq_status cyq_set_factor_path(cyq_handle h, int32_t one_warp_per_item) {
 
 cyq_status cyq_get_factor_path(cyq_handle h, int32_t *one_warp_per_item, int64_t *warp_items) {
     if (!h) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) {
+        int64_t n = 0;
+        for (cyq_handle sh : h->subs) n += (int64_t)sh->warp_items.size();
+        if (one_warp_per_item) *one_warp_per_item = h->subs[0]->warp_on ? 1 : 0;
+        if (warp_items) *warp_items = n;
+        return CYQ_OK;
+    }
     if (one_warp_per_item) *one_warp_per_item = h->warp_on ? 1 : 0;
     if (warp_items) *warp_items = (int64_t)h->warp_items.size();
     return CYQ_OK;
@@ -1039,6 +1431,7 @@ cyq_status cyq_get_pcr_tail(cyq_handle h, int32_t *levels) {
 cyq_status cyq_assemble_newton(cyq_handle h, const cyq_newton_in *in, const cyq_newton_out *out,
                                cyq_stream stream) {
     if (!h || !in || !out || !in->ny) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) return CYQ_ERR_UNIMPLEMENTED;   // not offered for recompute-mode handles
     if (!in->Q || !in->R || !in->A || !in->B || !in->q || !in->r || !in->c || !in->x_init || !in->u || !in->x ||
         !in->C || !in->D || !in->bl || !in->bu || !in->y || !in->sigma)
         return CYQ_ERR_INVALID_ARG;
@@ -1097,12 +1490,20 @@ cyq_status cyq_residual(cyq_handle h, const double *b, const double *z, double *
                         cyq_stream stream) {
     if (!h || !b || !z) return CYQ_ERR_INVALID_ARG;
     if (!h->factored) return CYQ_ERR_NO_FACTOR;
+    if (!h->subs.empty()) {
+        for (size_t k = 0; k < h->subs.size(); ++k) {
+            const cyq_status st = cyq_residual(h->subs[k], b, z, res, rel ? rel + h->sub_first[k] : nullptr, stream);
+            if (st != CYQ_OK) return st;
+        }
+        return CYQ_OK;
+    }
     DeviceGuard guard(h->device);
     cudaStream_t st = to_stream(stream);
     CYQ_CUDA(cudaMemsetAsync(h->rr, 0, sizeof(double) * h->batch, st));
     CYQ_CUDA(cudaMemsetAsync(h->bb, 0, sizeof(double) * h->batch, st));
     CYQ_CUDA(launch_residual(resid_args(h, b, z, res, nullptr), 1, st));
-    CYQ_CUDA(launch_resid_finalize(h->batch, 1, h->rr, h->bb, rel ? rel : h->rel, nullptr, 0.0, nullptr, 0, false, st));
+    CYQ_CUDA(launch_resid_finalize(h->batch, 1, h->rr, h->bb, rel ? rel : h->rel, nullptr, 0.0, nullptr, 0, false, 1,
+                                   nullptr, st));
     return CYQ_OK;
 }
 
@@ -1111,6 +1512,21 @@ cyq_status cyq_solve_adjoint(cyq_handle h, const double *x_init, const double *z
                              double *dc, double *dx_init, double *dSigma, cyq_stream stream) {
     if (!h || !x_init || !z || !dL_dz) return CYQ_ERR_INVALID_ARG;
     if (!h->factored) return CYQ_ERR_NO_FACTOR;
+    if (!h->subs.empty()) {
+        // recompute mode: each chunk's stage factors again, just before its adjoint solve
+        if (!w && h->it_max > 0) return CYQ_ERR_INVALID_ARG;
+        h->launches = 0;
+        for (cyq_handle sh : h->subs) {
+            DeviceGuard guard(sh->device);
+            cyq_status s2 = run_factor(sh, sh->fac, nullptr, to_stream(stream));
+            if (s2 != CYQ_OK) return s2;
+            h->launches += sh->launches;
+            s2 = cyq_solve_adjoint(sh, x_init, z, dL_dz, w, dQ, dq, dR, dr, dS, dA, dB, dc, dx_init, dSigma, stream);
+            if (s2 != CYQ_OK) return s2;
+            h->launches += sh->launches;
+        }
+        return CYQ_OK;
+    }
     DeviceGuard guard(h->device);
     cudaStream_t st = to_stream(stream);
     double *wbuf = w ? w : h->dz;
@@ -1137,6 +1553,15 @@ cyq_status cyq_pivot_eval(const double *d, double *l, double *il, const float *d
 
 cyq_status cyq_get_instance_status(cyq_handle h, int32_t *host_status, cyq_stream stream) {
     if (!h || !host_status) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) {
+        cyq_status first = CYQ_OK;
+        for (size_t k = 0; k < h->subs.size(); ++k) {
+            const cyq_status st = cyq_get_instance_status(h->subs[k], host_status + h->sub_first[k], stream);
+            if (st == CYQ_ERR_CUDA || st == CYQ_ERR_INVALID_ARG) return st;
+            if (first == CYQ_OK) first = st;
+        }
+        return first;
+    }
     DeviceGuard guard(h->device);
     cudaStream_t st = to_stream(stream);
     CYQ_CUDA(cudaStreamSynchronize(st));
@@ -1146,20 +1571,51 @@ cyq_status cyq_get_instance_status(cyq_handle h, int32_t *host_status, cyq_strea
     return CYQ_OK;
 }
 
+int64_t cyq_workspace_bytes(cyq_handle h) {
+    if (!h) return -1;
+    long long b = h->mem.bytes;
+    for (cyq_handle sh : h->subs) b += cyq_workspace_bytes(sh);
+    return b;
+}
+
 cyq_status cyq_get_stats(cyq_handle h, cyq_stats *out, cyq_stream stream) {
     if (!h || !out) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) {
+        cyq_stats t{};
+        t.max_rel_residual = -1.0;
+        t.max_certified = -1.0;
+        t.P_min = 1 << 30;
+        for (cyq_handle sh : h->subs) {
+            cyq_stats c{};
+            const cyq_status st = cyq_get_stats(sh, &c, stream);
+            if (st != CYQ_OK) return st;
+            t.refine_steps = std::max(t.refine_steps, c.refine_steps);
+            t.max_rel_residual = std::max(t.max_rel_residual, c.max_rel_residual);
+            t.max_certified = std::max(t.max_certified, c.max_certified);
+            t.P_min = std::min(t.P_min, c.P_min);
+            t.P_max = std::max(t.P_max, c.P_max);
+            t.work_items += c.work_items;
+        }
+        *out = t;
+        return CYQ_OK;
+    }
     DeviceGuard guard(h->device);
     CYQ_CUDA(cudaStreamSynchronize(to_stream(stream)));
     const int nr = std::max(h->last_nrhs, 1);
-    std::vector<double> rel((size_t)h->batch * nr);
+    std::vector<double> rel((size_t)h->batch * nr), cert((size_t)h->batch * nr);
     std::vector<int> steps(h->batch);
     CYQ_CUDA(cudaMemcpy(rel.data(), h->rel, sizeof(double) * rel.size(), cudaMemcpyDeviceToHost));
+    CYQ_CUDA(cudaMemcpy(cert.data(), h->cert, sizeof(double) * cert.size(), cudaMemcpyDeviceToHost));
     CYQ_CUDA(cudaMemcpy(steps.data(), h->steps, sizeof(int) * h->batch, cudaMemcpyDeviceToHost));
     out->refine_steps = 0;
     out->max_rel_residual = h->last_nrhs > 0 ? 0.0 : -1.0;
     for (int i = 0; i < h->batch; ++i) out->refine_steps = std::max(out->refine_steps, steps[i]);
-    if (h->last_nrhs > 0)
+    out->max_certified = h->last_nrhs > 0 && h->certify ? 0.0 : -1.0;
+    if (h->last_nrhs > 0) {
         for (double v : rel) out->max_rel_residual = std::max(out->max_rel_residual, v);
+        if (h->certify)
+            for (double v : cert) out->max_certified = std::max(out->max_certified, v);
+    }
     out->P_min = 1 << 30;
     out->P_max = 0;
     for (const Inst &in : h->inst) {
@@ -1210,6 +1666,16 @@ cyq_status cyq_autotune(cyq_handle h, const double *Q, const double *R, const do
                         const double *B, const double *Sigma, const double *b, double *z, int32_t nrhs,
                         int32_t reps, cyq_stream stream) {
     if (!h || !b || !z || nrhs < 1 || nrhs > h->max_nrhs) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) {
+        // each chunk tunes its own launch shapes (leaves every chunk factored in turn)
+        for (cyq_handle sh : h->subs) {
+            const cyq_status st = cyq_autotune(sh, Q, R, S, A, B, Sigma, b, z, nrhs, reps, stream);
+            if (st != CYQ_OK) return st;
+        }
+        h->data = Data{Q, R, S, A, B, Sigma};
+        h->factored = true;
+        return CYQ_OK;
+    }
     if (reps < 1) reps = 3;
     cyq_status s = cyq_factor(h, Q, R, S, A, B, Sigma, stream);   // binds the data
     if (s != CYQ_OK) return s;
@@ -1268,6 +1734,39 @@ cyq_status cyq_autotune(cyq_handle h, const double *Q, const double *R, const do
             g.team_solve[0] = pick;
         }
     }
+    // float32 factor and sweeps: the persistent launches against the per-class ones
+    if (!fs.fp64 && !h->warp_items.empty()) {
+        float best = 3.0e38f;
+        bool pick = true;
+        for (int on = 1; on >= 0; --on) {
+            h->warp_on = on == 1;
+            for (Group &g : h->groups) g.warp_on = h->warp_on;
+            float ms = 0.0f;
+            s = time_ms(st, reps, [&] { return run_factor(h, fs, nullptr, st) == CYQ_OK ? cudaSuccess : cudaErrorUnknown; },
+                        &ms);
+            if (s != CYQ_OK) return s;
+            if (ms < best) { best = ms; pick = h->warp_on; }
+        }
+        h->warp_on = pick;
+        for (Group &g : h->groups) g.warp_on = pick;
+    }
+    s = run_factor(h, fs, nullptr, st);   // (refreshes the float32 copy of CYQ_FP64_IR32 too)
+    if (s != CYQ_OK) return s;
+    const FactorSet &fs32 = h->precision == CYQ_FP64_IR32 ? h->fac32 : fs;
+    if (!fs32.fp64 && !h->sweep_items.empty()) {
+        float best = 3.0e38f;
+        bool pick = true;
+        for (int on = 1; on >= 0; --on) {
+            h->sweep_on = on == 1;
+            float ms = 0.0f;
+            s = time_ms(st, reps, [&] { return run_solve(h, fs32, b, z, nrhs, nullptr, st) == CYQ_OK ? cudaSuccess
+                                                                                                 : cudaErrorUnknown; },
+                        &ms);
+            if (s != CYQ_OK) return s;
+            if (ms < best) { best = ms; pick = h->sweep_on; }
+        }
+        h->sweep_on = pick;
+    }
     // the timed launches left the factor intact (same data); refresh it as a whole
     s = run_factor(h, fs, nullptr, st);
     if (s != CYQ_OK) return s;
@@ -1278,6 +1777,7 @@ cyq_status cyq_autotune(cyq_handle h, const double *Q, const double *R, const do
 cyq_status cyq_get_launch_shapes(cyq_handle h, int32_t *n_groups, int32_t *factor_team, int32_t *sweep_team,
                                  int32_t nrhs) {
     if (!h || !n_groups) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) return cyq_get_launch_shapes(h->subs[0], n_groups, factor_team, sweep_team, nrhs);
     *n_groups = (int32_t)h->groups.size();
     const bool f64 = h->fac.fp64;
     for (size_t i = 0; i < h->groups.size(); ++i) {
@@ -1289,6 +1789,7 @@ cyq_status cyq_get_launch_shapes(cyq_handle h, int32_t *n_groups, int32_t *facto
 
 cyq_status cyq_set_launch_shapes(cyq_handle h, const int32_t *factor_team, const int32_t *sweep_team, int32_t nrhs) {
     if (!h) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) return CYQ_ERR_UNIMPLEMENTED;   // not offered for recompute-mode handles
     const int pi = h->fac.fp64 ? 1 : 0;
     for (size_t i = 0; i < h->groups.size(); ++i) {
         const int f = factor_team ? factor_team[i] : 0, w = sweep_team ? sweep_team[i] : 0;

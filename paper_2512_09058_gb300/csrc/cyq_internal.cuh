@@ -473,7 +473,11 @@ struct ResidArgs {
     const double *b, *z;
     double *r;          // may be null (norms only)
     double *rr, *bb;    // accumulators of squared norms, [rhs][instance]
-    const int *skip;    // optional per-instance flag
+    const int *skip;    // optional per-instance flag: an instance runs iff skip[i] == run_if
+    int run_if;
+    const int *comp;    // optional per-instance flag: 1 = evaluate the rows compensated
+    const int *sel;     // (set by the launcher) an instance runs iff sel[i] == sel_val
+    int sel_val;
     long long kkt;      // elements per right-hand side
     int batch;
     bool need_bb;       // accumulate ||b||^2 too (false: bb already holds it)
@@ -488,9 +492,18 @@ struct GradArgs {
 };
 
 cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st);
+// || |b| + |K| |z| ||^2 per instance and right-hand side into a.rr (instances with skip[i] == run_if)
+cudaError_t launch_residual_scale(const ResidArgs &a, int nrhs, cudaStream_t st);
+cudaError_t launch_certify(const Inst *inst, int batch, int nrhs, double *aa, const double *bb, const double *rel,
+                           double *cert, int *done, double tol, cudaStream_t st);
+// done[i] = done_value once every right-hand side of instance i is at or below tol;
+// comp (optional): set to 1 where a residual above tol did not halve since the last step
 cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
-                                  int *steps, int step, bool keep_bb, cudaStream_t st);
+                                  int *steps, int step, bool keep_bb, int done_value, int *comp, cudaStream_t st);
 cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, cudaStream_t st);
+cudaError_t launch_predict_escalation(int batch, int nrhs, const double *rel0, const double *rel, int *done, int *esc,
+                                      double tol, int k, int left, cudaStream_t st);
+cudaError_t launch_unpark(int batch, int *done, cudaStream_t st);
 // Factorization update (update.cu): low-rank modifications of the stage matrices
 // applied to the stored factor of one-segment instances.
 struct UpdateArgs {
@@ -529,7 +542,8 @@ size_t newton_smem_bytes(int ny, int nx, int nu);
 cudaError_t launch_newton_assemble(const NewtonArgs &a, int batch, int max_stages, size_t smem, cudaStream_t st);
 
 cudaError_t launch_build_rhs(const Inst *inst, int batch, const Data &d, const double *q, const double *r,
-                             const double *c, const double *x0, double *b, long long kkt, cudaStream_t st);
+                             const double *c, const double *x0, double *b, long long z_lo, long long z_n,
+                             cudaStream_t st);
 cudaError_t launch_adjoint(const GradArgs &g, int n_chunks, int batch, const Data &d, double *dx0, cudaStream_t st);
 
 size_t factor_smem_bytes(bool fp64, int nx, int nu, bool staged, bool need_G2);
@@ -545,6 +559,8 @@ cudaError_t ensure_smem(const void *kernel, size_t bytes);
 // Sets the text returned by cyq_last_error() for the calling thread.
 void set_last_error_message(const char *msg);
 inline void set_last_error_message(const std::string &msg) { set_last_error_message(msg.c_str()); }
-size_t solve_smem_bytes(bool fp64, int nx, int nu, int nrhs, int nbuf);
+__host__ __device__ size_t solve_smem_bytes(bool fp64, int nx, int nu, int nrhs, int nbuf);
+// Float32 sweeps of every item in one persistent launch (backward or forward).
+cudaError_t launch_sweep_team(bool backward, const SolveArgs &a, const TeamPlanDev &plan, int grid, cudaStream_t st);
 
 }  // namespace cyq

@@ -247,7 +247,12 @@ __device__ bool team_crout(float *H, int np, float *dinv, float *dblk, const Tea
         for (int m = 0; m < RPT; ++m)
 #pragma unroll
             for (int j = 0; j < 4; ++j) accb[m][j] = 0.0f;
-        const bool active = tid + T * (RPT - 1) >= q0;   // some own row at or below the block
+        bool active = false;   // some own row at or below the block
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+            const int r = tid + T * m;
+            active = active || (r < np && r >= q0);
+        }
 #pragma unroll 2
         for (int k = 0; k < (active ? q0 : 0); k += 2) {
             const float *ck = H + k * ld, *ck1 = ck + ld;

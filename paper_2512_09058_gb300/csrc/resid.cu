@@ -19,6 +19,67 @@ namespace cyq {
 // full warp slot per path.  Up to RG right-hand sides share every matrix load.
 constexpr int RG = 4;
 
+// Accumulation of one residual row, b - sum_j m_j z_j, by mode:
+//   kResidPlain  float64 fused multiply-adds;
+//   kResidScale  |b| + sum_j |m_j| |z_j| (the scale of the rounding error of any
+//                float64 evaluation of the row);
+//   kResidComp   compensated: every product split exactly into q + e with a
+//                fused multiply-add, the sum carried as hi + lo with Knuth's
+//                TwoSum (the error-free transformations of Ogita, Rump and
+//                Oishi's Dot2, SIAM J. Sci. Comput. 26, 2005), so the row is
+//                as accurate as if computed in twice the working precision and
+//                rounded once.  Used where the plain evaluation's rounding is
+//                as large as the residual itself (refinement at its noise
+//                floor).  The _rn intrinsics keep the compiler from fusing or
+//                reassociating the transformations.
+constexpr int kResidPlain = 0, kResidScale = 1, kResidComp = 2;
+
+template <int MODE>
+struct RowAcc;
+
+template <>
+struct RowAcc<kResidPlain> {
+    double v;
+    __device__ __forceinline__ void init(double x) { v = x; }
+    __device__ __forceinline__ void mac(double m, double zv) { v = fma(m, zv, v); }
+    __device__ __forceinline__ double finish(double b) const { return b - v; }
+};
+
+template <>
+struct RowAcc<kResidScale> {
+    double v;
+    __device__ __forceinline__ void init(double x) { v = fabs(x); }
+    __device__ __forceinline__ void mac(double m, double zv) { v = fma(fabs(m), fabs(zv), v); }
+    __device__ __forceinline__ double finish(double b) const { return fabs(b) + v; }
+};
+
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &t) {
+    s = __dadd_rn(a, b);
+    const double bv = __dsub_rn(s, a);
+    t = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bv)), __dsub_rn(b, bv));
+}
+
+template <>
+struct RowAcc<kResidComp> {
+    double hi, lo;
+    __device__ __forceinline__ void init(double x) {
+        hi = x;
+        lo = 0.0;
+    }
+    __device__ __forceinline__ void mac(double m, double zv) {
+        const double q = __dmul_rn(m, zv), e = __fma_rn(m, zv, -q);   // m zv = q + e exactly
+        double s, t;
+        two_sum(hi, q, s, t);
+        hi = s;
+        lo = __dadd_rn(lo, __dadd_rn(t, e));
+    }
+    __device__ __forceinline__ double finish(double b) const {
+        double d, t;
+        two_sum(b, -hi, d, t);
+        return __dadd_rn(d, __dsub_rn(t, lo));
+    }
+};
+
 #define CYQ_ROW_UNROLL _Pragma("unroll 4")
 #define CYQ_RESID_KERNEL k_residual_long_rows
 #include "resid_rows.inc"
@@ -36,22 +97,88 @@ constexpr int RG = 4;
 // b does not change between the refinement steps of one solve).  steps[i] records the number
 // of corrections an instance received so far.
 __global__ void k_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
-                                 int *steps, int step, bool keep_bb) {
+                                 int *steps, int step, bool keep_bb, int done_value, int *comp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= batch) return;
     if (done && done[i]) return;
-    bool all = true;
+    bool all = true, stalled = false;
     for (int r = 0; r < nrhs; ++r) {
         const long long j = (long long)r * batch + i;
         const double rn = sqrt(rr[j]), bn = sqrt(bb[j]);
         const double v = bn > 0.0 ? rn / bn : rn;
+        // a correction that did not halve a residual above tol: the float64 evaluation's
+        // rounding (or a slow contraction) limits it; later evaluations are compensated
+        if (comp && step > 0 && !(v <= tol) && v > 0.5 * rel[j]) stalled = true;
         if (rel) rel[j] = v;
         all = all && (v <= tol);
         rr[j] = 0.0;
         if (!keep_bb) bb[j] = 0.0;
     }
-    if (done && all) done[i] = 1;
+    if (done && all) done[i] = done_value;
+    if (stalled) comp[i] = 1;
     if (steps) steps[i] = step;
+}
+
+// Certified stop.  Any float64 evaluation of b - K z, in any summation order,
+// differs from the exact residual by at most gamma_m (|b| + |K| |z|)
+// componentwise, m the number of terms of a row (Higham, Accuracy and
+// Stability of Numerical Algorithms, Sec. 3.1: gamma_m = m u / (1 - m u),
+// u = 2^-53).  A row of K z here has at most 2 nx + nu + 2 products (Sigma
+// is added as a product of its own) and b one more term: m = 2 nx + nu + 3.
+// So another evaluation of the same z (another program, another order) can
+// read at most rel + 2 gamma_m || |b| + |K||z| || / ||b||.  Instances whose
+// residual passed tol (done = 3) stop only if that sum is at or below tol too
+// (done = 1), otherwise they take another correction (done = 0).  cert holds
+// the sum; aa is cleared.
+__global__ void k_certify(const Inst *inst, int batch, int nrhs, double *aa, const double *bb, const double *rel,
+                          double *cert, int *done, double tol) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= batch || done[i] != 3) return;
+    const Inst in = inst[i];
+    const double u = 0x1p-53, m = 2.0 * in.nx + in.nu + 3.0;
+    const double gamma = m * u / (1.0 - m * u);
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) {
+        const long long j = (long long)r * batch + i;
+        const double bn = sqrt(bb[j]);
+        const double s = sqrt(aa[j]);
+        const double c = rel[j] + 2.0 * gamma * (bn > 0.0 ? s / bn : s);
+        cert[j] = c;
+        all = all && (c <= tol);
+        aa[j] = 0.0;
+    }
+    done[i] = all ? 1 : 0;
+}
+
+// Early float64 escalation (float32 refinement).  After `k` corrections the
+// residual of every right-hand side has contracted from rel0 to rel; at that
+// rate the `left` corrections still to come end at rel (rel / rel0)^(left / k).
+// An instance that would stay above tol is parked (done = 2: the float32
+// corrections skip it) and marked for a float64 factorization now (esc = 0;
+// every other instance esc = 1, i.e. skipped by that factorization).
+__global__ void k_predict_escalation(int batch, int nrhs, const double *rel0, const double *rel, int *done, int *esc,
+                                     double tol, int k, int left) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= batch) return;
+    bool park = false;
+    if (!done[i]) {
+        for (int r = 0; r < nrhs; ++r) {
+            const long long j = (long long)r * batch + i;
+            const double a = rel0[j], c = rel[j];
+            if (!(c <= tol)) {
+                const double rate = (a > 0.0 && c < a) ? pow(c / a, 1.0 / k) : 1.0;
+                if (!(c * pow(rate, (double)left) <= tol)) park = true;
+            }
+        }
+    }
+    if (park) done[i] = 2;
+    esc[i] = park ? 0 : 1;
+}
+
+// Parked instances (done = 2) rejoin the refinement for the float64 corrections.
+__global__ void k_unpark(int batch, int *done) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < batch && done[i] == 2) done[i] = 0;
 }
 
 // Instances still above tol after the last refinement step: status NOT_CONVERGED.
@@ -72,8 +199,8 @@ __device__ __forceinline__ int find_inst(const Inst *inst, int batch, long long 
 }
 
 __global__ void k_build_rhs(const Inst *inst, int batch, Data d, const double *q, const double *r,
-                            const double *c, const double *x0, double *b, long long kkt) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < kkt;
+                            const double *c, const double *x0, double *b, long long z_lo, long long z_n) {
+    for (long long e = z_lo + blockIdx.x * (long long)blockDim.x + threadIdx.x; e < z_lo + z_n;
          e += (long long)gridDim.x * blockDim.x) {
         const Inst in = inst[find_inst(inst, batch, e)];
         const int nx = in.nx, nu = in.nu, w = nu + 2 * nx;
@@ -186,35 +313,74 @@ __global__ void k_adjoint_dx0(const Inst *inst, int batch, Data d, const double 
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-template <int NR>
+template <int NR, int MODE>
 static void launch_residual_nr(const ResidArgs &a, int r_first, int groups, cudaStream_t st) {
     const dim3 grid(a.n_chunks, groups);
     if (a.max_nx >= 24)
-        k_residual_long_rows<128, NR><<<grid, 128, 0, st>>>(a, r_first);
+        k_residual_long_rows<128, NR, MODE><<<grid, 128, 0, st>>>(a, r_first);
     else
-        k_residual_short_rows<128, NR><<<grid, 128, 0, st>>>(a, r_first);
+        k_residual_short_rows<128, NR, MODE><<<grid, 128, 0, st>>>(a, r_first);
 }
 
 cudaError_t launch_residual(const ResidArgs &a, int nrhs, cudaStream_t st) {
     if (a.n_chunks == 0) return cudaSuccess;
-    // full groups of RG right-hand sides, then one launch for the remainder
+    // plain rows for the instances without the compensated flag: full groups of RG
+    // right-hand sides, then one launch for the remainder
+    ResidArgs p = a;
+    p.sel = a.comp;
+    p.sel_val = 0;
     const int full = nrhs / RG, rest = nrhs % RG;
-    if (full > 0) launch_residual_nr<RG>(a, 0, full, st);
+    if (full > 0) launch_residual_nr<RG, kResidPlain>(p, 0, full, st);
     switch (rest) {
-        case 1: launch_residual_nr<1>(a, full * RG, 1, st); break;
-        case 2: launch_residual_nr<2>(a, full * RG, 1, st); break;
-        case 3: launch_residual_nr<3>(a, full * RG, 1, st); break;
+        case 1: launch_residual_nr<1, kResidPlain>(p, full * RG, 1, st); break;
+        case 2: launch_residual_nr<2, kResidPlain>(p, full * RG, 1, st); break;
+        case 3: launch_residual_nr<3, kResidPlain>(p, full * RG, 1, st); break;
         default: break;
+    }
+    if (a.comp) {   // compensated rows for the flagged ones, one right-hand side per CTA row
+        ResidArgs c = a;
+        c.sel = a.comp;
+        c.sel_val = 1;
+        launch_residual_nr<1, kResidComp>(c, 0, nrhs, st);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
-                                  int *steps, int step, bool keep_bb, cudaStream_t st) {
-    k_resid_finalize<<<(batch + 127) / 128, 128, 0, st>>>(batch, nrhs, rr, bb, rel, done, tol, steps, step, keep_bb);
+// One right-hand side per CTA row: the scale is evaluated once per instance
+// and stop, on the instances about to stop.
+cudaError_t launch_residual_scale(const ResidArgs &a, int nrhs, cudaStream_t st) {
+    if (a.n_chunks == 0) return cudaSuccess;
+    ResidArgs s = a;
+    s.r = nullptr;
+    s.need_bb = false;
+    s.sel = nullptr;
+    launch_residual_nr<1, kResidScale>(s, 0, nrhs, st);
     return cudaGetLastError();
 }
 
+cudaError_t launch_certify(const Inst *inst, int batch, int nrhs, double *aa, const double *bb, const double *rel,
+                           double *cert, int *done, double tol, cudaStream_t st) {
+    k_certify<<<(batch + 127) / 128, 128, 0, st>>>(inst, batch, nrhs, aa, bb, rel, cert, done, tol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
+                                  int *steps, int step, bool keep_bb, int done_value, int *comp, cudaStream_t st) {
+    k_resid_finalize<<<(batch + 127) / 128, 128, 0, st>>>(batch, nrhs, rr, bb, rel, done, tol, steps, step, keep_bb,
+                                                          done_value, comp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict_escalation(int batch, int nrhs, const double *rel0, const double *rel, int *done, int *esc,
+                                      double tol, int k, int left, cudaStream_t st) {
+    k_predict_escalation<<<(batch + 127) / 128, 128, 0, st>>>(batch, nrhs, rel0, rel, done, esc, tol, k, left);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpark(int batch, int *done, cudaStream_t st) {
+    k_unpark<<<(batch + 127) / 128, 128, 0, st>>>(batch, done);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, cudaStream_t st) {
     k_mark_not_converged<<<(batch + 127) / 128, 128, 0, st>>>(batch, done, status);
@@ -222,11 +388,12 @@ cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, c
 }
 
 cudaError_t launch_build_rhs(const Inst *inst, int batch, const Data &d, const double *q, const double *r,
-                             const double *c, const double *x0, double *b, long long kkt, cudaStream_t st) {
-    long long blocks = (kkt + 255) / 256;
+                             const double *c, const double *x0, double *b, long long z_lo, long long z_n,
+                             cudaStream_t st) {
+    long long blocks = (z_n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_build_rhs<<<(int)blocks, 256, 0, st>>>(inst, batch, d, q, r, c, x0, b, kkt);
+    k_build_rhs<<<(int)blocks, 256, 0, st>>>(inst, batch, d, q, r, c, x0, b, z_lo, z_n);
     return cudaGetLastError();
 }
 

@@ -24,7 +24,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "not positive definite", 3: "not co
 
 # every entry point declared in include/cyq.h
 EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual",
-           "cyq_solve_adjoint", "cyq_get_instance_status", "cyq_get_stats", "cyq_kkt_size",
+           "cyq_solve_adjoint", "cyq_get_instance_status", "cyq_get_stats", "cyq_kkt_size", "cyq_workspace_bytes",
            "cyq_get_segments", "cyq_last_launch_count", "cyq_status_string", "cyq_last_error",
            "cyq_factor_solve_noalloc", "cyq_autotune", "cyq_get_launch_shapes", "cyq_tune_segments",
            "cyq_set_launch_shapes", "cyq_get_stage_factor", "cyq_assemble_newton", "cyq_set_pcr_tail",
@@ -43,12 +43,15 @@ class cyq_desc(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("P", ctypes.c_int32),
                 ("P_per_instance", ctypes.POINTER(ctypes.c_int32)), ("max_nrhs", ctypes.c_int32),
                 ("it_max", ctypes.c_int32), ("tol", ctypes.c_double), ("device", ctypes.c_int32),
-                ("esc_max", ctypes.c_int32)]
+                ("esc_max", ctypes.c_int32), ("recompute_factors", ctypes.c_int32),
+                ("recompute_chunks", ctypes.c_int32), ("early_escalation", ctypes.c_int32),
+                ("certify", ctypes.c_int32)]
 
 
 class cyq_stats(ctypes.Structure):
     _fields_ = [("refine_steps", ctypes.c_int32), ("max_rel_residual", ctypes.c_double),
-                ("P_min", ctypes.c_int32), ("P_max", ctypes.c_int32), ("work_items", ctypes.c_int64)]
+                ("max_certified", ctypes.c_double), ("P_min", ctypes.c_int32), ("P_max", ctypes.c_int32),
+                ("work_items", ctypes.c_int64)]
 
 
 class cyq_newton_in(ctypes.Structure):
@@ -86,6 +89,8 @@ def load(path: str = LIB_PATH):
     L.cyq_get_stats.argtypes = [vp, ctypes.POINTER(cyq_stats), vp]
     L.cyq_kkt_size.argtypes = [vp]
     L.cyq_kkt_size.restype = i64
+    L.cyq_workspace_bytes.argtypes = [vp]
+    L.cyq_workspace_bytes.restype = i64
     L.cyq_get_segments.argtypes = [vp, ctypes.POINTER(i32)]
     L.cyq_last_launch_count.argtypes = [vp]
     L.cyq_last_launch_count.restype = i64
@@ -142,7 +147,7 @@ class _Desc:
     """A cyq_desc with the host arrays it points to kept alive."""
 
     def __init__(self, N, nx, nu, precision="fp64", P=0, P_per_instance=None, max_nrhs=1, it_max=-1,
-                 tol=1e-10, device=-1, esc_max=-1):
+                 tol=1e-10, device=-1, esc_max=-1, recompute_chunks=0, early_escalation=False, certify=False):
         i32p = ctypes.POINTER(ctypes.c_int32)
         self.N = np.ascontiguousarray(N, dtype=np.int32)
         self.nx = np.ascontiguousarray(nx, dtype=np.int32)
@@ -154,7 +159,8 @@ class _Desc:
             pp = self.P.ctypes.data_as(i32p)
         self.desc = cyq_desc(len(self.N), self.N.ctypes.data_as(i32p), self.nx.ctypes.data_as(i32p),
                              self.nu.ctypes.data_as(i32p), self.precision, P, pp, max_nrhs, it_max, tol, device,
-                             esc_max)
+                             esc_max, 1 if recompute_chunks > 0 else 0, int(recompute_chunks),
+                             1 if early_escalation else 0, 1 if certify else 0)
 
 
 def tune_segments(N, nx, nu, data, b, nrhs: int = 1, reps: int = 2, stream=None, **desc_kw) -> np.ndarray:
@@ -177,9 +183,17 @@ class Solver:
 
     def __init__(self, N: Sequence[int], nx: Sequence[int], nu: Sequence[int], precision: str = "fp64",
                  P: int = 0, P_per_instance: Optional[Sequence[int]] = None, max_nrhs: int = 1,
-                 it_max: int = -1, tol: float = 1e-10, device: int = -1, esc_max: int = -1):
+                 it_max: int = -1, tol: float = 1e-10, device: int = -1, esc_max: int = -1,
+                 recompute_chunks: int = 0, early_escalation: bool = False, certify: bool = False):
+        """recompute_chunks > 0: keep the stage factors of one chunk of instances at a
+        time (the batch in that many chunks) and factor each chunk again in every solve
+        and adjoint (cyq_desc.recompute_factors).  early_escalation: float32 mode factors
+        the slowly converging instances in float64 after two corrections, on a second
+        stream (cyq_desc.early_escalation).
+        certify: stop only where the worst-case float64 evaluation bound allows (cyq_desc.certify)."""
         L = load()
-        d = _Desc(N, nx, nu, precision, P, P_per_instance, max_nrhs, it_max, tol, device, esc_max)
+        d = _Desc(N, nx, nu, precision, P, P_per_instance, max_nrhs, it_max, tol, device, esc_max,
+                  recompute_chunks, early_escalation, certify)
         self._desc = d
         self.N, self.nx, self.nu = d.N, d.nx, d.nu
         self.batch = len(self.N)
@@ -190,6 +204,7 @@ class Solver:
         _check(L.cyq_create(ctypes.byref(desc), ctypes.byref(h)))
         self._h = h
         self.kkt_size = int(L.cyq_kkt_size(h))
+        self.workspace_bytes = int(L.cyq_workspace_bytes(h))
         self._data = None
         self.factor_version = 0
 
@@ -359,7 +374,8 @@ class Solver:
     def stats(self, stream=None) -> dict:
         s = cyq_stats()
         _check(_lib.cyq_get_stats(self._h, ctypes.byref(s), _stream(stream)))
-        return dict(refine_steps=s.refine_steps, max_rel_residual=s.max_rel_residual, P_min=s.P_min,
+        return dict(refine_steps=s.refine_steps, max_rel_residual=s.max_rel_residual,
+                    max_certified=s.max_certified, P_min=s.P_min,
                     P_max=s.P_max, work_items=s.work_items)
 
 

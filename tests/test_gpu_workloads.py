@@ -8,14 +8,12 @@ on the device: status words and the refinement's own float64 residuals).
 * uneven4096: 4096 OCPs of uneven N, nx, nu; float32 + float64 refinement.
 * adjoint512_n128_nx24_nu8: 512 OCPs; float64 factor, refined solve, adjoint.
 
-Gates: refined solves reach <= 1e-10 relative KKT residual as evaluated by the
+Gates: refined solves reach the refinement target 5e-11 as evaluated by the
 library's float64 residual (device statistics), and the oracle's independent
-float64 evaluation on the same z is at most 1e-10 plus twice the rounding
-bound of a float64 evaluation (gamma_m || |b| + |K| |z| || / ||b||, computed by
-the oracle): near 1e-10 on the hardest instances of the uneven workload that
-bound is a few percent of the residual itself, so the two evaluations can
-straddle the target; plain float64 forward error <= 1e-9 against the oracle;
-the adjoint <= 1e-9 relative to the oracle's.
+float64 evaluation on the same z meets the gate 1e-10 itself (the two float64
+evaluations differ by a few percent near the gate, well inside the factor-2
+margin); plain float64 forward error <= 1e-9 against the oracle; the adjoint
+<= 1e-9 relative to the oracle's.
 """
 import numpy as np
 import pytest
@@ -23,21 +21,22 @@ import pytest
 import oracle
 from paper_2512_09058_gb300 import inputs
 
-from gpu_util import rel_err, require_gpu, split_instances
+from gpu_util import GATE, REFINE_TARGET, rel_err, require_gpu, split_instances
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-10
+TOL = GATE
 
 
 def eval_gate(inst, z, b):
-    """Largest oracle-evaluated residual consistent with a device-certified TOL."""
-    return TOL + 2.0 * oracle.residual_eval_bound(inst, z, b)
+    """The gate the oracle's own evaluation of a refined z must meet (no allowance)."""
+    return TOL
 
 
 def _solve(batch, precision, it_max, P=0, nrhs=1):
     torch, cyq = require_gpu()
-    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, P=P, max_nrhs=nrhs, it_max=it_max)
+    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision=precision, P=P, max_nrhs=nrhs, it_max=it_max,
+                   tol=REFINE_TARGET)
     data, rhs = cyq.to_device(batch)
     s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
     kk = s.kkt_size
@@ -62,7 +61,7 @@ def test_long_horizon_segments_and_cyclic_reduction(long_batch, precision, it_ma
     assert (s.instance_status() == 0).all()
     st = s.stats()
     if it_max:
-        assert st["max_rel_residual"] <= 1e-10
+        assert st["max_rel_residual"] <= REFINE_TARGET
     zs, bs = split_instances(batch, z[0]), split_instances(batch, b[0])
     for i in (0, 5):
         inst = batch.instances[i]
@@ -82,7 +81,7 @@ def test_uneven_batch_fp32_refinement():
     assert (s.instance_status() == 0).all()
     st = s.stats()
     print("uneven4096", st)
-    assert st["max_rel_residual"] <= 1e-10
+    assert st["max_rel_residual"] <= REFINE_TARGET
     rng = np.random.default_rng(4)
     sample = sorted(rng.choice(batch.size, size=12, replace=False))
     zs, bs = split_instances(batch, z[0]), split_instances(batch, b[0])
@@ -137,7 +136,7 @@ def test_mass_spring_workload_sampled(precision, it_max):
     assert (s.instance_status() == 0).all()
     st = s.stats()
     if it_max:
-        assert st["max_rel_residual"] <= 1e-10
+        assert st["max_rel_residual"] <= REFINE_TARGET
     zs, bs = split_instances(batch, z[0]), split_instances(batch, b[0])
     for i in (0, 74, 149):
         inst = batch.instances[i]
@@ -145,3 +144,21 @@ def test_mass_spring_workload_sampled(precision, it_max):
         assert rel_err(zs[i], zo) <= 1e-8
         if it_max:
             assert oracle.kkt_residual(inst, zs[i], bs[i]) <= eval_gate(inst, zs[i], bs[i])
+
+
+def test_noise_limited_uneven_instances_reach_the_target():
+    """Instances of the uneven batch whose plain float64 residual evaluation is
+    limited by its own rounding (nx >= 50, nu <= 4, Sigma up to 1e6: rows cancel
+    by six orders of magnitude, float64 readings scatter around 5e-11 - 1.7e-10
+    while the exact residual of the refined solution is ~2e-11).  Once a
+    correction stalls, the device evaluates their rows compensated, so they
+    reach the target, and the oracle's accurate evaluation agrees."""
+    batch = inputs.make_batch("uneven4096", [31, 586, 1795, 2456, 61, 79, 156, 384])
+    s, z, b, _, _ = _solve(batch, "fp32_refine", 10)
+    assert (s.instance_status() == 0).all()
+    st = s.stats()
+    assert st["max_rel_residual"] <= REFINE_TARGET
+    for inst, zi, bi in zip(batch.instances, split_instances(batch, z[0]), split_instances(batch, b[0])):
+        res, res64 = oracle.kkt_residual(inst, zi, bi), oracle.kkt_residual_fp64(inst, zi, bi)
+        print("N %d nx %d nu %d: residual %.3e (one float64 evaluation %.3e)" % (inst.N, inst.nx, inst.nu, res, res64))
+        assert res <= GATE
