@@ -78,7 +78,8 @@ WORKLOADS = {
     "single_n32_nx8_nu4": dict(methods=["fp64", "fp64_refine"], graph=True, adjoint=False, tune_segments=True),
     "long_n4096_nx32_nu16": dict(methods=["fp32_refine", "fp64", "fp64_refine"], graph=True, adjoint=False,
                                  tune_segments=True),
-    "uneven4096": dict(methods=["fp32_refine", "fp64_refine"], graph=True, adjoint=False, tune_segments=True),
+    "uneven4096": dict(methods=["fp32_refine", "fp64_refine"], graph=True, adjoint=False, tune_segments=True,
+                       steps=40),
     "adjoint512_n128_nx24_nu8": dict(methods=["fp64_refine", "fp64_refine_recompute"], graph=True, adjoint=True,
                                      tune_segments=True),
     "massspring150_M18_N96": dict(methods=["fp32_refine", "fp64_refine", "fp64_ir32"], graph=True, adjoint=False,
@@ -121,7 +122,8 @@ def tuned_solver(torch, cyq, batch, data, b, method, tune_segments, P=None):
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=0,
+                   help="timed steps (default: the workload's, about a minute of timed work)")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="cyq", choices=["cyq", "reference"])
     p.add_argument("--workload", default=WORKLOAD, choices=sorted(inputs.CONFIGS))
@@ -562,12 +564,14 @@ def run_method(torch, cyq, batch, data, b, x0, method, steps, warmup, dist, grap
             worst = max(worst, float(rel.max().item()))
         st["max_rel_residual"] = worst
     segments = s.segments
+    esc_seg = s.escalation_segments() if precision == "fp32_refine" else None
     wbytes = s.workspace_bytes
     s.close()
     return dict(total_ms=total_ms, factor_ms=float(np.mean(factor_ms)), solve_ms=float(np.mean(solve_ms)),
                 status_ok=bool((status == 0).all()), stats=st, segments=segments,
                 launches_per_step=launches_factor + launches_solve, P=P, shapes=shapes, phase=phase,
-                path=path, workspace_bytes=wbytes)
+                path=path, workspace_bytes=wbytes,
+                escalation_segments=None if esc_seg is None else [int(esc_seg.min()), int(esc_seg.max())])
 
 
 def run_e2e(torch, cyq, batch, method, steps, warmup, data, b, P=None, adjoint=False):
@@ -717,6 +721,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     cfg = inputs.CONFIGS[args.workload]
     prof = dict(WORKLOADS[args.workload])
+    if args.steps <= 0:
+        args.steps = prof.get("steps", 200)
     if args.graph >= 0:
         prof["graph"] = bool(args.graph)
     nominal = lambda key: cfg[key] if not isinstance(cfg[key], tuple) else "U%s" % (cfg[key],)
@@ -867,7 +873,8 @@ def main():
                        "segments_per_ocp": [int(r["segments"].min()), int(r["segments"].max())],
                        "segments_tuned": r["P"] is not None,
                        "threads_per_item": r["shapes"], "factor_path": r["path"],
-                       "workspace_bytes": r["workspace_bytes"]}
+                       "workspace_bytes": r["workspace_bytes"],
+                       "escalation_segments_per_ocp": r["escalation_segments"]}
         if rl is not None:
             variants[m]["factor_gflops"] = rl["factor"]["algorithmic_flops"] / (r["factor_ms"] / 1e3) / 1e9
             variants[m]["rooflines"] = {k: {kk: v[kk] for kk in ("bound", "achieved", "unit", "frac", "ms")}

@@ -416,6 +416,17 @@ cyq_status cyq_set_factor_path(cyq_handle h, int32_t one_warp_per_item);
 cyq_status cyq_get_factor_path(cyq_handle h, int32_t *one_warp_per_item, int64_t *warp_items);
 
 /*
+ * Float32 mode: segments per instance of the float64 escalation plan (host
+ * array [batch]).  Instances of 48 or more stages whose float64 stage blocks
+ * with the A^cl propagation fit in shared memory get up to 8 segments there
+ * (halved runs of at least 24 stages), so the float64 factor of an escalated
+ * long instance spreads over several SMs; 0 everywhere when the escalation
+ * runs on the handle's own plan (other precisions, recompute mode, short
+ * horizons).  Errors: INVALID_ARG (NULL).
+ */
+cyq_status cyq_get_escalation_segments(cyq_handle h, int32_t *host_P);
+
+/*
  * Newton system of the augmented Lagrangian inner problem (Sec. 5, eqs.
  * ocp-al, ocp-al-funcs, qpalm-ocp-hessians, newton-sys-with-x0, elim-x0).
  *

@@ -123,6 +123,10 @@ struct cyq_handle_s {
     Chunk *d_chunks = nullptr;
     FactorSet fac;                // factor in the handle's precision
     FactorSet fac64;              // float64 factor for precision escalation (float32 mode only)
+    // float32 mode: the escalation's float64 factor and corrections on a plan of its own with
+    // more segments per long instance (the same instances, data, r, dz and status words), so
+    // the float64 critical path of a long instance spreads over several SMs; null: fac64
+    cyq_handle_s *esc_h = nullptr;
     FactorSet fac32;              // float32 copy of the float64 factor (float64 mode with float32 corrections)
     double *Mf = nullptr, *Mb = nullptr, *Kc = nullptr, *U = nullptr, *Y = nullptr;
     double *dF = nullptr, *dB = nullptr, *lam = nullptr;
@@ -428,6 +432,21 @@ ResidArgs resid_args(cyq_handle h, const double *b, const double *z, double *r, 
     return a;
 }
 
+// The float64 factorization of the instances with skip[i] == 0 for the precision
+// escalation (a failed float32 pivot is cleared first): on the escalation plan
+// (more segments per long instance) or fac64.
+cyq_status run_escalation_factor(cyq_handle h, const int *skip, cudaStream_t st) {
+    CYQ_CUDA(launch_clear_not_pd(h->batch, skip, h->status, st));
+    ++h->launches;
+    if (!h->esc_h) return run_factor(h, h->fac64, skip, st);
+    cyq_handle e = h->esc_h;
+    e->data = h->data;
+    const long long l0 = e->launches;
+    const cyq_status s = run_factor(e, e->fac, skip, st);
+    h->launches += e->launches - l0;
+    return s;
+}
+
 // Solve + float64 iterative refinement on all right-hand sides at once:
 //   z = K~^{-1} b;  repeat: r = b - K z (float64), stop per instance once
 //   every ||r|| / ||b|| plus twice the rounding bound of its evaluation is
@@ -488,7 +507,7 @@ cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, int nrhs,
                                                h->it_max - kPredict, st));
             CYQ_CUDA(cudaEventRecord(h->ev_fork, st));
             CYQ_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-            s = run_factor(h, h->fac64, h->esc, h->side);
+            s = run_escalation_factor(h, h->esc, h->side);
             if (s != CYQ_OK) return s;
             CYQ_CUDA(cudaEventRecord(h->ev_join, h->side));
             h->launches += 1;
@@ -505,18 +524,21 @@ cyq_status run_refined_solve(cyq_handle h, const double *b, double *z, int nrhs,
         // the parked instances have theirs already, the others still above tol get it now)
         const bool refactor = !h->fac.fp64;
         if (refactor) {
-            s = run_factor(h, h->fac64, h->done, st);
+            s = run_escalation_factor(h, h->done, st);
             if (s != CYQ_OK) return s;
         }
         if (forked) {
             CYQ_CUDA(launch_unpark(B, h->done, st));
             ++h->launches;
         }
-        const FactorSet &f64 = refactor ? h->fac64 : h->fac;
+        cyq_handle ph = refactor && h->esc_h ? h->esc_h : h;   // the plan of the float64 factor
+        const FactorSet &f64 = refactor ? (h->esc_h ? h->esc_h->fac : h->fac64) : h->fac;
         for (int it = 0; it < h->esc_max; ++it) {
             ++step;
-            s = run_solve(h, f64, h->r, h->dz, nrhs, h->done, st, z);
+            const long long l0 = ph->launches;
+            s = run_solve(ph, f64, h->r, h->dz, nrhs, h->done, st, z);
             if (s != CYQ_OK) return s;
+            if (ph != h) h->launches += ph->launches - l0;
             CYQ_CUDA(evaluate(false));
         }
     }
@@ -559,8 +581,17 @@ struct CreateOpts {
     bool chunk = false;
     Inst base{};
     long long kkt_full = 0;
-    double *r = nullptr, *dz = nullptr;
+    double *r = nullptr, *dz = nullptr;   // shared refinement vectors (chunks, escalation plan)
+    int *status = nullptr;                // shared status words (escalation plan)
 };
+
+// Segments of an instance in the float64 escalation plan: halved stage runs of at
+// least 24 stages, at most 8 segments.
+int escalation_segments(int N) {
+    int P = 1;
+    while (P < 8 && N / (2 * P) >= 24) P *= 2;
+    return P;
+}
 
 cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *out) {
     if (!desc || !out) return CYQ_ERR_INVALID_ARG;
@@ -711,8 +742,8 @@ cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *ou
         // factor; used only when every item fits
         int smem_sm = 0;
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        const size_t half = (size_t)smem_sm / 2;
-        const size_t arena = std::min<size_t>((size_t)smem_optin, half > 2048 ? half - 2048 : 0);
+        const size_t part = (size_t)smem_sm / kSweepCtasPerSm;
+        const size_t arena = std::min<size_t>((size_t)smem_optin, part > 1536 ? (part - 1536) / 64 * 64 : 0);
         const int arena_floats = (int)(arena / 64 * 16);
         const size_t slot2 = (size_t)(arena_floats / 4) * 4, slot1 = (size_t)(arena_floats / 2) * 4,
                      slot0 = (size_t)arena_floats * 4;
@@ -744,7 +775,7 @@ cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *ou
                 tp.n[k] = off - tp.off[k];
             }
             tp.arena_floats = arena_floats;
-            const int grid = 2 * sms;
+            const int grid = kSweepCtasPerSm * sms;
             const double wsum = work[0] + work[1] + work[2];
             int gg[3] = {0, 0, 0};
             for (int k = 0; k < 2; ++k) {
@@ -761,14 +792,14 @@ cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *ou
     }
     if (h->precision == CYQ_FP32_REFINE) {
         // float32 factor: segments without A^cl (segment 0) whose padded blocks fit
-        // three rows per lane go to the one-warp-per-item launch, longest first,
-        // packed into CTA arenas (two CTAs per SM)
+        // three rows per lane go to the one-team-per-item launch, longest first,
+        // packed into CTA arenas (kFactorCtasPerSm CTAs per SM)
         int smem_sm = 0;
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        // two CTAs per SM: each takes its arena, its static shared memory and the 1 KB the
-        // system reserves per CTA
-        const size_t half = (size_t)smem_sm / 2;
-        const size_t arena = std::min<size_t>((size_t)smem_optin, half > 2048 ? half - 2048 : 0);
+        // each CTA takes its arena, its static shared memory and the 1 KB the system
+        // reserves per CTA
+        const size_t part = (size_t)smem_sm / kFactorCtasPerSm;
+        const size_t arena = std::min<size_t>((size_t)smem_optin, part > 1536 ? (part - 1536) / 64 * 64 : 0);
         struct Cand { Item it; double cost; size_t bytes; };
         std::vector<Cand> cand;
         for (Group &g : h->groups) {
@@ -809,7 +840,7 @@ cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *ou
         tp.arena_floats = arena_floats;
         // CTAs per configuration in proportion to the class's work (every CTA has four warps);
         // teams that run out of items continue with the smaller classes
-        const int grid = 2 * sms;
+        const int grid = kFactorCtasPerSm * sms;
         const double wsum = work[0] + work[1] + work[2];
         int g[3] = {0, 0, 0};
         for (int k = 0; k < 2; ++k) {
@@ -907,6 +938,11 @@ cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *ou
         ALLOC(h->d_ingest_chunks, h->ingest_chunks.size());
         if (!o.chunk) ALLOC(h->fac.Hf, (size_t)h->nHf);
     }
+    // float32 mode: a float64 escalation plan of its own where some instance gets more
+    // segments there (then no fac64 here; created at the end, fac64 again if that fails)
+    bool want_esc = false;
+    if (h->precision == CYQ_FP32_REFINE && !o.chunk && h->esc_max > 0)
+        for (const Inst &in : h->inst) want_esc |= escalation_segments(in.N) > in.P;
     // fac (the handle's factor) and, in float32 mode, fac64 (escalation), in float64
     // mode with float32 corrections, fac32 (float32 copy)
     for (int pass = 0; pass < (float_sweeps ? 2 : 1); ++pass) {
@@ -914,6 +950,7 @@ cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *ou
         fs.fp64 = pass == 0 ? fp64 : !fp64;
         const size_t el = fs.fp64 ? sizeof(double) : sizeof(float);
         if (o.chunk) continue;   // the chunk's stage factors live in the shared window
+        if (want_esc && &fs == &h->fac64) continue;
         char *p;
         ALLOC(p, (size_t)oL * el); fs.L = p;
         ALLOC(p, (size_t)oLB * el); fs.LB = p;
@@ -929,8 +966,9 @@ cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *ou
     ALLOC(h->dF, (size_t)oVec * h->max_nrhs);
     ALLOC(h->dB, (size_t)oVec * h->max_nrhs);
     ALLOC(h->lam, (size_t)oVec * h->max_nrhs);
-    ALLOC(h->status, (size_t)h->batch);
-    if (o.chunk) {
+    if (o.status) h->status = o.status;
+    else ALLOC(h->status, (size_t)h->batch);
+    if (o.r) {
         h->r = o.r;
         h->dz = o.dz;
     } else {
@@ -1004,6 +1042,49 @@ cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *ou
          (e = cudaMemcpy(h->d_ingest_chunks, h->ingest_chunks.data(), sizeof(IngestChunk) * h->ingest_chunks.size(),
                          cudaMemcpyHostToDevice))))
         return fail(e, "cudaMemcpy");
+    if (want_esc) {
+        // more segments only where the float64 stage blocks with the A^cl propagation still
+        // fit in shared memory: the widest instances first lose them until the plan is made
+        cyq_handle eh = nullptr;
+        std::vector<int32_t> Pe(h->batch);
+        for (int cap = 128; cap >= 16 && !eh; cap -= 16) {
+            bool any = false;
+            for (int i = 0; i < h->batch; ++i) {
+                const Inst &in = h->inst[i];
+                Pe[i] = in.nx + in.nu <= cap ? std::max(in.P, escalation_segments(in.N)) : in.P;
+                any |= Pe[i] > in.P;
+            }
+            if (!any) break;
+            cyq_desc d = *desc;
+            d.precision = CYQ_FP64;
+            d.P = 0;
+            d.P_per_instance = Pe.data();
+            d.it_max = 0;
+            d.esc_max = 0;
+            d.recompute_factors = 0;
+            d.early_escalation = 0;
+            d.certify = 0;
+            CreateOpts eo;
+            eo.r = h->r;
+            eo.dz = h->dz;
+            eo.status = h->status;
+            if (create_impl(&d, eo, &eh) != CYQ_OK) eh = nullptr;
+        }
+        if (eh) {
+            h->esc_h = eh;
+            h->esc_possible = true;
+        } else {   // the escalation on the handle's own plan
+            FactorSet &fs = h->fac64;
+            char *p[4] = {nullptr, nullptr, nullptr, nullptr};
+            const long long n[4] = {oL, oLB, oF, oDI};
+            for (int k = 0; k < 4; ++k)
+                if ((e = h->mem.alloc(&p[k], (size_t)n[k] * 8)) != cudaSuccess) return fail(e, "cudaMalloc");
+            fs.L = p[0];
+            fs.LB = p[1];
+            fs.F = p[2];
+            fs.DI = p[3];
+        }
+    }
     *out = h;
     return CYQ_OK;
 }
@@ -1144,6 +1225,7 @@ void cyq_destroy(cyq_handle h) {
     DeviceGuard guard(h->device);
     cudaDeviceSynchronize();
     for (cyq_handle sh : h->subs) cyq_destroy(sh);
+    if (h->esc_h) cyq_destroy(h->esc_h);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -1571,10 +1653,24 @@ cyq_status cyq_get_instance_status(cyq_handle h, int32_t *host_status, cyq_strea
     return CYQ_OK;
 }
 
+cyq_status cyq_get_escalation_segments(cyq_handle h, int32_t *host_P) {
+    if (!h || !host_P) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) {
+        for (size_t k = 0; k < h->subs.size(); ++k) {
+            const cyq_status st = cyq_get_escalation_segments(h->subs[k], host_P + h->sub_first[k]);
+            if (st != CYQ_OK) return st;
+        }
+        return CYQ_OK;
+    }
+    for (int i = 0; i < h->batch; ++i) host_P[i] = h->esc_h ? h->esc_h->inst[i].P : 0;
+    return CYQ_OK;
+}
+
 int64_t cyq_workspace_bytes(cyq_handle h) {
     if (!h) return -1;
     long long b = h->mem.bytes;
     for (cyq_handle sh : h->subs) b += cyq_workspace_bytes(sh);
+    if (h->esc_h) b += cyq_workspace_bytes(h->esc_h);
     return b;
 }
 

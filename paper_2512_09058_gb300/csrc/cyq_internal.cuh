@@ -423,6 +423,11 @@ cudaError_t launch_factor_segments(bool fp64, int team, int shape, size_t smem, 
 // of 32); teams take items from their class's counter, then from the classes
 // of smaller items.
 constexpr int kTeamCtaThreads = 128;
+// CTAs of the persistent float32 factor per SM (each with a third of the SM's shared memory)
+constexpr int kFactorCtasPerSm = 3;
+// CTAs of the persistent float32 sweeps per SM (deeper package rings matter more here
+// than a third CTA: measured on the uneven batch, 10.5 ms per correction with two, 20 with three)
+constexpr int kSweepCtasPerSm = 2;
 constexpr int kWarpMaxNp = 96;        // padded nu + nx
 constexpr int kWarpMaxNxp = 64;       // padded nx
 struct TeamPlanDev {
@@ -497,10 +502,11 @@ cudaError_t launch_residual_scale(const ResidArgs &a, int nrhs, cudaStream_t st)
 cudaError_t launch_certify(const Inst *inst, int batch, int nrhs, double *aa, const double *bb, const double *rel,
                            double *cert, int *done, double tol, cudaStream_t st);
 // done[i] = done_value once every right-hand side of instance i is at or below tol;
-// comp (optional): set to 1 where a residual above tol did not halve since the last step
+// comp (optional): set to 1 where a residual in (tol, 100 tol] stayed above 0.8 of the last step's
 cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, double *rel, int *done, double tol,
                                   int *steps, int step, bool keep_bb, int done_value, int *comp, cudaStream_t st);
 cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, cudaStream_t st);
+cudaError_t launch_clear_not_pd(int batch, const int *skip, int *status, cudaStream_t st);
 cudaError_t launch_predict_escalation(int batch, int nrhs, const double *rel0, const double *rel, int *done, int *esc,
                                       double tol, int k, int left, cudaStream_t st);
 cudaError_t launch_unpark(int batch, int *done, cudaStream_t st);

@@ -70,16 +70,17 @@ struct Team {
 }  // namespace
 
 // Geometry of one item (in floats).  Slot layout:
-//   dinv (np) | 4 x 4 block scratch (16) | H (np x np, column-major, ld np) | Hn (the next stage matrix,
-//   same layout) | BV (np x ldb: columns of [B A] of the next stage, then rows
-//   of V in place)
+//   dinv (np) | 4 x 4 block scratch (16) | H (np x np, column-major, ld np) |
+//   BV (np x ldb: columns of [B A] of the next stage, then rows of V in place)
+// (the next stage matrix is read from its ingested tile in global memory while
+// H^ is formed, so that three CTAs fit on an SM)
 // and at the end of the segment: the float64 coupling block (nx x nx) from
 // the start of H, L^{Q-1} (nxp x nxp, ld nxp) behind both H and that block.
 // The ingested stage matrices use the H layout (np x np per stage, lower
 // triangle).
 struct WarpGeom {
     int nx, nu, nux, nup, nxp, np, ldb;
-    int oD, oK, oH, oHn, oBV, oT, size;
+    int oD, oK, oH, oBV, oT, size;
     __host__ __device__ WarpGeom(int nx_, int nu_) {
         nx = nx_;
         nu = nu_;
@@ -91,8 +92,7 @@ struct WarpGeom {
         oD = 0;
         oK = np;
         oH = np + 16;                          // np is a multiple of 4: every tile starts 16-byte aligned
-        oHn = oH + np * np;
-        oBV = oHn + np * np;
+        oBV = oH + np * np;
         const int main_end = oBV + np * ldb;
         const int mfloats = 2 * nxp * nxp;     // float64 nx x nx block (ld nx) fits in 2 nxp^2 floats
         oT = oH + (np * np > mfloats ? np * np : mfloats);
@@ -130,9 +130,17 @@ __global__ void __launch_bounds__(256) k_ingest_f32(IngestArgs g) {
         const double *Su = d.Sig ? d.Sig + in.oSig + (long long)s * nux : nullptr;
         const double *Sx = d.Sig ? d.Sig + in.oSig + (long long)xq * nux + nu : nullptr;
         float *Ht = g.Hf + in.oHf + (long long)s * np * np;
-        for (int tq = 0; tq < np; ++tq) {
-            const bool padq = (tq >= nu && tq < nup) || tq >= nup + nx;
-            for (int tr = tq + lane; tr < np; tr += 32) {
+        // the tile column-major and flat over the lanes (several independent loads in
+        // flight per lane); entries above the diagonal are not written (never read)
+        int tq = 0, tr = lane;
+        while (tr >= np) {
+            tr -= np;
+            ++tq;
+        }
+#pragma unroll 4
+        for (int e = lane; e < np * np; e += 32) {
+            if (tr >= tq) {
+                const bool padq = (tq >= nu && tq < nup) || tq >= nup + nx;
                 const bool padr = (tr >= nu && tr < nup) || tr >= nup + nx;
                 float v;
                 if (padq || padr) {
@@ -147,7 +155,12 @@ __global__ void __launch_bounds__(256) k_ingest_f32(IngestArgs g) {
                     const double x = Q[i + j * nx];
                     v = (float)((i == j && Sx) ? x + Sx[i] : x);
                 }
-                Ht[tq * np + tr] = v;
+                Ht[e] = v;
+            }
+            tr += 32;
+            while (tr >= np) {
+                tr -= np;
+                ++tq;
             }
         }
         if (t > 0 && g.BAf) {
@@ -421,10 +434,13 @@ __device__ void team_form_V(float *BV, const float *H, const WarpGeom &G, const 
     }
 }
 
-// H^ = Hn + V V^T (lower triangle, tile indices; Hn is the next stage matrix)
-// on 4 x 4 tiles (block row bi >= block column bj) dealt out over the team.
+// H^ = Hn + V V^T (lower triangle, tile indices; Hn is the next stage matrix's
+// ingested tile in global memory, read at the start of each 4 x 4 tile so that
+// the loads overlap the products) on 4 x 4 tiles (block row bi >= block column
+// bj) dealt out over the team.
 template <int T, int NXP>
-__device__ void team_form_H(float *H, const float *Hn, const float *BV, const WarpGeom &G, const Team<T> &tm) {
+__device__ void team_form_H(float *H, const float *__restrict__ Hn, const float *BV, const WarpGeom &G,
+                            const Team<T> &tm) {
     const int nb = G.np >> 2, nxp = G.nxp, ldb = G.ldb, ld = G.np;
     const int ntiles = nb * (nb + 1) / 2;
     int bi, bj;
@@ -432,10 +448,15 @@ __device__ void team_form_H(float *H, const float *Hn, const float *BV, const Wa
     for (int e = tm.tid; e < ntiles; e += T, tri_advance(bi, bj, T)) {
         const float *r0 = BV + (4 * bi) * ldb, *c0 = BV + (4 * bj) * ldb;
         float a[4][4];
+        // column 4 bj + j, rows 4 bi .. 4 bi + 3 of Hn (16-byte aligned: np, ld are multiples of 4)
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) a[i][j] = 0.0f;
+        for (int j = 0; j < 4; ++j) {
+            const float4 h = __ldg(reinterpret_cast<const float4 *>(Hn + (4 * bj + j) * ld + 4 * bi));
+            a[0][j] = h.x;
+            a[1][j] = h.y;
+            a[2][j] = h.z;
+            a[3][j] = h.w;
+        }
 #pragma unroll
         for (int kc = 0; kc < NXP; kc += 4) {
             if (kc < nxp) {
@@ -458,18 +479,15 @@ __device__ void team_form_H(float *H, const float *Hn, const float *BV, const Wa
                     }
             }
         }
-        // column 4 bj + j, rows 4 bi .. 4 bi + 3
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int o = (4 * bj + j) * ld + 4 * bi;
             if (bi != bj) {
-                const float4 h = *reinterpret_cast<const float4 *>(Hn + o);
-                *reinterpret_cast<float4 *>(H + o) =
-                    make_float4(h.x + a[0][j], h.y + a[1][j], h.z + a[2][j], h.w + a[3][j]);
+                *reinterpret_cast<float4 *>(H + o) = make_float4(a[0][j], a[1][j], a[2][j], a[3][j]);
             } else {
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    if (i >= j) H[o + i] = Hn[o + i] + a[i][j];
+                    if (i >= j) H[o + i] = a[i][j];
             }
         }
     }
@@ -560,7 +578,7 @@ __device__ void team_factor_item(const FactorArgs &a, const Item wi, float *slot
     const int len = seg_len(c, N, P);
     const WarpGeom G(in.nx, in.nu);
     const int nx = G.nx, nu = G.nu, nux = G.nux, nup = G.nup, nxp = G.nxp, np = G.np, ld = G.np;
-    float *dinv = slot + G.oD, *H = slot + G.oH, *Hn = slot + G.oHn, *BV = slot + G.oBV;
+    float *dinv = slot + G.oD, *H = slot + G.oH, *BV = slot + G.oBV;
     float *dblk = slot + G.oK;   // 4 x 4 diagonal block of the Crout factorization
     float *Lg = reinterpret_cast<float *>(a.L) + in.oL;
     float *DIg = reinterpret_cast<float *>(a.DI) + in.oDI;
@@ -581,8 +599,7 @@ __device__ void team_factor_item(const FactorArgs &a, const Item wi, float *slot
         const bool last = t == len - 1;
         const int s2 = last ? 0 : seg_stage(c, t + 1, N, P);
         if (t > 0 && !last) {
-            // the next stage matrix and [B A] land while this stage is factored
-            fetch_tile_lower<T>(Hn, Hg + (long long)s2 * np * np, np, tm);
+            // the next stage's [B A] lands while this stage is factored
             fetch_BV<T>(BV, BAg + (long long)s2 * nx * nux, G, tm);
             cp_async_commit();
             cp_async_wait_one();   // (no older group is pending)
@@ -626,7 +643,6 @@ __device__ void team_factor_item(const FactorArgs &a, const Item wi, float *slot
             for (int e = tid; e < np * G.ldb; e += T) BV[e] = 0.0f;   // restore the zero padding
             tm.sync();
             if (!last) {
-                fetch_tile_lower<T>(Hn, Hg + (long long)s2 * np * np, np, tm);
                 fetch_BV<T>(BV, BAg + (long long)s2 * nx * nux, G, tm);
                 cp_async_commit();
             }
@@ -636,7 +652,7 @@ __device__ void team_factor_item(const FactorArgs &a, const Item wi, float *slot
             tm.sync();
             team_form_V<T, NXP>(BV, H, G, tm);
             tm.sync();
-            team_form_H<T, NXP>(H, Hn, BV, G, tm);
+            team_form_H<T, NXP>(H, Hg + (long long)s2 * np * np, BV, G, tm);
             tm.sync();
         } else {
             // close the segment: T = L^{Q-1}, its strict lower part (transposed) into the
@@ -719,7 +735,7 @@ __device__ void team_loop(const FactorArgs &a, const TeamPlanDev &plan, int cls,
 // once that class's counter is exhausted, re-forms its teams for the other
 // classes in turn (largest items first), so that no SM idles while items are
 // left.  Class c items run with teams of 128 >> c threads (c = 0, 1, 2).
-__global__ void __launch_bounds__(kTeamCtaThreads) k_factor_team(FactorArgs a, TeamPlanDev plan) {
+__global__ void __launch_bounds__(kTeamCtaThreads, kFactorCtasPerSm) k_factor_team(FactorArgs a, TeamPlanDev plan) {
     extern __shared__ __align__(16) unsigned char smem_all[];
     __shared__ int cmd[4];
     float *arena = reinterpret_cast<float *>(smem_all);

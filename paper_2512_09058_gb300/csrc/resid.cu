@@ -106,9 +106,11 @@ __global__ void k_resid_finalize(int batch, int nrhs, double *rr, double *bb, do
         const long long j = (long long)r * batch + i;
         const double rn = sqrt(rr[j]), bn = sqrt(bb[j]);
         const double v = bn > 0.0 ? rn / bn : rn;
-        // a correction that did not halve a residual above tol: the float64 evaluation's
-        // rounding (or a slow contraction) limits it; later evaluations are compensated
-        if (comp && step > 0 && !(v <= tol) && v > 0.5 * rel[j]) stalled = true;
+        // a correction that left a residual within a factor 100 above tol above 0.8 of the
+        // previous one: the float64 evaluation's rounding (or a very slow contraction) limits
+        // it; later evaluations of the instance are compensated (noise floors lie far below
+        // 100 tol otherwise)
+        if (comp && step > 0 && !(v <= tol) && v <= 100.0 * tol && v > 0.8 * rel[j]) stalled = true;
         if (rel) rel[j] = v;
         all = all && (v <= tol);
         rr[j] = 0.0;
@@ -173,6 +175,14 @@ __global__ void k_predict_escalation(int batch, int nrhs, const double *rel0, co
     }
     if (park) done[i] = 2;
     esc[i] = park ? 0 : 1;
+}
+
+// Instances about to be factored again in float64 (skip[i] == 0) lose a failed
+// float32 pivot (status NOT_PD); the float64 factorization sets it again if its
+// own pivot fails.
+__global__ void k_clear_not_pd(int batch, const int *skip, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < batch && !skip[i] && status[i] == ST_NOT_PD) status[i] = 0;
 }
 
 // Parked instances (done = 2) rejoin the refinement for the float64 corrections.
@@ -374,6 +384,11 @@ cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, d
 cudaError_t launch_predict_escalation(int batch, int nrhs, const double *rel0, const double *rel, int *done, int *esc,
                                       double tol, int k, int left, cudaStream_t st) {
     k_predict_escalation<<<(batch + 127) / 128, 128, 0, st>>>(batch, nrhs, rel0, rel, done, esc, tol, k, left);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear_not_pd(int batch, const int *skip, int *status, cudaStream_t st) {
+    k_clear_not_pd<<<(batch + 127) / 128, 128, 0, st>>>(batch, skip, status);
     return cudaGetLastError();
 }
 

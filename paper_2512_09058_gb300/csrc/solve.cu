@@ -766,7 +766,7 @@ __device__ void sweep_team_loop(const SolveArgs &a, const TeamPlanDev &plan, int
 }
 
 template <bool BACKWARD>
-__global__ void __launch_bounds__(kTeamCtaThreads) k_sweep_team(SolveArgs a, TeamPlanDev plan) {
+__global__ void __launch_bounds__(kTeamCtaThreads, kSweepCtasPerSm) k_sweep_team(SolveArgs a, TeamPlanDev plan) {
     extern __shared__ __align__(16) unsigned char smem_all[];
     __shared__ int cmd[4];
     const int first = (int)blockIdx.x < plan.g0 ? 0 : ((int)blockIdx.x < plan.g0 + plan.g1 ? 1 : 2);

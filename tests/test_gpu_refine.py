@@ -106,15 +106,25 @@ def test_float64_escalation_rescues_hard_instances():
 
 
 @pytest.mark.parametrize("early", [False, True])
-def test_float64_escalation_after_the_float32_budget_and_predicted_early(early):
+@pytest.mark.parametrize("long", [False, True])
+def test_float64_escalation_after_the_float32_budget_and_predicted_early(early, long):
     """Float32 corrections with float64 escalation: either after every float32
     correction, or predicted after two of them (the slow instances parked and
-    factored in float64 on a second stream while the others continue)."""
+    factored in float64 on a second stream while the others continue).  Long
+    horizons (N >= 48) escalate on a float64 plan of their own with several
+    segments per instance."""
     dims = [(30, 4, 24), (25, 5, 30), (16, 8, 8), (40, 3, 12), (20, 12, 4)]
+    if long:
+        dims = [(200, 4, 24), (97, 5, 30), (16, 8, 8), (64, 3, 12), (130, 12, 4), (48, 6, 20)]
     batch = ragged_batch(25, dims, sigma=(1e-7, 1e7))
     torch, cyq = require_gpu()
-    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision="fp32_refine", it_max=6, tol=REFINE_TARGET,
+    s = cyq.Solver(batch.N, batch.nx, batch.nu, precision="fp32_refine", P=1, it_max=6, tol=REFINE_TARGET,
                    early_escalation=early)
+    Pe = s.escalation_segments()
+    if long:   # a float64 plan of its own: up to 8 segments of >= 24 stages per long instance
+        assert list(Pe) == [8, 4, 1, 2, 4, 2], Pe
+    else:
+        assert (Pe == 0).all()
     data, _ = cyq.to_device(batch)
     s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
     b = oracle_rhs(batch)
