@@ -800,7 +800,7 @@ cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *ou
         // reserves per CTA
         const size_t part = (size_t)smem_sm / kFactorCtasPerSm;
         const size_t arena = std::min<size_t>((size_t)smem_optin, part > 1536 ? (part - 1536) / 64 * 64 : 0);
-        struct Cand { Item it; double cost; size_t bytes; };
+        struct Cand { Item it; double cost; size_t bytes; int np; };
         std::vector<Cand> cand;
         for (Group &g : h->groups) {
             g.rest_set = true;
@@ -812,7 +812,7 @@ cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *ou
                 if (it.seg == 0 && nup + nxp <= kWarpMaxNp && nxp <= kWarpMaxNxp && nup <= 32 && bytes <= arena) {
                     const double np = nup + nxp;
                     const double per = np * np * np / 6.0 + 0.5 * np * np * nxp + 0.5 * np * nxp * nxp;
-                    cand.push_back(Cand{it, seg_len(it.seg, in.N, in.P) * per, bytes});
+                    cand.push_back(Cand{it, seg_len(it.seg, in.N, in.P) * per, bytes, nup + nxp});
                 } else {
                     g.items_rest.push_back(it);
                 }
@@ -825,7 +825,8 @@ cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *ou
         std::vector<Item> cls[3];
         double work[3] = {0.0, 0.0, 0.0};
         for (const Cand &c : cand) {
-            const int k = c.bytes <= slot2 ? 2 : (c.bytes <= slot1 ? 1 : 0);
+            int k = c.bytes <= slot2 ? 2 : (c.bytes <= slot1 ? 1 : 0);
+            while (k > 0 && c.np > kTeamRows[k]) --k;   // the class's team must cover every row
             cls[k].push_back(c.it);
             work[k] += c.cost;
         }

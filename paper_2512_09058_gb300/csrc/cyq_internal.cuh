@@ -429,6 +429,9 @@ constexpr int kFactorCtasPerSm = 3;
 // than a third CTA: measured on the uneven batch, 10.5 ms per correction with two, 20 with three)
 constexpr int kSweepCtasPerSm = 2;
 constexpr int kWarpMaxNp = 96;        // padded nu + nx
+// rows a team of class c covers in the Crout factorization (threads x rows per thread:
+// 128 x 1, 64 x 2, 32 x 2)
+constexpr int kTeamRows[3] = {128, 128, 64};
 constexpr int kWarpMaxNxp = 64;       // padded nx
 struct TeamPlanDev {
     const Item *items = nullptr;      // class 0, 1, 2 items (each sorted longest first)

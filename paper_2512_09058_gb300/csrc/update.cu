@@ -19,7 +19,9 @@
 // besides its own new rows.  The rank carried from stage to stage grows by the
 // rows added on the way.
 //
-// Scope: instances with one segment (P = 1); the single coupling block
+// Stages before the first change in the order of the recursion keep their
+// factor and are not touched.  Scope: instances with one segment (P = 1); the
+// single coupling block
 // M = L^B L^B^T + (L^Q L^Q^T)^{-1} of Sec. 4.3 is rebuilt from the updated
 // factors and factored again (nx^3 / 2 flops), which is what the low-rank
 // Schur-complement update of Sec. 6.3 and the cyclic-reduction update of
@@ -172,17 +174,27 @@ __global__ void __launch_bounds__(32) k_update_factor(UpdateArgs u) {
     const long long rbase = in.oN * u.m_max;    // rows of this instance: [stage][m_max]
     const long long wbase = in.oNn * u.m_max;   // their entries: [stage][m_max][nu + nx]
     bool ok = true, rank_over = false;
+    bool lb_loaded = false;
     int mp = 0;   // columns carried from the previous stage (their Phi and signs)
     for (int t = 0; t < N; ++t) {
         const int s = seg_stage(0, t, N, 1);
+        // a stage without carried columns and without rows of its own keeps its factor
+        // (every stage before the first change in the order of the recursion)
+        if (mp == 0) {
+            bool any = false;
+            for (int r = 0; r < u.m_max; ++r) any |= u.delta[rbase + (long long)s * u.m_max + r] != 0.0;
+            if (!any) continue;
+        }
         // the stage factor and 1 / diag into the working tile
         for (int e = lane; e < n * n; e += 32) {
             const int b = e / n, a = e - b * n;
             if (a >= b) L[a + b * ld] = Lg[(long long)s * n * n + e];
         }
         for (int i = lane; i < n; i += 32) dinv[i] = DIg[(long long)s * n + i];
-        if (t == 0)
+        if (t == 0) {
             for (int e = lane; e < nx * nu; e += 32) LB[e] = LBg[(long long)s * nx * nu + e];
+            lb_loaded = true;
+        }
         // [B A] of this stage (the carried columns enter through it): float64 data
         if (t > 0 && mp > 0) {
             const double *B = u.data.B + in.oB + (long long)s * nx * nu;
@@ -246,6 +258,10 @@ __global__ void __launch_bounds__(32) k_update_factor(UpdateArgs u) {
             const T *LQ = L + nu + nu * ld;
             const T *dq = dinv + nu;
             T *Ti = W;   // nx x nx, ld nx (mcap >= nx is checked by the host)
+            if (!lb_loaded) {   // the first stage kept its factor: its L^B rows from the store
+                const int s0 = seg_stage(0, 0, N, 1);
+                for (int e = lane; e < nx * nu; e += 32) LB[e] = LBg[(long long)s0 * nx * nu + e];
+            }
             for (int cc = lane; cc < nx; cc += 32) {
                 for (int i = 0; i < cc; ++i) Ti[i + cc * nx] = T(0);
                 for (int i = cc; i < nx; ++i) {
