@@ -51,9 +51,10 @@ FP32_FMA_PER_CLK_SM = 128
 HBM_FALLBACK_GBS = 6800.0
 WORKLOAD = "uneven4096"
 # method -> (factor precision, refinement step budget).  Float64 refinement
-# converges in one step here; float32 needs ~5 at cond(K) ~ 1e11.
-METHODS = {"fp64": ("fp64", 0), "fp64_refine": ("fp64", 3), "fp32_refine": ("fp32_refine", 8),
-           "fp64_ir32": ("fp64_ir32", 3), "fp64_refine_recompute": ("fp64", 3)}
+# converges in one or two steps (a few more where the compensated residual rows
+# take over near the target); float32 needs ~5-8 at cond(K) ~ 1e11.
+METHODS = {"fp64": ("fp64", 0), "fp64_refine": ("fp64", 5), "fp32_refine": ("fp32_refine", 8),
+           "fp64_ir32": ("fp64_ir32", 3), "fp64_refine_recompute": ("fp64", 5)}
 # methods that keep the stage factors of one chunk of instances at a time and factor
 # every chunk again in each solve and adjoint: method -> chunks
 RECOMPUTE = {"fp64_refine_recompute": 4}
@@ -63,11 +64,19 @@ RECOMPUTE = {"fp64_refine_recompute": 4}
 # worst-case evaluation bound (cyq_desc.certify) lies above 1e-10 for many
 # instances of these workloads and cannot serve as the stop criterion
 REFINE_TOL = 5e-11
-# DRAM bytes (read + write) per step of the factor phase, from one ncu capture of
-# its current kernels (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
-# workload, factor precision and kernel; absent where no capture exists
+# DRAM bytes (read + write) per launch of a part of the step, from ncu captures
+# of its current kernels (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
+# workload, factor precision and the part's kernels; absent where no capture of
+# the current kernels exists.  Uneven batch: captured on its first 512 instances
+# (71,441 stages) and scaled by stages to the whole batch (551,381): every stage's
+# data, tile and factor moves once per launch, so the traffic grows in proportion.
+_UNEVEN_SCALE = 551381.0 / 71441.0
 NCU_TRAFFIC = {("batch1024_n64_nx12_nu4", "fp64_ir32", "k_factor_pairs<12, 4>"): 217.1e6 + 219.5e6,
-               ("batch1024_n64_nx12_nu4", "fp32_refine", "k_factor_segments<float>"): 217.0e6 + 88.5e6}
+               ("uneven4096", "fp32_refine", "k_ingest_f32 + k_factor_team + k_inv_R_f32"):
+                   (3701e6 + 2272e6 + 296.9e6) * _UNEVEN_SCALE,
+               ("uneven4096", "fp32_refine", "k_sweep_team<true> + k_cr_solve + k_sweep_team<false> (1 rhs)"):
+                   (1563e6 + 1592e6) * _UNEVEN_SCALE,
+               ("uneven4096", "fp32_refine", "k_residual (1 rhs) + k_resid_finalize"): 5054e6 * _UNEVEN_SCALE}
 # workload -> methods (headline: the first one that certifies every instance),
 # CUDA-graph replay, adjoint in the step, segment counts tuned by timing
 # (cyq_tune_segments); launch shapes are always tuned by timing (cyq_autotune)
@@ -849,14 +858,19 @@ def main():
         fac = roofline_of(kname, fl, dbytes + el * felems, r["factor_ms"], peaks["fp64" if f64 else "fp32"],
                           peaks["hbm"], "fp64" if f64 else "fp32", peaks, NCU_TRAFFIC.get(tkey))
         kk8 = 8.0 * batch.kkt_size
-        res = roofline_of("k_residual (1 rhs) + k_resid_finalize", 2.0 * residual_fma(batch), dbytes + 3 * kk8,
-                          r["phase"]["residual"], peaks["fp64"], peaks["hbm"], "fp64", peaks)
+        rname = "k_residual (1 rhs) + k_resid_finalize"   # the phase is timed on one right-hand side
+        res = roofline_of(rname, 2.0 * residual_fma(batch), dbytes + 3 * kk8,
+                          r["phase"]["residual"], peaks["fp64"], peaks["hbm"], "fp64", peaks,
+                          NCU_TRAFFIC.get((args.workload, prec, rname)))
         cel = 8 if prec == "fp64" else 4   # the correction's factor
         nux = np.asarray(batch.nx, np.int64) + np.asarray(batch.nu, np.int64)
         cfl = 2.0 * nrhs * float((np.asarray(batch.N, np.int64) * (2 * nux * nux + 2 * np.asarray(batch.nx) * nux)).sum())
-        cor = roofline_of("k_solve_backward + k_cr_solve + k_solve_forward (%d rhs)" % nrhs, cfl,
-                          2.0 * cel * felems + nrhs * 4 * kk8, r["phase"]["correction"],
-                          peaks["fp64" if cel == 8 else "fp32"], peaks["hbm"], "fp64" if cel == 8 else "fp32", peaks)
+        team = cel == 4 and (r.get("path") or {}).get("sweep_persistent", False)
+        cname = ("k_sweep_team<true> + k_cr_solve + k_sweep_team<false> (%d rhs)" if team else
+                 "k_solve_backward + k_cr_solve + k_solve_forward (%d rhs)") % nrhs
+        cor = roofline_of(cname, cfl, 2.0 * cel * felems + nrhs * 4 * kk8, r["phase"]["correction"],
+                          peaks["fp64" if cel == 8 else "fp32"], peaks["hbm"], "fp64" if cel == 8 else "fp32", peaks,
+                          NCU_TRAFFIC.get((args.workload, prec, cname)))
         return {"factor": fac, "residual": res, "correction": cor}
 
     variants = {}

@@ -415,6 +415,12 @@ cyq_status cyq_set_factor_path(cyq_handle h, int32_t one_warp_per_item);
  * launch covers (0 for float64 handles); either pointer may be NULL. */
 cyq_status cyq_get_factor_path(cyq_handle h, int32_t *one_warp_per_item, int64_t *warp_items);
 
+/* The float32 sweep path in use: 1 if each sweep of a float32 solve is one
+ * persistent launch over the whole batch (k_sweep_team), 0 for the per-class
+ * launches, and the number of work items the persistent launch covers (0 if it
+ * has none); either pointer may be NULL.  Errors: INVALID_ARG (NULL handle). */
+cyq_status cyq_get_sweep_path(cyq_handle h, int32_t *persistent, int64_t *items);
+
 /*
  * Float32 mode: segments per instance of the float64 escalation plan (host
  * array [batch]).  Instances of 48 or more stages whose float64 stage blocks

@@ -130,38 +130,55 @@ __global__ void __launch_bounds__(256) k_ingest_f32(IngestArgs g) {
         const double *Su = d.Sig ? d.Sig + in.oSig + (long long)s * nux : nullptr;
         const double *Sx = d.Sig ? d.Sig + in.oSig + (long long)xq * nux + nu : nullptr;
         float *Ht = g.Hf + in.oHf + (long long)s * np * np;
-        // the tile column-major and flat over the lanes (several independent loads in
-        // flight per lane); entries above the diagonal are not written (never read)
+        // the tile column-major and flat over the lanes, four entries per lane at a time:
+        // their sources first, then all loads, then the conversions (eight loads in flight
+        // per lane); entries above the diagonal are not written (never read)
         int tq = 0, tr = lane;
         while (tr >= np) {
             tr -= np;
             ++tq;
         }
-#pragma unroll 4
-        for (int e = lane; e < np * np; e += 32) {
-            if (tr >= tq) {
-                const bool padq = (tq >= nu && tq < nup) || tq >= nup + nx;
-                const bool padr = (tr >= nu && tr < nup) || tr >= nup + nx;
-                float v;
-                if (padq || padr) {
-                    v = tr == tq ? 1.0f : 0.0f;
-                } else if (tr < nu) {
-                    const double x = R[tr + tq * nu];
-                    v = (float)((tr == tq && Su) ? x + Su[tr] : x);
-                } else if (tq < nu) {
-                    v = S ? (float)S[tq + (tr - nup) * nu] : 0.0f;
-                } else {
-                    const int i = tr - nup, j = tq - nup;
-                    const double x = Q[i + j * nx];
-                    v = (float)((i == j && Sx) ? x + Sx[i] : x);
+        for (int e0 = lane; e0 < np * np; e0 += 128) {
+            const double *src[4], *sga[4];
+            float cv[4];
+            bool st[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                st[u] = e0 + 32 * u < np * np && tr >= tq;
+                src[u] = nullptr;
+                sga[u] = nullptr;
+                cv[u] = 0.0f;
+                if (st[u]) {
+                    const bool padq = (tq >= nu && tq < nup) || tq >= nup + nx;
+                    const bool padr = (tr >= nu && tr < nup) || tr >= nup + nx;
+                    if (padq || padr) {
+                        cv[u] = tr == tq ? 1.0f : 0.0f;
+                    } else if (tr < nu) {
+                        src[u] = R + tr + tq * nu;
+                        if (tr == tq && Su) sga[u] = Su + tr;
+                    } else if (tq < nu) {
+                        if (S) src[u] = S + tq + (tr - nup) * nu;
+                    } else {
+                        const int i = tr - nup, j = tq - nup;
+                        src[u] = Q + i + j * nx;
+                        if (i == j && Sx) sga[u] = Sx + i;
+                    }
                 }
-                Ht[e] = v;
+                tr += 32;
+                while (tr >= np) {
+                    tr -= np;
+                    ++tq;
+                }
             }
-            tr += 32;
-            while (tr >= np) {
-                tr -= np;
-                ++tq;
+            double x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                x[u] = src[u] ? __ldg(src[u]) : 0.0;
+                y[u] = sga[u] ? __ldg(sga[u]) : 0.0;
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (st[u]) Ht[e0 + 32 * u] = src[u] ? (float)(x[u] + y[u]) : cv[u];
         }
         if (t > 0 && g.BAf) {
             // [B A] of the stages whose predecessor propagates into them (all but the first)
@@ -169,7 +186,8 @@ __global__ void __launch_bounds__(256) k_ingest_f32(IngestArgs g) {
             const double *A = d.A + in.oA + (long long)s * nx * nx;
             float *o = g.BAf + in.oBA + (long long)s * nx * nux;
             const int nb = nx * nu, n = nx * nux;
-            for (int e = lane; e < n; e += 32) o[e] = (float)(e < nb ? B[e] : A[e - nb]);
+#pragma unroll 4
+            for (int e = lane; e < n; e += 32) o[e] = (float)(e < nb ? __ldg(B + e) : __ldg(A + e - nb));
         }
     }
 }

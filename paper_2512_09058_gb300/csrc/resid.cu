@@ -14,9 +14,12 @@
 namespace cyq {
 
 
-// Rows are processed one kind at a time (u rows, then x rows, then lambda rows)
+// Rows are processed one kind at a time (u rows, then lambda rows, then x rows)
 // so that a warp runs one code path: a divergent FP64 instruction costs a
-// full warp slot per path.  Up to RG right-hand sides share every matrix load.
+// full warp slot per path.  The order keeps the second read of B_k (u and lambda
+// rows) and of A_k (lambda rows of record k, x rows of record k - 1) close to
+// the first, while the chunk's blocks are still in L2.  Up to RG right-hand
+// sides share every matrix load.
 constexpr int RG = 4;
 
 // Accumulation of one residual row, b - sum_j m_j z_j, by mode:
