@@ -423,9 +423,9 @@ cyq_status cyq_get_sweep_path(cyq_handle h, int32_t *persistent, int64_t *items)
 
 /*
  * Float32 mode: segments per instance of the float64 escalation plan (host
- * array [batch]).  Instances of 48 or more stages whose float64 stage blocks
- * with the A^cl propagation fit in shared memory get up to 8 segments there
- * (halved runs of at least 24 stages), so the float64 factor of an escalated
+ * array [batch]).  Instances of 24 or more stages whose float64 stage blocks
+ * with the A^cl propagation fit in shared memory get up to 16 segments there
+ * (halved runs of at least 12 stages), so the float64 factor of an escalated
  * long instance spreads over several SMs; 0 everywhere when the escalation
  * runs on the handle's own plan (other precisions, recompute mode, short
  * horizons).  Errors: INVALID_ARG (NULL).

@@ -199,10 +199,11 @@ struct DeviceGuard {
 constexpr int kUpdateColumns = 32;
 
 // Records per residual work item: small enough that the last refinement steps,
-// with few instances left, still spread over many SMs (16 for one right-hand
-// side: uneven batch residual 9.6 -> 8.2 ms; 32 where several right-hand sides
-// share every matrix load and the CTAs already carry more work).
-constexpr int kResidChunk1 = 16, kResidChunkN = 32;
+// with few instances left, still spread over many SMs (8 for one right-hand
+// side: uneven batch step 192.5 ms with 32, 188.0 with 16, 184.3 with 8; 32
+// where several right-hand sides share every matrix load and the CTAs already
+// carry more work).
+constexpr int kResidChunk1 = 8, kResidChunkN = 32;
 
 int choose_team(int nx, int nu) {
     const int nux = nx + nu;
@@ -588,10 +589,10 @@ struct CreateOpts {
 };
 
 // Segments of an instance in the float64 escalation plan: halved stage runs of at
-// least 24 stages, at most 8 segments.
+// least 12 stages, at most 16 segments.
 int escalation_segments(int N) {
     int P = 1;
-    while (P < 8 && N / (2 * P) >= 24) P *= 2;
+    while (P < 16 && N / (2 * P) >= 12) P *= 2;
     return P;
 }
 

@@ -111,8 +111,8 @@ def test_float64_escalation_after_the_float32_budget_and_predicted_early(early, 
     """Float32 corrections with float64 escalation: either after every float32
     correction, or predicted after two of them (the slow instances parked and
     factored in float64 on a second stream while the others continue).  Long
-    horizons (N >= 48) escalate on a float64 plan of their own with several
-    segments per instance."""
+    horizons escalate on a float64 plan of their own with several segments
+    per instance (halved runs of at least 12 stages)."""
     dims = [(30, 4, 24), (25, 5, 30), (16, 8, 8), (40, 3, 12), (20, 12, 4)]
     if long:
         dims = [(200, 4, 24), (97, 5, 30), (16, 8, 8), (64, 3, 12), (130, 12, 4), (48, 6, 20)]
@@ -121,10 +121,11 @@ def test_float64_escalation_after_the_float32_budget_and_predicted_early(early, 
     s = cyq.Solver(batch.N, batch.nx, batch.nu, precision="fp32_refine", P=1, it_max=6, tol=REFINE_TARGET,
                    early_escalation=early)
     Pe = s.escalation_segments()
-    if long:   # a float64 plan of its own: up to 8 segments of >= 24 stages per long instance
-        assert list(Pe) == [8, 4, 1, 2, 4, 2], Pe
+    # a float64 plan of its own: up to 16 segments of >= 12 stages per instance
+    if long:
+        assert list(Pe) == [16, 8, 1, 4, 8, 4], Pe
     else:
-        assert (Pe == 0).all()
+        assert list(Pe) == [2, 2, 1, 2, 1], Pe
     data, _ = cyq.to_device(batch)
     s.factor(data["Q"], data["R"], data["S"], data["A"], data["B"], data["Sigma"])
     b = oracle_rhs(batch)
