@@ -102,13 +102,21 @@ WORKLOADS = {
 # Fixed segment count / launch shapes (--segments, --launch-shapes) in place of
 # the timing tuners, e.g. to reproduce a tuned configuration under a profiler,
 # whose serialised launches distort the tuners' timings.
-FIXED = {"P": 0, "shapes": None, "pcr_tail": 0, "early_esc": False}
+FIXED = {"P": 0, "shapes": None, "pcr_tail": 0, "early_esc": False, "it_max": -1}
+
+
+def method_budget(method):
+    """(factor precision, refinement step budget) of a method (--it-max overrides the budget)."""
+    precision, it_max = METHODS[method]
+    if FIXED["it_max"] >= 0 and it_max > 0:
+        it_max = FIXED["it_max"]
+    return precision, it_max
 
 
 def tuned_solver(torch, cyq, batch, data, b, method, tune_segments, P=None):
     """A solver for `method` with timed-autotuned segment counts (when asked, or
     the given P) and launch shapes; returns (solver, P).  Untimed setup."""
-    precision, it_max = METHODS[method]
+    precision, it_max = method_budget(method)
     nrhs = len(batch.rhs)
     if P is None and FIXED["P"] > 0:
         P = np.minimum(np.asarray(batch.N), FIXED["P"]).astype(np.int32)
@@ -147,6 +155,8 @@ def parse():
                    help="levels of the coupling solve done by parallel cyclic reduction (0: plain)")
     p.add_argument("--update-sweep", action="store_true",
                    help="also time factorization updates against refactorization (one-segment workloads)")
+    p.add_argument("--it-max", type=int, default=-1,
+                   help="refinement step budget of the refined methods instead of theirs")
     p.add_argument("--early-escalation", action="store_true",
                    help="float32 refinement: predicted float64 escalation after two corrections")
     p.add_argument("--launch-shapes", default="",
@@ -485,7 +495,7 @@ def run_method(torch, cyq, batch, data, b, x0, method, steps, warmup, dist, grap
     the step time is the sum of the per-step event intervals.  With `newton`
     (newton_setup's context) the factor part starts with the Newton-system
     assembly and the solve part with building its right-hand side."""
-    precision, it_max = METHODS[method]
+    precision, it_max = method_budget(method)
     nrhs = len(batch.rhs)
     s, P = tuned_solver(torch, cyq, batch, data, b, method, tune_segments)
     shapes = s.launch_shapes(nrhs=nrhs)
@@ -625,7 +635,7 @@ def run_e2e(torch, cyq, batch, method, steps, warmup, data, b, P=None, adjoint=F
     the data and (q, r, c, x_init) from pinned host memory, builds the KKT
     right-hand sides, factors, solves and copies z back to pinned memory.  The
     solver is tuned like the device-resident one (same segment counts)."""
-    precision, it_max = METHODS[method]
+    precision, it_max = method_budget(method)
     nrhs = len(batch.rhs)
     s, _ = tuned_solver(torch, cyq, batch, data, b, method, False, P=P)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -760,6 +770,7 @@ def main():
     FIXED["P"] = args.segments
     FIXED["pcr_tail"] = args.pcr_tail
     FIXED["early_esc"] = args.early_escalation
+    FIXED["it_max"] = args.it_max
     if args.launch_shapes:
         FIXED["shapes"] = tuple(int(v) for v in args.launch_shapes.split(","))
     rank = int(os.environ.get("RANK", "0"))
