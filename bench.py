@@ -76,7 +76,7 @@ NCU_TRAFFIC = {("batch1024_n64_nx12_nu4", "fp64_ir32", "k_factor_pairs<12, 4>"):
                    (3701e6 + 2272e6 + 296.9e6) * _UNEVEN_SCALE,
                ("uneven4096", "fp32_refine", "k_sweep_team<true> + k_cr_solve + k_sweep_team<false> (1 rhs)"):
                    (1563e6 + 1592e6) * _UNEVEN_SCALE,
-               ("uneven4096", "fp32_refine", "k_residual (1 rhs) + k_resid_finalize"): 5054e6 * _UNEVEN_SCALE}
+               ("uneven4096", "fp32_refine", "k_residual (1 rhs) + k_resid_finalize"): 4711e6 * _UNEVEN_SCALE}
 # workload -> methods (headline: the first one that certifies every instance),
 # CUDA-graph replay, adjoint in the step, segment counts tuned by timing
 # (cyq_tune_segments); launch shapes are always tuned by timing (cyq_autotune)
@@ -380,9 +380,9 @@ def time_oracle(batch, nrhs, budget_s=2.0, max_instances=None):
 
 def _oracle_proc(name, indices, nrhs, q_in, q_out):
     """One host core, pinned to its instances: regenerates them from the seeded
-    generator (untimed, once, at most 64 of them, cycled) and, for every budget
-    it receives, solves them with the oracle until that many seconds of solving;
-    answers (count, seconds)."""
+    generator (untimed, at most 64 of them, all before the first timed step) and,
+    for every budget it receives, solves them in turn, cycling, until that many
+    seconds of solving; answers (count, seconds)."""
     import oracle   # CPU-baseline / reference leg only
     cache = []
     pos = 0
@@ -390,6 +390,12 @@ def _oracle_proc(name, indices, nrhs, q_in, q_out):
         budget = q_in.get()
         if budget is None:
             return
+        if budget < 0:   # generate every instance first, so that no step times a neighbour's generation
+            for k in range(len(cache), len(indices)):
+                x = inputs.make_batch(name, [indices[k]]).instances[0]
+                cache.append((x, np.stack([oracle.build_rhs(x, *x.rhs[j]) for j in range(nrhs)])))
+            q_out.put((0, 0.0))
+            continue
         done, el = 0, 0.0
         while el < budget:
             k = pos % len(indices)
@@ -415,14 +421,30 @@ class OraclePool:
         ctx = multiprocessing.get_context("spawn")
         workers = workers or os.cpu_count() or 1
         self.procs, self.qin, self.qout = [], [], []
-        for w in range(min(workers, n_instances)):
-            qi, qo = ctx.Queue(), ctx.Queue()
-            idx = list(range(w, n_instances, workers))[:64]
-            p = ctx.Process(target=_oracle_proc, args=(name, idx, nrhs, qi, qo), daemon=True)
-            p.start()
-            self.procs.append(p)
-            self.qin.append(qi)
-            self.qout.append(qo)
+        # one thread per process: the oracle is single-threaded, and library threads of the
+        # generator would compete with the other processes' timed solves
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            for w in range(min(workers, n_instances)):
+                qi, qo = ctx.Queue(), ctx.Queue()
+                idx = list(range(w, n_instances, workers))[:64]
+                p = ctx.Process(target=_oracle_proc, args=(name, idx, nrhs, qi, qo), daemon=True)
+                p.start()
+                self.procs.append(p)
+                self.qin.append(qi)
+                self.qout.append(qo)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        for q in self.qin:   # every instance generated before any timed step
+            q.put(-1.0)
+        for q in self.qout:
+            q.get()
 
     def step(self, budget_s):
         """(OCP/s summed over the concurrent processes, instances solved, cores)."""
