@@ -204,6 +204,9 @@ constexpr int kUpdateColumns = 32;
 // where several right-hand sides share every matrix load and the CTAs already
 // carry more work).
 constexpr int kResidChunk1 = 8, kResidChunkN = 32;
+// Stages per warp of the float32 ingest and of the L^{R-1} pass: short runs keep many
+// warps in flight on the memory-bound ingest and balance the uneven instances.
+constexpr int kIngestChunk = 4;
 
 int choose_team(int nx, int nu) {
     const int nux = nx + nu;
@@ -864,7 +867,8 @@ cyq_status create_impl(const cyq_desc *desc, const CreateOpts &o, cyq_handle *ou
             in.oHf = oHf;
             oHf += (long long)in.N * (long long)warp_stage_floats(in.nx, in.nu);
             const int len = seg_len(it.seg, in.N, in.P);
-            for (int t0 = 0; t0 < len; t0 += 16) h->ingest_chunks.push_back(IngestChunk{it.inst, t0, std::min(len, t0 + 16)});
+            for (int t0 = 0; t0 < len; t0 += kIngestChunk)
+                h->ingest_chunks.push_back(IngestChunk{it.inst, t0, std::min(len, t0 + kIngestChunk)});
         }
         h->nHf = oHf;
         h->warp_arena = arena;
