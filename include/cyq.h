@@ -415,6 +415,14 @@ cyq_status cyq_set_factor_path(cyq_handle h, int32_t one_warp_per_item);
  * launch covers (0 for float64 handles); either pointer may be NULL. */
 cyq_status cyq_get_factor_path(cyq_handle h, int32_t *one_warp_per_item, int64_t *warp_items);
 
+/* Selects the float32 sweep path: 1 = each sweep of a float32 solve is one
+ * persistent launch over the whole batch (k_sweep_team), 0 = one launch per
+ * size class.  Both run the same per-item code with the same order of
+ * operations, so they give the same solution bit for bit; the factor is kept.
+ * Errors: INVALID_ARG (NULL handle, a value other than 0 / 1, or 1 for a batch
+ * without a persistent sweep plan). */
+cyq_status cyq_set_sweep_path(cyq_handle h, int32_t persistent);
+
 /* The float32 sweep path in use: 1 if each sweep of a float32 solve is one
  * persistent launch over the whole batch (k_sweep_team), 0 for the per-class
  * launches, and the number of work items the persistent launch covers (0 if it

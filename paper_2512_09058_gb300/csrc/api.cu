@@ -1499,6 +1499,20 @@ cyq_status cyq_set_factor_path(cyq_handle h, int32_t one_warp_per_item) {
     return CYQ_OK;
 }
 
+cyq_status cyq_set_sweep_path(cyq_handle h, int32_t persistent) {
+    if (!h || persistent < 0 || persistent > 1) return CYQ_ERR_INVALID_ARG;
+    if (!h->subs.empty()) {
+        for (cyq_handle sh : h->subs) {
+            const cyq_status st = cyq_set_sweep_path(sh, persistent);
+            if (st != CYQ_OK) return st;
+        }
+        return CYQ_OK;
+    }
+    if (persistent == 1 && h->sweep_items.empty()) return CYQ_ERR_INVALID_ARG;
+    h->sweep_on = persistent == 1;
+    return CYQ_OK;
+}
+
 cyq_status cyq_get_sweep_path(cyq_handle h, int32_t *persistent, int64_t *items) {
     if (!h) return CYQ_ERR_INVALID_ARG;
     if (!h->subs.empty()) return cyq_get_sweep_path(h->subs[0], persistent, items);

@@ -29,7 +29,7 @@ EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rh
            "cyq_factor_solve_noalloc", "cyq_autotune", "cyq_get_launch_shapes", "cyq_tune_segments",
            "cyq_set_launch_shapes", "cyq_get_stage_factor", "cyq_assemble_newton", "cyq_set_pcr_tail",
            "cyq_get_pcr_tail", "cyq_pivot_eval", "cyq_set_factor_path", "cyq_get_factor_path", "cyq_apply_factor", "cyq_update_factor",
-           "cyq_get_escalation_segments", "cyq_get_sweep_path"]
+           "cyq_get_escalation_segments", "cyq_get_sweep_path", "cyq_set_sweep_path"]
 
 
 class CyqError(RuntimeError):
@@ -115,9 +115,10 @@ def load(path: str = LIB_PATH):
     L.cyq_get_factor_path.argtypes = [vp, pi32, ctypes.POINTER(i64)]
     L.cyq_get_escalation_segments.argtypes = [vp, pi32]
     L.cyq_get_sweep_path.argtypes = [vp, pi32, ctypes.POINTER(i64)]
+    L.cyq_set_sweep_path.argtypes = [vp, i32]
     for name in ["cyq_create", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual", "cyq_solve_adjoint",
                  "cyq_get_instance_status", "cyq_get_stats", "cyq_get_segments", "cyq_autotune",
-                 "cyq_get_escalation_segments", "cyq_get_sweep_path",
+                 "cyq_get_escalation_segments", "cyq_get_sweep_path", "cyq_set_sweep_path",
                  "cyq_get_launch_shapes", "cyq_tune_segments", "cyq_set_launch_shapes",
                  "cyq_get_stage_factor", "cyq_pivot_eval", "cyq_set_factor_path", "cyq_get_factor_path",
                  "cyq_apply_factor", "cyq_update_factor"]:
@@ -319,6 +320,10 @@ class Solver:
         _check(_lib.cyq_get_sweep_path(self._h, ctypes.byref(p), ctypes.byref(m)))
         return {"one_warp_per_item": bool(on.value), "warp_items": int(n.value), "sweep_persistent": bool(p.value),
                 "sweep_items": int(m.value)}
+
+    def set_sweep_path(self, persistent: bool):
+        """Float32 sweeps as one persistent launch (True) or per size class (False)."""
+        _check(_lib.cyq_set_sweep_path(self._h, 1 if persistent else 0))
 
     def escalation_segments(self) -> np.ndarray:
         """Segments per instance of the float64 escalation plan (0: the handle's own plan)."""
