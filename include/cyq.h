@@ -227,6 +227,19 @@ cyq_status cyq_residual(cyq_handle h, const double *b, const double *z, double *
                         cyq_stream stream);
 
 /*
+ * The same residual with every row evaluated compensated: each product split
+ * exactly with a fused multiply-add and the row's sum carried in two parts
+ * (the error-free transformations of Ogita, Rump and Oishi's Dot2), then
+ * rounded once, so res and rel are as accurate as if computed in twice the
+ * float64 precision.  Where a row's terms cancel by many orders of magnitude a
+ * plain float64 evaluation (cyq_residual) can be as large as the residual
+ * itself; this one is not.  About ten float64 instructions per term instead of
+ * one.  Same arguments and errors as cyq_residual.
+ */
+cyq_status cyq_residual_compensated(cyq_handle h, const double *b, const double *z, double *res, double *rel,
+                                    cyq_stream stream);
+
+/*
  * Adjoint of z = K^{-1} b(theta) (implicit differentiation of K z = b).
  * Given z (the solution for the right-hand side built from x_init) and
  * dL_dz, solves K w = dL_dz with the stored factor (K is symmetric) and

@@ -1599,13 +1599,16 @@ cyq_status cyq_assemble_newton(cyq_handle h, const cyq_newton_in *in, const cyq_
     return CYQ_OK;
 }
 
-cyq_status cyq_residual(cyq_handle h, const double *b, const double *z, double *res, double *rel,
-                        cyq_stream stream) {
+namespace {
+
+cyq_status residual_impl(cyq_handle h, const double *b, const double *z, double *res, double *rel,
+                         cyq_stream stream, bool compensated) {
     if (!h || !b || !z) return CYQ_ERR_INVALID_ARG;
     if (!h->factored) return CYQ_ERR_NO_FACTOR;
     if (!h->subs.empty()) {
         for (size_t k = 0; k < h->subs.size(); ++k) {
-            const cyq_status st = cyq_residual(h->subs[k], b, z, res, rel ? rel + h->sub_first[k] : nullptr, stream);
+            const cyq_status st = residual_impl(h->subs[k], b, z, res, rel ? rel + h->sub_first[k] : nullptr, stream,
+                                                compensated);
             if (st != CYQ_OK) return st;
         }
         return CYQ_OK;
@@ -1614,10 +1617,27 @@ cyq_status cyq_residual(cyq_handle h, const double *b, const double *z, double *
     cudaStream_t st = to_stream(stream);
     CYQ_CUDA(cudaMemsetAsync(h->rr, 0, sizeof(double) * h->batch, st));
     CYQ_CUDA(cudaMemsetAsync(h->bb, 0, sizeof(double) * h->batch, st));
-    CYQ_CUDA(launch_residual(resid_args(h, b, z, res, nullptr), 1, st));
+    ResidArgs ra = resid_args(h, b, z, res, nullptr);
+    if (compensated) {   // every instance's rows compensated (the refinement resets these flags)
+        CYQ_CUDA(launch_fill_int(h->batch, h->comp, 1, st));
+        ra.comp = h->comp;
+    }
+    CYQ_CUDA(launch_residual(ra, 1, st));
     CYQ_CUDA(launch_resid_finalize(h->batch, 1, h->rr, h->bb, rel ? rel : h->rel, nullptr, 0.0, nullptr, 0, false, 1,
                                    nullptr, st));
     return CYQ_OK;
+}
+
+}  // namespace
+
+cyq_status cyq_residual(cyq_handle h, const double *b, const double *z, double *res, double *rel,
+                        cyq_stream stream) {
+    return residual_impl(h, b, z, res, rel, stream, false);
+}
+
+cyq_status cyq_residual_compensated(cyq_handle h, const double *b, const double *z, double *res, double *rel,
+                                    cyq_stream stream) {
+    return residual_impl(h, b, z, res, rel, stream, true);
 }
 
 cyq_status cyq_solve_adjoint(cyq_handle h, const double *x_init, const double *z, const double *dL_dz, double *w,

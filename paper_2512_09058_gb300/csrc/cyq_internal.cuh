@@ -510,6 +510,7 @@ cudaError_t launch_resid_finalize(int batch, int nrhs, double *rr, double *bb, d
                                   int *steps, int step, bool keep_bb, int done_value, int *comp, cudaStream_t st);
 cudaError_t launch_mark_not_converged(int batch, const int *done, int *status, cudaStream_t st);
 cudaError_t launch_clear_not_pd(int batch, const int *skip, int *status, cudaStream_t st);
+cudaError_t launch_fill_int(int n, int *p, int v, cudaStream_t st);
 cudaError_t launch_predict_escalation(int batch, int nrhs, const double *rel0, const double *rel, int *done, int *esc,
                                       double tol, int k, int left, cudaStream_t st);
 cudaError_t launch_unpark(int batch, int *done, cudaStream_t st);

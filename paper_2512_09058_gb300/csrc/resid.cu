@@ -390,6 +390,16 @@ cudaError_t launch_predict_escalation(int batch, int nrhs, const double *rel0, c
     return cudaGetLastError();
 }
 
+__global__ void k_fill_int(int n, int *p, int v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+cudaError_t launch_fill_int(int n, int *p, int v, cudaStream_t st) {
+    k_fill_int<<<(n + 127) / 128, 128, 0, st>>>(n, p, v);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_clear_not_pd(int batch, const int *skip, int *status, cudaStream_t st) {
     k_clear_not_pd<<<(batch + 127) / 128, 128, 0, st>>>(batch, skip, status);
     return cudaGetLastError();

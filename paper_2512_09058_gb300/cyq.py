@@ -29,7 +29,7 @@ EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rh
            "cyq_factor_solve_noalloc", "cyq_autotune", "cyq_get_launch_shapes", "cyq_tune_segments",
            "cyq_set_launch_shapes", "cyq_get_stage_factor", "cyq_assemble_newton", "cyq_set_pcr_tail",
            "cyq_get_pcr_tail", "cyq_pivot_eval", "cyq_set_factor_path", "cyq_get_factor_path", "cyq_apply_factor", "cyq_update_factor",
-           "cyq_get_escalation_segments", "cyq_get_sweep_path", "cyq_set_sweep_path"]
+           "cyq_get_escalation_segments", "cyq_get_sweep_path", "cyq_set_sweep_path", "cyq_residual_compensated"]
 
 
 class CyqError(RuntimeError):
@@ -116,9 +116,11 @@ def load(path: str = LIB_PATH):
     L.cyq_get_escalation_segments.argtypes = [vp, pi32]
     L.cyq_get_sweep_path.argtypes = [vp, pi32, ctypes.POINTER(i64)]
     L.cyq_set_sweep_path.argtypes = [vp, i32]
+    L.cyq_residual_compensated.argtypes = [vp] * 6
     for name in ["cyq_create", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual", "cyq_solve_adjoint",
                  "cyq_get_instance_status", "cyq_get_stats", "cyq_get_segments", "cyq_autotune",
                  "cyq_get_escalation_segments", "cyq_get_sweep_path", "cyq_set_sweep_path",
+                 "cyq_residual_compensated",
                  "cyq_get_launch_shapes", "cyq_tune_segments", "cyq_set_launch_shapes",
                  "cyq_get_stage_factor", "cyq_pivot_eval", "cyq_set_factor_path", "cyq_get_factor_path",
                  "cyq_apply_factor", "cyq_update_factor"]:
@@ -362,10 +364,13 @@ class Solver:
         _check(_lib.cyq_assemble_newton(self._h, ctypes.byref(a), ctypes.byref(o), _stream(stream)))
         return out
 
-    def residual(self, b, z, res=None, stream=None):
+    def residual(self, b, z, res=None, stream=None, compensated=False):
+        """Per-instance ||b - K z|| / ||b|| (res: optional output of b - K z); compensated
+        rows evaluate it as if in twice the float64 precision (cyq_residual_compensated)."""
         import torch
         rel = torch.empty(self.batch, dtype=torch.float64, device=b.device)
-        _check(_lib.cyq_residual(self._h, _ptr(b), _ptr(z), _ptr(res), _ptr(rel), _stream(stream)))
+        fn = _lib.cyq_residual_compensated if compensated else _lib.cyq_residual
+        _check(fn(self._h, _ptr(b), _ptr(z), _ptr(res), _ptr(rel), _stream(stream)))
         return rel
 
     def solve_adjoint(self, x0, z, dL_dz, stream=None, want=("w", "dQ", "dq", "dR", "dr", "dS", "dA", "dB", "dc",
