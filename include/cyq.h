@@ -385,9 +385,8 @@ cyq_status cyq_tune_segments(const cyq_desc *desc, const double *Q, const double
  *   call's contents: calls that overlap on the GPU (different streams or host
  *   threads) race and must be serialised.  The first call on a device looks up
  *   the workspace address with that device current and keeps it for the life
- *   of the process (a device reset after it is not supported); make that first
- *   call before any stream capture.  The plan records are written on the
- *   device by a small kernel.  Asynchronous on `stream` (the data pointers must
+ *   of the process (a device reset after it is not supported).  The plan
+ *   records are written on the device by a small kernel.  Asynchronous on `stream` (the data pointers must
  *   stay valid until it completes).
  */
 cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu, const double *Q, const double *R,

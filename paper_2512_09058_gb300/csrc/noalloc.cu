@@ -12,9 +12,8 @@
 // race on it; serialise them.  The first call on a device looks up the
 // array's device address (cudaGetSymbolAddress, with that device current) and
 // keeps it for the life of the process, so a device reset after that first
-// call is not supported; make the first call before any stream capture.  The
-// plan records are written by a one-thread kernel from its arguments, so
-// nothing is copied from host memory.
+// call is not supported.  The plan records are written by a one-thread
+// kernel from its arguments, so nothing is copied from host memory.
 #include <cuda_runtime.h>
 
 #include <mutex>
