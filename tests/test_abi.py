@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "cyq.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"\b(cyq_[a-z_]+)\s*\(", text)
+    names = re.findall(r"\b(cyq_[a-z0-9_]+)\s*\(", text)
     return sorted(set(names))
 
 
