@@ -200,7 +200,8 @@ constexpr int kUpdateColumns = 32;
 
 // Records per residual work item: small enough that the last refinement steps,
 // with few instances left, still spread over many SMs (8 for one right-hand
-// side: uneven batch step 192.5 ms with 32, 188.0 with 16, 184.3 with 8; 32
+// side: uneven batch step 192.5 ms with 32, 188.0 with 16, 184.3 with 8, 184.6
+// with 4, where the full-batch residual itself slows from 8.4 to 8.9 ms; 32
 // where several right-hand sides share every matrix load and the CTAs already
 // carry more work).
 constexpr int kResidChunk1 = 8, kResidChunkN = 32;
