@@ -73,7 +73,7 @@ REFINE_TOL = 5e-11
 _UNEVEN_SCALE = 551381.0 / 71441.0
 NCU_TRAFFIC = {("batch1024_n64_nx12_nu4", "fp64_ir32", "k_factor_pairs<12, 4>"): 217.1e6 + 219.5e6,
                ("uneven4096", "fp32_refine", "k_ingest_f32 + k_factor_team + k_inv_R_f32"):
-                   (3701e6 + 2272e6 + 296.9e6) * _UNEVEN_SCALE,
+                   (3727e6 + 2272e6 + 296.9e6) * _UNEVEN_SCALE,
                ("uneven4096", "fp32_refine", "k_sweep_team<true> + k_cr_solve + k_sweep_team<false> (1 rhs)"):
                    (1563e6 + 1592e6) * _UNEVEN_SCALE,
                ("uneven4096", "fp32_refine", "k_residual (1 rhs) + k_resid_finalize"): 4711e6 * _UNEVEN_SCALE}

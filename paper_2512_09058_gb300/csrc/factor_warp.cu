@@ -112,7 +112,9 @@ namespace {
 // ---------------------------------------------------------------------------
 // Ingest: float32 stage matrices (padded tile layout) and [B A] copies
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_ingest_f32(IngestArgs g) {
+// A streaming pass bound by load latency: four blocks per SM (64 registers a
+// thread) keep a third more loads in flight than three.
+__global__ void __launch_bounds__(256, 4) k_ingest_f32(IngestArgs g) {
     const int w = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     if (w >= g.n_chunks) return;
     const IngestChunk ch = g.chunks[w];
