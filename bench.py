@@ -261,9 +261,18 @@ def factor_store_elems(batch):
 
 
 def residual_fma(batch):
-    """FMAs of one float64 residual (rows of eq. opt-cond-ocp-eq) per right-hand side."""
+    """FMAs of one float64 residual (rows of eq. opt-cond-ocp-eq) per right-hand
+    side, as the kernel runs them: per stage k, R u, B^T lambda, B u and Q x;
+    A x and S x for k > 0; A^T lambda and S^T u for k < N - 1; Sigma as its own
+    term of the u and x rows; the identity couplings of x and lambda are not
+    products.  S terms only where S is given, Sigma terms where Sigma is."""
     N, nx, nu = (np.asarray(v, np.int64) for v in (batch.N, batch.nx, batch.nu))
-    return int((N * (nu * nu + 4 * nx * nu + 3 * nx * nx + nu + nx)).sum())
+    f = N * (nu * nu + 2 * nx * nu + nx * nx) + 2 * (N - 1) * nx * nx
+    if batch.S is not None:
+        f = f + 2 * (N - 1) * nx * nu
+    if batch.Sigma is not None:
+        f = f + N * (nu + nx)
+    return int(f.sum())
 
 
 def roofline_of(name, flops, bytes_alg, ms, pipe_peak, hbm_peak, pipe_name, peaks, traffic=None):
