@@ -2,7 +2,7 @@
 """KKT factor+solve benchmark on one node.
 
 Workload (default): the uneven batch, 4096 independent linear-quadratic OCPs
-with N uniform in [16, 256], nx in {4..64}, nu in {2..32} (565,757 stages,
+with N uniform in [16, 256], nx in {4..64}, nu in {2..32} (551,381 stages,
 20 GB of float64 data), stage cross terms S and diagonal regularisation Sigma
 log-uniform in [1e-6, 1e6]; one factorization + one right-hand side per OCP.
 One step = factor all OCPs + solve, with the inputs resident in device
@@ -14,13 +14,13 @@ to the tolerance.
 
 Methods (each timed over the same K steps):
   fp64_refine  float64 factor + solve, float64 residual and refinement until
-               ||b - Kz|| / ||b|| <= 1e-10 for every OCP and right-hand side
-               (float64 arithmetic, certified at the metric's gate)
+               ||b - Kz|| / ||b|| <= 5e-11 for every OCP and right-hand side
+               (the metric's gate 1e-10 with a factor-2 margin)
   fp64         plain float64 factor + solve (no residual computed)
-  fp32_refine  float32 factor + solve, float64 residual + refinement to 1e-10,
-               float64 factor for the instances float32 cannot bring to 1e-10
+  fp32_refine  float32 factor + solve, float64 residual + refinement to 5e-11,
+               float64 factor for the instances float32 cannot bring there
   fp64_ir32    float64 factor + solve; corrections by float32 sweeps with a
-               float32 copy of the factor, float64 residual to 1e-10
+               float32 copy of the factor, float64 residual to 5e-11
 
 Prints ONE JSON line on rank 0.  ``--impl reference`` times the CPU oracle
 (plain FP64 C Riccati recursion) on the host instead.  Under torchrun every
@@ -75,8 +75,7 @@ NCU_TRAFFIC = {("batch1024_n64_nx12_nu4", "fp64_ir32", "k_factor_pairs<12, 4>"):
                ("uneven4096", "fp32_refine", "k_ingest_f32 + k_factor_team + k_inv_R_f32"):
                    (3727e6 + 2272e6 + 296.9e6) * _UNEVEN_SCALE,
                ("uneven4096", "fp32_refine", "k_sweep_team<true> + k_cr_solve + k_sweep_team<false> (1 rhs)"):
-                   (1563e6 + 1592e6) * _UNEVEN_SCALE,
-               ("uneven4096", "fp32_refine", "k_residual (1 rhs) + k_resid_finalize"): 4711e6 * _UNEVEN_SCALE}
+                   (1563e6 + 1592e6) * _UNEVEN_SCALE}
 # workload -> methods (headline: the first one that certifies every instance),
 # CUDA-graph replay, adjoint in the step, segment counts tuned by timing
 # (cyq_tune_segments); launch shapes are always tuned by timing (cyq_autotune)
