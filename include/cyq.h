@@ -221,7 +221,9 @@ cyq_status cyq_build_rhs(cyq_handle h, const double *q, const double *r, const d
 /*
  * Float64 residual  res = b - K z  and per-instance relative residual
  * ||res||_2 / ||b||_2 (rel, device float64 array [batch], may be NULL; res may
- * be NULL).  Uses the data of the last cyq_factor.  One right-hand side.
+ * be NULL).  Uses the data of the last cyq_factor.  One right-hand side; b, z
+ * and res are device arrays of kkt_size elements.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (NULL handle, b or z), NO_FACTOR (no cyq_factor yet), CUDA.
  */
 cyq_status cyq_residual(cyq_handle h, const double *b, const double *z, double *res, double *rel,
                         cyq_stream stream);
