@@ -97,10 +97,14 @@ def kkt_abs_matvec(inst, z) -> np.ndarray:
 
 def residual_eval_bound(inst, z, b) -> float:
     """Bound on the error of any float64 evaluation of ||b - K z|| / ||b||:
-    gamma_m || |b| + |K| |z| ||_2 / ||b||_2 with m = 2 nx + nu + 2 terms per row
-    (componentwise bound of a float64 sum of m products, Higham Sec. 3.1)."""
+    gamma_m || |b| + |K| |z| ||_2 / ||b||_2, the componentwise bound of a float64
+    sum of products (Higham Sec. 3.1) with m the most roundings on one term's
+    path.  A row has at most 2 nx + nu + 1 products and b: 2 nx + nu + 2 summands,
+    and the diagonal term carries one rounding more, either forming Q_ii + Sigma_i
+    (R_ii + Sigma_i) first or adding Sigma_i z_i as a summand of its own, so
+    m = 2 nx + nu + 3."""
     u = 2.0 ** -53
-    m = 2 * inst.nx + inst.nu + 2
+    m = 2 * inst.nx + inst.nu + 3
     gamma = m * u / (1.0 - m * u)
     b = _f(b)
     return float(gamma * np.linalg.norm(np.abs(b) + kkt_abs_matvec(inst, z)) / np.linalg.norm(b))

@@ -247,7 +247,9 @@ static void abs_mat_tvec_add(int m, int n, const double *A, const double *x, dou
  * entry of z replaced by its absolute value (the identity couplings of the
  * dynamics count +1).  Componentwise, an evaluation of b - K z in float64 with
  * any summation order is within gamma_m (|b| + |K| |z|) of the exact value,
- * gamma_m = m u / (1 - m u), m the number of terms of a row plus one
+ * gamma_m = m u / (1 - m u), m the most roundings on one term's path: the
+ * terms of a row plus b, plus one for the diagonal entry, whose Sigma is
+ * either added to Q_ii (R_ii) first or summed as a product of its own
  * (Higham, Accuracy and Stability of Numerical Algorithms, Sec. 3.1). */
 void oracle_kkt_abs_matvec(int N, int nx, int nu, const double *Q, const double *R, const double *S,
                            const double *A, const double *B, const double *Sigma, const double *z, double *y) {
