@@ -62,3 +62,47 @@ def test_new_entry_points_reject_bad_arguments_without_a_device():
     assert L.cyq_get_pcr_tail(None, ctypes.byref(v)) == INVALID
     a, o = cyq.cyq_newton_in(), cyq.cyq_newton_out()
     assert L.cyq_assemble_newton(None, ctypes.byref(a), ctypes.byref(o), None) == INVALID
+
+
+def test_every_entry_point_refuses_a_null_handle_without_device_work():
+    """The error behaviour include/cyq.h states for missing arguments: every
+    entry point that takes a handle returns CYQ_ERR_INVALID_ARG for NULL (the
+    size queries -1, cyq_destroy nothing) before any device call, so this runs
+    on a host without a GPU as well."""
+    from paper_2512_09058_gb300 import build, cyq
+    build.build()
+    L = cyq.load()
+    INVALID = 1
+    one = ctypes.c_int32(1)
+    calls = {
+        "cyq_factor": (None,) * 8,
+        "cyq_solve": (None, None, None, 1, None),
+        "cyq_apply_factor": (None, None, None, 1, None),
+        "cyq_update_factor": (None,) * 6 + (1, None),
+        "cyq_build_rhs": (None,) * 7,
+        "cyq_residual": (None,) * 6,
+        "cyq_residual_compensated": (None,) * 6,
+        "cyq_solve_adjoint": (None,) * 16,
+        "cyq_get_instance_status": (None, None, None),
+        "cyq_get_stats": (None, None, None),
+        "cyq_get_segments": (None, None),
+        "cyq_get_escalation_segments": (None, None),
+        "cyq_get_stage_factor": (None, 0, 0, None),
+        "cyq_autotune": (None,) * 9 + (1, 1, None),
+        "cyq_get_launch_shapes": (None, None, None, None, 1),
+        "cyq_set_launch_shapes": (None, None, None, 1),
+        "cyq_set_pcr_tail": (None, 1),
+        "cyq_get_pcr_tail": (None, ctypes.byref(one)),
+        "cyq_set_factor_path": (None, 1),
+        "cyq_get_factor_path": (None, None, None),
+        "cyq_set_sweep_path": (None, 1),
+        "cyq_get_sweep_path": (None, None, None),
+        "cyq_assemble_newton": (None, None, None, None),
+        "cyq_tune_segments": (None,) * 9 + (1, 1, None, None),
+        "cyq_pivot_eval": (None,) * 6 + (-1, None),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == INVALID, name
+    for name in ("cyq_kkt_size", "cyq_workspace_bytes", "cyq_last_launch_count"):
+        assert getattr(L, name)(None) == -1, name
+    L.cyq_destroy(None)
