@@ -213,7 +213,8 @@ cyq_status cyq_update_factor(cyq_handle h, const double *Q, const double *R, con
  * b = -(r~, q, f~) for one right-hand side of the original problem
  * (eq. opt-cond-ocp-eq: r~^0 = r^0 + S_0 x_init, f~^0 = f^0 + A_0 x_init),
  * using the data passed to the last cyq_factor.  q, r, c, x_init are device
- * float64 arrays in the layout above; b has kkt_size elements.
+ * float64 arrays in the layout above; b has kkt_size elements.  Asynchronous
+ * on `stream`.  Errors: INVALID_ARG (NULL handle or array), NO_FACTOR, CUDA.
  */
 cyq_status cyq_build_rhs(cyq_handle h, const double *q, const double *r, const double *c,
                          const double *x_init, double *b, cyq_stream stream);
@@ -254,7 +255,10 @@ cyq_status cyq_residual_compensated(cyq_handle h, const double *b, const double 
  *   dSigma_u^k = -w_u^k .* u^k, dSigma_x^k = -w_x^k .* x^k.
  * Every output is a device float64 array in the data layout (w: kkt_size);
  * entries that do not enter K (dQ_0, dq_0, dSigma_x^0, dSigma_u^N) are set to
- * zero; any output pointer may be NULL.  One right-hand side.
+ * zero; any output pointer may be NULL, except w on a handle that refines
+ * (it_max > 0: the refinement's own vectors are in use).  One right-hand side.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG (NULL handle, x_init, z or
+ * dL_dz; NULL w with it_max > 0), NO_FACTOR, the errors of cyq_solve, CUDA.
  */
 cyq_status cyq_solve_adjoint(cyq_handle h, const double *x_init, const double *z, const double *dL_dz,
                              double *w, double *dQ, double *dq, double *dR, double *dr, double *dS,
@@ -262,7 +266,8 @@ cyq_status cyq_solve_adjoint(cyq_handle h, const double *x_init, const double *z
                              cyq_stream stream);
 
 /* Synchronises `stream` and copies the per-instance status words
- * (cyq_status values) into host_status[batch]. Returns the first non-OK one. */
+ * (cyq_status values) into host_status[batch]. Returns the first non-OK one,
+ * or INVALID_ARG (NULL handle or array) or CUDA. */
 cyq_status cyq_get_instance_status(cyq_handle h, int32_t *host_status, cyq_stream stream);
 
 /* Statistics of the last cyq_solve (host copy; synchronises `stream`). */
@@ -277,6 +282,7 @@ typedef struct cyq_stats {
     int32_t P_min, P_max;    /* segments per instance chosen by the plan */
     int64_t work_items;      /* (instance, segment) pairs */
 } cyq_stats;
+/* Errors: INVALID_ARG (NULL handle or out), CUDA. */
 cyq_status cyq_get_stats(cyq_handle h, cyq_stats *out, cyq_stream stream);
 
 /* Device bytes the handle allocated (its workspace: stage factors, coupling
@@ -286,7 +292,7 @@ int64_t cyq_workspace_bytes(cyq_handle h);
 
 /* Number of float64 elements of one right-hand side (sum_i N_i (nu_i + 2 nx_i)). */
 int64_t cyq_kkt_size(cyq_handle h);
-/* Segments chosen for each instance (host array [batch]). */
+/* Segments chosen for each instance (host array [batch]).  Errors: INVALID_ARG. */
 cyq_status cyq_get_segments(cyq_handle h, int32_t *P_out);
 /*
  * Diagnostics: the stored factor of one stage (instance, stage s in 0..N-1),
@@ -336,7 +342,8 @@ cyq_status cyq_autotune(cyq_handle h, const double *Q, const double *R, const do
 
 /* Launch shapes in use: threads per work item of the stage factor and of the
  * sweeps (for nrhs right-hand sides) per size class; arrays of *n_groups
- * entries (either may be NULL; call with both NULL to get *n_groups). */
+ * entries (either may be NULL; call with both NULL to get *n_groups).
+ * Errors: INVALID_ARG (NULL handle or n_groups). */
 cyq_status cyq_get_launch_shapes(cyq_handle h, int32_t *n_groups, int32_t *factor_team,
                                  int32_t *sweep_team, int32_t nrhs);
 
@@ -409,24 +416,25 @@ cyq_status cyq_factor_solve_noalloc(int32_t N, int32_t nx, int32_t nu, const dou
  * is the same up to rounding.  Errors: INVALID_ARG, CUDA.
  */
 cyq_status cyq_set_pcr_tail(cyq_handle h, int32_t levels);
-/* Tail levels in use (after clamping). */
+/* Tail levels in use (after clamping).  Errors: INVALID_ARG. */
 cyq_status cyq_get_pcr_tail(cyq_handle h, int32_t *levels);
 
 /*
  * Float32 factor path (CYQ_FP32_REFINE handles).  With one_warp_per_item = 1
  * (the default) every segment that carries no A^cl (segment 0 of every
  * instance, i.e. whole horizons when P = 1) whose padded blocks satisfy
- * nu <= 32, nx <= 64 is factored by one warp in one persistent launch for the
- * whole batch (the modified Riccati recursion of Alg. fact-mod-riccati and the
- * segment's compute-schur blocks, same stored factor layout); the other
- * segments, and every segment when one_warp_per_item = 0, run the
- * per-size-class kernels.  Both
- * paths compute the same factor up to float32 rounding (different summation
- * order).  The next cyq_solve needs a new cyq_factor.  Errors: INVALID_ARG.
+ * nu <= 32, nx <= 64 is factored in one persistent launch for the whole batch,
+ * each by a team of 32, 64 or 128 threads chosen by the shared memory it needs
+ * (the modified Riccati recursion of Alg. fact-mod-riccati and the segment's
+ * compute-schur blocks, same stored factor layout; the flag's name dates from
+ * one warp per item); the other segments, and every segment when
+ * one_warp_per_item = 0, run the per-size-class kernels.  Both paths compute
+ * the same factor up to float32 rounding (different summation order).  The next cyq_solve needs a new cyq_factor.  Errors: INVALID_ARG.
  */
 cyq_status cyq_set_factor_path(cyq_handle h, int32_t one_warp_per_item);
-/* The float32 factor path in use and the number of work items the one-warp
- * launch covers (0 for float64 handles); either pointer may be NULL. */
+/* The float32 factor path in use and the number of work items the persistent
+ * launch covers (0 for float64 handles); either pointer may be NULL.
+ * Errors: INVALID_ARG (NULL handle). */
 cyq_status cyq_get_factor_path(cyq_handle h, int32_t *one_warp_per_item, int64_t *warp_items);
 
 /* Selects the float32 sweep path: 1 = each sweep of a float32 solve is one

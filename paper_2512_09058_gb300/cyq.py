@@ -311,8 +311,9 @@ class Solver:
         _check(_lib.cyq_set_pcr_tail(self._h, int(levels)))
 
     def set_factor_path(self, one_warp_per_item: bool):
-        """Float32 factor: one warp per item in one launch (True, the default) or
-        the per-size-class kernels (False); factor again afterwards."""
+        """Float32 factor: one persistent launch, a team of 32, 64 or 128 threads
+        per item (True, the default), or the per-size-class kernels (False);
+        factor again afterwards."""
         _check(_lib.cyq_set_factor_path(self._h, 1 if one_warp_per_item else 0))
 
     def factor_path(self) -> dict:
