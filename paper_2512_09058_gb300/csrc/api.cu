@@ -49,7 +49,7 @@ struct Group {
     int max_nx = 0, max_nu = 0;
     std::vector<Item> items;
     Item *d_items = nullptr;
-    // float32 factor: the items not covered by the one-warp-per-item launch
+    // float32 factor: the items not covered by the persistent team launch
     std::vector<Item> items_rest;
     Item *d_items_rest = nullptr;
     bool rest_set = false;                     // items_rest replaces items in float32 factor launches
@@ -59,7 +59,7 @@ struct Group {
 struct FactorSet {
     void *L = nullptr, *LB = nullptr, *F = nullptr, *DI = nullptr;
     void *BA = nullptr;   // float32 [B A] copies (float32 sets only)
-    float *Hf = nullptr;  // float32 stage matrices of the one-warp factor (float32 sets only)
+    float *Hf = nullptr;  // float32 stage matrices of the persistent team factor (float32 sets only)
     bool fp64 = true;
 };
 

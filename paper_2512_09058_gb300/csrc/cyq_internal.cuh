@@ -367,7 +367,7 @@ struct FactorArgs {
     bool need_G2;                   // some item propagates A^cl (P > 1): second [B^ A^] buffer
     const int *skip;                // optional per-instance flag: nonzero = do not factor this instance
     unsigned smem_team;             // shared-memory bytes per team (set by the launcher)
-    const float *Hf;                // float32 stage matrices (one-warp factor; written by the ingest)
+    const float *Hf;                // float32 stage matrices (persistent team factor; written by the ingest)
 };
 
 struct SolveArgs {
@@ -442,7 +442,7 @@ struct TeamPlanDev {
 };
 size_t warp_slot_bytes(int nx, int nu);
 size_t warp_stage_floats(int nx, int nu);   // floats of one ingested stage matrix
-// Ingest of the one-warp factor's stages: float32 stage matrices in the padded
+// Ingest of the persistent team factor's stages: float32 stage matrices in the padded
 // tile layout and float32 [B A]; one warp per chunk of stages of segment 0.
 struct IngestChunk {
     int inst, t0, t1;

@@ -1,5 +1,6 @@
-"""The float32 factor with one warp per work item (one persistent launch for
-the whole batch) against the per-size-class kernels and the oracle.
+"""The persistent float32 factor (one launch for the whole batch, a team of 32,
+64 or 128 threads per work item) against the per-size-class kernels and the
+oracle.
 
 The two paths run the same recursion (Alg. fact-mod-riccati without the A^cl
 terms on segment 0, then compute-schur) with different summation orders, so
@@ -8,7 +9,7 @@ solutions of both agree with the oracle at the refinement gate.  The shapes
 cover every residue of nu and nx modulo 4 (the kernel pads both to multiples
 of 4), the three register buckets (padded nx <= 16, 32, 64), the largest
 padded blocks (nu + nx up to 96), horizons of one and two stages, and segment
-counts 1 and 3 (segment 0 by the one-warp kernel, the others by the
+counts 1 and 3 (segment 0 by the persistent kernel, the others by the
 per-class kernels).
 """
 import numpy as np
