@@ -295,6 +295,17 @@ int64_t cyq_kkt_size(cyq_handle h);
 /* Segments chosen for each instance (host array [batch]).  Errors: INVALID_ARG. */
 cyq_status cyq_get_segments(cyq_handle h, int32_t *P_out);
 /*
+ * The stages of segment c of a horizon of N stages cut into P segments, in the
+ * order the factorization processes them (Sec. 4.1, eq. block-matrix-example-4:
+ * block column c >= 1 holds the stages b(c-1)+1 .. b(c), b(c) = floor(c N / P),
+ * in reverse order; block column 0 holds stage 0, whose u^0 is paired with x^N,
+ * then the last stages N-1 .. b(P-1)+1, indices taken modulo N).  *len receives
+ * the count; stages (host, at least *len entries) may be NULL to ask for it.
+ * The kernels walk their segments with the same rule.  Host only, no device.
+ * Errors: INVALID_ARG (N < 1, P < 1, P > N, c outside 0..P-1, NULL len).
+ */
+cyq_status cyq_segment_stages(int32_t N, int32_t P, int32_t c, int32_t *stages, int32_t *len);
+/*
  * Diagnostics: the stored factor of one stage (instance, stage s in 0..N-1),
  * copied to the host as (nu+nx) x (nu+nx) float64, column-major.  Its lower
  * triangle is the Cholesky factor [L^R 0; L^S L^Q] of the stage matrix H^_s of

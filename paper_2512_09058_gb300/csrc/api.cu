@@ -1277,6 +1277,14 @@ cyq_status cyq_get_segments(cyq_handle h, int32_t *P_out) {
     return CYQ_OK;
 }
 
+cyq_status cyq_segment_stages(int32_t N, int32_t P, int32_t c, int32_t *stages, int32_t *len) {
+    if (N < 1 || P < 1 || P > N || c < 0 || c >= P || !len) return CYQ_ERR_INVALID_ARG;
+    *len = seg_len(c, N, P);
+    if (stages)
+        for (int t = 0; t < *len; ++t) stages[t] = seg_stage(c, t, N, P);
+    return CYQ_OK;
+}
+
 int64_t cyq_last_launch_count(cyq_handle h) { return h ? h->launches : -1; }
 
 cyq_status cyq_factor(cyq_handle h, const double *Q, const double *R, const double *S, const double *A,

@@ -29,7 +29,8 @@ EXPORTS = ["cyq_create", "cyq_destroy", "cyq_factor", "cyq_solve", "cyq_build_rh
            "cyq_factor_solve_noalloc", "cyq_autotune", "cyq_get_launch_shapes", "cyq_tune_segments",
            "cyq_set_launch_shapes", "cyq_get_stage_factor", "cyq_assemble_newton", "cyq_set_pcr_tail",
            "cyq_get_pcr_tail", "cyq_pivot_eval", "cyq_set_factor_path", "cyq_get_factor_path", "cyq_apply_factor", "cyq_update_factor",
-           "cyq_get_escalation_segments", "cyq_get_sweep_path", "cyq_set_sweep_path", "cyq_residual_compensated"]
+           "cyq_get_escalation_segments", "cyq_get_sweep_path", "cyq_set_sweep_path", "cyq_residual_compensated",
+           "cyq_segment_stages"]
 
 
 class CyqError(RuntimeError):
@@ -117,10 +118,11 @@ def load(path: str = LIB_PATH):
     L.cyq_get_sweep_path.argtypes = [vp, pi32, ctypes.POINTER(i64)]
     L.cyq_set_sweep_path.argtypes = [vp, i32]
     L.cyq_residual_compensated.argtypes = [vp] * 6
+    L.cyq_segment_stages.argtypes = [i32, i32, i32, pi32, pi32]
     for name in ["cyq_create", "cyq_factor", "cyq_solve", "cyq_build_rhs", "cyq_residual", "cyq_solve_adjoint",
                  "cyq_get_instance_status", "cyq_get_stats", "cyq_get_segments", "cyq_autotune",
                  "cyq_get_escalation_segments", "cyq_get_sweep_path", "cyq_set_sweep_path",
-                 "cyq_residual_compensated",
+                 "cyq_residual_compensated", "cyq_segment_stages",
                  "cyq_get_launch_shapes", "cyq_tune_segments", "cyq_set_launch_shapes",
                  "cyq_get_stage_factor", "cyq_pivot_eval", "cyq_set_factor_path", "cyq_get_factor_path",
                  "cyq_apply_factor", "cyq_update_factor"]:
@@ -182,6 +184,18 @@ def tune_segments(N, nx, nu, data, b, nrhs: int = 1, reps: int = 2, stream=None,
     _check(L.cyq_tune_segments(ctypes.byref(d.desc), _ptr(data["Q"]), _ptr(data["R"]), _ptr(data.get("S")),
                                _ptr(data["A"]), _ptr(data["B"]), _ptr(data.get("Sigma")), _ptr(b), _ptr(z), nrhs,
                                reps, _stream(stream), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return out
+
+
+def segment_stages(N: int, P: int, c: int) -> np.ndarray:
+    """Stages of segment c (of P) of a horizon of N stages, in the order the
+    factorization processes them (cyq_segment_stages; host only)."""
+    L = load()
+    n = ctypes.c_int32(0)
+    _check(L.cyq_segment_stages(int(N), int(P), int(c), None, ctypes.byref(n)))
+    out = np.zeros(n.value, np.int32)
+    _check(L.cyq_segment_stages(int(N), int(P), int(c), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                ctypes.byref(n)))
     return out
 
 
