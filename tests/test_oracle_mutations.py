@@ -5,13 +5,17 @@ of tests/test_oracle_pins.py, run against that library, must fail for every
 mutant, and pass for the unmodified source compiled the same way.  Every
 mutation stays inside the arrays it touches (signs, dropped terms, transposes
 of square blocks), so a mutant computes wrong numbers but never faults.
+The Newton-system oracle (numpy) gets the same treatment against the pins of
+tests/test_newton_oracle.py.
 """
 import os
 import subprocess
+import types
 
 import pytest
 
 import oracle
+import test_newton_oracle as npins
 import test_oracle_pins as pins
 
 SRC_DIR = os.path.dirname(os.path.abspath(oracle.__file__))
@@ -108,3 +112,62 @@ def test_every_planted_mistake_fails_a_pin(monkeypatch, tmp_path, name, old, new
     assert source.count(old) == 1, name
     lib = _compile(source.replace(old, new), str(tmp_path / "mutant"))
     assert _failures(monkeypatch, lib), name
+
+
+# The Newton-system oracle (numpy): each mutant is its source with one planted
+# error, executed as a module of its own and put in place of oracle.newton for
+# the pins of tests/test_newton_oracle.py.
+NEWTON_MUTANTS = [
+    ("multiplier estimate: sign of the penalty term",
+     "yhat = y + sig * (w - proj)", "yhat = y - sig * (w - proj)"),
+    ("active set: Sigma y instead of Sigma^-1 y",
+     "zz = w + y / sig", "zz = w + y * sig"),
+    ("gradient: sign of the proximal centre in q~",
+     "gx * (xk - _vec(alm.xbar, k, nx))", "gx * (xk + _vec(alm.xbar, k, nx))"),
+    ("gradient: S^T u dropped from q~",
+     "qk = qk + Sk.T @ uk", "qk = qk + 0.0 * (Sk.T @ uk)"),
+    ("Hessian: D^T Sigma^J C dropped from S~",
+     "St[k] = Sk + Dk.T @ (sJ[:, None] * Ck)", "St[k] = Sk + 0.0 * (Dk.T @ (sJ[:, None] * Ck))"),
+    ("Hessian: Gamma_x^-1 dropped from Q~",
+     "Qt[k] = Qk + Ck.T @ (sJ[:, None] * Ck) + np.diag(gx)", "Qt[k] = Qk + Ck.T @ (sJ[:, None] * Ck)"),
+    ("dynamics residual: sign of x^{k+1}",
+     "+ _vec(f, k, nx) - xn", "+ _vec(f, k, nx) + xn"),
+    ("stationarity: A^T lambda dropped",
+     "v = v + _blk(inst.A, k, nx, nx).T @ lam[k]", "v = v + 0.0 * (_blk(inst.A, k, nx, nx).T @ lam[k])"),
+]
+
+NEWTON_BATTERY = [
+    lambda: npins.test_gradient_is_the_derivative_of_the_al_value((6, 3, 2, 4)),
+    lambda: npins.test_hessian_is_the_derivative_of_the_gradient((6, 3, 2, 4)),
+    lambda: npins.test_without_constraints_the_newton_step_solves_the_proximal_lq_problem(),
+    lambda: npins.test_newton_step_is_stationary_when_the_active_set_is_fixed((5, 3, 2, 4)),
+    lambda: npins.test_active_set_and_multiplier_estimate_by_hand(),
+]
+
+
+def _newton_failures(monkeypatch, source):
+    mod = types.ModuleType("newton_under_test")
+    exec(compile(source, "newton_under_test.py", "exec"), mod.__dict__)
+    monkeypatch.setattr(npins, "newton", mod)
+    failed = []
+    for k, pin in enumerate(NEWTON_BATTERY):
+        try:
+            pin()
+        except Exception:
+            failed.append(k)
+    return failed
+
+
+def _newton_source():
+    return open(os.path.join(SRC_DIR, "newton.py")).read()
+
+
+def test_unmodified_newton_oracle_passes_the_battery(monkeypatch):
+    assert _newton_failures(monkeypatch, _newton_source()) == []
+
+
+@pytest.mark.parametrize("name,old,new", NEWTON_MUTANTS, ids=[m[0] for m in NEWTON_MUTANTS])
+def test_every_planted_newton_mistake_fails_a_pin(monkeypatch, name, old, new):
+    source = _newton_source()
+    assert source.count(old) == 1, name
+    assert _newton_failures(monkeypatch, source.replace(old, new)), name
